@@ -1,0 +1,416 @@
+#!/usr/bin/env python3
+"""Benchmark of the NFSGLFT hot path on GB300: Mpoints/s at bandwidth B = 64.
+
+One step = one pass of the whole path over M = 10^6 synthetic points:
+  set_points (rho, transformed points, bin sort, radial matrices)
+  + forward  (radial and polar conversions, pruned inverse FFT, interpolation)
+  + adjoint  (spreading, pruned forward FFT, adjoint conversions; one all-reduce when N > 1)
+  + point gradient (conversions, inverse FFT, window-derivative interpolation)
+with sigma = 2, Kaiser-Bessel window, cutoff q = 8, run in the FP32-mixed precision
+(the headline value) and in FP64 (reported beside it).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Prints one JSON line (rank 0).  Timing: CUDA events on the launching stream around
+each step, an L2 flush (a 256 MiB write) between steps, outside the timed events.
+"""
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "NDSGLFT Mpoints/s at B=64 fwd/adj: FP32-mixed vs FP64 on GB300 at stated error"
+UNIT = "Mpoints/s"
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128          # FFMA lanes per SM
+FP64_FMA_PER_SM_CLK = 2          # DFMA per SM per clock on GB300 (measured 1.0 TFLOP/s at ~1.9 GHz)
+FALLBACK = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        try:
+            d = json.load(open(path))
+            return d, "measured"
+        except Exception:
+            pass
+    return dict(FALLBACK), "fallback"
+
+
+def alu_peaks(peaks):
+    mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    fp32 = SM_COUNT * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
+    fp64 = SM_COUNT * FP64_FMA_PER_SM_CLK * 2 * mhz * 1e6 / 1e12
+    return fp32, fp64
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(gpu_index)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out = ""
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(smax), "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- algorithmic work per stage
+def stage_work(info, M, q, prec):
+    """Algorithmic bytes (HBM-bound stages) or flops (ALU-bound stages) of one call of each stage."""
+    B = info["B"]
+    K0, K1 = 2 * B - 2, B - 1
+    W = 2 * K1 + 1
+    rows0, rows1, N2 = info["rows"][0], info["rows"][1], info["N"][2]
+    cs = 8 if prec == "fp32_mixed" else 16
+    taps = (2 * q) ** 3
+    fft_fwd = ((K0 + 1) * (K1 + 1) * W * 16 + rows0 * W * W * cs          # pass A: zeta in, X0 out
+               + rows0 * W * W * cs + rows0 * rows1 * W * cs                # pass B
+               + rows0 * rows1 * W * cs + rows0 * rows1 * N2 * cs)          # pass C
+    fft_adj = (rows0 * rows1 * N2 * cs + rows0 * rows1 * W * cs
+               + rows0 * rows1 * W * cs + rows0 * W * W * cs
+               + rows0 * W * W * cs + (2 * K0 + 1) * W * W * 16)
+    radial = 4 * sum((K0 + 1) * (2 * l + 1) * (B - l) for l in range(B))
+    polar = 4 * (K0 + 1) * (K1 + 1) * sum(B - abs(m) for m in range(-(B - 1), B))
+    alu = "fp32" if prec == "fp32_mixed" else "fp64"
+    return {
+        "points": ("hbm", M * (24 + 24 + 4)),
+        "radial_matrix": ("fp64", 2 * (K0 + 1) * 2 * B * B * (B + 1) // 2),
+        "radial": ("fp64", radial),
+        "polar": ("fp64", polar),
+        "fft_forward": ("hbm", fft_fwd),
+        "interp": (alu, 4 * taps * M),
+        "spread": (alu, 4 * taps * M),
+        "fft_adjoint": ("hbm", fft_adj),
+        "polar_adjoint": ("fp64", polar),
+        "radial_adjoint": ("fp64", radial),
+        "grad_interp": (alu, 12 * taps * M),
+    }
+
+
+def traffic_for(stage, prec):
+    """DRAM bytes per launch of a stage from the committed ncu summary, if its kernel source is unchanged."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if not os.path.exists(path):
+        return None
+    try:
+        rec = json.load(open(path)).get("%s/%s" % (prec, stage))
+    except Exception:
+        return None
+    if not rec:
+        return None
+    src = os.path.join(ROOT, "paper_1809_10786_gb300", "csrc", rec["source"])
+    if not os.path.exists(src) or hashlib.sha256(open(src, "rb").read()).hexdigest() != rec["source_sha256"]:
+        return None
+    return rec["bytes_per_launch_full_size"]
+
+
+# ---------------------------------------------------------------- our arm
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import paper_1809_10786_gb300 as sgl
+    from paper_1809_10786_gb300 import distributed as sd
+    from paper_1809_10786_gb300 import inputs
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world != args.gpus:
+        raise SystemExit("--gpus %d but WORLD_SIZE %d" % (args.gpus, world))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    B, M, q = args.B, args.M, args.q
+    c_h = inputs.coefficients(B, inputs.seed_for(2))
+    x_h = inputs.points_gaussian(M, inputs.seed_for(2, 1 + rank))       # weak scaling: M points per rank
+    y_h = inputs.values(M, inputs.seed_for(2, 100 + rank))
+    g_h = inputs.complex_normal(M, inputs.seed_for(2, 200 + rank))
+    c, x, y, g = (torch.from_numpy(a).to(dev) for a in (c_h, x_h, y_h, g_h))
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    peaks, peak_src = load_peaks()
+    fp32_peak, fp64_peak = alu_peaks(peaks)
+    hbm_peak = float(peaks.get("hbm_gbs", FALLBACK["hbm_gbs"]))
+
+    results = {}
+    keep = {}
+    for prec_name, prec in (("fp32_mixed", sgl.PREC_FP32_MIXED), ("fp64", sgl.PREC_FP64)):
+        plan = sgl.Plan(B, M, precision=prec, window=sgl.WIN_KB, q=q, sigma=2.0, profile=True, device=dev)
+        out = {}
+
+        def step():
+            plan.set_points(x)
+            out["f"] = plan.forward(c)
+            a = plan.adjoint(y)
+            out["a"] = sd.allreduce_coefficients(a)
+            out["g"] = plan.grad_points(c, g)
+
+        for _ in range(args.warmup):
+            step()
+        barrier()
+        plan.profile()                                    # drop warm-up stage times
+        launches0 = plan.info()["kernel_launches"]
+        sampler = ClockSampler(local) if prec_name == "fp32_mixed" else None
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        barrier()
+        for k in range(args.steps):
+            flush.zero_()                                  # evict L2 between steps (untimed)
+            evs[k][0].record()
+            step()
+            evs[k][1].record()
+        barrier()
+        clocks = sampler.stop() if sampler else None
+        ms = sum(a.elapsed_time(b) for a, b in evs)
+        ms_max = sd.max_over_ranks(ms, dev)
+        stages = plan.profile()
+        launches = plan.info()["kernel_launches"] - launches0
+        info = plan.info()
+        work = stage_work(info, M, q, prec_name)
+        table = {}
+        for name, (t, n) in stages.items():
+            if n == 0 or name not in work:
+                continue
+            kind, amount = work[name]
+            per_launch_ms = t / n
+            if kind == "hbm":
+                achieved, peak, unit = amount / (per_launch_ms * 1e-3) / 1e9, hbm_peak, "GB/s"
+            else:
+                achieved = amount / (per_launch_ms * 1e-3) / 1e12
+                peak, unit = (fp32_peak, "TFLOP/s") if kind == "fp32" else (fp64_peak, "TFLOP/s")
+            table[name] = {"ms": round(per_launch_ms, 4), "share": None, "bound": "hbm" if kind == "hbm" else "alu",
+                           "alu": None if kind == "hbm" else kind, "achieved": round(achieved, 3), "peak": round(peak, 2),
+                           "unit": unit, "frac": round(achieved / peak, 4), "algorithmic": amount}
+        total_stage = sum(v["ms"] for v in table.values())
+        for v in table.values():
+            v["share"] = round(v["ms"] / total_stage, 4) if total_stage > 0 else None
+        results[prec_name] = {"ms_per_step": ms_max / args.steps,
+                              "value": world * M / (ms_max / args.steps * 1e-3) / 1e6,
+                              "gpu_launches": launches, "stages": table, "clocks": clocks}
+        keep[prec_name] = {k: v.detach().cpu().numpy() for k, v in out.items()}
+        plan.close()
+        del plan
+        torch.cuda.empty_cache()
+
+    # ---- end to end through the C-ABI with host buffers (copies inside the timed region)
+    e2e = None
+    if not args.no_e2e:
+        hplan = sgl.Plan(B, M, precision=sgl.PREC_FP32_MIXED, window=sgl.WIN_KB, q=q, sigma=2.0, host_io=True, device=dev)
+        xp = torch.from_numpy(x_h).pin_memory()
+        cp = torch.from_numpy(c_h).pin_memory()
+        yp = torch.from_numpy(y_h).pin_memory()
+        gp = torch.from_numpy(g_h).pin_memory()
+        fo = torch.empty(M, dtype=torch.complex128).pin_memory()
+        ao = torch.empty(hplan.Nc, dtype=torch.complex128).pin_memory()
+        go = torch.empty((M, 3), dtype=torch.float64).pin_memory()
+
+        def hstep():
+            hplan.forward_host(xp, cp, fo)
+            hplan.adjoint_host(xp, yp, ao)
+            hplan.grad_points_host(xp, cp, gp, go)
+
+        for _ in range(args.warmup):
+            hstep()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            hstep()
+        barrier()
+        el = sd.max_over_ranks(time.perf_counter() - t0, dev)
+        Nc = hplan.Nc
+        e2e = {"value": world * M / (el / args.steps) / 1e6, "unit": UNIT,
+               "h2d_bytes_per_step": 3 * 24 * M + 2 * 16 * Nc + 16 * M + 16 * M,
+               "d2h_bytes_per_step": 16 * M + 16 * Nc + 24 * M,
+               "path": "sgl_forward_host + sgl_adjoint_host + sgl_grad_points_host, pinned host buffers"}
+        hplan.close()
+
+    head = results["fp32_mixed"]
+    dom_name = max(head["stages"], key=lambda k: head["stages"][k]["ms"])
+    dom = head["stages"][dom_name]
+    traffic = traffic_for(dom_name, "fp32_mixed")
+    roofline = {"kernel": dom_name, "bound": dom["bound"], "achieved": dom["achieved"], "peak": dom["peak"],
+                "unit": dom["unit"], "frac": dom["frac"], "traffic": traffic,
+                "peak_source": (peak_src if dom["bound"] == "hbm" else
+                                "derived: 152 SMs x %s x 2 flop x %.0f MHz" % (
+                                    "128 FFMA lanes" if dom["alu"] == "fp32" else "2 DFMA", float(peaks.get("sm_max_mhz", 2070))))}
+
+    line = {"metric": METRIC, "value": round(head["value"], 4), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(head["ms_per_step"], 4), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+            "data": "synthetic (seeded): coefficients U[-1/2,1/2]^2, points N(0, I/2) in |x| <= 5, values U[-1/2,1/2]^2",
+            "config": {"workload": "B=64 (Nc=89440), M=1e6 points per GPU, sigma=2, Kaiser-Bessel q=8; step = set_points"
+                                   " + forward + adjoint + point gradient",
+                       "B": B, "M_per_gpu": M, "q": q, "sigma": 2.0, "window": "kaiser-bessel",
+                       "precision": "fp32-mixed (FFT, spreading, interpolation in FP32; conversions FP64)",
+                       "parallelism": "points sharded, adjoint coefficients all-reduced" if world > 1 else "single GPU",
+                       "l2": "256 MiB write between timed steps (flush), inputs and grid exceed L2 in total"},
+            "gpu_launches": head["gpu_launches"],
+            "roofline": roofline, "clocks": head["clocks"],
+            "fp64": {"value": round(results["fp64"]["value"], 4), "unit": UNIT,
+                     "ms_per_step": round(results["fp64"]["ms_per_step"], 4),
+                     "gpu_launches": results["fp64"]["gpu_launches"], "stages": results["fp64"]["stages"]},
+            "stages_fp32_mixed": head["stages"],
+            "e2e": e2e}
+
+    # ---- CPU baseline (oracle on the host cores, rank 0, N = 1) and the measured error on its sample
+    if rank == 0 and world == 1 and not args.no_cpu:
+        base, err = cpu_baseline(args, x_h, c_h, y_h, g_h, keep, dev)
+        line["cpu_baseline"] = base
+        line["error_vs_oracle"] = err
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def cpu_baseline(args, x_h, c_h, y_h, g_h, keep, dev):
+    """Oracle (direct sum) timed on a bounded sample; its outputs also give the GPU error on that sample."""
+    import numpy as np
+    import torch
+
+    import paper_1809_10786_gb300 as sgl
+    from oracle import direct
+
+    S = args.cpu_sample
+    idx = np.arange(S)
+    xs = np.ascontiguousarray(x_h[idx])
+    t0 = time.perf_counter()
+    f_ref, threads = direct.forward(args.B, xs, c_h)
+    a_ref, _ = direct.adjoint(args.B, xs, y_h[idx])
+    g_ref, _ = direct.grad_points(args.B, xs, c_h, g_h[idx])
+    el = time.perf_counter() - t0
+    base = {"value": round(S / el / 1e6, 8), "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": "%d of the %d points (forward + adjoint + point gradient, direct sum, FP64); %.1f s" % (S, args.M, el)}
+    err = {}
+    for prec_name, prec in (("fp32_mixed", sgl.PREC_FP32_MIXED), ("fp64", sgl.PREC_FP64)):
+        k = keep[prec_name]
+        ef = np.abs(k["f"][idx] - f_ref).max() / np.abs(f_ref).max()
+        eg = np.abs(k["g"][idx] - g_ref).max() / np.abs(g_ref).max()
+        # adjoint on the sample alone: same plan type, values zero outside the sample
+        plan = sgl.Plan(args.B, args.M, precision=prec, window=sgl.WIN_KB, q=args.q, sigma=2.0, device=dev)
+        plan.set_points(torch.from_numpy(x_h).to(dev))
+        ym = np.zeros_like(y_h)
+        ym[idx] = y_h[idx]
+        a = plan.adjoint(torch.from_numpy(ym).to(dev)).cpu().numpy()
+        plan.close()
+        ea = np.abs(a - a_ref).max() / np.abs(a_ref).max()
+        err[prec_name] = {"forward": float(ef), "adjoint": float(ea), "grad": float(eg),
+                          "measure": "max |gpu - oracle| / max |oracle| on the sample"}
+    return base, err
+
+
+# ---------------------------------------------------------------- reference arm (the oracle)
+def run_reference(args):
+    import numpy as np
+
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from oracle import direct
+    from paper_1809_10786_gb300 import inputs
+
+    S = args.cpu_sample
+    B = args.B
+    c = inputs.coefficients(B, inputs.seed_for(2))
+    x = inputs.points_gaussian(S, inputs.seed_for(2, 1))
+    y = inputs.values(S, inputs.seed_for(2, 100))
+    g = inputs.complex_normal(S, inputs.seed_for(2, 200))
+
+    def step():
+        _, t = direct.forward(B, x, c)
+        direct.adjoint(B, x, y)
+        direct.grad_points(B, x, c, g)
+        return t
+
+    for _ in range(args.warmup):
+        threads = step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        threads = step()
+    el = (time.perf_counter() - t0) / args.steps
+    value = S / el / 1e6
+    line = {"impl": "reference", "metric": METRIC, "value": round(value, 8), "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(el * 1e3, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded), same generators",
+            "config": {"workload": "B=64 (Nc=89440), sample of %d of the 1e6 points per step; step = forward + adjoint"
+                                   " + point gradient by direct summation (the CPU oracle)" % S,
+                       "B": B, "M_sample": S},
+            "cpu_baseline": {"value": round(value, 8), "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": "%d points per step" % S},
+            "e2e": {"value": round(value, 8), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--B", type=int, default=64)
+    ap.add_argument("--M", type=int, default=1_000_000)
+    ap.add_argument("--q", type=int, default=8)
+    ap.add_argument("--cpu-sample", type=int, default=8000)
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        raise SystemExit("--warmup must be >= 3")
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

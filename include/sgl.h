@@ -1,0 +1,203 @@
+/*
+ * sgl.h -- C-ABI of the GB300 (sm_103a) implementation of the non-lattice fast
+ * SGL Fourier transform (NFSGLFT), its adjoint and its point gradient, after
+ * C. Wuelker, "Fast SGL Fourier transforms for scattered data" (arXiv:1809.10786).
+ *
+ * Notation (paper, Sect. 1):
+ *   H_nlm(x) = N_nl R_nl(r) Y_lm(theta, phi), 1 <= n <= B, 0 <= l < n, |m| <= l.
+ *   Coefficients are stored in the paper's linear order
+ *       mu(n, l, m) = n(n-1)(2n-1)/6 + l(l+1) + m,   0 <= mu < Nc = B(B+1)(2B+1)/6.
+ *   The NDSGLFT matrix is Lambda = [H_{n(mu) l(mu) m(mu)}(x_i)]_{i, mu} (Def. of the NDSGLFT);
+ *   the forward transform computes f = Lambda fhat, the adjoint fhat' = Lambda^H f.
+ *
+ * Method (Sect. 6, Thm. on the factorization of Lambda): dense radial and polar
+ * conversion products (FP64) turn fhat into the coefficients eta_k of a 3-D
+ * trigonometric polynomial in xtilde = [arccos((2r - rho)/rho), theta, phi];
+ * a 3-D NFFT (Sect. 2: window deconvolution, oversampled inverse FFT, windowed
+ * interpolation) evaluates it at the points.  The adjoint runs the conjugate
+ * transposed factors in reverse order (Sect. 6, Cor. on Lambda^H).  The only
+ * approximation is the NFFT (Sect. 7).
+ *
+ * Conventions for every call below:
+ *   - Device pointers are CUDA global-memory pointers on the plan's device,
+ *     8-byte aligned at least (16-byte aligned recommended).  Host pointers are
+ *     ordinary (pageable or pinned) host memory.  The caller owns every buffer
+ *     passed in; the library never frees or retains them beyond the call.
+ *   - Complex numbers are interleaved (re, im) pairs of double (complex128).
+ *     Outputs are always complex128, in both precisions.
+ *   - Points are [M][3] double, row-major (x, y, z).
+ *   - All device-pointer calls are asynchronous on the plan's stream; results
+ *     are ready when that stream reaches the call's position.  Input buffers
+ *     must stay valid until then.
+ *   - A plan owns its workspace (allocated by sgl_plan_create) and is not
+ *     re-entrant: use one plan per stream / host thread at a time.
+ *   - Every function returns an sgl_status; none throws or aborts.  On failure
+ *     sgl_last_error() returns a message (thread-local, valid until the next
+ *     call on that thread).  Errors raised asynchronously on the device (a
+ *     non-finite input point) are reported by the next sgl_sync().
+ */
+#ifndef SGL_H
+#define SGL_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SGL_OK = 0,
+    SGL_ERR_ARG = 1,          /* invalid argument (size, pointer, alignment, enum) */
+    SGL_ERR_ALLOC = 2,        /* device or host allocation failed */
+    SGL_ERR_CUDA = 3,         /* a CUDA runtime call or kernel launch failed */
+    SGL_ERR_NONFINITE = 4,    /* a point coordinate was NaN or infinite */
+    SGL_ERR_TIMEOUT = 5,      /* a bounded device wait gave up */
+    SGL_ERR_UNSUPPORTED = 6,  /* valid but not supported by this build (e.g. FFT size) */
+    SGL_ERR_STATE = 7         /* call out of order (e.g. forward before set_points) */
+} sgl_status;
+
+typedef enum {
+    SGL_FP64 = 0,             /* every step in IEEE binary64 */
+    SGL_FP32_MIXED = 1        /* FFT, interpolation and spreading in binary32; conversions,
+                                 recurrences and deconvolution factors in binary64 */
+} sgl_precision;
+
+typedef enum {
+    SGL_WIN_KB = 0,           /* Kaiser-Bessel window (sinh form, shape b = pi(2 - 1/sigma)) */
+    SGL_WIN_GAUSS = 1         /* Gaussian window of Sect. 2 (lambda = sigma q / ((2 sigma - 1) pi)) */
+} sgl_window;
+
+/* plan flags */
+#define SGL_FLAG_HOST_IO 1u   /* also allocate staging buffers for the *_host calls */
+#define SGL_FLAG_PROFILE 2u   /* record CUDA events around every stage (read with sgl_profile) */
+
+/* stages reported by sgl_profile (index order) */
+#define SGL_NUM_STAGES 12
+
+typedef struct sgl_plan sgl_plan;
+
+/* Sizes of a plan (filled by sgl_plan_info). */
+typedef struct {
+    int B;                    /* bandwidth */
+    int q;                    /* window cutoff: half-width in oversampled grid cells (2q taps per axis) */
+    int precision;            /* sgl_precision */
+    int window;               /* sgl_window */
+    int64_t num_coeffs;       /* Nc = B(B+1)(2B+1)/6 */
+    int64_t M_max;            /* capacity in points */
+    int64_t M;                /* points of the last sgl_set_points */
+    int n[3];                 /* conversion grid (4B, 2B, 2B), axes (radial, polar, azimuthal) */
+    int N[3];                 /* oversampled FFT grid (>= sigma n, 2-3-5-smooth) */
+    int rows[3];              /* grid rows held per axis after the pruned FFT */
+    double sigma_eff[3];      /* N[d] / n[d] */
+    int64_t workspace_bytes;  /* device bytes owned by the plan */
+    int64_t kernel_launches;  /* CUDA kernels this plan has launched so far */
+} sgl_plan_info_t;
+
+/* Nc = B(B+1)(2B+1)/6 (Sect. 1); -1 if B < 1. */
+int64_t sgl_num_coeffs(int B);
+
+/*
+ * Create a plan for bandwidth B (1 <= B <= 128) and at most M_max points
+ * (0 <= M_max < 2^31).  precision: sgl_precision; window: sgl_window; q: window
+ * cutoff, 1 <= q <= 16 (the paper's cutoff parameter, Sect. 2); sigma: requested
+ * oversampling factor, 1.5 <= sigma <= 4 (the FFT grid is rounded up to the next
+ * even 2-3-5-smooth size per axis, so the effective factor is >= sigma).
+ * cuda_stream: a cudaStream_t (NULL: the legacy default stream).  The plan
+ * uses the current CUDA device.  Host work: FP64 precompute of the polar
+ * conversion matrices (Sect. 6, P_m = W_m D C~ Vtilde L_m^T diag Q) and the window
+ * Fourier factors.  On failure *out is NULL and nothing is leaked.
+ */
+sgl_status sgl_plan_create(sgl_plan **out, int B, int64_t M_max, int precision, int window,
+                           int q, double sigma, unsigned flags, void *cuda_stream);
+
+/* Release the plan and all of its device memory (synchronizes its stream). NULL is a no-op. */
+void sgl_plan_destroy(sgl_plan *plan);
+
+/* Change the stream later calls are issued on. */
+sgl_status sgl_set_stream(sgl_plan *plan, void *cuda_stream);
+
+/* Fill *info with the plan's sizes. */
+sgl_status sgl_plan_info(const sgl_plan *plan, sgl_plan_info_t *info);
+
+/*
+ * Set the M points (0 <= M <= M_max) the next transforms use: xyz_dev [M][3]
+ * (device).  Computes rho = max_i |x_i| on the device (Sect. 7 choice of rho,
+ * with a relative margin of 2^-20 so that every point has arccos argument < 1),
+ * the transformed points xtilde_i (Sect. 6, eq. of the transformed points) and a
+ * spatial bin sort of the points (no host synchronization).  The coordinates
+ * are copied; xyz_dev may be reused once the stream passes this call.
+ * Non-finite coordinates set a device flag reported by sgl_sync().
+ */
+sgl_status sgl_set_points(sgl_plan *plan, const double *xyz_dev, int64_t M);
+
+/* rho used by the plan (synchronizes the stream); SGL_ERR_STATE before set_points. */
+sgl_status sgl_get_rho(sgl_plan *plan, double *rho_host);
+
+/*
+ * Forward NFSGLFT: vals_dev[i] ~= f(x_i) = sum_mu coef_dev[mu] H_mu(x_i), i < M
+ * (Def. of the NDSGLFT; Sect. 6 factorization, Sect. 2 NFFT).
+ * coef_dev: complex128 [Nc] in mu order (device); vals_dev: complex128 [M] in the
+ * order the points were given (device).  SGL_ERR_STATE before sgl_set_points.
+ */
+sgl_status sgl_forward(sgl_plan *plan, const double *coef_dev, double *vals_dev);
+
+/*
+ * Adjoint NFSGLFT: coef_dev[mu] ~= sum_i conj(H_mu(x_i)) vals_dev[i] (Lambda^H,
+ * Sect. 6 corollary).  vals_dev: complex128 [M]; coef_dev: complex128 [Nc], fully
+ * overwritten (zeros when M = 0).
+ */
+sgl_status sgl_adjoint(sgl_plan *plan, const double *vals_dev, double *coef_dev);
+
+/*
+ * Point gradient of the forward map:
+ *   gxyz_dev[i][d] = Re( conj(gout_dev[i]) * d f(x_i) / d x_{i,d} ),  f = Lambda coef,
+ * the vector-Jacobian product of the forward transform with respect to the points
+ * (rho held fixed: the exact factorization holds for every rho >= max r).
+ * The derivative of the NFFT approximant is taken through the window derivative.
+ * coef_dev: complex128 [Nc]; gout_dev: complex128 [M]; gxyz_dev: double [M][3].
+ */
+sgl_status sgl_grad_points(sgl_plan *plan, const double *coef_dev, const double *gout_dev,
+                           double *gxyz_dev);
+
+/*
+ * The trigonometric coefficients of Sect. 6 (eq. of the NFFT sum): eta_dev receives
+ * eta_k for |k0| <= 2B-2, |k1| <= B-1, |k2| <= B-1 as complex128
+ * [4B-3][2B-1][2B-1], index (k0 + 2B-2, k1 + B-1, k2 + B-1), so that
+ *   f(x) = sum_k eta_k exp(i <k, xtilde>)  exactly (before any NFFT approximation).
+ * Needs sgl_set_points (eta depends on rho).  coef_dev: complex128 [Nc].
+ */
+sgl_status sgl_trig_coeffs(sgl_plan *plan, const double *coef_dev, double *eta_dev);
+
+/*
+ * Host-buffer variants (need SGL_FLAG_HOST_IO): copy the inputs from host memory
+ * into the plan's staging buffers, run set_points + forward (or adjoint) on the
+ * plan's stream, copy the result back and synchronize the stream before returning.
+ * xyz_host [M][3] double; coef_host complex128 [Nc]; vals_host complex128 [M].
+ */
+sgl_status sgl_forward_host(sgl_plan *plan, const double *xyz_host, int64_t M,
+                            const double *coef_host, double *vals_host);
+sgl_status sgl_adjoint_host(sgl_plan *plan, const double *xyz_host, int64_t M,
+                            const double *vals_host, double *coef_host);
+/* gout_host complex128 [M]; gxyz_host double [M][3] (see sgl_grad_points). */
+sgl_status sgl_grad_points_host(sgl_plan *plan, const double *xyz_host, int64_t M, const double *coef_host,
+                                const double *gout_host, double *gxyz_host);
+
+/*
+ * Per-stage device times of a plan created with SGL_FLAG_PROFILE: synchronizes the
+ * stream, writes the summed milliseconds (ms_out) and the number of timed calls
+ * (count_out) of each of the SGL_NUM_STAGES stages since the last call, then resets.
+ * Either output may be NULL.  Stage names: sgl_stage_name(i).
+ */
+sgl_status sgl_profile(sgl_plan *plan, double *ms_out, int64_t *count_out);
+const char *sgl_stage_name(int stage);
+
+/* Synchronize the plan's stream and report deferred device errors (non-finite points). */
+sgl_status sgl_sync(sgl_plan *plan);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char *sgl_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SGL_H */

@@ -1,0 +1,237 @@
+"""Thin ctypes binding of libsgl.so (include/sgl.h): argument marshalling only.
+
+Every transform step runs in the library's CUDA kernels.  PyTorch supplies the
+device memory and the stream: tensors are passed by ``data_ptr()`` and calls are
+issued on ``torch.cuda.current_stream()``.  There is no CPU fallback: without the
+library (or without a GPU) every call raises :class:`SGLError`.
+"""
+import ctypes
+import os
+import threading
+
+import torch
+
+from . import build as _build
+
+PREC_FP64, PREC_FP32_MIXED = 0, 1
+WIN_KB, WIN_GAUSS = 0, 1
+FLAG_HOST_IO, FLAG_PROFILE = 1, 2
+NUM_STAGES = 12
+
+_STATUS = {0: "SGL_OK", 1: "SGL_ERR_ARG", 2: "SGL_ERR_ALLOC", 3: "SGL_ERR_CUDA", 4: "SGL_ERR_NONFINITE",
+           5: "SGL_ERR_TIMEOUT", 6: "SGL_ERR_UNSUPPORTED", 7: "SGL_ERR_STATE"}
+
+_LIB = None
+_LOCK = threading.Lock()
+
+
+class SGLError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (_STATUS.get(status, status), msg))
+        self.status = status
+
+
+class PlanInfo(ctypes.Structure):
+    _fields_ = [("B", ctypes.c_int), ("q", ctypes.c_int), ("precision", ctypes.c_int), ("window", ctypes.c_int),
+                ("num_coeffs", ctypes.c_int64), ("M_max", ctypes.c_int64), ("M", ctypes.c_int64),
+                ("n", ctypes.c_int * 3), ("N", ctypes.c_int * 3), ("rows", ctypes.c_int * 3),
+                ("sigma_eff", ctypes.c_double * 3), ("workspace_bytes", ctypes.c_int64),
+                ("kernel_launches", ctypes.c_int64)]
+
+
+def library_path():
+    return _build.LIB
+
+
+def load_library(build_if_missing=True):
+    """Load libsgl.so (building it in-tree first if it is missing and nvcc exists)."""
+    global _LIB
+    with _LOCK:
+        if _LIB is not None:
+            return _LIB
+        path = library_path()
+        if not os.path.exists(path):
+            if not build_if_missing:
+                raise SGLError(3, "libsgl.so is not built (%s)" % path)
+            _build.build()
+        lib = ctypes.CDLL(path)
+        vp, dp, i64 = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int64
+        lib.sgl_num_coeffs.restype = i64
+        lib.sgl_num_coeffs.argtypes = [ctypes.c_int]
+        lib.sgl_last_error.restype = ctypes.c_char_p
+        lib.sgl_plan_create.restype = ctypes.c_int
+        lib.sgl_plan_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int, i64, ctypes.c_int, ctypes.c_int,
+                                        ctypes.c_int, ctypes.c_double, ctypes.c_uint, vp]
+        lib.sgl_plan_destroy.restype = None
+        lib.sgl_plan_destroy.argtypes = [vp]
+        for name, args in [("sgl_set_stream", [vp, vp]), ("sgl_plan_info", [vp, ctypes.POINTER(PlanInfo)]),
+                           ("sgl_set_points", [vp, vp, i64]), ("sgl_get_rho", [vp, dp]),
+                           ("sgl_forward", [vp, vp, vp]), ("sgl_adjoint", [vp, vp, vp]),
+                           ("sgl_grad_points", [vp, vp, vp, vp]), ("sgl_trig_coeffs", [vp, vp, vp]),
+                           ("sgl_forward_host", [vp, vp, i64, vp, vp]), ("sgl_adjoint_host", [vp, vp, i64, vp, vp]),
+                           ("sgl_grad_points_host", [vp, vp, i64, vp, vp, vp]),
+                           ("sgl_profile", [vp, dp, ctypes.POINTER(i64)]), ("sgl_sync", [vp])]:
+            f = getattr(lib, name)
+            f.restype = ctypes.c_int
+            f.argtypes = args
+        lib.sgl_stage_name.restype = ctypes.c_char_p
+        lib.sgl_stage_name.argtypes = [ctypes.c_int]
+        _LIB = lib
+        return lib
+
+
+def _check(st):
+    if st != 0:
+        raise SGLError(st, _LIB.sgl_last_error().decode())
+
+
+def num_coeffs(B):
+    return int(load_library().sgl_num_coeffs(int(B)))
+
+
+def _stream_handle(device):
+    return ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+
+
+def _dev_tensor(t, dtype, shape, name, device):
+    if not isinstance(t, torch.Tensor):
+        raise TypeError("%s must be a torch.Tensor" % name)
+    if t.device.type != "cuda" or t.device != device:
+        raise ValueError("%s must live on %s" % (name, device))
+    if t.dtype != dtype:
+        raise TypeError("%s must be %s, got %s" % (name, dtype, t.dtype))
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError("%s must have shape %s, got %s" % (name, tuple(shape), tuple(t.shape)))
+    return t.contiguous()
+
+
+class Plan:
+    """One NFSGLFT plan (sgl_plan_create): bandwidth B, up to M_max points."""
+
+    def __init__(self, B, M_max, precision=PREC_FP64, window=WIN_KB, q=8, sigma=2.0, host_io=False, profile=False,
+                 device=None):
+        if not torch.cuda.is_available():
+            raise SGLError(3, "no CUDA device: the NFSGLFT runs only on the GPU")
+        self.lib = load_library()
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else torch.device(device).index or 0)
+        self.B, self.M_max = int(B), int(M_max)
+        self.precision, self.window, self.q, self.sigma = int(precision), int(window), int(q), float(sigma)
+        self._h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            st = self.lib.sgl_plan_create(ctypes.byref(self._h), self.B, self.M_max, self.precision, self.window,
+                                          self.q, self.sigma, (FLAG_HOST_IO if host_io else 0) | (FLAG_PROFILE if profile else 0),
+                                          _stream_handle(self.device))
+        _check(st)
+        self.Nc = num_coeffs(self.B)
+        self.M = 0
+        self._xyz = None
+
+    def close(self):
+        if self._h:
+            self.lib.sgl_plan_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _stream(self):
+        _check(self.lib.sgl_set_stream(self._h, _stream_handle(self.device)))
+
+    def info(self):
+        inf = PlanInfo()
+        _check(self.lib.sgl_plan_info(self._h, ctypes.byref(inf)))
+        return {"B": inf.B, "q": inf.q, "precision": inf.precision, "window": inf.window,
+                "num_coeffs": inf.num_coeffs, "M_max": inf.M_max, "M": inf.M, "n": list(inf.n), "N": list(inf.N),
+                "rows": list(inf.rows), "sigma_eff": list(inf.sigma_eff), "workspace_bytes": inf.workspace_bytes,
+                "kernel_launches": inf.kernel_launches}
+
+    def profile(self):
+        """{stage: (milliseconds, timed calls)} since the last call (plan made with profile=True)."""
+        ms = (ctypes.c_double * NUM_STAGES)()
+        cnt = (ctypes.c_int64 * NUM_STAGES)()
+        _check(self.lib.sgl_profile(self._h, ms, cnt))
+        return {self.lib.sgl_stage_name(i).decode(): (ms[i], cnt[i]) for i in range(NUM_STAGES)}
+
+    def set_points(self, xyz):
+        xyz = _dev_tensor(xyz, torch.float64, (xyz.shape[0], 3), "xyz", self.device)
+        self._stream()
+        _check(self.lib.sgl_set_points(self._h, ctypes.c_void_p(xyz.data_ptr()), xyz.shape[0]))
+        self.M = xyz.shape[0]
+        self._xyz = xyz            # keep alive until the stream has consumed it
+        return self
+
+    def rho(self):
+        v = ctypes.c_double()
+        _check(self.lib.sgl_get_rho(self._h, ctypes.byref(v)))
+        return v.value
+
+    def forward(self, coef, out=None):
+        coef = _dev_tensor(coef, torch.complex128, (self.Nc,), "coef", self.device)
+        if out is None:
+            out = torch.empty(self.M, dtype=torch.complex128, device=self.device)
+        out = _dev_tensor(out, torch.complex128, (self.M,), "out", self.device)
+        self._stream()
+        _check(self.lib.sgl_forward(self._h, ctypes.c_void_p(coef.data_ptr()), ctypes.c_void_p(out.data_ptr())))
+        return out
+
+    def adjoint(self, vals, out=None):
+        vals = _dev_tensor(vals, torch.complex128, (self.M,), "vals", self.device)
+        if out is None:
+            out = torch.empty(self.Nc, dtype=torch.complex128, device=self.device)
+        out = _dev_tensor(out, torch.complex128, (self.Nc,), "out", self.device)
+        self._stream()
+        _check(self.lib.sgl_adjoint(self._h, ctypes.c_void_p(vals.data_ptr()), ctypes.c_void_p(out.data_ptr())))
+        return out
+
+    def grad_points(self, coef, gout, out=None):
+        coef = _dev_tensor(coef, torch.complex128, (self.Nc,), "coef", self.device)
+        gout = _dev_tensor(gout, torch.complex128, (self.M,), "gout", self.device)
+        if out is None:
+            out = torch.empty((self.M, 3), dtype=torch.float64, device=self.device)
+        out = _dev_tensor(out, torch.float64, (self.M, 3), "out", self.device)
+        self._stream()
+        _check(self.lib.sgl_grad_points(self._h, ctypes.c_void_p(coef.data_ptr()), ctypes.c_void_p(gout.data_ptr()),
+                                        ctypes.c_void_p(out.data_ptr())))
+        return out
+
+    def trig_coeffs(self, coef):
+        """eta_k on |k0| <= 2B-2, |k1|, |k2| <= B-1 as complex128 [4B-3, 2B-1, 2B-1]."""
+        coef = _dev_tensor(coef, torch.complex128, (self.Nc,), "coef", self.device)
+        B = self.B
+        out = torch.empty((4 * B - 3, 2 * B - 1, 2 * B - 1), dtype=torch.complex128, device=self.device)
+        self._stream()
+        _check(self.lib.sgl_trig_coeffs(self._h, ctypes.c_void_p(coef.data_ptr()), ctypes.c_void_p(out.data_ptr())))
+        return out
+
+    def forward_host(self, xyz_host, coef_host, vals_host):
+        """numpy or pinned-CPU-tensor buffers; copies inside the call, synchronous."""
+        _check(self.lib.sgl_forward_host(self._h, _host_ptr(xyz_host), int(xyz_host.shape[0]),
+                                         _host_ptr(coef_host), _host_ptr(vals_host)))
+        return vals_host
+
+    def adjoint_host(self, xyz_host, vals_host, coef_host):
+        _check(self.lib.sgl_adjoint_host(self._h, _host_ptr(xyz_host), int(xyz_host.shape[0]),
+                                         _host_ptr(vals_host), _host_ptr(coef_host)))
+        return coef_host
+
+    def grad_points_host(self, xyz_host, coef_host, gout_host, gxyz_host):
+        _check(self.lib.sgl_grad_points_host(self._h, _host_ptr(xyz_host), int(xyz_host.shape[0]), _host_ptr(coef_host),
+                                             _host_ptr(gout_host), _host_ptr(gxyz_host)))
+        return gxyz_host
+
+    def sync(self):
+        _check(self.lib.sgl_sync(self._h))
+
+
+def _host_ptr(a):
+    if isinstance(a, torch.Tensor):
+        if a.device.type != "cpu" or not a.is_contiguous():
+            raise ValueError("host buffers must be contiguous CPU tensors")
+        return ctypes.c_void_p(a.data_ptr())
+    import numpy as np
+    if not isinstance(a, np.ndarray) or not a.flags["C_CONTIGUOUS"]:
+        raise ValueError("host buffers must be C-contiguous numpy arrays or CPU tensors")
+    return ctypes.c_void_p(a.ctypes.data)

@@ -1,0 +1,625 @@
+// sgl_capi.cu -- the C-ABI of include/sgl.h: argument checks, plan set-up (FP64 host
+// precompute of the polar conversion matrices, window Fourier factors and FFT tables),
+// workspace ownership and the order of the kernel launches.
+#include "sgl_internal.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+namespace sgl {
+
+static thread_local std::string g_last_error;
+
+// Event pairs recorded around each stage; read (and recycled) by sgl_profile.
+struct Profiler {
+    struct Pair { cudaEvent_t a, b; int stage; };
+    std::vector<Pair> open, pool;
+    cudaEvent_t take() {
+        if (!pool.empty()) {
+            cudaEvent_t e = pool.back().a;
+            pool.pop_back();
+            return e;
+        }
+        cudaEvent_t e = nullptr;
+        cudaEventCreate(&e);
+        return e;
+    }
+    ~Profiler() {
+        for (auto &p : open) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
+        for (auto &p : pool) cudaEventDestroy(p.a);
+    }
+};
+
+// RAII scope: records a start event on construction and an end event on destruction.
+struct StageScope {
+    sgl_plan *p;
+    int stage;
+    cudaEvent_t a = nullptr;
+    StageScope(sgl_plan *pl, int st) : p(pl), stage(st) {
+        if (p->prof) { a = p->prof->take(); cudaEventRecord(a, p->stream); }
+    }
+    ~StageScope() {
+        if (p->prof && a) {
+            cudaEvent_t b = p->prof->take();
+            cudaEventRecord(b, p->stream);
+            p->prof->open.push_back({a, b, stage});
+        }
+    }
+};
+
+sgl_status set_error(sgl_status code, const std::string &msg) {
+    g_last_error = msg;
+    return code;
+}
+
+namespace {
+
+sgl_status ok() {
+    g_last_error.clear();
+    return SGL_OK;
+}
+
+bool is_235_smooth(int n) {
+    for (int f : {2, 3, 5})
+        while (n % f == 0) n /= f;
+    return n == 1;
+}
+
+int next_fft_size(double target) {
+    int n = (int)std::ceil(target - 1e-9);
+    if (n % 2) ++n;
+    while (!is_235_smooth(n)) n += 2;
+    return n;
+}
+
+void factor(int N, int *rad, int &nrad) {
+    nrad = 0;
+    while (N % 8 == 0) { rad[nrad++] = 8; N /= 8; }
+    while (N % 4 == 0) { rad[nrad++] = 4; N /= 4; }
+    while (N % 2 == 0) { rad[nrad++] = 2; N /= 2; }
+    while (N % 3 == 0) { rad[nrad++] = 3; N /= 3; }
+    while (N % 5 == 0) { rad[nrad++] = 5; N /= 5; }
+}
+
+// modified Bessel function I_0 by its power series (all terms positive)
+double bessel_i0(double z) {
+    const double x = 0.25 * z * z;
+    double term = 1.0, sum = 1.0;
+    for (int k = 1; k < 500; ++k) {
+        term *= x / ((double)k * k);
+        sum += term;
+        if (term < 1e-17 * sum) break;
+    }
+    return sum;
+}
+
+// Fourier transform int psi(x) e^{-i w x} dx of the peak-normalized window (x in grid cells).
+// Kaiser-Bessel: psi = [sinh(b s)/s] / [sinh(b q)/q], s = sqrt(q^2 - x^2); the pair
+//   int sinh(b sqrt(q^2-x^2)) / sqrt(q^2-x^2) e^{-i w x} dx = pi I_0(q sqrt(b^2 - w^2))  (|w| <= b)
+// Gaussian: psi = exp(-x^2 / (2 lambda)),  transform sqrt(2 pi lambda) exp(-lambda w^2 / 2)
+// (Lemma on the Gaussian's Fourier transform, Sect. 2, after the change of variables).
+double window_hat(int window, double w, double q, double par) {
+    if (window == SGL_WIN_KB) {
+        const double b = par;
+        const double arg = std::sqrt(std::max(b * b - w * w, 0.0));
+        // q / sinh(b q) = 2 q e^{-b q} / (1 - e^{-2 b q})
+        const double scale = 2.0 * q * std::exp(-b * q) / (-std::expm1(-2.0 * b * q));
+        return kPi * bessel_i0(q * arg) * scale;
+    }
+    return std::sqrt(2.0 * kPi * par) * std::exp(-0.5 * par * w * w);
+}
+
+// Normalized associated Legendre values Pbar_lm(x) = Q_lm P_lm(x) for 0 <= m <= l < B
+// (Condon-Shortley phase included), out[l * B + m], by the standard stable recurrences
+//   Pbar_mm = -sqrt((2m+1)/(2m)) sin Pbar_{m-1,m-1},  Pbar_{m+1,m} = sqrt(2m+3) x Pbar_mm,
+//   Pbar_lm = a_lm (x Pbar_{l-1,m} - b_lm Pbar_{l-2,m}),
+//   a_lm = sqrt((4l^2-1)/(l^2-m^2)),  b_lm = sqrt(((l-1)^2-m^2)/(4(l-1)^2-1)).
+void legendre_normalized(int B, double x, double sn, std::vector<double> &out) {
+    out.assign((size_t)B * B, 0.0);
+    double pmm = 1.0 / std::sqrt(4.0 * kPi);
+    for (int m = 0; m < B; ++m) {
+        if (m > 0) pmm *= -std::sqrt((2.0 * m + 1.0) / (2.0 * m)) * sn;
+        out[(size_t)m * B + m] = pmm;
+        if (m + 1 < B) out[(size_t)(m + 1) * B + m] = std::sqrt(2.0 * m + 3.0) * x * pmm;
+        for (int l = m + 2; l < B; ++l) {
+            const double a = std::sqrt((4.0 * l * l - 1.0) / ((double)l * l - (double)m * m));
+            const double bb = std::sqrt(((l - 1.0) * (l - 1.0) - (double)m * m) / (4.0 * (l - 1.0) * (l - 1.0) - 1.0));
+            out[(size_t)l * B + m] = a * (x * out[(size_t)(l - 1) * B + m] - bb * out[(size_t)(l - 2) * B + m]);
+        }
+    }
+}
+
+// Polar conversion matrices (Sect. 6, spherical subtransform; Thm. on the factorization):
+// for m >= 0, kappa1 = 0..K1, l = m..B-1, with w_j = (2j+1) pi / (4B), j < 2B:
+//  m even: P[m][k][l] = (1/2B) sum_j cos(k w_j) Pbar_lm(cos w_j)       (DCT, then Chebyshev -> exponential)
+//  m odd:  eps_k = (c_k/2B) sum_j cos(k w_j) Pbar_lm(cos w_j) / sin w_j  (c_0 = 1, c_k = 2; V_B weighting)
+//          zeta_k = (1/4i) {2eps_0 - eps_2 (k=1); eps_{k-1} - eps_{k+1} (1<k<2B-2); eps_{k-1} (k >= 2B-2)}
+//          and P[m][k][l] holds the real factor 4i zeta_k / 4 (the kernels apply the -i).
+// The matrices for -m are (-1)^m times those for m.
+void polar_matrices(int B, std::vector<double> &P) {
+    const int K1 = B - 1, n2 = 2 * B;
+    P.assign((size_t)B * (K1 + 1) * B, 0.0);
+    std::vector<std::vector<double>> leg(n2);
+    std::vector<double> w(n2);
+    for (int j = 0; j < n2; ++j) {
+        w[j] = (2.0 * j + 1.0) * kPi / (4.0 * B);
+        legendre_normalized(B, std::cos(w[j]), std::sin(w[j]), leg[j]);
+    }
+    std::vector<double> eps(n2 + 2);
+    for (int m = 0; m < B; ++m) {
+        for (int l = m; l < B; ++l) {
+            if (m % 2 == 0) {
+                for (int k = 0; k <= K1; ++k) {
+                    long double s = 0.0L;
+                    for (int j = 0; j < n2; ++j) s += (long double)std::cos(k * w[j]) * leg[j][(size_t)l * B + m];
+                    P[((size_t)m * (K1 + 1) + k) * B + l] = (double)(s / n2);
+                }
+            } else {
+                std::fill(eps.begin(), eps.end(), 0.0);
+                for (int k = 0; k < n2; ++k) {
+                    long double s = 0.0L;
+                    for (int j = 0; j < n2; ++j) s += (long double)std::cos(k * w[j]) * leg[j][(size_t)l * B + m] / std::sin(w[j]);
+                    eps[k] = (double)(s * (k == 0 ? 1.0L : 2.0L) / n2);
+                }
+                for (int k = 1; k <= K1; ++k) {
+                    double v;
+                    if (k == 1) v = 2.0 * eps[0] - eps[2];
+                    else if (k < n2 - 2) v = eps[k - 1] - eps[k + 1];
+                    else v = eps[k - 1];
+                    P[((size_t)m * (K1 + 1) + k) * B + l] = v / 4.0;
+                }
+            }
+        }
+    }
+}
+
+struct DevAlloc {
+    std::vector<void *> ptrs;
+    int64_t bytes = 0;
+    template <typename T>
+    cudaError_t get(T **p, size_t count) {
+        *p = nullptr;
+        if (count == 0) count = 1;
+        void *q = nullptr;
+        cudaError_t e = cudaMalloc(&q, count * sizeof(T));
+        if (e != cudaSuccess) return e;
+        ptrs.push_back(q);
+        bytes += (int64_t)(count * sizeof(T));
+        *p = (T *)q;
+        return cudaSuccess;
+    }
+    void release() {
+        for (void *q : ptrs) cudaFree(q);
+        ptrs.clear();
+    }
+};
+
+struct PlanHolder {
+    sgl_plan plan;
+    DevAlloc alloc;
+};
+
+const char *kStageNames[ST_COUNT] = {"points", "radial_matrix", "radial", "polar", "fft_forward", "interp",
+                                     "spread", "fft_adjoint", "polar_adjoint", "radial_adjoint", "grad_interp",
+                                     "trig_export"};
+
+PlanHolder *holder_of(sgl_plan *p) { return reinterpret_cast<PlanHolder *>(p); }
+
+bool aligned8(const void *p) { return ((uintptr_t)p & 7u) == 0; }
+
+sgl_status check_plan(const sgl_plan *p) {
+    if (!p) return set_error(SGL_ERR_ARG, "plan is NULL");
+    return SGL_OK;
+}
+
+sgl_status launch_status(cudaError_t e, const char *what) {
+    if (e != cudaSuccess) return set_error(SGL_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+    return ok();
+}
+
+template <typename T>
+cudaError_t upload(T *dst, const std::vector<T> &src, cudaStream_t s) {
+    return cudaMemcpyAsync(dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice, s);
+}
+
+}  // namespace
+}  // namespace sgl
+
+using namespace sgl;
+
+extern "C" {
+
+int64_t sgl_num_coeffs(int B) {
+    if (B < 1) return -1;
+    return (int64_t)B * (B + 1) * (2 * B + 1) / 6;
+}
+
+const char *sgl_last_error(void) { return g_last_error.c_str(); }
+
+sgl_status sgl_plan_create(sgl_plan **out, int B, int64_t M_max, int precision, int window, int q, double sigma,
+                           unsigned flags, void *cuda_stream) {
+    if (!out) return set_error(SGL_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (B < 1 || B > 128) return set_error(SGL_ERR_ARG, "B must be in [1, 128]");
+    if (M_max < 0 || M_max >= ((int64_t)1 << 31)) return set_error(SGL_ERR_ARG, "M_max must be in [0, 2^31)");
+    if (precision != SGL_FP64 && precision != SGL_FP32_MIXED) return set_error(SGL_ERR_ARG, "unknown precision");
+    if (window != SGL_WIN_KB && window != SGL_WIN_GAUSS) return set_error(SGL_ERR_ARG, "unknown window");
+    if (q < 1 || q > kMaxQ) return set_error(SGL_ERR_ARG, "q must be in [1, 16]");
+    if (!(sigma >= 1.5 && sigma <= 4.0)) return set_error(SGL_ERR_ARG, "sigma must be in [1.5, 4]");
+
+    PlanHolder *h = new (std::nothrow) PlanHolder();
+    if (!h) return set_error(SGL_ERR_ALLOC, "host allocation failed");
+    sgl_plan *p = &h->plan;
+    std::memset(p, 0, sizeof(sgl_plan));
+    cudaGetDevice(&p->device);
+    p->stream = (cudaStream_t)cuda_stream;
+    p->B = B; p->q = q; p->prec = precision; p->window = window; p->flags = flags; p->sigma = sigma;
+    p->M_max = M_max; p->M = 0; p->Nc = sgl_num_coeffs(B);
+    p->K0 = 2 * B - 2; p->K1 = B - 1;
+    const int nsz[3] = {4 * B, 2 * B, 2 * B};
+    const int Ksz[3] = {p->K0, p->K1, p->K1};
+    auto fail = [&](sgl_status st, const std::string &m) {
+        h->alloc.release();
+        delete p->prof;
+        delete h;
+        return set_error(st, m);
+    };
+    for (int d = 0; d < 3; ++d) {
+        Axis &a = p->ax[d];
+        a.n = nsz[d];
+        a.N = next_fft_size(sigma * nsz[d]);
+        a.K = Ksz[d];
+        if (a.N > 1024) return fail(SGL_ERR_UNSUPPORTED, "FFT length above 1024");
+        if (q >= a.N) return fail(SGL_ERR_ARG, "q must be smaller than every oversampled grid size");
+        a.sigma = (double)a.N / a.n;
+        a.windowed = (d < 2) && (a.N / 2 + 2 * q + 1 <= a.N);
+        a.rows = a.windowed ? a.N / 2 + 2 * q + 1 : a.N;
+        a.first = a.windowed ? -q : 0;
+        a.wpar = (window == SGL_WIN_KB) ? kPi * (2.0 - 1.0 / a.sigma) : a.sigma * q / ((2.0 * a.sigma - 1.0) * kPi);
+        factor(a.N, a.rad, a.nrad);
+    }
+    p->nbin[0] = p->ax[0].N / 2 + 1;
+    p->nbin[1] = p->ax[1].N / 2 + 1;
+    p->nbin[2] = (p->ax[2].N + kBinS2 - 1) / kBinS2;
+    p->nbins = (int64_t)p->nbin[0] * p->nbin[1] * p->nbin[2];
+
+    // ---- device allocations
+    DevAlloc &A = h->alloc;
+    Buffers &b = p->b;
+    const int K0 = p->K0, K1 = p->K1;
+    const int64_t W = 2 * K1 + 1;
+    const size_t csz = precision == SGL_FP32_MIXED ? sizeof(float2) : sizeof(double2);
+    const Axis &A0 = p->ax[0], &A1 = p->ax[1], &A2 = p->ax[2];
+    const size_t nA = std::max<size_t>((size_t)A0.rows * W * W, (size_t)A0.rows * A1.rows * A2.N);
+    const size_t bytesB = std::max<size_t>((size_t)A0.rows * A1.rows * W * csz, (size_t)(2 * K0 + 1) * W * W * sizeof(double2));
+    cudaError_t e = cudaSuccess;
+#define ALLOC(ptr, n) do { if ((e = A.get(&(ptr), (n))) != cudaSuccess) return fail(SGL_ERR_ALLOC, std::string("cudaMalloc: ") + cudaGetErrorString(e)); } while (0)
+    ALLOC(b.P, (size_t)B * (K1 + 1) * B);
+    ALLOC(b.costab, (size_t)8 * B);
+    ALLOC(b.radv, (size_t)B * B * (B + 1));
+    ALLOC(b.Kmat, (size_t)(K0 + 1) * B * (B + 1) / 2);
+    ALLOC(b.beta, (size_t)(2 * B - 1) * (K0 + 1) * B);
+    ALLOC(b.zeta, (size_t)(K0 + 1) * (K1 + 1) * W);
+    ALLOC(b.linescale, (size_t)(W * W));
+    {
+        unsigned char *pa = nullptr, *pb = nullptr;
+        ALLOC(pa, nA * csz);
+        ALLOC(pb, bytesB);
+        b.bufA = pa; b.bufB = pb;
+        b.bufA_bytes = nA * csz; b.bufB_bytes = bytesB;
+    }
+    for (int d = 0; d < 3; ++d) {
+        Axis &a = p->ax[d];
+        ALLOC(a.tw_d, (size_t)a.N);
+        ALLOC(a.tw_f, (size_t)a.N);
+        ALLOC(a.rev, (size_t)a.N);
+        ALLOC(a.deconv, (size_t)(2 * a.K + 1));
+    }
+    ALLOC(b.r2max, 1);
+    ALLOC(b.dev_flags, 1);
+    const size_t Mc = (size_t)std::max<int64_t>(M_max, 1);
+    ALLOC(b.u_tmp, 3 * Mc);
+    ALLOC(b.u_sorted, 3 * Mc);
+    ALLOC(b.perm, Mc);
+    ALLOC(b.bin_of, Mc);
+    ALLOC(b.rank_of, Mc);
+    ALLOC(b.bin_count, (size_t)p->nbins);
+    ALLOC(b.bin_off, (size_t)p->nbins);
+    ALLOC(b.scan_tmp, (size_t)(p->nbins / 2048 + 2));
+    if (flags & SGL_FLAG_HOST_IO) {
+        ALLOC(b.io_xyz, 3 * Mc);
+        ALLOC(b.io_coef, (size_t)(2 * p->Nc));
+        ALLOC(b.io_vals, 2 * Mc);
+        ALLOC(b.io_grad, 3 * Mc);
+    }
+#undef ALLOC
+    p->work_bytes = A.bytes;
+    if (flags & SGL_FLAG_PROFILE) p->prof = new (std::nothrow) Profiler();
+
+    // ---- host precompute (FP64) and upload
+    std::vector<double> P;
+    polar_matrices(B, P);
+    std::vector<double> costab(8 * B);
+    for (int m = 0; m < 8 * B; ++m) costab[m] = (double)cosl((long double)m * 3.14159265358979323846264338327950288L / (4.0L * B));
+    std::vector<double> dec[3];
+    for (int d = 0; d < 3; ++d) {
+        Axis &a = p->ax[d];
+        dec[d].resize(2 * a.K + 1);
+        for (int k = -a.K; k <= a.K; ++k)
+            dec[d][k + a.K] = 1.0 / window_hat(window, 2.0 * kPi * k / a.N, (double)q, a.wpar);
+        std::vector<double2> twd(a.N);
+        std::vector<float2> twf(a.N);
+        for (int m = 0; m < a.N; ++m) {
+            const long double ang = 2.0L * 3.14159265358979323846264338327950288L * m / a.N;
+            twd[m] = make_double2((double)cosl(ang), (double)sinl(ang));
+            twf[m] = make_float2((float)twd[m].x, (float)twd[m].y);
+        }
+        std::vector<int> rev(a.N);
+        for (int k = 0; k < a.N; ++k) {
+            int kk = k, pos = 0, S = a.N;
+            for (int s = 0; s < a.nrad; ++s) {
+                S /= a.rad[s];
+                pos += (kk % a.rad[s]) * S;
+                kk /= a.rad[s];
+            }
+            rev[k] = pos;
+        }
+        if ((e = upload(a.tw_d, twd, p->stream)) != cudaSuccess) return fail(SGL_ERR_CUDA, "upload twiddles");
+        if ((e = upload(a.tw_f, twf, p->stream)) != cudaSuccess) return fail(SGL_ERR_CUDA, "upload twiddles");
+        if ((e = upload(a.rev, rev, p->stream)) != cudaSuccess) return fail(SGL_ERR_CUDA, "upload digit reversal");
+        if ((e = upload(a.deconv, dec[d], p->stream)) != cudaSuccess) return fail(SGL_ERR_CUDA, "upload deconvolution");
+    }
+    std::vector<double> ls((size_t)(W * W));
+    for (int k1 = -K1; k1 <= K1; ++k1)
+        for (int m = -K1; m <= K1; ++m) ls[(size_t)(k1 + K1) * W + (m + K1)] = dec[1][k1 + K1] * dec[2][m + K1];
+    if ((e = upload(b.P, P, p->stream)) != cudaSuccess) return fail(SGL_ERR_CUDA, "upload polar matrices");
+    if ((e = upload(b.costab, costab, p->stream)) != cudaSuccess) return fail(SGL_ERR_CUDA, "upload cosine table");
+    if ((e = upload(b.linescale, ls, p->stream)) != cudaSuccess) return fail(SGL_ERR_CUDA, "upload line scales");
+    if ((e = cudaMemsetAsync(b.dev_flags, 0, sizeof(int), p->stream)) != cudaSuccess) return fail(SGL_ERR_CUDA, "memset");
+    // the host vectors above are released on return: wait for the copies
+    if ((e = cudaStreamSynchronize(p->stream)) != cudaSuccess) return fail(SGL_ERR_CUDA, std::string("plan upload: ") + cudaGetErrorString(e));
+    *out = p;
+    return ok();
+}
+
+void sgl_plan_destroy(sgl_plan *plan) {
+    if (!plan) return;
+    PlanHolder *h = holder_of(plan);
+    cudaStreamSynchronize(plan->stream);
+    delete plan->prof;
+    h->alloc.release();
+    delete h;
+}
+
+sgl_status sgl_set_stream(sgl_plan *plan, void *cuda_stream) {
+    if (sgl_status s = check_plan(plan)) return s;
+    plan->stream = (cudaStream_t)cuda_stream;
+    return ok();
+}
+
+sgl_status sgl_plan_info(const sgl_plan *plan, sgl_plan_info_t *info) {
+    if (sgl_status s = check_plan(plan)) return s;
+    if (!info) return set_error(SGL_ERR_ARG, "info is NULL");
+    info->B = plan->B; info->q = plan->q; info->precision = plan->prec; info->window = plan->window;
+    info->num_coeffs = plan->Nc; info->M_max = plan->M_max; info->M = plan->M;
+    for (int d = 0; d < 3; ++d) {
+        info->n[d] = plan->ax[d].n; info->N[d] = plan->ax[d].N; info->rows[d] = plan->ax[d].rows;
+        info->sigma_eff[d] = plan->ax[d].sigma;
+    }
+    info->workspace_bytes = plan->work_bytes;
+    info->kernel_launches = plan->launches;
+    return ok();
+}
+
+sgl_status sgl_set_points(sgl_plan *plan, const double *xyz_dev, int64_t M) {
+    if (sgl_status s = check_plan(plan)) return s;
+    if (M < 0 || M > plan->M_max) return set_error(SGL_ERR_ARG, "M must be in [0, M_max]");
+    if (M > 0 && (!xyz_dev || !aligned8(xyz_dev))) return set_error(SGL_ERR_ARG, "xyz must be a non-NULL, 8-byte aligned device pointer");
+    cudaError_t e;
+    {
+        StageScope sc(plan, ST_POINTS);
+        e = launch_points(plan, xyz_dev, M);
+    }
+    if (e != cudaSuccess) return launch_status(e, "set_points");
+    {
+        StageScope sc(plan, ST_RADIAL_MATRIX);
+        e = launch_radial_matrices(plan);
+    }
+    if (e != cudaSuccess) return launch_status(e, "radial matrices");
+    plan->M = M;
+    plan->points_set = true;
+    return ok();
+}
+
+sgl_status sgl_get_rho(sgl_plan *plan, double *rho_host) {
+    if (sgl_status s = check_plan(plan)) return s;
+    if (!rho_host) return set_error(SGL_ERR_ARG, "rho_host is NULL");
+    if (!plan->points_set) return set_error(SGL_ERR_STATE, "sgl_set_points has not been called");
+    unsigned long long bits = 0;
+    SGL_CUDA_TRY(cudaMemcpyAsync(&bits, plan->b.r2max, sizeof(bits), cudaMemcpyDeviceToHost, plan->stream));
+    SGL_CUDA_TRY(cudaStreamSynchronize(plan->stream));
+    double r2;
+    std::memcpy(&r2, &bits, sizeof(r2));
+    double rho = std::sqrt(r2) * (1.0 + 0x1p-20);
+    *rho_host = rho > 0.0 ? rho : 1.0;
+    return ok();
+}
+
+static sgl_status coef_to_zeta(sgl_plan *plan, const double *coef_dev) {
+    cudaError_t e;
+    {
+        StageScope sc(plan, ST_RADIAL);
+        e = launch_radial_forward(plan, (const double2 *)coef_dev);
+    }
+    if (e != cudaSuccess) return launch_status(e, "radial conversion");
+    {
+        StageScope sc(plan, ST_POLAR);
+        e = launch_polar_forward(plan);
+    }
+    if (e != cudaSuccess) return launch_status(e, "polar conversion");
+    return ok();
+}
+
+static sgl_status zeta_to_grid(sgl_plan *plan) {
+    StageScope sc(plan, ST_FFT_FWD);
+    return launch_status(launch_fft_forward(plan), "forward FFT");
+}
+
+sgl_status sgl_forward(sgl_plan *plan, const double *coef_dev, double *vals_dev) {
+    if (sgl_status s = check_plan(plan)) return s;
+    if (!plan->points_set) return set_error(SGL_ERR_STATE, "sgl_set_points has not been called");
+    if (!coef_dev || !aligned8(coef_dev)) return set_error(SGL_ERR_ARG, "coef must be a non-NULL, 8-byte aligned device pointer");
+    if (plan->M > 0 && (!vals_dev || !aligned8(vals_dev))) return set_error(SGL_ERR_ARG, "vals must be a non-NULL, 8-byte aligned device pointer");
+    if (plan->M == 0) return ok();
+    if (sgl_status s = coef_to_zeta(plan, coef_dev)) return s;
+    if (sgl_status s = zeta_to_grid(plan)) return s;
+    StageScope sc(plan, ST_INTERP);
+    return launch_status(launch_interp(plan, (double2 *)vals_dev), "interpolation");
+}
+
+sgl_status sgl_adjoint(sgl_plan *plan, const double *vals_dev, double *coef_dev) {
+    if (sgl_status s = check_plan(plan)) return s;
+    if (!plan->points_set) return set_error(SGL_ERR_STATE, "sgl_set_points has not been called");
+    if (!coef_dev || !aligned8(coef_dev)) return set_error(SGL_ERR_ARG, "coef must be a non-NULL, 8-byte aligned device pointer");
+    if (plan->M > 0 && (!vals_dev || !aligned8(vals_dev))) return set_error(SGL_ERR_ARG, "vals must be a non-NULL, 8-byte aligned device pointer");
+    if (plan->M == 0) {
+        SGL_CUDA_TRY(cudaMemsetAsync(coef_dev, 0, sizeof(double2) * plan->Nc, plan->stream));
+        return ok();
+    }
+    const Axis &A0 = plan->ax[0], &A1 = plan->ax[1], &A2 = plan->ax[2];
+    const size_t csz = plan->prec == SGL_FP32_MIXED ? sizeof(float2) : sizeof(double2);
+    cudaError_t e;
+    {
+        StageScope sc(plan, ST_SPREAD);
+        e = cudaMemsetAsync(plan->b.bufA, 0, (size_t)A0.rows * A1.rows * A2.N * csz, plan->stream);
+        if (e == cudaSuccess) e = launch_spread(plan, (const double2 *)vals_dev);
+    }
+    if (e != cudaSuccess) return launch_status(e, "spreading");
+    {
+        StageScope sc(plan, ST_FFT_ADJ);
+        e = launch_fft_adjoint(plan);
+    }
+    if (e != cudaSuccess) return launch_status(e, "adjoint FFT");
+    {
+        StageScope sc(plan, ST_POLAR_ADJ);
+        e = launch_polar_adjoint(plan, (const double2 *)plan->b.bufB);
+    }
+    if (e != cudaSuccess) return launch_status(e, "adjoint polar conversion");
+    StageScope sc(plan, ST_RADIAL_ADJ);
+    return launch_status(launch_radial_adjoint(plan, (double2 *)coef_dev), "adjoint radial conversion");
+}
+
+sgl_status sgl_grad_points(sgl_plan *plan, const double *coef_dev, const double *gout_dev, double *gxyz_dev) {
+    if (sgl_status s = check_plan(plan)) return s;
+    if (!plan->points_set) return set_error(SGL_ERR_STATE, "sgl_set_points has not been called");
+    if (!coef_dev || !aligned8(coef_dev)) return set_error(SGL_ERR_ARG, "coef must be a non-NULL, 8-byte aligned device pointer");
+    if (plan->M > 0 && (!gout_dev || !gxyz_dev || !aligned8(gout_dev) || !aligned8(gxyz_dev)))
+        return set_error(SGL_ERR_ARG, "gout and gxyz must be non-NULL, 8-byte aligned device pointers");
+    if (plan->M == 0) return ok();
+    if (sgl_status s = coef_to_zeta(plan, coef_dev)) return s;
+    if (sgl_status s = zeta_to_grid(plan)) return s;
+    StageScope sc(plan, ST_GRAD);
+    return launch_status(launch_grad(plan, (const double2 *)gout_dev, gxyz_dev), "gradient interpolation");
+}
+
+sgl_status sgl_trig_coeffs(sgl_plan *plan, const double *coef_dev, double *eta_dev) {
+    if (sgl_status s = check_plan(plan)) return s;
+    if (!plan->points_set) return set_error(SGL_ERR_STATE, "sgl_set_points has not been called");
+    if (!coef_dev || !eta_dev || !aligned8(coef_dev) || !aligned8(eta_dev))
+        return set_error(SGL_ERR_ARG, "coef and eta must be non-NULL, 8-byte aligned device pointers");
+    if (sgl_status s = coef_to_zeta(plan, coef_dev)) return s;
+    StageScope sc(plan, ST_TRIG);
+    return launch_status(launch_trig_export(plan, (double2 *)eta_dev), "trig export");
+}
+
+sgl_status sgl_forward_host(sgl_plan *plan, const double *xyz_host, int64_t M, const double *coef_host, double *vals_host) {
+    if (sgl_status s = check_plan(plan)) return s;
+    if (!(plan->flags & SGL_FLAG_HOST_IO)) return set_error(SGL_ERR_STATE, "plan was created without SGL_FLAG_HOST_IO");
+    if (M < 0 || M > plan->M_max) return set_error(SGL_ERR_ARG, "M must be in [0, M_max]");
+    if (!coef_host || (M > 0 && (!xyz_host || !vals_host))) return set_error(SGL_ERR_ARG, "NULL host buffer");
+    cudaStream_t st = plan->stream;
+    if (M > 0) SGL_CUDA_TRY(cudaMemcpyAsync(plan->b.io_xyz, xyz_host, sizeof(double) * 3 * M, cudaMemcpyHostToDevice, st));
+    SGL_CUDA_TRY(cudaMemcpyAsync(plan->b.io_coef, coef_host, sizeof(double2) * plan->Nc, cudaMemcpyHostToDevice, st));
+    if (sgl_status s = sgl_set_points(plan, plan->b.io_xyz, M)) return s;
+    if (sgl_status s = sgl_forward(plan, plan->b.io_coef, plan->b.io_vals)) return s;
+    if (M > 0) SGL_CUDA_TRY(cudaMemcpyAsync(vals_host, plan->b.io_vals, sizeof(double2) * M, cudaMemcpyDeviceToHost, st));
+    return sgl_sync(plan);
+}
+
+sgl_status sgl_adjoint_host(sgl_plan *plan, const double *xyz_host, int64_t M, const double *vals_host, double *coef_host) {
+    if (sgl_status s = check_plan(plan)) return s;
+    if (!(plan->flags & SGL_FLAG_HOST_IO)) return set_error(SGL_ERR_STATE, "plan was created without SGL_FLAG_HOST_IO");
+    if (M < 0 || M > plan->M_max) return set_error(SGL_ERR_ARG, "M must be in [0, M_max]");
+    if (!coef_host || (M > 0 && (!xyz_host || !vals_host))) return set_error(SGL_ERR_ARG, "NULL host buffer");
+    cudaStream_t st = plan->stream;
+    if (M > 0) {
+        SGL_CUDA_TRY(cudaMemcpyAsync(plan->b.io_xyz, xyz_host, sizeof(double) * 3 * M, cudaMemcpyHostToDevice, st));
+        SGL_CUDA_TRY(cudaMemcpyAsync(plan->b.io_vals, vals_host, sizeof(double2) * M, cudaMemcpyHostToDevice, st));
+    }
+    if (sgl_status s = sgl_set_points(plan, plan->b.io_xyz, M)) return s;
+    if (sgl_status s = sgl_adjoint(plan, plan->b.io_vals, plan->b.io_coef)) return s;
+    SGL_CUDA_TRY(cudaMemcpyAsync(coef_host, plan->b.io_coef, sizeof(double2) * plan->Nc, cudaMemcpyDeviceToHost, st));
+    return sgl_sync(plan);
+}
+
+const char *sgl_stage_name(int stage) {
+    if (stage < 0 || stage >= ST_COUNT) return "";
+    return kStageNames[stage];
+}
+
+sgl_status sgl_profile(sgl_plan *plan, double *ms_out, int64_t *count_out) {
+    if (sgl_status s = check_plan(plan)) return s;
+    if (!plan->prof) return set_error(SGL_ERR_STATE, "plan was created without SGL_FLAG_PROFILE");
+    SGL_CUDA_TRY(cudaStreamSynchronize(plan->stream));
+    double ms[ST_COUNT] = {0};
+    int64_t cnt[ST_COUNT] = {0};
+    for (auto &pr : plan->prof->open) {
+        float t = 0.f;
+        if (cudaEventElapsedTime(&t, pr.a, pr.b) == cudaSuccess) { ms[pr.stage] += t; cnt[pr.stage] += 1; }
+        plan->prof->pool.push_back({pr.a, nullptr, 0});
+        plan->prof->pool.push_back({pr.b, nullptr, 0});
+    }
+    plan->prof->open.clear();
+    for (int i = 0; i < ST_COUNT; ++i) {
+        if (ms_out) ms_out[i] = ms[i];
+        if (count_out) count_out[i] = cnt[i];
+    }
+    return ok();
+}
+
+sgl_status sgl_grad_points_host(sgl_plan *plan, const double *xyz_host, int64_t M, const double *coef_host,
+                                const double *gout_host, double *gxyz_host) {
+    if (sgl_status s = check_plan(plan)) return s;
+    if (!(plan->flags & SGL_FLAG_HOST_IO)) return set_error(SGL_ERR_STATE, "plan was created without SGL_FLAG_HOST_IO");
+    if (M < 0 || M > plan->M_max) return set_error(SGL_ERR_ARG, "M must be in [0, M_max]");
+    if (!coef_host || (M > 0 && (!xyz_host || !gout_host || !gxyz_host))) return set_error(SGL_ERR_ARG, "NULL host buffer");
+    cudaStream_t st = plan->stream;
+    if (M > 0) {
+        SGL_CUDA_TRY(cudaMemcpyAsync(plan->b.io_xyz, xyz_host, sizeof(double) * 3 * M, cudaMemcpyHostToDevice, st));
+        SGL_CUDA_TRY(cudaMemcpyAsync(plan->b.io_vals, gout_host, sizeof(double2) * M, cudaMemcpyHostToDevice, st));
+    }
+    SGL_CUDA_TRY(cudaMemcpyAsync(plan->b.io_coef, coef_host, sizeof(double2) * plan->Nc, cudaMemcpyHostToDevice, st));
+    if (sgl_status s = sgl_set_points(plan, plan->b.io_xyz, M)) return s;
+    if (sgl_status s = sgl_grad_points(plan, plan->b.io_coef, plan->b.io_vals, plan->b.io_grad)) return s;
+    if (M > 0) SGL_CUDA_TRY(cudaMemcpyAsync(gxyz_host, plan->b.io_grad, sizeof(double) * 3 * M, cudaMemcpyDeviceToHost, st));
+    return sgl_sync(plan);
+}
+
+sgl_status sgl_sync(sgl_plan *plan) {
+    if (sgl_status s = check_plan(plan)) return s;
+    SGL_CUDA_TRY(cudaStreamSynchronize(plan->stream));
+    int flagsv = 0;
+    SGL_CUDA_TRY(cudaMemcpy(&flagsv, plan->b.dev_flags, sizeof(int), cudaMemcpyDeviceToHost));
+    if (flagsv & 1) {
+        SGL_CUDA_TRY(cudaMemset(plan->b.dev_flags, 0, sizeof(int)));
+        return set_error(SGL_ERR_NONFINITE, "a point coordinate was NaN or infinite (treated as the origin)");
+    }
+    return ok();
+}
+
+}  // extern "C"

@@ -1,0 +1,305 @@
+// sgl_fft.cu -- the oversampled 3-D FFT of the NFFT (Sect. 2: alpha = (sigma n)^{-d} F^H beta),
+// as three batched 1-D passes over tiles of lines staged in shared memory.
+//
+// The transform is pruned on both sides: the input eta is nonzero only on
+// |k0| <= 2B-2, |k1| <= B-1, |k2| <= B-1 (degrees stated in Sect. 6), and the
+// interpolation only reads grid rows within q of the range the points can reach
+// (t0, theta in [0, pi]: rows [-q, N/2+q] on the first two axes).  Each pass
+// places its L_in input elements at positions (e + in_first) mod N of a length-N
+// line (zeros elsewhere), runs an in-place mixed-radix decimation-in-frequency
+// FFT (radices 8, 4, 2, 3, 5; output in digit-reversed slots), and writes the
+// L_out output positions (e + out_first) mod N.  The (sigma n)^{-d} scale and the
+// window deconvolution 1/phitilde_k are folded into per-element and per-line factors.
+#include "sgl_internal.cuh"
+
+#include <type_traits>
+
+namespace sgl {
+namespace {
+
+template <typename T> struct CT;
+template <> struct CT<float> { using type = float2; };
+template <> struct CT<double> { using type = double2; };
+template <typename T> using C2 = typename CT<T>::type;
+
+template <typename T> __device__ __forceinline__ C2<T> mk(T x, T y) { C2<T> r; r.x = x; r.y = y; return r; }
+template <typename T> __device__ __forceinline__ C2<T> add(C2<T> a, C2<T> b) { return mk<T>(a.x + b.x, a.y + b.y); }
+template <typename T> __device__ __forceinline__ C2<T> sub(C2<T> a, C2<T> b) { return mk<T>(a.x - b.x, a.y - b.y); }
+template <typename T> __device__ __forceinline__ C2<T> mul(C2<T> a, C2<T> b) { return mk<T>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
+// multiply by s*i (s = +-1)
+template <typename T> __device__ __forceinline__ C2<T> mul_si(C2<T> a, int s) { return s > 0 ? mk<T>(-a.y, a.x) : mk<T>(a.y, -a.x); }
+
+// in-place r-point DFT  y_u = sum_t x_t e^{s 2 pi i t u / r}
+template <typename T>
+__device__ __forceinline__ void dft2(C2<T> *x) { C2<T> a = x[0], b = x[1]; x[0] = add<T>(a, b); x[1] = sub<T>(a, b); }
+
+template <typename T>
+__device__ __forceinline__ void dft4(C2<T> *x, int s) {
+    C2<T> a = add<T>(x[0], x[2]), b = sub<T>(x[0], x[2]);
+    C2<T> c = add<T>(x[1], x[3]), d = mul_si<T>(sub<T>(x[1], x[3]), s);
+    x[0] = add<T>(a, c); x[2] = sub<T>(a, c); x[1] = add<T>(b, d); x[3] = sub<T>(b, d);
+}
+
+template <typename T>
+__device__ __forceinline__ void dft8(C2<T> *x, int s) {
+    C2<T> e[4] = {x[0], x[2], x[4], x[6]}, o[4] = {x[1], x[3], x[5], x[7]};
+    dft4<T>(e, s);
+    dft4<T>(o, s);
+    const T h = (T)0.70710678118654752440;
+    // W8^u = e^{s 2 pi i u / 8}
+    C2<T> w1 = mk<T>(h, s * h), w3 = mk<T>(-h, s * h);
+    C2<T> t0 = o[0], t1 = mul<T>(o[1], w1), t2 = mul_si<T>(o[2], s), t3 = mul<T>(o[3], w3);
+    x[0] = add<T>(e[0], t0); x[4] = sub<T>(e[0], t0);
+    x[1] = add<T>(e[1], t1); x[5] = sub<T>(e[1], t1);
+    x[2] = add<T>(e[2], t2); x[6] = sub<T>(e[2], t2);
+    x[3] = add<T>(e[3], t3); x[7] = sub<T>(e[3], t3);
+}
+
+template <typename T>
+__device__ __forceinline__ void dft3(C2<T> *x, int s) {
+    const T c = (T)-0.5, d = (T)0.86602540378443864676 * s;   // W3 = c + i d
+    C2<T> a = add<T>(x[1], x[2]), b = sub<T>(x[1], x[2]);
+    C2<T> y0 = add<T>(x[0], a);
+    C2<T> m = mk<T>(x[0].x + c * a.x, x[0].y + c * a.y);
+    C2<T> n = mk<T>(-d * b.y, d * b.x);                        // i d (x1 - x2)
+    x[0] = y0; x[1] = add<T>(m, n); x[2] = sub<T>(m, n);
+}
+
+template <typename T>
+__device__ __forceinline__ void dft5(C2<T> *x, int s) {
+    const T c1 = (T)0.30901699437494742410, c2 = (T)-0.80901699437494742410;
+    const T s1 = (T)0.95105651629515357212 * s, s2 = (T)0.58778525229247312917 * s;
+    C2<T> a1 = add<T>(x[1], x[4]), b1 = sub<T>(x[1], x[4]);
+    C2<T> a2 = add<T>(x[2], x[3]), b2 = sub<T>(x[2], x[3]);
+    C2<T> y0 = add<T>(x[0], add<T>(a1, a2));
+    C2<T> m1 = mk<T>(x[0].x + c1 * a1.x + c2 * a2.x, x[0].y + c1 * a1.y + c2 * a2.y);
+    C2<T> m2 = mk<T>(x[0].x + c2 * a1.x + c1 * a2.x, x[0].y + c2 * a1.y + c1 * a2.y);
+    // i (s1 b1 + s2 b2) and i (s2 b1 - s1 b2)
+    C2<T> n1 = mk<T>(-(s1 * b1.y + s2 * b2.y), s1 * b1.x + s2 * b2.x);
+    C2<T> n2 = mk<T>(-(s2 * b1.y - s1 * b2.y), s2 * b1.x - s1 * b2.x);
+    x[0] = y0; x[1] = add<T>(m1, n1); x[4] = sub<T>(m1, n1); x[2] = add<T>(m2, n2); x[3] = sub<T>(m2, n2);
+}
+
+enum { LOAD_STRIDED = 0, LOAD_ZETA = 1 };
+
+struct ZetaSrc {
+    const double2 *zeta;   // [K0+1][K1+1][2K1+1]
+    int K0, K1;
+};
+
+template <typename C> __device__ __forceinline__ double2 to_d2(C v) { return make_double2((double)v.x, (double)v.y); }
+
+template <typename T, typename InC, typename OutC, int MODE>
+__global__ void __launch_bounds__(256) k_fft_pass(FftPass ps, int TB, const InC *__restrict__ in, OutC *__restrict__ out,
+                                                  ZetaSrc zs, int scale_on_output) {
+    extern __shared__ unsigned char smem_raw[];
+    C2<T> *buf = reinterpret_cast<C2<T> *>(smem_raw);
+    const int N = ps.N;
+    const int LS = N + 1;                          // padded line stride in shared memory
+    const int64_t tiles_inner = (ps.nb_inner + TB - 1) / TB;
+    const int64_t outer = blockIdx.x / tiles_inner;
+    const int64_t inner0 = (blockIdx.x % tiles_inner) * TB;
+    const int nlines = (int)min((int64_t)TB, ps.nb_inner - inner0);
+    const int tid = threadIdx.x, NT = blockDim.x;
+
+    // ---- load (zero outside the input window), optional scale on input
+    const bool in_elem_fast = (MODE == LOAD_STRIDED) && (ps.in_se == 1);
+    for (int idx = tid; idx < TB * N; idx += NT) {
+        int bl, pos;
+        if (in_elem_fast) { bl = idx / N; pos = idx % N; } else { bl = idx % TB; pos = idx / TB; }
+        int e = pos - ps.in_first;
+        e %= N;
+        if (e < 0) e += N;
+        C2<T> v = mk<T>((T)0, (T)0);
+        if (bl < nlines && e < ps.L_in) {
+            const int64_t inner = inner0 + bl;
+            double2 d;
+            if (MODE == LOAD_ZETA) {
+                // line = (k1, m) over (2K1+1)^2, element = k0 + K0; eta mirrored from zeta
+                const int W = 2 * zs.K1 + 1;
+                const int mi = (int)(inner % W);
+                const int k1 = (int)(inner / W) - zs.K1;
+                const int k0 = e - zs.K0;
+                d = zs.zeta[((int64_t)abs(k0) * (zs.K1 + 1) + abs(k1)) * W + mi];
+                if (k1 < 0 && ((mi - zs.K1) & 1)) { d.x = -d.x; d.y = -d.y; }
+            } else {
+                d = to_d2(in[outer * ps.in_so + inner * ps.in_si + (int64_t)e * ps.in_se]);
+            }
+            if (!scale_on_output) {
+                double f = 1.0;
+                if (ps.elem_scale) f *= ps.elem_scale[e];
+                if (ps.line_scale) f *= ps.line_scale[outer * ps.nb_inner + inner];
+                d.x *= f; d.y *= f;
+            }
+            v = mk<T>((T)d.x, (T)d.y);
+        }
+        buf[bl * LS + pos] = v;
+    }
+    __syncthreads();
+
+    // ---- in-place decimation-in-frequency passes
+    const C2<T> *tw = reinterpret_cast<const C2<T> *>(ps.tw);
+    int L = N;
+    for (int st = 0; st < ps.nrad; ++st) {
+        const int r = ps.rad[st];
+        const int S = L / r;
+        const int per_line = N / r;
+        const int stride_tw = N / L;
+        for (int w = tid; w < TB * per_line; w += NT) {
+            const int bl = w / per_line, j = w % per_line;
+            const int g = j / S, nn = j % S;
+            C2<T> *base = buf + bl * LS + g * L + nn;
+            C2<T> x[8];
+            for (int t = 0; t < r; ++t) x[t] = base[t * S];
+            switch (r) {
+                case 2: dft2<T>(x); break;
+                case 3: dft3<T>(x, ps.sign); break;
+                case 4: dft4<T>(x, ps.sign); break;
+                case 5: dft5<T>(x, ps.sign); break;
+                default: dft8<T>(x, ps.sign); break;
+            }
+            base[0] = x[0];
+            for (int u = 1; u < r; ++u) {
+                C2<T> wv = tw[(int)(((int64_t)nn * u * stride_tw) % N)];
+                if (ps.sign < 0) wv.y = -wv.y;
+                base[u * S] = mul<T>(x[u], wv);
+            }
+        }
+        __syncthreads();
+        L = S;
+    }
+
+    // ---- store the output window (digit-reversed slots), optional scale on output
+    const bool out_elem_fast = (ps.out_se == 1);
+    for (int idx = tid; idx < TB * ps.L_out; idx += NT) {
+        int bl, e;
+        if (out_elem_fast) { bl = idx / ps.L_out; e = idx % ps.L_out; } else { bl = idx % TB; e = idx / TB; }
+        if (bl >= nlines) continue;
+        const int64_t inner = inner0 + bl;
+        int pos = (e + ps.out_first) % N;
+        if (pos < 0) pos += N;
+        const C2<T> v = buf[bl * LS + ps.rev[pos]];
+        double vx = (double)v.x, vy = (double)v.y;
+        if (scale_on_output) {
+            double f = 1.0;
+            if (ps.elem_scale) f *= ps.elem_scale[e];
+            if (ps.line_scale) f *= ps.line_scale[outer * ps.nb_inner + inner];
+            vx *= f; vy *= f;
+        }
+        OutC o;
+        o.x = (decltype(o.x))vx;
+        o.y = (decltype(o.y))vy;
+        out[outer * ps.out_so + inner * ps.out_si + (int64_t)e * ps.out_se] = o;
+    }
+}
+
+int lines_per_tile(int N) {
+    int tb = 4096 / N;
+    if (tb < 8) tb = 8;
+    if (tb > 64) tb = 64;
+    return tb;
+}
+
+template <typename T, typename InC, typename OutC, int MODE>
+cudaError_t run_pass(sgl_plan *p, FftPass ps, const void *in, void *out, ZetaSrc zs, int scale_on_output) {
+    const int TB = lines_per_tile(ps.N);
+    const size_t smem = (size_t)TB * (ps.N + 1) * sizeof(C2<T>);
+    auto kern = k_fft_pass<T, InC, OutC, MODE>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int64_t tiles = ps.nb_outer * ((ps.nb_inner + TB - 1) / TB);
+    if (tiles <= 0) return cudaSuccess;
+    kern<<<(unsigned)tiles, 256, smem, p->stream>>>(ps, TB, (const InC *)in, (OutC *)out, zs, scale_on_output);
+    p->launches += 1;
+    return cudaGetLastError();
+}
+
+FftPass base_pass(const Axis &a, int sign, bool fp32) {
+    FftPass ps{};
+    ps.N = a.N;
+    ps.nrad = a.nrad;
+    for (int i = 0; i < a.nrad; ++i) ps.rad[i] = a.rad[i];
+    ps.sign = sign;
+    ps.tw = fp32 ? (const void *)a.tw_f : (const void *)a.tw_d;
+    ps.rev = a.rev;
+    return ps;
+}
+
+template <typename T>
+cudaError_t forward_passes(sgl_plan *p) {
+    const Axis &A0 = p->ax[0], &A1 = p->ax[1], &A2 = p->ax[2];
+    const bool f32 = std::is_same<T, float>::value;
+    const int64_t W = 2 * p->K1 + 1;
+    ZetaSrc zs{p->b.zeta, p->K0, p->K1};
+    cudaError_t e;
+    // pass A (axis 0): zeta (mirrored, deconvolved) -> X0[l0 row][k1][m]
+    FftPass a = base_pass(A0, +1, f32);
+    a.L_in = 2 * p->K0 + 1; a.in_first = -p->K0;
+    a.L_out = A0.rows; a.out_first = A0.first;
+    a.nb_outer = 1; a.nb_inner = W * W;
+    a.out_so = 0; a.out_si = 1; a.out_se = W * W;
+    a.elem_scale = A0.deconv; a.line_scale = p->b.linescale;
+    if ((e = run_pass<T, double2, C2<T>, LOAD_ZETA>(p, a, nullptr, p->b.bufA, zs, 0)) != cudaSuccess) return e;
+    // pass B (axis 1): X0 -> X1[l0][l1 row][m]
+    FftPass b = base_pass(A1, +1, f32);
+    b.L_in = (int)W; b.in_first = -p->K1;
+    b.L_out = A1.rows; b.out_first = A1.first;
+    b.nb_outer = A0.rows; b.nb_inner = W;
+    b.in_so = W * W; b.in_si = 1; b.in_se = W;
+    b.out_so = (int64_t)A1.rows * W; b.out_si = 1; b.out_se = W;
+    if ((e = run_pass<T, C2<T>, C2<T>, LOAD_STRIDED>(p, b, p->b.bufA, p->b.bufB, zs, 0)) != cudaSuccess) return e;
+    // pass C (axis 2): X1 -> grid[l0][l1][l2], full lines
+    FftPass c = base_pass(A2, +1, f32);
+    c.L_in = (int)W; c.in_first = -p->K1;
+    c.L_out = A2.N; c.out_first = 0;
+    c.nb_outer = 1; c.nb_inner = (int64_t)A0.rows * A1.rows;
+    c.in_so = 0; c.in_si = W; c.in_se = 1;
+    c.out_so = 0; c.out_si = A2.N; c.out_se = 1;
+    return run_pass<T, C2<T>, C2<T>, LOAD_STRIDED>(p, c, p->b.bufB, p->b.bufA, zs, 0);
+}
+
+template <typename T>
+cudaError_t adjoint_passes(sgl_plan *p) {
+    const Axis &A0 = p->ax[0], &A1 = p->ax[1], &A2 = p->ax[2];
+    const bool f32 = std::is_same<T, float>::value;
+    const int64_t W = 2 * p->K1 + 1;
+    ZetaSrc zs{p->b.zeta, p->K0, p->K1};
+    cudaError_t e;
+    // pass C' (axis 2): grid -> Y1[l0][l1][m]
+    FftPass c = base_pass(A2, -1, f32);
+    c.L_in = A2.N; c.in_first = 0;
+    c.L_out = (int)W; c.out_first = -p->K1;
+    c.nb_outer = 1; c.nb_inner = (int64_t)A0.rows * A1.rows;
+    c.in_so = 0; c.in_si = A2.N; c.in_se = 1;
+    c.out_so = 0; c.out_si = W; c.out_se = 1;
+    if ((e = run_pass<T, C2<T>, C2<T>, LOAD_STRIDED>(p, c, p->b.bufA, p->b.bufB, zs, 1)) != cudaSuccess) return e;
+    // pass B' (axis 1): Y1 -> Y0[l0][k1][m]
+    FftPass b = base_pass(A1, -1, f32);
+    b.L_in = A1.rows; b.in_first = A1.first;
+    b.L_out = (int)W; b.out_first = -p->K1;
+    b.nb_outer = A0.rows; b.nb_inner = W;
+    b.in_so = (int64_t)A1.rows * W; b.in_si = 1; b.in_se = W;
+    b.out_so = W * W; b.out_si = 1; b.out_se = W;
+    if ((e = run_pass<T, C2<T>, C2<T>, LOAD_STRIDED>(p, b, p->b.bufB, p->b.bufA, zs, 1)) != cudaSuccess) return e;
+    // pass A' (axis 0): Y0 -> eta'[k0][k1][m] (FP64), deconvolved
+    FftPass a = base_pass(A0, -1, f32);
+    a.L_in = A0.rows; a.in_first = A0.first;
+    a.L_out = 2 * p->K0 + 1; a.out_first = -p->K0;
+    a.nb_outer = 1; a.nb_inner = W * W;
+    a.in_so = 0; a.in_si = 1; a.in_se = W * W;
+    a.out_so = 0; a.out_si = 1; a.out_se = W * W;
+    a.elem_scale = A0.deconv; a.line_scale = p->b.linescale;
+    return run_pass<T, C2<T>, double2, LOAD_STRIDED>(p, a, p->b.bufA, p->b.bufB, zs, 1);
+}
+
+}  // namespace
+
+cudaError_t launch_fft_forward(sgl_plan *p) {
+    return p->prec == SGL_FP32_MIXED ? forward_passes<float>(p) : forward_passes<double>(p);
+}
+
+cudaError_t launch_fft_adjoint(sgl_plan *p) {
+    return p->prec == SGL_FP32_MIXED ? adjoint_passes<float>(p) : adjoint_passes<double>(p);
+}
+
+}  // namespace sgl

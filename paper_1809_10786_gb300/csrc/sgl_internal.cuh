@@ -1,0 +1,132 @@
+// sgl_internal.cuh -- plan layout and kernel entry points shared by the CUDA
+// translation units of libsgl.so.  Not part of the public C-ABI (include/sgl.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string>
+
+#include "../../include/sgl.h"
+
+namespace sgl {
+
+constexpr double kPi = 3.14159265358979323846;
+constexpr int kMaxQ = 16;          // 2q taps per axis must fit one warp
+constexpr int kMaxRadices = 16;
+constexpr int kBinS2 = 16;         // bin extent along the azimuthal axis (cells)
+
+// Sets the thread-local message returned by sgl_last_error() and returns code.
+sgl_status set_error(sgl_status code, const std::string &msg);
+
+// One axis of the oversampled grid and its pruned 1-D FFT.
+struct Axis {
+    int n;          // conversion grid size (4B or 2B)
+    int N;          // oversampled FFT length (2-3-5-smooth, even)
+    int K;          // support half-width of eta on this axis (2B-2 or B-1)
+    int rows;       // rows kept after the pruned inverse FFT (N if periodic)
+    int first;      // first kept grid index (-q if windowed, 0 if periodic)
+    bool windowed;  // rows = N/2 + 2q + 1 < N: only [-q, N/2+q] is stored
+    double sigma;   // N / n
+    double wpar;    // Kaiser-Bessel shape b, or Gaussian lambda
+    int nrad;
+    int rad[kMaxRadices];
+    // device tables
+    double2 *tw_d;  // exp(2 pi i m / N), m < N
+    float2 *tw_f;
+    int *rev;       // digit-reversed slot of output index p after the DIF passes
+    double *deconv; // 1 / Psihat(2 pi k / N), k = -K..K (index k + K)
+};
+
+// Description of one batched, pruned 1-D DFT pass (see sgl_fft.cu).
+struct FftPass {
+    int N, nrad, rad[kMaxRadices];
+    int sign;                       // +1: e^{+2 pi i kl/N}; -1: e^{-2 pi i kl/N}
+    int L_in, in_first;             // input element e sits at position (e + in_first) mod N
+    int L_out, out_first;           // output element e is position (e + out_first) mod N
+    int64_t nb_outer, nb_inner;     // lines = outer x inner; inner lines are adjacent in memory
+    int64_t in_so, in_si, in_se;    // input strides in complex elements
+    int64_t out_so, out_si, out_se; // output strides in complex elements
+    const double *elem_scale;       // optional factor per element index (input or output side, per launch)
+    const double *line_scale;       // optional factor per flattened line index outer*nb_inner+inner
+    const void *tw;                 // twiddle table (double2 or float2)
+    const int *rev;
+};
+
+struct Buffers {
+    // conversions (FP64)
+    double *P;        // polar matrices [B][K1+1][B]  (m >= 0; P_{-m} = (-1)^m P_m)
+    double *costab;   // cos(m pi / 4B), m < 8B
+    double *radv;     // radial values [sum_l 2B (B-l)]
+    double *Kmat;     // radial conversion matrices [sum_l (K0+1)(B-l)]
+    double2 *beta;    // [2B-1][K0+1][B]     beta_{kappa0, l, m}, kappa0 >= 0
+    double2 *zeta;    // [K0+1][K1+1][2B-1]  zeta_{kappa0, kappa1, m}, kappa0, kappa1 >= 0
+    double *linescale;// [(2K1+1)^2] d1[k1] d2[m]
+    // FFT work buffers (complex, precision of the plan)
+    void *bufA, *bufB;
+    size_t bufA_bytes, bufB_bytes;
+    // points
+    unsigned long long *r2max; // bit pattern of max |x|^2 (non-negative doubles order like integers)
+    int *dev_flags;            // bit 0: non-finite coordinate seen
+    double *u_tmp;             // [M][3] grid coordinates, input order
+    double *u_sorted;          // [M][3] grid coordinates, bin order
+    int *perm;                 // sorted position -> input index
+    int *bin_of, *rank_of;     // per input point
+    int *bin_count, *bin_off;  // [nbins]
+    int *scan_tmp;             // block sums
+    // host-IO staging
+    double *io_xyz, *io_coef, *io_vals, *io_grad;
+};
+
+}  // namespace sgl
+
+namespace sgl {
+enum Stage {
+    ST_POINTS = 0, ST_RADIAL_MATRIX, ST_RADIAL, ST_POLAR, ST_FFT_FWD, ST_INTERP,
+    ST_SPREAD, ST_FFT_ADJ, ST_POLAR_ADJ, ST_RADIAL_ADJ, ST_GRAD, ST_TRIG, ST_COUNT
+};
+static_assert(ST_COUNT == SGL_NUM_STAGES, "stage list and SGL_NUM_STAGES disagree");
+struct Profiler;   // CUDA-event bookkeeping (sgl_capi.cu)
+}  // namespace sgl
+
+struct sgl_plan {
+    int device;
+    int64_t launches;       // kernels launched (host-side count)
+    sgl::Profiler *prof;    // non-NULL with SGL_FLAG_PROFILE
+    cudaStream_t stream;
+    int B, q, prec, window;
+    unsigned flags;
+    double sigma;
+    int64_t M_max, M, Nc;
+    int K0, K1;
+    sgl::Axis ax[3];
+    int nbin[3];
+    int64_t nbins;
+    int64_t work_bytes;
+    bool points_set;
+    sgl::Buffers b;
+};
+
+namespace sgl {
+
+// ---- launchers (all asynchronous on plan->stream); return cudaGetLastError() ----
+cudaError_t launch_points(sgl_plan *p, const double *xyz, int64_t M);
+cudaError_t launch_radial_matrices(sgl_plan *p);
+cudaError_t launch_radial_forward(sgl_plan *p, const double2 *coef);
+cudaError_t launch_polar_forward(sgl_plan *p);
+cudaError_t launch_trig_export(sgl_plan *p, double2 *eta);
+cudaError_t launch_polar_adjoint(sgl_plan *p, const double2 *eta_full);
+cudaError_t launch_radial_adjoint(sgl_plan *p, double2 *coef);
+cudaError_t launch_fft_forward(sgl_plan *p);    // zeta -> grid (bufA)
+cudaError_t launch_fft_adjoint(sgl_plan *p);    // grid (bufA) -> eta' full support (bufB, FP64)
+cudaError_t launch_interp(sgl_plan *p, double2 *vals);
+cudaError_t launch_spread(sgl_plan *p, const double2 *vals);
+cudaError_t launch_grad(sgl_plan *p, const double2 *gout, double *gxyz);
+
+}  // namespace sgl
+
+#define SGL_CUDA_TRY(expr)                                                              \
+    do {                                                                                \
+        cudaError_t _e = (expr);                                                        \
+        if (_e != cudaSuccess)                                                          \
+            return sgl::set_error(SGL_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(_e)); \
+    } while (0)

@@ -1,0 +1,197 @@
+// sgl_points.cu -- point preprocessing for the NFSGLFT (Sect. 6 and 7 of the paper):
+//   rho = max_i |x_i| (Sect. 7, choice of rho), the transformed points
+//   xtilde_i = [arccos gamma(r_i), theta_i, phi_i] with gamma(r) = (2r - rho)/rho
+//   (Sect. 6, eq. of the transformed points), their oversampled-grid coordinates
+//   u_d = N_d xtilde_d / (2 pi), and a counting sort of the points by spatial bin.
+#include "sgl_internal.cuh"
+
+namespace sgl {
+namespace {
+
+constexpr int kThreads = 256;
+
+__global__ void k_max_radius(const double *__restrict__ xyz, int64_t M,
+                             unsigned long long *__restrict__ r2max, int *__restrict__ flags) {
+    double best = 0.0;
+    bool bad = false;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < M; i += (int64_t)gridDim.x * blockDim.x) {
+        const double x = xyz[3 * i], y = xyz[3 * i + 1], z = xyz[3 * i + 2];
+        if (!(isfinite(x) && isfinite(y) && isfinite(z))) { bad = true; continue; }
+        best = fmax(best, x * x + y * y + z * z);
+    }
+    for (int o = 16; o > 0; o >>= 1) best = fmax(best, __shfl_xor_sync(0xffffffffu, best, o));
+    __shared__ double wmax[kThreads / 32];
+    if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = best;
+    if (bad) atomicOr(flags, 1);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double m = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmax(m, wmax[w]);
+        // non-negative doubles order like their bit patterns
+        atomicMax(r2max, (unsigned long long)__double_as_longlong(m));
+    }
+}
+
+struct PointGeom {
+    int N[3];
+    int nbin1, nbin2;   // bins along axes 1 and 2
+    int cmax0, cmax1;   // largest cell index on axes 0 and 1 (N/2)
+};
+
+__device__ __forceinline__ double rho_of(const unsigned long long *r2max) {
+    double rho = sqrt(__longlong_as_double((long long)*r2max)) * (1.0 + 0x1p-20);
+    return rho > 0.0 ? rho : 1.0;
+}
+
+// grid coordinates u_d = N_d t_d / (2 pi) of one point
+__device__ __forceinline__ void grid_coords(double x, double y, double z, double rho, const PointGeom &g,
+                                            double &u0, double &u1, double &u2) {
+    const double rxy = hypot(x, y);
+    const double r = hypot(rxy, z);
+    double gam = (2.0 * r - rho) / rho;
+    gam = fmin(1.0, fmax(-1.0, gam));
+    const double t0 = acos(gam);
+    const double t1 = atan2(rxy, z);           // [0, pi]
+    double t2 = atan2(y, x);                   // (-pi, pi]
+    if (t2 < 0.0) t2 += 2.0 * kPi;
+    const double inv2pi = 1.0 / (2.0 * kPi);
+    u0 = g.N[0] * t0 * inv2pi;
+    u1 = g.N[1] * t1 * inv2pi;
+    u2 = g.N[2] * t2 * inv2pi;
+    if (u2 >= g.N[2]) u2 -= g.N[2];
+    if (u2 < 0.0) u2 = 0.0;
+}
+
+__device__ __forceinline__ int bin_of_coords(double u0, double u1, double u2, const PointGeom &g) {
+    int c0 = min(max((int)floor(u0), 0), g.cmax0);
+    int c1 = min(max((int)floor(u1), 0), g.cmax1);
+    int c2 = min(max((int)floor(u2), 0), g.N[2] - 1);
+    return (c0 * g.nbin1 + c1) * g.nbin2 + c2 / kBinS2;
+}
+
+__global__ void k_transform_points(const double *__restrict__ xyz, int64_t M, const unsigned long long *__restrict__ r2max,
+                                   PointGeom g, double *__restrict__ u_tmp, int *__restrict__ bin_of,
+                                   int *__restrict__ rank_of, int *__restrict__ bin_count) {
+    const double rho = rho_of(r2max);
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < M; i += (int64_t)gridDim.x * blockDim.x) {
+        double x = xyz[3 * i], y = xyz[3 * i + 1], z = xyz[3 * i + 2];
+        if (!(isfinite(x) && isfinite(y) && isfinite(z))) { x = 0.0; y = 0.0; z = 0.0; }
+        double u0, u1, u2;
+        grid_coords(x, y, z, rho, g, u0, u1, u2);
+        u_tmp[3 * i] = u0; u_tmp[3 * i + 1] = u1; u_tmp[3 * i + 2] = u2;
+        const int b = bin_of_coords(u0, u1, u2, g);
+        bin_of[i] = b;
+        rank_of[i] = atomicAdd(&bin_count[b], 1);
+    }
+}
+
+// exclusive scan, three phases: per-block totals, scan of totals, final offsets
+constexpr int kScanItems = 8;
+constexpr int kScanBlock = kThreads * kScanItems;
+
+__global__ void k_scan_block_totals(const int *__restrict__ cnt, int64_t n, int *__restrict__ totals) {
+    __shared__ int ws[kThreads / 32];
+    const int64_t base = (int64_t)blockIdx.x * kScanBlock;
+    int s = 0;
+    for (int k = 0; k < kScanItems; ++k) {
+        int64_t i = base + (int64_t)k * kThreads + threadIdx.x;
+        if (i < n) s += cnt[i];
+    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int t = 0;
+        for (int w = 0; w < kThreads / 32; ++w) t += ws[w];
+        totals[blockIdx.x] = t;
+    }
+}
+
+// single block: exclusive scan of nblk totals in place (nblk small)
+__global__ void k_scan_totals(int *__restrict__ totals, int nblk) {
+    __shared__ int buf[kThreads];
+    int carry = 0;
+    for (int start = 0; start < nblk; start += kThreads) {
+        int i = start + threadIdx.x;
+        int v = (i < nblk) ? totals[i] : 0;
+        buf[threadIdx.x] = v;
+        __syncthreads();
+        for (int o = 1; o < kThreads; o <<= 1) {
+            int t = (threadIdx.x >= o) ? buf[threadIdx.x - o] : 0;
+            __syncthreads();
+            buf[threadIdx.x] += t;
+            __syncthreads();
+        }
+        if (i < nblk) totals[i] = carry + buf[threadIdx.x] - v;
+        __syncthreads();
+        carry += buf[kThreads - 1];
+        __syncthreads();
+    }
+}
+
+__global__ void k_scan_final(const int *__restrict__ cnt, int64_t n, const int *__restrict__ totals, int *__restrict__ off) {
+    __shared__ int buf[kScanBlock];
+    const int64_t base = (int64_t)blockIdx.x * kScanBlock;
+    for (int k = 0; k < kScanItems; ++k) {
+        int j = k * kThreads + threadIdx.x;
+        buf[j] = (base + j < n) ? cnt[base + j] : 0;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {      // serial scan inside the block keeps this simple; n/kScanBlock blocks run in parallel
+        int acc = totals[blockIdx.x];
+        for (int j = 0; j < kScanBlock; ++j) { int v = buf[j]; buf[j] = acc; acc += v; }
+    }
+    __syncthreads();
+    for (int k = 0; k < kScanItems; ++k) {
+        int j = k * kThreads + threadIdx.x;
+        if (base + j < n) off[base + j] = buf[j];
+    }
+}
+
+__global__ void k_scatter_points(int64_t M, const double *__restrict__ u_tmp, const int *__restrict__ bin_of,
+                                 const int *__restrict__ rank_of, const int *__restrict__ off,
+                                 double *__restrict__ u_sorted, int *__restrict__ perm) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < M; i += (int64_t)gridDim.x * blockDim.x) {
+        const int pos = off[bin_of[i]] + rank_of[i];
+        u_sorted[3 * pos] = u_tmp[3 * i];
+        u_sorted[3 * pos + 1] = u_tmp[3 * i + 1];
+        u_sorted[3 * pos + 2] = u_tmp[3 * i + 2];
+        perm[pos] = (int)i;
+    }
+}
+
+int grid_blocks(int64_t work, int threads) {
+    int64_t b = (work + threads - 1) / threads;
+    if (b < 1) b = 1;
+    if (b > 152 * 32) b = 152 * 32;
+    return (int)b;
+}
+
+}  // namespace
+
+cudaError_t launch_points(sgl_plan *p, const double *xyz, int64_t M) {
+    Buffers &b = p->b;
+    cudaStream_t s = p->stream;
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(b.r2max, 0, sizeof(unsigned long long), s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(b.bin_count, 0, sizeof(int) * p->nbins, s)) != cudaSuccess) return e;
+    if (M > 0) { k_max_radius<<<grid_blocks(M, kThreads), kThreads, 0, s>>>(xyz, M, b.r2max, b.dev_flags); p->launches += 1; }
+    PointGeom g;
+    for (int d = 0; d < 3; ++d) g.N[d] = p->ax[d].N;
+    g.nbin1 = p->nbin[1];
+    g.nbin2 = p->nbin[2];
+    g.cmax0 = p->ax[0].N / 2;
+    g.cmax1 = p->ax[1].N / 2;
+    if (M > 0) {
+        k_transform_points<<<grid_blocks(M, kThreads), kThreads, 0, s>>>(xyz, M, b.r2max, g, b.u_tmp, b.bin_of, b.rank_of, b.bin_count);
+        const int nblk = (int)((p->nbins + kScanBlock - 1) / kScanBlock);
+        k_scan_block_totals<<<nblk, kThreads, 0, s>>>(b.bin_count, p->nbins, b.scan_tmp);
+        k_scan_totals<<<1, kThreads, 0, s>>>(b.scan_tmp, nblk);
+        k_scan_final<<<nblk, kThreads, 0, s>>>(b.bin_count, p->nbins, b.scan_tmp, b.bin_off);
+        k_scatter_points<<<grid_blocks(M, kThreads), kThreads, 0, s>>>(M, b.u_tmp, b.bin_of, b.rank_of, b.bin_off, b.u_sorted, b.perm);
+        p->launches += 5;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace sgl
