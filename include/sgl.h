@@ -191,6 +191,31 @@ sgl_status sgl_grad_points_host(sgl_plan *plan, const double *xyz_host, int64_t 
 sgl_status sgl_profile(sgl_plan *plan, double *ms_out, int64_t *count_out);
 const char *sgl_stage_name(int stage);
 
+/*
+ * Allocation-free trigonometric coefficients (the paper has no counterpart: this is an
+ * interface for callers that cannot allocate device memory).  Some applications own all
+ * of their device memory through their own pool allocator, or run under a fixed memory
+ * budget; for them a library call to cudaMalloc/cudaFree may fail or synchronize the
+ * device at a bad moment, and sgl_plan_create allocates.  This entry point computes the
+ * same eta as sgl_trig_coeffs for the points xyz_dev (rho = max |x_i| with the same
+ * 2^-20 margin) without allocating: no cudaMalloc, no cudaFree, no allocating library
+ * routine.  Its scratch is one static device array sized for B <= SGL_NOALLOC_MAX_B
+ * (about 4.9 MB), which every GPU that loads the library holds until process exit.
+ *   B: 1 <= B <= SGL_NOALLOC_MAX_B, otherwise SGL_ERR_ARG with a message naming the limit.
+ *   xyz_dev [M][3] double (device, M >= 0); coef_dev complex128 [Nc] (device);
+ *   eta_dev complex128 [4B-3][2B-1][2B-1] (device), layout as in sgl_trig_coeffs.
+ *   cuda_stream: the stream the work is issued on (asynchronous, like the plan calls).
+ * Set-up: the first call on a device looks up the scratch array's device address on the
+ * current device (once per device); make that first call before capturing a stream.
+ * All calls share the one scratch array, which keeps the last call's contents (the
+ * reduction cell is cleared by each call): calls that overlap on the GPU -- on different
+ * streams, or from different host threads -- race on it and must be serialized by the caller.
+ * Non-finite coordinates are left out of rho and not reported.
+ */
+#define SGL_NOALLOC_MAX_B 32
+sgl_status sgl_trig_coeffs_noalloc(int B, const double *xyz_dev, int64_t M, const double *coef_dev,
+                                   double *eta_dev, void *cuda_stream);
+
 /* Synchronize the plan's stream and report deferred device errors (non-finite points). */
 sgl_status sgl_sync(sgl_plan *plan);
 

@@ -70,7 +70,8 @@ def load_library(build_if_missing=True):
                            ("sgl_grad_points", [vp, vp, vp, vp]), ("sgl_trig_coeffs", [vp, vp, vp]),
                            ("sgl_forward_host", [vp, vp, i64, vp, vp]), ("sgl_adjoint_host", [vp, vp, i64, vp, vp]),
                            ("sgl_grad_points_host", [vp, vp, i64, vp, vp, vp]),
-                           ("sgl_profile", [vp, dp, ctypes.POINTER(i64)]), ("sgl_sync", [vp])]:
+                           ("sgl_profile", [vp, dp, ctypes.POINTER(i64)]), ("sgl_sync", [vp]),
+                           ("sgl_trig_coeffs_noalloc", [ctypes.c_int, vp, i64, vp, vp, vp])]:
             f = getattr(lib, name)
             f.restype = ctypes.c_int
             f.argtypes = args
@@ -224,6 +225,27 @@ class Plan:
 
     def sync(self):
         _check(self.lib.sgl_sync(self._h))
+
+
+NOALLOC_MAX_B = 32
+
+
+def trig_coeffs_noalloc(B, xyz, coef, out=None):
+    """eta for points xyz and coefficients coef without any device allocation by the library
+    (sgl_trig_coeffs_noalloc; B <= 32).  Tensors on the current CUDA device; the output
+    tensor may be passed in so that no allocation happens on this side either."""
+    lib = load_library()
+    dev = xyz.device
+    xyz = _dev_tensor(xyz, torch.float64, (xyz.shape[0], 3), "xyz", dev)
+    coef = _dev_tensor(coef, torch.complex128, (num_coeffs(B),), "coef", dev)
+    if out is None:
+        out = torch.empty((4 * B - 3, 2 * B - 1, 2 * B - 1), dtype=torch.complex128, device=dev)
+    out = _dev_tensor(out, torch.complex128, (4 * B - 3, 2 * B - 1, 2 * B - 1), "out", dev)
+    with torch.cuda.device(dev):
+        _check(lib.sgl_trig_coeffs_noalloc(int(B), ctypes.c_void_p(xyz.data_ptr()), xyz.shape[0],
+                                           ctypes.c_void_p(coef.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                                           _stream_handle(dev)))
+    return out
 
 
 def _host_ptr(a):

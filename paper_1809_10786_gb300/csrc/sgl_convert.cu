@@ -262,6 +262,18 @@ cudaError_t launch_polar_adjoint(sgl_plan *p, const double2 *eta_full) {
     return cudaGetLastError();
 }
 
+cudaError_t launch_trig_raw(cudaStream_t s, int B, const unsigned long long *r2max, const double *costab, const double *P,
+                            double *radv, double *Kmat, double2 *beta, double2 *zeta, const double2 *coef, double2 *eta) {
+    const int K0 = 2 * B - 2, K1 = B - 1;
+    const int64_t W = 2 * K1 + 1;
+    k_radial_values<<<dim3(blocks_for(2 * B, 128), B), 128, 0, s>>>(B, r2max, costab, radv);
+    k_radial_matrix<<<dim3(blocks_for((int64_t)(K0 + 1) * B, kT), B), kT, 0, s>>>(B, K0, costab, radv, Kmat);
+    k_radial_forward<<<dim3(blocks_for((int64_t)(2 * B - 1) * (K0 + 1), kT), B), kT, 0, s>>>(B, K0, Kmat, coef, beta);
+    k_polar_forward<<<blocks_for((int64_t)(K0 + 1) * (K1 + 1) * W, kT), kT, 0, s>>>(B, K0, K1, P, beta, zeta);
+    k_trig_export<<<blocks_for((int64_t)(2 * K0 + 1) * W * W, kT), kT, 0, s>>>(K0, K1, zeta, eta);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_radial_adjoint(sgl_plan *p, double2 *coef) {
     k_radial_adjoint<<<blocks_for(p->Nc, kT), kT, 0, p->stream>>>(p->B, p->K0, p->Nc, p->b.Kmat, p->b.beta, coef);
     p->launches += 1;

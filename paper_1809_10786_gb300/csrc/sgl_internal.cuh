@@ -122,6 +122,11 @@ cudaError_t launch_interp(sgl_plan *p, double2 *vals);
 cudaError_t launch_spread(sgl_plan *p, const double2 *vals);
 cudaError_t launch_grad(sgl_plan *p, const double2 *gout, double *gxyz);
 
+// explicit-pointer launchers (no plan) used by the allocation-free entry point
+cudaError_t launch_max_radius_raw(cudaStream_t s, const double *xyz, int64_t M, unsigned long long *r2max, int *flags);
+cudaError_t launch_trig_raw(cudaStream_t s, int B, const unsigned long long *r2max, const double *costab, const double *P,
+                            double *radv, double *Kmat, double2 *beta, double2 *zeta, const double2 *coef, double2 *eta);
+
 }  // namespace sgl
 
 #define SGL_CUDA_TRY(expr)                                                              \

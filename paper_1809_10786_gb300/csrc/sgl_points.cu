@@ -194,4 +194,9 @@ cudaError_t launch_points(sgl_plan *p, const double *xyz, int64_t M) {
     return cudaGetLastError();
 }
 
+cudaError_t launch_max_radius_raw(cudaStream_t s, const double *xyz, int64_t M, unsigned long long *r2max, int *flags) {
+    if (M > 0) k_max_radius<<<grid_blocks(M, kThreads), kThreads, 0, s>>>(xyz, M, r2max, flags);
+    return cudaGetLastError();
+}
+
 }  // namespace sgl
