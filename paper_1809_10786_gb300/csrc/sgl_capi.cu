@@ -283,10 +283,21 @@ sgl_status sgl_plan_create(sgl_plan **out, int B, int64_t M_max, int precision, 
         a.wpar = (window == SGL_WIN_KB) ? kPi * (2.0 - 1.0 / a.sigma) : a.sigma * q / ((2.0 * a.sigma - 1.0) * kPi);
         factor(a.N, a.rad, a.nrad);
     }
-    p->nbin[0] = p->ax[0].N / 2 + 1;
-    p->nbin[1] = p->ax[1].N / 2 + 1;
-    p->nbin[2] = (p->ax[2].N + kBinS2 - 1) / kBinS2;
-    p->nbins = (int64_t)p->nbin[0] * p->nbin[1] * p->nbin[2];
+    {
+        BinGeom &g = p->bins;
+        g.S2 = 33 - 2 * q;
+        g.C0 = (precision == SGL_FP32_MIXED) ? 8 : 4;   // must match the spreading kernels' template sizes
+        g.C1 = (precision == SGL_FP32_MIXED) ? 8 : 2;
+        g.ncell[0] = p->ax[0].N / 2 + 1;
+        g.ncell[1] = p->ax[1].N / 2 + 1;
+        g.nsb[0] = (g.ncell[0] + g.C0 - 1) / g.C0;
+        g.nsb[1] = (g.ncell[1] + g.C1 - 1) / g.C1;
+        g.nsb[2] = (p->ax[2].N + g.S2 - 1) / g.S2;
+        g.nsuper = (int64_t)g.nsb[0] * g.nsb[1] * g.nsb[2];
+        g.nbins = g.nsuper * g.C0 * g.C1;
+        p->nbins = g.nbins;
+        p->max_items = M_max / kItemPoints + std::min<int64_t>(M_max, g.nbins) + 1;
+    }
 
     // ---- device allocations
     DevAlloc &A = h->alloc;
@@ -331,6 +342,10 @@ sgl_status sgl_plan_create(sgl_plan **out, int B, int64_t M_max, int precision, 
     ALLOC(b.bin_count, (size_t)p->nbins);
     ALLOC(b.bin_off, (size_t)p->nbins);
     ALLOC(b.scan_tmp, (size_t)(p->nbins / 2048 + 2));
+    ALLOC(b.item_count, (size_t)p->nbins);
+    ALLOC(b.item_off, (size_t)p->nbins);
+    ALLOC(b.items, (size_t)p->max_items);
+    ALLOC(b.n_items, 1);
     if (flags & SGL_FLAG_HOST_IO) {
         ALLOC(b.io_xyz, 3 * Mc);
         ALLOC(b.io_coef, (size_t)(2 * p->Nc));

@@ -13,7 +13,19 @@ namespace sgl {
 constexpr double kPi = 3.14159265358979323846;
 constexpr int kMaxQ = 16;          // 2q taps per axis must fit one warp
 constexpr int kMaxRadices = 16;
-constexpr int kBinS2 = 16;         // bin extent along the azimuthal axis (cells)
+constexpr int kItemPoints = 8;     // points per interpolation work item (one column bin)
+
+// Spatial bins: a column bin holds the points of one (i0, i1) cell column and one chunk of
+// S2 = 33 - 2q cells on the azimuthal axis, so the taps of all its points cover one warp's
+// 32 lanes on that axis and share their (2q)^2 rows.  C0 x C1 columns form a super-bin.
+struct BinGeom {
+    int S2;             // azimuthal cells per chunk
+    int C0, C1;         // columns per super-bin along axes 0 and 1
+    int nsb[3];         // super-bins per axis (axis 2 counts chunks)
+    int ncell[2];       // cell columns per axis 0 and 1 (N/2 + 1)
+    int64_t nbins;      // nsb0 * nsb2 * nsb1 * C0 * C1
+    int64_t nsuper;     // nsb0 * nsb2 * nsb1
+};
 
 // Sets the thread-local message returned by sgl_last_error() and returns code.
 sgl_status set_error(sgl_status code, const std::string &msg);
@@ -73,6 +85,9 @@ struct Buffers {
     int *bin_of, *rank_of;     // per input point
     int *bin_count, *bin_off;  // [nbins]
     int *scan_tmp;             // block sums
+    int *item_count, *item_off; // per bin: interpolation work items and their prefix sum
+    int2 *items;               // (first sorted point, count <= kItemPoints) per work item
+    int *n_items;              // total work items (device)
     // host-IO staging
     double *io_xyz, *io_coef, *io_vals, *io_grad;
 };
@@ -99,8 +114,9 @@ struct sgl_plan {
     int64_t M_max, M, Nc;
     int K0, K1;
     sgl::Axis ax[3];
-    int nbin[3];
+    sgl::BinGeom bins;
     int64_t nbins;
+    int64_t max_items;
     int64_t work_bytes;
     bool points_set;
     sgl::Buffers b;

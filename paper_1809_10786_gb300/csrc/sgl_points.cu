@@ -34,7 +34,8 @@ __global__ void k_max_radius(const double *__restrict__ xyz, int64_t M,
 
 struct PointGeom {
     int N[3];
-    int nbin1, nbin2;   // bins along axes 1 and 2
+    int S2, C0, C1;     // azimuthal chunk, columns per super-bin
+    int nsb1, nsb2;     // super-bins along axes 1 and 2
     int cmax0, cmax1;   // largest cell index on axes 0 and 1 (N/2)
 };
 
@@ -62,11 +63,14 @@ __device__ __forceinline__ void grid_coords(double x, double y, double z, double
     if (u2 < 0.0) u2 = 0.0;
 }
 
+// bin key: super-bin (axis 0, azimuthal chunk, axis 1) first, then the column inside it, so the
+// points of one column are contiguous and the columns of one super-bin are contiguous
 __device__ __forceinline__ int bin_of_coords(double u0, double u1, double u2, const PointGeom &g) {
-    int c0 = min(max((int)floor(u0), 0), g.cmax0);
-    int c1 = min(max((int)floor(u1), 0), g.cmax1);
-    int c2 = min(max((int)floor(u2), 0), g.N[2] - 1);
-    return (c0 * g.nbin1 + c1) * g.nbin2 + c2 / kBinS2;
+    const int c0 = min(max((int)floor(u0), 0), g.cmax0);
+    const int c1 = min(max((int)floor(u1), 0), g.cmax1);
+    const int c2 = min(max((int)floor(u2), 0), g.N[2] - 1);
+    const int sb = ((c0 / g.C0) * g.nsb2 + c2 / g.S2) * g.nsb1 + c1 / g.C1;
+    return (sb * g.C0 + c0 % g.C0) * g.C1 + c1 % g.C1;
 }
 
 __global__ void k_transform_points(const double *__restrict__ xyz, int64_t M, const unsigned long long *__restrict__ r2max,
@@ -160,6 +164,28 @@ __global__ void k_scatter_points(int64_t M, const double *__restrict__ u_tmp, co
     }
 }
 
+// work items for interpolation: each nonempty column bin is cut into pieces of <= kItemPoints points
+__global__ void k_item_count(const int *__restrict__ cnt, int64_t n, int *__restrict__ item_count) {
+    for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < n; b += (int64_t)gridDim.x * blockDim.x)
+        item_count[b] = (cnt[b] + kItemPoints - 1) / kItemPoints;
+}
+
+__global__ void k_item_fill(const int *__restrict__ cnt, const int *__restrict__ off, const int *__restrict__ item_count,
+                            const int *__restrict__ item_off, int64_t n, int2 *__restrict__ items, int *__restrict__ n_items) {
+    for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < n; b += (int64_t)gridDim.x * blockDim.x) {
+        const int c = cnt[b], k = item_count[b], o = item_off[b], first = off[b];
+        for (int j = 0; j < k; ++j) items[o + j] = make_int2(first + j * kItemPoints, min(kItemPoints, c - j * kItemPoints));
+        if (b == n - 1) *n_items = o + k;
+    }
+}
+
+void scan(const int *cnt, int64_t n, int *tmp, int *off, cudaStream_t s) {
+    const int nblk = (int)((n + kScanBlock - 1) / kScanBlock);
+    k_scan_block_totals<<<nblk, kThreads, 0, s>>>(cnt, n, tmp);
+    k_scan_totals<<<1, kThreads, 0, s>>>(tmp, nblk);
+    k_scan_final<<<nblk, kThreads, 0, s>>>(cnt, n, tmp, off);
+}
+
 int grid_blocks(int64_t work, int threads) {
     int64_t b = (work + threads - 1) / threads;
     if (b < 1) b = 1;
@@ -178,18 +204,22 @@ cudaError_t launch_points(sgl_plan *p, const double *xyz, int64_t M) {
     if (M > 0) { k_max_radius<<<grid_blocks(M, kThreads), kThreads, 0, s>>>(xyz, M, b.r2max, b.dev_flags); p->launches += 1; }
     PointGeom g;
     for (int d = 0; d < 3; ++d) g.N[d] = p->ax[d].N;
-    g.nbin1 = p->nbin[1];
-    g.nbin2 = p->nbin[2];
+    g.S2 = p->bins.S2;
+    g.C0 = p->bins.C0;
+    g.C1 = p->bins.C1;
+    g.nsb1 = p->bins.nsb[1];
+    g.nsb2 = p->bins.nsb[2];
     g.cmax0 = p->ax[0].N / 2;
     g.cmax1 = p->ax[1].N / 2;
     if (M > 0) {
         k_transform_points<<<grid_blocks(M, kThreads), kThreads, 0, s>>>(xyz, M, b.r2max, g, b.u_tmp, b.bin_of, b.rank_of, b.bin_count);
-        const int nblk = (int)((p->nbins + kScanBlock - 1) / kScanBlock);
-        k_scan_block_totals<<<nblk, kThreads, 0, s>>>(b.bin_count, p->nbins, b.scan_tmp);
-        k_scan_totals<<<1, kThreads, 0, s>>>(b.scan_tmp, nblk);
-        k_scan_final<<<nblk, kThreads, 0, s>>>(b.bin_count, p->nbins, b.scan_tmp, b.bin_off);
+        scan(b.bin_count, p->nbins, b.scan_tmp, b.bin_off, s);
         k_scatter_points<<<grid_blocks(M, kThreads), kThreads, 0, s>>>(M, b.u_tmp, b.bin_of, b.rank_of, b.bin_off, b.u_sorted, b.perm);
-        p->launches += 5;
+        k_item_count<<<grid_blocks(p->nbins, kThreads), kThreads, 0, s>>>(b.bin_count, p->nbins, b.item_count);
+        scan(b.item_count, p->nbins, b.scan_tmp, b.item_off, s);
+        k_item_fill<<<grid_blocks(p->nbins, kThreads), kThreads, 0, s>>>(b.bin_count, b.bin_off, b.item_count, b.item_off,
+                                                                          p->nbins, b.items, b.n_items);
+        p->launches += 10;
     }
     return cudaGetLastError();
 }
