@@ -336,6 +336,7 @@ sgl_status sgl_plan_create(sgl_plan **out, int B, int64_t M_max, int precision, 
     const size_t Mc = (size_t)std::max<int64_t>(M_max, 1);
     ALLOC(b.u_tmp, 3 * Mc);
     ALLOC(b.u_sorted, 3 * Mc);
+    ALLOC(b.pts32, Mc);
     ALLOC(b.perm, Mc);
     ALLOC(b.bin_of, Mc);
     ALLOC(b.rank_of, Mc);

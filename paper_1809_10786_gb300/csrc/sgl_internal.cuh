@@ -81,6 +81,7 @@ struct Buffers {
     int *dev_flags;            // bit 0: non-finite coordinate seen
     double *u_tmp;             // [M][3] grid coordinates, input order
     double *u_sorted;          // [M][3] grid coordinates, bin order
+    float4 *pts32;             // [M] bin order: (u0 - c0, u1 - c1, u2 - c2, cells c0 | c1 << 10 | c2 << 20 as bits)
     int *perm;                 // sorted position -> input index
     int *bin_of, *rank_of;     // per input point
     int *bin_count, *bin_off;  // [nbins]

@@ -99,61 +99,6 @@ __device__ __forceinline__ int row_of(int t, int first, int rows, int N) {
     return r;
 }
 
-template <typename T, int WIN, int G>
-__global__ void __launch_bounds__(256) k_interp(NGeom g, int64_t M, const double *__restrict__ u_sorted,
-                                                const int *__restrict__ perm, const C2<T> *__restrict__ grid,
-                                                double2 *__restrict__ vals) {
-    const int lane = threadIdx.x & 31;
-    const int gl = lane % G;
-    const int q2 = 2 * g.q;
-    const T qT = (T)g.q;
-    const int64_t ppw = 32 / G;
-    const int64_t warp0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / 32;
-    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) / 32;
-    const int64_t s1 = g.N[2], s0 = (int64_t)g.rows[1] * g.N[2];
-    for (int64_t base = warp0 * ppw; base < M; base += nwarps * ppw) {
-        const int64_t i = base + lane / G;
-        const bool live = i < M;
-        const int64_t ii = live ? i : M - 1;
-        const double u0 = u_sorted[3 * ii], u1 = u_sorted[3 * ii + 1], u2 = u_sorted[3 * ii + 2];
-        const int a0 = (int)floor(u0) - g.q + 1, a1 = (int)floor(u1) - g.q + 1, a2 = (int)floor(u2) - g.q + 1;
-        T w1[G];
-#pragma unroll
-        for (int b = 0; b < G; ++b) w1[b] = (b < q2) ? window<WIN, T>((T)(u1 - (a1 + b)), qT, (T)g.par[1], (T)g.norm[1]) : (T)0;
-        const T w2 = (gl < q2) ? window<WIN, T>((T)(u2 - (a2 + gl)), qT, (T)g.par[2], (T)g.norm[2]) : (T)0;
-        int c = a2 + gl;
-        if (c < 0) c += g.N[2];
-        if (c >= g.N[2]) c -= g.N[2];
-        if (gl >= q2) c = 0;
-        T ax = 0, ay = 0;
-        for (int a = 0; a < q2; ++a) {
-            const T w0 = window<WIN, T>((T)(u0 - (a0 + a)), qT, (T)g.par[0], (T)g.norm[0]);
-            const int r0 = row_of(a0 + a, g.first[0], g.rows[0], g.N[0]);
-            const C2<T> *rowp = grid + r0 * s0 + c;
-            T rx = 0, ry = 0;                 // row sum over axis 1, then one multiply by w0
-#pragma unroll
-            for (int b = 0; b < G; ++b) {
-                if (b < q2) {
-                    const int r1 = row_of(a1 + b, g.first[1], g.rows[1], g.N[1]);
-                    const C2<T> v = rowp[r1 * s1];
-                    rx += w1[b] * v.x;
-                    ry += w1[b] * v.y;
-                }
-            }
-            ax += w0 * rx;
-            ay += w0 * ry;
-        }
-        ax *= w2;
-        ay *= w2;
-#pragma unroll
-        for (int o = G / 2; o > 0; o >>= 1) {
-            ax += __shfl_xor_sync(0xffffffffu, ax, o);
-            ay += __shfl_xor_sync(0xffffffffu, ay, o);
-        }
-        if (live && gl == 0) vals[perm[i]] = make_double2((double)ax, (double)ay);
-    }
-}
-
 __device__ __forceinline__ void atomic_add_c(float2 *p, float x, float y) { atomicAdd(&p->x, x); atomicAdd(&p->y, y); }
 __device__ __forceinline__ void atomic_add_c(double2 *p, double x, double y) { atomicAdd(&p->x, x); atomicAdd(&p->y, y); }
 
@@ -193,189 +138,169 @@ __global__ void __launch_bounds__(256) k_spread(NGeom g, int64_t M, const double
     }
 }
 
-// gxyz[perm[i]] = Re(conj(g_i) grad_x s(t(x_i))): window derivatives give ds/du_d; the
-// chain rule goes through t0 = arccos(2r/rho - 1), t1 = theta, t2 = phi.
-template <typename T, int WIN, int G>
-__global__ void __launch_bounds__(256) k_grad(NGeom g, int64_t M, const double *__restrict__ u_sorted,
-                                              const int *__restrict__ perm, const unsigned long long *__restrict__ r2max,
-                                              const C2<T> *__restrict__ grid, const double2 *__restrict__ gout,
-                                              double *__restrict__ gxyz) {
-    const int lane = threadIdx.x & 31;
-    const int gl = lane % G;
-    const int q2 = 2 * g.q;
-    const T qT = (T)g.q;
-    const int64_t ppw = 32 / G;
+// ---------------------------------------------------------------------------------------------
+// FP32 path.  Points come packed as float4 (fractional grid coordinates, cells in 10-bit fields),
+// so window arguments are exact float sums (frac + integer offset) and no FP64 work is left in
+// the loops (the FP64 pipe of GB300 runs at 1/64 of the FP32 rate).  G = 8/16/32 >= 2q lanes
+// serve one point: lane j evaluates the weights of tap j on each axis and shares them by
+// shuffle; the (2q)^2 rows are read once per point, lane = azimuthal tap, packed FP32 FMA.
+
+__device__ __forceinline__ void unpack_cells(float w, int &c0, int &c1, int &c2) {
+    const int v = __float_as_int(w);
+    c0 = v & 1023;
+    c1 = (v >> 10) & 1023;
+    c2 = (v >> 20) & 1023;
+}
+
+template <int WIN, int G>
+__global__ void __launch_bounds__(256) k_interp32(NGeom g, int64_t M, const float4 *__restrict__ pts, const int *__restrict__ perm,
+                                                  const float2 *__restrict__ grid, double2 *__restrict__ vals) {
+    const int lane = threadIdx.x & 31, gl = lane & (G - 1);
+    const int q = g.q, q2 = 2 * q;
+    const float qf = (float)q;
+    const float par0 = (float)g.par[0], par1 = (float)g.par[1], par2 = (float)g.par[2];
+    const float nrm0 = (float)g.norm[0], nrm1 = (float)g.norm[1], nrm2 = (float)g.norm[2];
+    const int64_t s1 = g.N[2], s0 = (int64_t)g.rows[1] * g.N[2];
+    constexpr int PPW = 32 / G;
     const int64_t warp0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / 32;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) / 32;
-    const int64_t s1 = g.N[2], s0 = (int64_t)g.rows[1] * g.N[2];
-    double rho = sqrt(__longlong_as_double((long long)*r2max)) * (1.0 + 0x1p-20);
-    if (!(rho > 0.0)) rho = 1.0;
-    for (int64_t base = warp0 * ppw; base < M; base += nwarps * ppw) {
+    for (int64_t base = warp0 * PPW; base < M; base += nwarps * PPW) {
         const int64_t i = base + lane / G;
         const bool live = i < M;
-        const int64_t ii = live ? i : M - 1;
-        const double u0 = u_sorted[3 * ii], u1 = u_sorted[3 * ii + 1], u2 = u_sorted[3 * ii + 2];
-        const int a0 = (int)floor(u0) - g.q + 1, a1 = (int)floor(u1) - g.q + 1, a2 = (int)floor(u2) - g.q + 1;
-        T w1[G], d1[G];
+        const float4 pt = pts[live ? i : M - 1];
+        int c0, c1, c2;
+        unpack_cells(pt.w, c0, c1, c2);
+        const int a0 = c0 - q + 1, a1 = c1 - q + 1, a2 = c2 - q + 1;
+        const bool tap = gl < q2;
+        const float off = (float)(q - 1 - gl);          // u - (a + gl) = frac + q - 1 - gl
+        const float w0_own = tap ? window<WIN, float>(pt.x + off, qf, par0, nrm0) : 0.f;
+        const float w1_own = tap ? window<WIN, float>(pt.y + off, qf, par1, nrm1) : 0.f;
+        const float w2 = tap ? window<WIN, float>(pt.z + off, qf, par2, nrm2) : 0.f;
+        const int col = tap ? wrap_index(a2 + gl, g.N[2]) : 0;
+        float2 w1p[G];
+        int off1[G];
 #pragma unroll
         for (int b = 0; b < G; ++b) {
-            const T x = (T)(u1 - (a1 + b));
-            w1[b] = (b < q2) ? window<WIN, T>(x, qT, (T)g.par[1], (T)g.norm[1]) : (T)0;
-            d1[b] = (b < q2) ? window_deriv<WIN, T>(x, qT, (T)g.par[1], (T)g.norm[1]) : (T)0;
+            const float w = __shfl_sync(0xffffffffu, w1_own, b, G);
+            w1p[b] = make_float2(w, w);
+            off1[b] = (b < q2) ? row_of(a1 + b, g.first[1], g.rows[1], g.N[1]) * (int)s1 + col : col;
         }
-        const T x2 = (T)(u2 - (a2 + gl));
-        const T w2 = (gl < q2) ? window<WIN, T>(x2, qT, (T)g.par[2], (T)g.norm[2]) : (T)0;
-        const T d2 = (gl < q2) ? window_deriv<WIN, T>(x2, qT, (T)g.par[2], (T)g.norm[2]) : (T)0;
-        int c = a2 + gl;
-        if (c < 0) c += g.N[2];
-        if (c >= g.N[2]) c -= g.N[2];
-        if (gl >= q2) c = 0;
-        T fx = 0, fy = 0, ax = 0, ay = 0, bx = 0, by = 0;   // s, ds/du0, ds/du1 before the axis-2 weight
+        float2 acc = make_float2(0.f, 0.f);
         for (int a = 0; a < q2; ++a) {
-            const T x0 = (T)(u0 - (a0 + a));
-            const T w0 = window<WIN, T>(x0, qT, (T)g.par[0], (T)g.norm[0]);
-            const T dw0 = window_deriv<WIN, T>(x0, qT, (T)g.par[0], (T)g.norm[0]);
-            const int r0 = row_of(a0 + a, g.first[0], g.rows[0], g.N[0]);
-            const C2<T> *rowp = grid + r0 * s0 + c;
-            T rx = 0, ry = 0, sx = 0, sy = 0;
+            const float w0 = __shfl_sync(0xffffffffu, w0_own, a, G);
+            const float2 *rowp = grid + row_of(a0 + a, g.first[0], g.rows[0], g.N[0]) * s0;
+            float2 rs = make_float2(0.f, 0.f);
 #pragma unroll
-            for (int b = 0; b < G; ++b) {
-                if (b < q2) {
-                    const int r1 = row_of(a1 + b, g.first[1], g.rows[1], g.N[1]);
-                    const C2<T> v = rowp[r1 * s1];
-                    rx += w1[b] * v.x; ry += w1[b] * v.y;
-                    sx += d1[b] * v.x; sy += d1[b] * v.y;
-                }
-            }
-            fx += w0 * rx; fy += w0 * ry;
-            ax += dw0 * rx; ay += dw0 * ry;
-            bx += w0 * sx; by += w0 * sy;
+            for (int b = 0; b < G; ++b)
+                if (b < q2) rs = ffma2(w1p[b], __ldg(rowp + off1[b]), rs);
+            acc = ffma2(make_float2(w0, w0), rs, acc);
         }
-        // d/du of psi(u - l) is psi'(u - l)
-        T f2x = d2 * fx, f2y = d2 * fy;
-        fx *= w2; fy *= w2; ax *= w2; ay *= w2; bx *= w2; by *= w2;
+        float x = acc.x * w2, y = acc.y * w2;
 #pragma unroll
         for (int o = G / 2; o > 0; o >>= 1) {
-            ax += __shfl_xor_sync(0xffffffffu, ax, o);
-            ay += __shfl_xor_sync(0xffffffffu, ay, o);
-            bx += __shfl_xor_sync(0xffffffffu, bx, o);
-            by += __shfl_xor_sync(0xffffffffu, by, o);
-            f2x += __shfl_xor_sync(0xffffffffu, f2x, o);
-            f2y += __shfl_xor_sync(0xffffffffu, f2y, o);
+            x += __shfl_xor_sync(0xffffffffu, x, o);
+            y += __shfl_xor_sync(0xffffffffu, y, o);
         }
-        if (live && gl == 0) {
-            const double twopi = 2.0 * kPi;
-            // ds/dt_d = (N_d / 2 pi) ds/du_d
-            const double g0x = ax * (g.N[0] / twopi), g0y = ay * (g.N[0] / twopi);
-            const double g1x = bx * (g.N[1] / twopi), g1y = by * (g.N[1] / twopi);
-            const double g2x = f2x * (g.N[2] / twopi), g2y = f2y * (g.N[2] / twopi);
-            const double t0 = twopi * u0 / g.N[0], t1 = twopi * u1 / g.N[1], t2 = twopi * u2 / g.N[2];
-            const double ch = cos(0.5 * t0);
-            const double r = rho * ch * ch;                 // r = rho (1 + cos t0) / 2
-            const double st0 = sin(t0), st1 = sin(t1), ct1 = cos(t1), sp = sin(t2), cp = cos(t2);
-            const double dt0dr = (st0 > 0.0) ? -2.0 / (rho * st0) : 0.0;
-            const double ir = (r > 0.0) ? 1.0 / r : 0.0;
-            const double irs = (r > 0.0 && st1 > 0.0) ? 1.0 / (r * st1) : 0.0;
-            const double er[3] = {st1 * cp, st1 * sp, ct1}, et[3] = {ct1 * cp, ct1 * sp, -st1}, ep[3] = {-sp, cp, 0.0};
-            const double2 gv = gout[perm[i]];
-            double *outp = gxyz + 3 * (int64_t)perm[i];
-            for (int d = 0; d < 3; ++d) {
-                const double vx = g0x * dt0dr * er[d] + g1x * ir * et[d] + g2x * irs * ep[d];
-                const double vy = g0y * dt0dr * er[d] + g1y * ir * et[d] + g2y * irs * ep[d];
-                outp[d] = gv.x * vx + gv.y * vy;          // Re(conj(g) v)
-            }
-        }
+        if (live && gl == 0) vals[perm[i]] = make_double2((double)x, (double)y);
     }
 }
 
-// ---------------------------------------------------------------------------------------------
-// FP32 interpolation by column work items.  One warp per item (<= kItemPoints points of one
-// column bin: the same rows on axes 0 and 1, all azimuthal taps inside the warp's 32 lanes).
-// Each grid row is read once per KC points (lane = azimuthal cell, coalesced) and used for all
-// of them: s = sum_a w0[a] sum_b w1[b] g[a][b][lane], then a lane reduction with w2[lane].
-// Window weights are staged per warp in shared memory; the inner products use packed FP32 FMA.
-template <int WIN, int Q2MAX, int KC>
-__global__ void __launch_bounds__(256) k_interp_col(NGeom g, const int2 *__restrict__ items, const int *__restrict__ n_items,
-                                                    const double *__restrict__ u_sorted, const int *__restrict__ perm,
-                                                    const float2 *__restrict__ grid, double2 *__restrict__ vals) {
-    __shared__ float2 s_w1[8][KC][Q2MAX];   // (w1, w1) pairs
-    __shared__ float s_w0[8][KC][Q2MAX];
-    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+// FP32 window-derivative interpolation: s, ds/du0, ds/du1 in one sweep of the rows, ds/du2 from
+// psi' on the lanes, then the chain rule in FP32 (sincospi of the torus coordinates).
+template <int WIN, int G>
+__global__ void __launch_bounds__(256) k_grad32(NGeom g, int64_t M, const float4 *__restrict__ pts, const int *__restrict__ perm,
+                                                const unsigned long long *__restrict__ r2max, const float2 *__restrict__ grid,
+                                                const double2 *__restrict__ gout, double *__restrict__ gxyz) {
+    const int lane = threadIdx.x & 31, gl = lane & (G - 1);
     const int q = g.q, q2 = 2 * q;
     const float qf = (float)q;
+    const float par0 = (float)g.par[0], par1 = (float)g.par[1], par2 = (float)g.par[2];
+    const float nrm0 = (float)g.norm[0], nrm1 = (float)g.norm[1], nrm2 = (float)g.norm[2];
     const int64_t s1 = g.N[2], s0 = (int64_t)g.rows[1] * g.N[2];
-    const int nit = *n_items;
-    const int nw = gridDim.x * (blockDim.x >> 5);
-    for (int it = blockIdx.x * (blockDim.x >> 5) + wib; it < nit; it += nw) {
-        const int2 item = items[it];
-        const int first = item.x, cnt = item.y;
-        const int c0 = cell_clamped(u_sorted[3 * (int64_t)first], g.cmax0);
-        const int c1 = cell_clamped(u_sorted[3 * (int64_t)first + 1], g.cmax1);
-        const int cz = min(max((int)floor(u_sorted[3 * (int64_t)first + 2]), 0), g.N[2] - 1);
-        const int a0 = c0 - q + 1, a1 = c1 - q + 1;
-        const int cbase = (cz / g.S2) * g.S2 - q + 1;
-        const int col = wrap_index(cbase + lane, g.N[2]);
-        int off1[Q2MAX];
+    double rhod = sqrt(__longlong_as_double((long long)*r2max)) * (1.0 + 0x1p-20);
+    if (!(rhod > 0.0)) rhod = 1.0;
+    const float rho = (float)rhod;
+    constexpr int PPW = 32 / G;
+    const int64_t warp0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / 32;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) / 32;
+    for (int64_t base = warp0 * PPW; base < M; base += nwarps * PPW) {
+        const int64_t i = base + lane / G;
+        const bool live = i < M;
+        const float4 pt = pts[live ? i : M - 1];
+        int c0, c1, c2;
+        unpack_cells(pt.w, c0, c1, c2);
+        const int a0 = c0 - q + 1, a1 = c1 - q + 1, a2 = c2 - q + 1;
+        const bool tap = gl < q2;
+        const float off = (float)(q - 1 - gl);
+        const float x0 = pt.x + off, x1 = pt.y + off, x2 = pt.z + off;
+        const float w0_own = tap ? window<WIN, float>(x0, qf, par0, nrm0) : 0.f;
+        const float d0_own = tap ? window_deriv<WIN, float>(x0, qf, par0, nrm0) : 0.f;
+        const float w1_own = tap ? window<WIN, float>(x1, qf, par1, nrm1) : 0.f;
+        const float d1_own = tap ? window_deriv<WIN, float>(x1, qf, par1, nrm1) : 0.f;
+        const float w2 = tap ? window<WIN, float>(x2, qf, par2, nrm2) : 0.f;
+        const float d2 = tap ? window_deriv<WIN, float>(x2, qf, par2, nrm2) : 0.f;
+        const int col = tap ? wrap_index(a2 + gl, g.N[2]) : 0;
+        float2 w1p[G], d1p[G];
+        int off1[G];
 #pragma unroll
-        for (int b = 0; b < Q2MAX; ++b) off1[b] = (b < q2) ? row_of(a1 + b, g.first[1], g.rows[1], g.N[1]) * (int)s1 + col : col;
-        for (int p0 = 0; p0 < cnt; p0 += KC) {
-            const int np = min(KC, cnt - p0);
-            for (int t = lane; t < KC * Q2MAX; t += 32) {
-                const int k = t / Q2MAX, j = t % Q2MAX;
-                float w0 = 0.f, w1 = 0.f;
-                if (k < np && j < q2) {
-                    const int64_t pi = first + p0 + k;
-                    w0 = window<WIN, float>((float)(u_sorted[3 * pi] - (a0 + j)), qf, (float)g.par[0], (float)g.norm[0]);
-                    w1 = window<WIN, float>((float)(u_sorted[3 * pi + 1] - (a1 + j)), qf, (float)g.par[1], (float)g.norm[1]);
+        for (int b = 0; b < G; ++b) {
+            const float w = __shfl_sync(0xffffffffu, w1_own, b, G);
+            const float d = __shfl_sync(0xffffffffu, d1_own, b, G);
+            w1p[b] = make_float2(w, w);
+            d1p[b] = make_float2(d, d);
+            off1[b] = (b < q2) ? row_of(a1 + b, g.first[1], g.rows[1], g.N[1]) * (int)s1 + col : col;
+        }
+        float2 af = make_float2(0.f, 0.f), ad0 = af, ad1 = af;
+        for (int a = 0; a < q2; ++a) {
+            const float w0 = __shfl_sync(0xffffffffu, w0_own, a, G);
+            const float d0 = __shfl_sync(0xffffffffu, d0_own, a, G);
+            const float2 *rowp = grid + row_of(a0 + a, g.first[0], g.rows[0], g.N[0]) * s0;
+            float2 rs = make_float2(0.f, 0.f), rd = rs;
+#pragma unroll
+            for (int b = 0; b < G; ++b)
+                if (b < q2) {
+                    const float2 v = __ldg(rowp + off1[b]);
+                    rs = ffma2(w1p[b], v, rs);
+                    rd = ffma2(d1p[b], v, rd);
                 }
-                s_w0[wib][k][j] = w0;
-                s_w1[wib][k][j] = make_float2(w1, w1);
+            af = ffma2(make_float2(w0, w0), rs, af);
+            ad0 = ffma2(make_float2(d0, d0), rs, ad0);
+            ad1 = ffma2(make_float2(w0, w0), rd, ad1);
+        }
+        float v0x = ad0.x * w2, v0y = ad0.y * w2, v1x = ad1.x * w2, v1y = ad1.y * w2;
+        float v2x = af.x * d2, v2y = af.y * d2;
+#pragma unroll
+        for (int o = G / 2; o > 0; o >>= 1) {
+            v0x += __shfl_xor_sync(0xffffffffu, v0x, o);
+            v0y += __shfl_xor_sync(0xffffffffu, v0y, o);
+            v1x += __shfl_xor_sync(0xffffffffu, v1x, o);
+            v1y += __shfl_xor_sync(0xffffffffu, v1y, o);
+            v2x += __shfl_xor_sync(0xffffffffu, v2x, o);
+            v2y += __shfl_xor_sync(0xffffffffu, v2y, o);
+        }
+        if (live && gl == 0) {
+            // ds/dt_d = (N_d / 2 pi) ds/du_d;  t_d / pi = 2 u_d / N_d
+            const float k0 = g.N[0] * 0.15915494309189535f, k1 = g.N[1] * 0.15915494309189535f, k2 = g.N[2] * 0.15915494309189535f;
+            const float h0 = 2.f * ((float)c0 + pt.x) / g.N[0], h1 = 2.f * ((float)c1 + pt.y) / g.N[1], h2 = 2.f * ((float)c2 + pt.z) / g.N[2];
+            float st0, ct0h, sth, st1, ct1, sp, cp;
+            sincospif(h0, &st0, &ct0h);
+            sincospif(0.5f * h0, &sth, &ct0h);          // cos(t0 / 2)
+            sincospif(h1, &st1, &ct1);
+            sincospif(h2, &sp, &cp);
+            const float r = rho * ct0h * ct0h;            // r = rho (1 + cos t0) / 2
+            const float dt0dr = (st0 > 0.f) ? -2.f / (rho * st0) : 0.f;
+            const float ir = (r > 0.f) ? 1.f / r : 0.f;
+            const float irs = (r > 0.f && st1 > 0.f) ? 1.f / (r * st1) : 0.f;
+            const float er[3] = {st1 * cp, st1 * sp, ct1}, et[3] = {ct1 * cp, ct1 * sp, -st1}, ep[3] = {-sp, cp, 0.f};
+            const int dst = perm[i];
+            const double2 gv = gout[dst];
+            const float gx = (float)gv.x, gy = (float)gv.y;
+            const float A = k0 * dt0dr, Bq = k1 * ir, Cq = k2 * irs;
+            for (int d = 0; d < 3; ++d) {
+                const float vx = A * v0x * er[d] + Bq * v1x * et[d] + Cq * v2x * ep[d];
+                const float vy = A * v0y * er[d] + Bq * v1y * et[d] + Cq * v2y * ep[d];
+                gxyz[3 * (int64_t)dst + d] = (double)(gx * vx + gy * vy);     // Re(conj(g) v)
             }
-            float w2[KC];
-#pragma unroll
-            for (int k = 0; k < KC; ++k) {
-                w2[k] = 0.f;
-                if (k < np) {
-                    const double u2 = u_sorted[3 * (int64_t)(first + p0 + k) + 2];
-                    const int rel = cbase + lane - ((int)floor(u2) - q + 1);
-                    if (rel >= 0 && rel < q2)
-                        w2[k] = window<WIN, float>((float)(u2 - (cbase + lane)), qf, (float)g.par[2], (float)g.norm[2]);
-                }
-            }
-            __syncwarp();
-            float2 acc[KC];
-#pragma unroll
-            for (int k = 0; k < KC; ++k) acc[k] = make_float2(0.f, 0.f);
-            for (int a = 0; a < q2; ++a) {
-                const float2 *rowp = grid + row_of(a0 + a, g.first[0], g.rows[0], g.N[0]) * s0;
-                float2 rs[KC];
-#pragma unroll
-                for (int k = 0; k < KC; ++k) rs[k] = make_float2(0.f, 0.f);
-#pragma unroll
-                for (int b = 0; b < Q2MAX; ++b) {
-                    if (b < q2) {
-                        const float2 v = __ldg(rowp + off1[b]);
-#pragma unroll
-                        for (int k = 0; k < KC; ++k) rs[k] = ffma2(s_w1[wib][k][b], v, rs[k]);
-                    }
-                }
-#pragma unroll
-                for (int k = 0; k < KC; ++k) {
-                    const float w0 = s_w0[wib][k][a];
-                    acc[k] = ffma2(make_float2(w0, w0), rs[k], acc[k]);
-                }
-            }
-#pragma unroll
-            for (int k = 0; k < KC; ++k) {
-                float x = acc[k].x * w2[k], y = acc[k].y * w2[k];
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) {
-                    x += __shfl_xor_sync(0xffffffffu, x, o);
-                    y += __shfl_xor_sync(0xffffffffu, y, o);
-                }
-                if (lane == 0 && k < np) vals[perm[first + p0 + k]] = make_double2((double)x, (double)y);
-            }
-            __syncwarp();
         }
     }
 }
@@ -403,122 +328,6 @@ __device__ __forceinline__ void write_point_gradient(const NGeom &g, double rho,
     }
 }
 
-// FP32 window-derivative interpolation by column work items (same layout as k_interp_col):
-// per point s, ds/du0, ds/du1 from one pass over the rows, ds/du2 from psi' on the lanes.
-template <int WIN, int Q2MAX, int KC>
-__global__ void __launch_bounds__(256) k_grad_col(NGeom g, const int2 *__restrict__ items, const int *__restrict__ n_items,
-                                                  const double *__restrict__ u_sorted, const int *__restrict__ perm,
-                                                  const unsigned long long *__restrict__ r2max, const float2 *__restrict__ grid,
-                                                  const double2 *__restrict__ gout, double *__restrict__ gxyz) {
-    __shared__ float2 s_w1[8][KC][Q2MAX], s_d1[8][KC][Q2MAX];
-    __shared__ float s_w0[8][KC][Q2MAX], s_d0[8][KC][Q2MAX];
-    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-    const int q = g.q, q2 = 2 * q;
-    const float qf = (float)q;
-    const int64_t s1 = g.N[2], s0 = (int64_t)g.rows[1] * g.N[2];
-    double rho = sqrt(__longlong_as_double((long long)*r2max)) * (1.0 + 0x1p-20);
-    if (!(rho > 0.0)) rho = 1.0;
-    const int nit = *n_items;
-    const int nw = gridDim.x * (blockDim.x >> 5);
-    for (int it = blockIdx.x * (blockDim.x >> 5) + wib; it < nit; it += nw) {
-        const int2 item = items[it];
-        const int first = item.x, cnt = item.y;
-        const int c0 = cell_clamped(u_sorted[3 * (int64_t)first], g.cmax0);
-        const int c1 = cell_clamped(u_sorted[3 * (int64_t)first + 1], g.cmax1);
-        const int cz = min(max((int)floor(u_sorted[3 * (int64_t)first + 2]), 0), g.N[2] - 1);
-        const int a0 = c0 - q + 1, a1 = c1 - q + 1;
-        const int cbase = (cz / g.S2) * g.S2 - q + 1;
-        const int col = wrap_index(cbase + lane, g.N[2]);
-        int off1[Q2MAX];
-#pragma unroll
-        for (int b = 0; b < Q2MAX; ++b) off1[b] = (b < q2) ? row_of(a1 + b, g.first[1], g.rows[1], g.N[1]) * (int)s1 + col : col;
-        for (int p0 = 0; p0 < cnt; p0 += KC) {
-            const int np = min(KC, cnt - p0);
-            for (int t = lane; t < KC * Q2MAX; t += 32) {
-                const int k = t / Q2MAX, j = t % Q2MAX;
-                float w0 = 0.f, d0 = 0.f, w1 = 0.f, d1 = 0.f;
-                if (k < np && j < q2) {
-                    const int64_t pi = first + p0 + k;
-                    const float x0 = (float)(u_sorted[3 * pi] - (a0 + j)), x1 = (float)(u_sorted[3 * pi + 1] - (a1 + j));
-                    w0 = window<WIN, float>(x0, qf, (float)g.par[0], (float)g.norm[0]);
-                    d0 = window_deriv<WIN, float>(x0, qf, (float)g.par[0], (float)g.norm[0]);
-                    w1 = window<WIN, float>(x1, qf, (float)g.par[1], (float)g.norm[1]);
-                    d1 = window_deriv<WIN, float>(x1, qf, (float)g.par[1], (float)g.norm[1]);
-                }
-                s_w0[wib][k][j] = w0;
-                s_d0[wib][k][j] = d0;
-                s_w1[wib][k][j] = make_float2(w1, w1);
-                s_d1[wib][k][j] = make_float2(d1, d1);
-            }
-            float w2[KC], d2[KC];
-#pragma unroll
-            for (int k = 0; k < KC; ++k) {
-                w2[k] = 0.f;
-                d2[k] = 0.f;
-                if (k < np) {
-                    const double u2 = u_sorted[3 * (int64_t)(first + p0 + k) + 2];
-                    const int rel = cbase + lane - ((int)floor(u2) - q + 1);
-                    if (rel >= 0 && rel < q2) {
-                        const float x2 = (float)(u2 - (cbase + lane));
-                        w2[k] = window<WIN, float>(x2, qf, (float)g.par[2], (float)g.norm[2]);
-                        d2[k] = window_deriv<WIN, float>(x2, qf, (float)g.par[2], (float)g.norm[2]);
-                    }
-                }
-            }
-            __syncwarp();
-            float2 af[KC], a0v[KC], a1v[KC];
-#pragma unroll
-            for (int k = 0; k < KC; ++k) { af[k] = make_float2(0.f, 0.f); a0v[k] = af[k]; a1v[k] = af[k]; }
-            for (int a = 0; a < q2; ++a) {
-                const float2 *rowp = grid + row_of(a0 + a, g.first[0], g.rows[0], g.N[0]) * s0;
-                float2 rs[KC], rd[KC];
-#pragma unroll
-                for (int k = 0; k < KC; ++k) { rs[k] = make_float2(0.f, 0.f); rd[k] = rs[k]; }
-#pragma unroll
-                for (int b = 0; b < Q2MAX; ++b) {
-                    if (b < q2) {
-                        const float2 v = __ldg(rowp + off1[b]);
-#pragma unroll
-                        for (int k = 0; k < KC; ++k) {
-                            rs[k] = ffma2(s_w1[wib][k][b], v, rs[k]);
-                            rd[k] = ffma2(s_d1[wib][k][b], v, rd[k]);
-                        }
-                    }
-                }
-#pragma unroll
-                for (int k = 0; k < KC; ++k) {
-                    const float w0 = s_w0[wib][k][a], d0 = s_d0[wib][k][a];
-                    af[k] = ffma2(make_float2(w0, w0), rs[k], af[k]);
-                    a0v[k] = ffma2(make_float2(d0, d0), rs[k], a0v[k]);
-                    a1v[k] = ffma2(make_float2(w0, w0), rd[k], a1v[k]);
-                }
-            }
-#pragma unroll
-            for (int k = 0; k < KC; ++k) {
-                float v0x = a0v[k].x * w2[k], v0y = a0v[k].y * w2[k];
-                float v1x = a1v[k].x * w2[k], v1y = a1v[k].y * w2[k];
-                float v2x = af[k].x * d2[k], v2y = af[k].y * d2[k];
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) {
-                    v0x += __shfl_xor_sync(0xffffffffu, v0x, o);
-                    v0y += __shfl_xor_sync(0xffffffffu, v0y, o);
-                    v1x += __shfl_xor_sync(0xffffffffu, v1x, o);
-                    v1y += __shfl_xor_sync(0xffffffffu, v1y, o);
-                    v2x += __shfl_xor_sync(0xffffffffu, v2x, o);
-                    v2y += __shfl_xor_sync(0xffffffffu, v2y, o);
-                }
-                if (lane == 0 && k < np) {
-                    const int64_t pi = first + p0 + k;
-                    const int dst = perm[pi];
-                    write_point_gradient(g, rho, u_sorted[3 * pi], u_sorted[3 * pi + 1], u_sorted[3 * pi + 2],
-                                         v0x, v0y, v1x, v1y, v2x, v2y, gout[dst], gxyz + 3 * (int64_t)dst);
-                }
-            }
-            __syncwarp();
-        }
-    }
-}
-
 // Spreading by super-bins.  One CTA per super-bin (C0 x C1 columns x one azimuthal chunk);
 // warp w owns tile slab a = w (one grid row on axis 0) and keeps the sums for all T1 rows of
 // axis 1 and its 32 azimuthal lanes in registers while it sweeps every point of the super-bin;
@@ -526,7 +335,7 @@ __global__ void __launch_bounds__(256) k_grad_col(NGeom g, const int2 *__restric
 template <typename T, int WIN, int Q2MAX, int C1>
 struct SpreadSmem {
     static constexpr int PCH = 64;
-    static constexpr int T1MAX = C1 + Q2MAX - 1;
+    static constexpr int T1MAX = (C1 + Q2MAX - 1 + 1) & ~1;   // rounded up to even: pairs load as 128 bits
     C2<T> y[PCH];
     T w0[PCH][Q2MAX];
     C2<T> w1[PCH][T1MAX];     // (w1, w1) pairs
@@ -537,11 +346,11 @@ struct SpreadSmem {
 template <typename T, int WIN, int Q2MAX, int C0, int C1>
 __global__ void __launch_bounds__(32 * (C0 + Q2MAX - 1)) k_spread_slab(NGeom g, const int *__restrict__ bin_off, int64_t M,
                                                                        int64_t nsuper, const double *__restrict__ u_sorted,
-                                                                       const int *__restrict__ perm, const double2 *__restrict__ vals,
-                                                                       C2<T> *__restrict__ grid) {
+                                                                       const float4 *__restrict__ pts32, const int *__restrict__ perm,
+                                                                       const double2 *__restrict__ vals, C2<T> *__restrict__ grid) {
     using S = SpreadSmem<T, WIN, Q2MAX, C1>;
     constexpr int PCH = S::PCH, T1MAX = S::T1MAX;
-    __shared__ S sm;
+    __shared__ __align__(16) S sm;
     const int lane = threadIdx.x & 31, ta = threadIdx.x >> 5;
     const int q = g.q, q2 = 2 * q;
     const T qT = (T)q;
@@ -554,6 +363,8 @@ __global__ void __launch_bounds__(32 * (C0 + Q2MAX - 1)) k_spread_slab(NGeom g, 
     const int ta_org = sb0 * C0 - q + 1, tb_org = sb1 * C1 - q + 1, cbase = sb2 * g.S2 - q + 1;
     const int T1 = C1 + q2 - 1;
     constexpr int E = Q2MAX + T1MAX + 32 + 1;    // staged values per point
+    const T par0 = (T)g.par[0], par1 = (T)g.par[1], par2 = (T)g.par[2];
+    const T nrm0 = (T)g.norm[0], nrm1 = (T)g.norm[1], nrm2 = (T)g.norm[2];
     C2<T> acc[T1MAX];
 #pragma unroll
     for (int tb = 0; tb < T1MAX; ++tb) { acc[tb].x = (T)0; acc[tb].y = (T)0; }
@@ -563,26 +374,37 @@ __global__ void __launch_bounds__(32 * (C0 + Q2MAX - 1)) k_spread_slab(NGeom g, 
         for (int t = threadIdx.x; t < np * E; t += blockDim.x) {
             const int p = t / E, e = t % E;
             const int64_t pi = cs + p;
-            const double u0 = u_sorted[3 * pi], u1 = u_sorted[3 * pi + 1], u2 = u_sorted[3 * pi + 2];
+            // cells and fractional coordinates (FP32: from the packed record, no FP64 work)
+            int c0, c1, c2;
+            T f0, f1, f2;
+            if constexpr (sizeof(T) == 4) {
+                const float4 pt = pts32[pi];
+                unpack_cells(pt.w, c0, c1, c2);
+                f0 = pt.x; f1 = pt.y; f2 = pt.z;
+            } else {
+                const double u0 = u_sorted[3 * pi], u1 = u_sorted[3 * pi + 1], u2 = u_sorted[3 * pi + 2];
+                c0 = cell_clamped(u0, g.cmax0);
+                c1 = cell_clamped(u1, g.cmax1);
+                c2 = min(max((int)floor(u2), 0), g.N[2] - 1);
+                f0 = u0 - c0; f1 = u1 - c1; f2 = u2 - c2;
+            }
             if (e < Q2MAX) {
-                const int a0p = cell_clamped(u0, g.cmax0) - q + 1;
-                sm.w0[p][e] = (e < q2) ? window<WIN, T>((T)(u0 - (a0p + e)), qT, (T)g.par[0], (T)g.norm[0]) : (T)0;
+                sm.w0[p][e] = (e < q2) ? window<WIN, T>(f0 + (T)(q - 1 - e), qT, par0, nrm0) : (T)0;
             } else if (e < Q2MAX + T1MAX) {
                 const int tb = e - Q2MAX;
-                const int rel = tb - (cell_clamped(u1, g.cmax1) - sb1 * C1);
-                T w = (T)0;
-                if (rel >= 0 && rel < q2) w = window<WIN, T>((T)(u1 - (tb_org + tb)), qT, (T)g.par[1], (T)g.norm[1]);
+                const int rel = tb - (c1 - sb1 * C1);      // tap index of row tb for this point
+                const T w = (rel >= 0 && rel < q2 && tb < T1) ? window<WIN, T>(f1 + (T)(q - 1 - rel), qT, par1, nrm1) : (T)0;
                 sm.w1[p][tb].x = w;
                 sm.w1[p][tb].y = w;
             } else if (e < Q2MAX + T1MAX + 32) {
                 const int L = e - Q2MAX - T1MAX;
-                const int rel = cbase + L - ((int)floor(u2) - q + 1);
-                sm.w2[p][L] = (rel >= 0 && rel < q2) ? window<WIN, T>((T)(u2 - (cbase + L)), qT, (T)g.par[2], (T)g.norm[2]) : (T)0;
+                const int rel = cbase + L - (c2 - q + 1);
+                sm.w2[p][L] = (rel >= 0 && rel < q2) ? window<WIN, T>(f2 + (T)(q - 1 - rel), qT, par2, nrm2) : (T)0;
             } else {
                 const double2 y = vals[perm[pi]];
                 sm.y[p].x = (T)y.x;
                 sm.y[p].y = (T)y.y;
-                sm.ta0[p] = cell_clamped(u0, g.cmax0) - sb0 * C0;
+                sm.ta0[p] = c0 - sb0 * C0;
             }
         }
         __syncthreads();
@@ -593,14 +415,20 @@ __global__ void __launch_bounds__(32 * (C0 + Q2MAX - 1)) k_spread_slab(NGeom g, 
             C2<T> z;
             z.x = sm.y[p].x * wz;
             z.y = sm.y[p].y * wz;
+            if constexpr (sizeof(T) == 4) {
+                const float4 *w1v = reinterpret_cast<const float4 *>(&sm.w1[p][0]);
 #pragma unroll
-            for (int tb = 0; tb < T1MAX; ++tb) {
-                const C2<T> w = sm.w1[p][tb];
-                if constexpr (sizeof(T) == 4) {
-                    acc[tb] = ffma2(w, z, acc[tb]);
-                } else {
-                    acc[tb].x = fma(w.x, z.x, acc[tb].x);
-                    acc[tb].y = fma(w.y, z.y, acc[tb].y);
+                for (int h = 0; h < T1MAX / 2; ++h) {
+                    const float4 w = w1v[h];
+                    acc[2 * h] = ffma2(make_float2(w.x, w.y), z, acc[2 * h]);
+                    acc[2 * h + 1] = ffma2(make_float2(w.z, w.w), z, acc[2 * h + 1]);
+                }
+            } else {
+#pragma unroll
+                for (int tb = 0; tb < T1MAX; ++tb) {
+                    const T w = sm.w1[p][tb].x;
+                    acc[tb].x = fma(w, z.x, acc[tb].x);
+                    acc[tb].y = fma(w, z.y, acc[tb].y);
                 }
             }
         }
@@ -622,6 +450,132 @@ __global__ void __launch_bounds__(32 * (C0 + Q2MAX - 1)) k_spread_slab(NGeom g, 
                 atomicAdd(&cell->x, acc[tb].x);
                 atomicAdd(&cell->y, acc[tb].y);
             }
+        }
+    }
+}
+
+// FP64 path: same lane layout as the FP32 kernels, binary64 throughout (coordinates from the
+// double grid coordinates); lane j evaluates tap j's weights once and shares them by shuffle.
+template <int WIN, int G>
+__global__ void __launch_bounds__(256) k_interp64(NGeom g, int64_t M, const double *__restrict__ u_sorted,
+                                                  const int *__restrict__ perm, const double2 *__restrict__ grid,
+                                                  double2 *__restrict__ vals) {
+    const int lane = threadIdx.x & 31, gl = lane & (G - 1);
+    const int q = g.q, q2 = 2 * q;
+    const double qd = (double)q;
+    const int64_t s1 = g.N[2], s0 = (int64_t)g.rows[1] * g.N[2];
+    constexpr int PPW = 32 / G;
+    const int64_t warp0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / 32;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) / 32;
+    for (int64_t base = warp0 * PPW; base < M; base += nwarps * PPW) {
+        const int64_t i = base + lane / G;
+        const bool live = i < M;
+        const int64_t ii = live ? i : M - 1;
+        const double u0 = u_sorted[3 * ii], u1 = u_sorted[3 * ii + 1], u2 = u_sorted[3 * ii + 2];
+        const int a0 = cell_clamped(u0, g.cmax0) - q + 1, a1 = cell_clamped(u1, g.cmax1) - q + 1;
+        const int a2 = min(max((int)floor(u2), 0), g.N[2] - 1) - q + 1;
+        const bool tap = gl < q2;
+        const double w0_own = tap ? window<WIN, double>(u0 - (a0 + gl), qd, g.par[0], g.norm[0]) : 0.0;
+        const double w1_own = tap ? window<WIN, double>(u1 - (a1 + gl), qd, g.par[1], g.norm[1]) : 0.0;
+        const double w2 = tap ? window<WIN, double>(u2 - (a2 + gl), qd, g.par[2], g.norm[2]) : 0.0;
+        const int col = tap ? wrap_index(a2 + gl, g.N[2]) : 0;
+        double w1[G];
+        int off1[G];
+#pragma unroll
+        for (int b = 0; b < G; ++b) {
+            w1[b] = __shfl_sync(0xffffffffu, w1_own, b, G);
+            off1[b] = (b < q2) ? row_of(a1 + b, g.first[1], g.rows[1], g.N[1]) * (int)s1 + col : col;
+        }
+        double ax = 0.0, ay = 0.0;
+        for (int a = 0; a < q2; ++a) {
+            const double w0 = __shfl_sync(0xffffffffu, w0_own, a, G);
+            const double2 *rowp = grid + row_of(a0 + a, g.first[0], g.rows[0], g.N[0]) * s0;
+            double rx = 0.0, ry = 0.0;
+#pragma unroll
+            for (int b = 0; b < G; ++b)
+                if (b < q2) {
+                    const double2 v = __ldg(rowp + off1[b]);
+                    rx = fma(w1[b], v.x, rx);
+                    ry = fma(w1[b], v.y, ry);
+                }
+            ax = fma(w0, rx, ax);
+            ay = fma(w0, ry, ay);
+        }
+        ax *= w2;
+        ay *= w2;
+#pragma unroll
+        for (int o = G / 2; o > 0; o >>= 1) {
+            ax += __shfl_xor_sync(0xffffffffu, ax, o);
+            ay += __shfl_xor_sync(0xffffffffu, ay, o);
+        }
+        if (live && gl == 0) vals[perm[i]] = make_double2(ax, ay);
+    }
+}
+
+template <int WIN, int G>
+__global__ void __launch_bounds__(256) k_grad64(NGeom g, int64_t M, const double *__restrict__ u_sorted,
+                                                const int *__restrict__ perm, const unsigned long long *__restrict__ r2max,
+                                                const double2 *__restrict__ grid, const double2 *__restrict__ gout,
+                                                double *__restrict__ gxyz) {
+    const int lane = threadIdx.x & 31, gl = lane & (G - 1);
+    const int q = g.q, q2 = 2 * q;
+    const double qd = (double)q;
+    const int64_t s1 = g.N[2], s0 = (int64_t)g.rows[1] * g.N[2];
+    double rho = sqrt(__longlong_as_double((long long)*r2max)) * (1.0 + 0x1p-20);
+    if (!(rho > 0.0)) rho = 1.0;
+    constexpr int PPW = 32 / G;
+    const int64_t warp0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / 32;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) / 32;
+    for (int64_t base = warp0 * PPW; base < M; base += nwarps * PPW) {
+        const int64_t i = base + lane / G;
+        const bool live = i < M;
+        const int64_t ii = live ? i : M - 1;
+        const double u0 = u_sorted[3 * ii], u1 = u_sorted[3 * ii + 1], u2 = u_sorted[3 * ii + 2];
+        const int a0 = cell_clamped(u0, g.cmax0) - q + 1, a1 = cell_clamped(u1, g.cmax1) - q + 1;
+        const int a2 = min(max((int)floor(u2), 0), g.N[2] - 1) - q + 1;
+        const bool tap = gl < q2;
+        const double x0 = u0 - (a0 + gl), x1 = u1 - (a1 + gl), x2 = u2 - (a2 + gl);
+        const double w0_own = tap ? window<WIN, double>(x0, qd, g.par[0], g.norm[0]) : 0.0;
+        const double d0_own = tap ? window_deriv<WIN, double>(x0, qd, g.par[0], g.norm[0]) : 0.0;
+        const double w1_own = tap ? window<WIN, double>(x1, qd, g.par[1], g.norm[1]) : 0.0;
+        const double d1_own = tap ? window_deriv<WIN, double>(x1, qd, g.par[1], g.norm[1]) : 0.0;
+        const double w2 = tap ? window<WIN, double>(x2, qd, g.par[2], g.norm[2]) : 0.0;
+        const double d2 = tap ? window_deriv<WIN, double>(x2, qd, g.par[2], g.norm[2]) : 0.0;
+        const int col = tap ? wrap_index(a2 + gl, g.N[2]) : 0;
+        double fx = 0, fy = 0, ax = 0, ay = 0, bx = 0, by = 0;
+        for (int a = 0; a < q2; ++a) {
+            const double w0 = __shfl_sync(0xffffffffu, w0_own, a, G);
+            const double dw0 = __shfl_sync(0xffffffffu, d0_own, a, G);
+            const double2 *rowp = grid + row_of(a0 + a, g.first[0], g.rows[0], g.N[0]) * s0 + col;
+            double rx = 0, ry = 0, sx = 0, sy = 0;
+#pragma unroll
+            for (int b = 0; b < G; ++b) {
+                const double w1 = __shfl_sync(0xffffffffu, w1_own, b, G);
+                const double d1 = __shfl_sync(0xffffffffu, d1_own, b, G);
+                if (b < q2) {
+                    const double2 v = __ldg(rowp + row_of(a1 + b, g.first[1], g.rows[1], g.N[1]) * s1);
+                    rx = fma(w1, v.x, rx); ry = fma(w1, v.y, ry);
+                    sx = fma(d1, v.x, sx); sy = fma(d1, v.y, sy);
+                }
+            }
+            fx = fma(w0, rx, fx); fy = fma(w0, ry, fy);
+            ax = fma(dw0, rx, ax); ay = fma(dw0, ry, ay);
+            bx = fma(w0, sx, bx); by = fma(w0, sy, by);
+        }
+        double f2x = d2 * fx, f2y = d2 * fy;
+        ax *= w2; ay *= w2; bx *= w2; by *= w2;
+#pragma unroll
+        for (int o = G / 2; o > 0; o >>= 1) {
+            ax += __shfl_xor_sync(0xffffffffu, ax, o);
+            ay += __shfl_xor_sync(0xffffffffu, ay, o);
+            bx += __shfl_xor_sync(0xffffffffu, bx, o);
+            by += __shfl_xor_sync(0xffffffffu, by, o);
+            f2x += __shfl_xor_sync(0xffffffffu, f2x, o);
+            f2y += __shfl_xor_sync(0xffffffffu, f2y, o);
+        }
+        if (live && gl == 0) {
+            const int dst = perm[i];
+            write_point_gradient(g, rho, u0, u1, u2, ax, ay, bx, by, f2x, f2y, gout[dst], gxyz + 3 * (int64_t)dst);
         }
     }
 }
@@ -655,35 +609,26 @@ int nufft_blocks(int64_t M, int G) {
     return (int)b;
 }
 
-int col_blocks(const sgl_plan *p) {
-    int64_t b = (p->max_items + 7) / 8;
-    if (b > 152 * 8) b = 152 * 8;
-    return (int)std::max<int64_t>(b, 1);
-}
-
 template <typename T, int WIN>
 cudaError_t interp_t(sgl_plan *p, double2 *vals) {
     NGeom g = make_geom(p);
     if constexpr (sizeof(T) == 4) {
         const float2 *gridf = (const float2 *)p->b.bufA;
-        if (p->q <= 4) {
-            k_interp_col<WIN, 8, 4><<<col_blocks(p), 256, 0, p->stream>>>(g, p->b.items, p->b.n_items, p->b.u_sorted, p->b.perm, gridf, vals);
-            p->launches += 1;
-            return cudaGetLastError();
-        }
-        if (p->q <= 8) {
-            k_interp_col<WIN, 16, 4><<<col_blocks(p), 256, 0, p->stream>>>(g, p->b.items, p->b.n_items, p->b.u_sorted, p->b.perm, gridf, vals);
-            p->launches += 1;
-            return cudaGetLastError();
-        }
+        const int q2 = 2 * p->q;
+        if (q2 <= 8) k_interp32<WIN, 8><<<nufft_blocks(p->M, 8), 256, 0, p->stream>>>(g, p->M, p->b.pts32, p->b.perm, gridf, vals);
+        else if (q2 <= 16) k_interp32<WIN, 16><<<nufft_blocks(p->M, 16), 256, 0, p->stream>>>(g, p->M, p->b.pts32, p->b.perm, gridf, vals);
+        else k_interp32<WIN, 32><<<nufft_blocks(p->M, 32), 256, 0, p->stream>>>(g, p->M, p->b.pts32, p->b.perm, gridf, vals);
+        p->launches += 1;
+        return cudaGetLastError();
+    } else {
+        const double2 *gridd = (const double2 *)p->b.bufA;
+        const int q2 = 2 * p->q;
+        if (q2 <= 8) k_interp64<WIN, 8><<<nufft_blocks(p->M, 8), 256, 0, p->stream>>>(g, p->M, p->b.u_sorted, p->b.perm, gridd, vals);
+        else if (q2 <= 16) k_interp64<WIN, 16><<<nufft_blocks(p->M, 16), 256, 0, p->stream>>>(g, p->M, p->b.u_sorted, p->b.perm, gridd, vals);
+        else k_interp64<WIN, 32><<<nufft_blocks(p->M, 32), 256, 0, p->stream>>>(g, p->M, p->b.u_sorted, p->b.perm, gridd, vals);
+        p->launches += 1;
+        return cudaGetLastError();
     }
-    const C2<T> *grid = (const C2<T> *)p->b.bufA;
-    const int q2 = 2 * p->q;
-    if (q2 <= 8) k_interp<T, WIN, 8><<<nufft_blocks(p->M, 8), 256, 0, p->stream>>>(g, p->M, p->b.u_sorted, p->b.perm, grid, vals);
-    else if (q2 <= 16) k_interp<T, WIN, 16><<<nufft_blocks(p->M, 16), 256, 0, p->stream>>>(g, p->M, p->b.u_sorted, p->b.perm, grid, vals);
-    else k_interp<T, WIN, 32><<<nufft_blocks(p->M, 32), 256, 0, p->stream>>>(g, p->M, p->b.u_sorted, p->b.perm, grid, vals);
-    p->launches += 1;
-    return cudaGetLastError();
 }
 
 template <typename T, int WIN, int Q2MAX, int C0, int C1>
@@ -691,7 +636,7 @@ cudaError_t spread_slab_t(sgl_plan *p, const NGeom &g, const double2 *vals) {
     if (g.C0 != C0 || g.C1 != C1) return cudaErrorInvalidConfiguration;
     const int threads = 32 * (C0 + 2 * p->q - 1);
     k_spread_slab<T, WIN, Q2MAX, C0, C1><<<(unsigned)p->bins.nsuper, threads, 0, p->stream>>>(
-        g, p->b.bin_off, p->M, p->bins.nsuper, p->b.u_sorted, p->b.perm, vals, (C2<T> *)p->b.bufA);
+        g, p->b.bin_off, p->M, p->bins.nsuper, p->b.u_sorted, p->b.pts32, p->b.perm, vals, (C2<T> *)p->b.bufA);
     p->launches += 1;
     return cudaGetLastError();
 }
@@ -718,26 +663,24 @@ cudaError_t spread_t(sgl_plan *p, const double2 *vals) {
 template <typename T, int WIN>
 cudaError_t grad_t(sgl_plan *p, const double2 *gout, double *gxyz) {
     NGeom g = make_geom(p);
+    const int q2 = 2 * p->q;
     if constexpr (sizeof(T) == 4) {
         const float2 *gridf = (const float2 *)p->b.bufA;
-        if (p->q <= 4) {
-            k_grad_col<WIN, 8, 2><<<col_blocks(p), 256, 0, p->stream>>>(g, p->b.items, p->b.n_items, p->b.u_sorted, p->b.perm,
-                                                                         p->b.r2max, gridf, gout, gxyz);
-            p->launches += 1;
-            return cudaGetLastError();
-        }
-        if (p->q <= 8) {
-            k_grad_col<WIN, 16, 2><<<col_blocks(p), 256, 0, p->stream>>>(g, p->b.items, p->b.n_items, p->b.u_sorted, p->b.perm,
-                                                                          p->b.r2max, gridf, gout, gxyz);
-            p->launches += 1;
-            return cudaGetLastError();
-        }
+        if (q2 <= 8)
+            k_grad32<WIN, 8><<<nufft_blocks(p->M, 8), 256, 0, p->stream>>>(g, p->M, p->b.pts32, p->b.perm, p->b.r2max, gridf, gout, gxyz);
+        else if (q2 <= 16)
+            k_grad32<WIN, 16><<<nufft_blocks(p->M, 16), 256, 0, p->stream>>>(g, p->M, p->b.pts32, p->b.perm, p->b.r2max, gridf, gout, gxyz);
+        else
+            k_grad32<WIN, 32><<<nufft_blocks(p->M, 32), 256, 0, p->stream>>>(g, p->M, p->b.pts32, p->b.perm, p->b.r2max, gridf, gout, gxyz);
+    } else {
+        const double2 *gridd = (const double2 *)p->b.bufA;
+        if (q2 <= 8)
+            k_grad64<WIN, 8><<<nufft_blocks(p->M, 8), 256, 0, p->stream>>>(g, p->M, p->b.u_sorted, p->b.perm, p->b.r2max, gridd, gout, gxyz);
+        else if (q2 <= 16)
+            k_grad64<WIN, 16><<<nufft_blocks(p->M, 16), 256, 0, p->stream>>>(g, p->M, p->b.u_sorted, p->b.perm, p->b.r2max, gridd, gout, gxyz);
+        else
+            k_grad64<WIN, 32><<<nufft_blocks(p->M, 32), 256, 0, p->stream>>>(g, p->M, p->b.u_sorted, p->b.perm, p->b.r2max, gridd, gout, gxyz);
     }
-    const C2<T> *grid = (const C2<T> *)p->b.bufA;
-    const int q2 = 2 * p->q;
-    if (q2 <= 8) k_grad<T, WIN, 8><<<nufft_blocks(p->M, 8), 256, 0, p->stream>>>(g, p->M, p->b.u_sorted, p->b.perm, p->b.r2max, grid, gout, gxyz);
-    else if (q2 <= 16) k_grad<T, WIN, 16><<<nufft_blocks(p->M, 16), 256, 0, p->stream>>>(g, p->M, p->b.u_sorted, p->b.perm, p->b.r2max, grid, gout, gxyz);
-    else k_grad<T, WIN, 32><<<nufft_blocks(p->M, 32), 256, 0, p->stream>>>(g, p->M, p->b.u_sorted, p->b.perm, p->b.r2max, grid, gout, gxyz);
     p->launches += 1;
     return cudaGetLastError();
 }

@@ -153,13 +153,19 @@ __global__ void k_scan_final(const int *__restrict__ cnt, int64_t n, const int *
 }
 
 __global__ void k_scatter_points(int64_t M, const double *__restrict__ u_tmp, const int *__restrict__ bin_of,
-                                 const int *__restrict__ rank_of, const int *__restrict__ off,
-                                 double *__restrict__ u_sorted, int *__restrict__ perm) {
+                                 const int *__restrict__ rank_of, const int *__restrict__ off, PointGeom g,
+                                 double *__restrict__ u_sorted, float4 *__restrict__ pts32, int *__restrict__ perm) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < M; i += (int64_t)gridDim.x * blockDim.x) {
         const int pos = off[bin_of[i]] + rank_of[i];
-        u_sorted[3 * pos] = u_tmp[3 * i];
-        u_sorted[3 * pos + 1] = u_tmp[3 * i + 1];
-        u_sorted[3 * pos + 2] = u_tmp[3 * i + 2];
+        const double u0 = u_tmp[3 * i], u1 = u_tmp[3 * i + 1], u2 = u_tmp[3 * i + 2];
+        u_sorted[3 * pos] = u0;
+        u_sorted[3 * pos + 1] = u1;
+        u_sorted[3 * pos + 2] = u2;
+        // cells as in the bin key; fractional parts relative to them (exact in binary64, rounded once)
+        const int c0 = min(max((int)floor(u0), 0), g.cmax0);
+        const int c1 = min(max((int)floor(u1), 0), g.cmax1);
+        const int c2 = min(max((int)floor(u2), 0), g.N[2] - 1);
+        pts32[pos] = make_float4((float)(u0 - c0), (float)(u1 - c1), (float)(u2 - c2), __int_as_float(c0 | (c1 << 10) | (c2 << 20)));
         perm[pos] = (int)i;
     }
 }
@@ -214,7 +220,8 @@ cudaError_t launch_points(sgl_plan *p, const double *xyz, int64_t M) {
     if (M > 0) {
         k_transform_points<<<grid_blocks(M, kThreads), kThreads, 0, s>>>(xyz, M, b.r2max, g, b.u_tmp, b.bin_of, b.rank_of, b.bin_count);
         scan(b.bin_count, p->nbins, b.scan_tmp, b.bin_off, s);
-        k_scatter_points<<<grid_blocks(M, kThreads), kThreads, 0, s>>>(M, b.u_tmp, b.bin_of, b.rank_of, b.bin_off, b.u_sorted, b.perm);
+        k_scatter_points<<<grid_blocks(M, kThreads), kThreads, 0, s>>>(M, b.u_tmp, b.bin_of, b.rank_of, b.bin_off, g, b.u_sorted,
+                                                                       b.pts32, b.perm);
         k_item_count<<<grid_blocks(p->nbins, kThreads), kThreads, 0, s>>>(b.bin_count, p->nbins, b.item_count);
         scan(b.item_count, p->nbins, b.scan_tmp, b.item_off, s);
         k_item_fill<<<grid_blocks(p->nbins, kThreads), kThreads, 0, s>>>(b.bin_count, b.bin_off, b.item_count, b.item_off,
