@@ -296,7 +296,6 @@ sgl_status sgl_plan_create(sgl_plan **out, int B, int64_t M_max, int precision, 
         g.nsuper = (int64_t)g.nsb[0] * g.nsb[1] * g.nsb[2];
         g.nbins = g.nsuper * g.C0 * g.C1;
         p->nbins = g.nbins;
-        p->max_items = M_max / kItemPoints + std::min<int64_t>(M_max, g.nbins) + 1;
     }
 
     // ---- device allocations
@@ -343,10 +342,6 @@ sgl_status sgl_plan_create(sgl_plan **out, int B, int64_t M_max, int precision, 
     ALLOC(b.bin_count, (size_t)p->nbins);
     ALLOC(b.bin_off, (size_t)p->nbins);
     ALLOC(b.scan_tmp, (size_t)(p->nbins / 2048 + 2));
-    ALLOC(b.item_count, (size_t)p->nbins);
-    ALLOC(b.item_off, (size_t)p->nbins);
-    ALLOC(b.items, (size_t)p->max_items);
-    ALLOC(b.n_items, 1);
     if (flags & SGL_FLAG_HOST_IO) {
         ALLOC(b.io_xyz, 3 * Mc);
         ALLOC(b.io_coef, (size_t)(2 * p->Nc));

@@ -89,8 +89,62 @@ struct ZetaSrc {
 
 template <typename C> __device__ __forceinline__ double2 to_d2(C v) { return make_double2((double)v.x, (double)v.y); }
 
+template <typename T, int R>
+__device__ __forceinline__ void dft_r(C2<T> *x, int s) {
+    if constexpr (R == 2) dft2<T>(x);
+    else if constexpr (R == 3) dft3<T>(x, s);
+    else if constexpr (R == 4) dft4<T>(x, s);
+    else if constexpr (R == 5) dft5<T>(x, s);
+    else dft8<T>(x, s);
+}
+
+// q / d and q % d for d > 0; a shift and a mask when d is a power of two
+__device__ __forceinline__ void divmod(int q, int d, int &quo, int &rem) {
+    if ((d & (d - 1)) == 0) {
+        const int sh = __ffs(d) - 1;
+        quo = q >> sh;
+        rem = q & (d - 1);
+    } else {
+        quo = q / d;
+        rem = q - quo * d;
+    }
+}
+
+// One decimation-in-frequency pass of radix R over every line of the tile (in place):
+// sub-problem length L, span S = L / R; butterfly (g, nn) combines positions g L + nn + t S.
+template <typename T, int R>
+__device__ __forceinline__ void dif_stage(C2<T> *buf, int LS, int TB, int N, int L, int sign, const C2<T> *__restrict__ tw) {
+    const int S = L / R;
+    const int per_line = N / R;
+    const int stride_tw = N / L;
+    for (int w = threadIdx.x; w < TB * per_line; w += blockDim.x) {
+        int bl, j, g, nn;
+        divmod(w, per_line, bl, j);
+        divmod(j, S, g, nn);
+        C2<T> *base = buf + bl * LS + g * L + nn;
+        C2<T> x[R];
+#pragma unroll
+        for (int t = 0; t < R; ++t) x[t] = base[t * S];
+        dft_r<T, R>(x, sign);
+        base[0] = x[0];
+        const int tstep = nn * stride_tw;         // nn * u * stride_tw < N: no reduction needed
+#pragma unroll
+        for (int u = 1; u < R; ++u) {
+            C2<T> wv = tw[tstep * u];
+            if (sign < 0) wv.y = -wv.y;
+            base[u * S] = mul<T>(x[u], wv);
+        }
+    }
+}
+
+__device__ __forceinline__ int wrapN(int e, int N) {
+    if (e < 0) e += N;
+    if (e >= N) e -= N;
+    return e;
+}
+
 template <typename T, typename InC, typename OutC, int MODE>
-__global__ void __launch_bounds__(256) k_fft_pass(FftPass ps, int TB, const InC *__restrict__ in, OutC *__restrict__ out,
+__global__ void __launch_bounds__(256) k_fft_pass(FftPass ps, int TB, int lgTB, const InC *__restrict__ in, OutC *__restrict__ out,
                                                   ZetaSrc zs, int scale_on_output) {
     extern __shared__ unsigned char smem_raw[];
     C2<T> *buf = reinterpret_cast<C2<T> *>(smem_raw);
@@ -102,38 +156,45 @@ __global__ void __launch_bounds__(256) k_fft_pass(FftPass ps, int TB, const InC 
     const int nlines = (int)min((int64_t)TB, ps.nb_inner - inner0);
     const int tid = threadIdx.x, NT = blockDim.x;
 
-    // ---- load (zero outside the input window), optional scale on input
+    // ---- load: position pos of a line holds input element e = pos - in_first (mod N), zero if e >= L_in
     const bool in_elem_fast = (MODE == LOAD_STRIDED) && (ps.in_se == 1);
-    for (int idx = tid; idx < TB * N; idx += NT) {
-        int bl, pos;
-        if (in_elem_fast) { bl = idx / N; pos = idx % N; } else { bl = idx % TB; pos = idx / TB; }
-        int e = pos - ps.in_first;
-        e %= N;
-        if (e < 0) e += N;
-        C2<T> v = mk<T>((T)0, (T)0);
-        if (bl < nlines && e < ps.L_in) {
-            const int64_t inner = inner0 + bl;
-            double2 d;
-            if (MODE == LOAD_ZETA) {
-                // line = (k1, m) over (2K1+1)^2, element = k0 + K0; eta mirrored from zeta
-                const int W = 2 * zs.K1 + 1;
-                const int mi = (int)(inner % W);
-                const int k1 = (int)(inner / W) - zs.K1;
-                const int k0 = e - zs.K0;
-                d = zs.zeta[((int64_t)abs(k0) * (zs.K1 + 1) + abs(k1)) * W + mi];
-                if (k1 < 0 && ((mi - zs.K1) & 1)) { d.x = -d.x; d.y = -d.y; }
-            } else {
-                d = to_d2(in[outer * ps.in_so + inner * ps.in_si + (int64_t)e * ps.in_se]);
+    const int bl_fast = tid & (TB - 1), pos_step = NT >> lgTB;
+    for (int it = 0; it < (in_elem_fast ? TB : 1); ++it) {
+        for (int k = in_elem_fast ? tid : (tid >> lgTB); k < N; k += in_elem_fast ? NT : pos_step) {
+            const int bl = in_elem_fast ? it : bl_fast;
+            const int pos = k;
+            const int e = wrapN(pos - ps.in_first, N);
+            C2<T> v = mk<T>((T)0, (T)0);
+            if (bl < nlines && e < ps.L_in) {
+                const int64_t inner = inner0 + bl;
+                double2 d;
+                if (MODE == LOAD_ZETA) {
+                    // line = (k1, m) over (2K1+1)^2, element = k0 + K0; eta mirrored from zeta
+                    const int W = 2 * zs.K1 + 1;
+                    const int mi = (int)(inner % W);
+                    const int k1 = (int)(inner / W) - zs.K1;
+                    const int k0 = e - zs.K0;
+                    d = zs.zeta[((int64_t)abs(k0) * (zs.K1 + 1) + abs(k1)) * W + mi];
+                    if (k1 < 0 && ((mi - zs.K1) & 1)) { d.x = -d.x; d.y = -d.y; }
+                } else if (sizeof(InC) == sizeof(C2<T>) && (scale_on_output || (!ps.elem_scale && !ps.line_scale))) {
+                    // same precision in and out, no factor: no conversion
+                    const InC x = in[outer * ps.in_so + inner * ps.in_si + (int64_t)e * ps.in_se];
+                    v = mk<T>((T)x.x, (T)x.y);
+                    buf[bl * LS + pos] = v;
+                    continue;
+                } else {
+                    d = to_d2(in[outer * ps.in_so + inner * ps.in_si + (int64_t)e * ps.in_se]);
+                }
+                if (!scale_on_output) {
+                    double f = 1.0;
+                    if (ps.elem_scale) f *= ps.elem_scale[e];
+                    if (ps.line_scale) f *= ps.line_scale[outer * ps.nb_inner + inner];
+                    d.x *= f; d.y *= f;
+                }
+                v = mk<T>((T)d.x, (T)d.y);
             }
-            if (!scale_on_output) {
-                double f = 1.0;
-                if (ps.elem_scale) f *= ps.elem_scale[e];
-                if (ps.line_scale) f *= ps.line_scale[outer * ps.nb_inner + inner];
-                d.x *= f; d.y *= f;
-            }
-            v = mk<T>((T)d.x, (T)d.y);
+            buf[bl * LS + pos] = v;
         }
-        buf[bl * LS + pos] = v;
     }
     __syncthreads();
 
@@ -141,75 +202,66 @@ __global__ void __launch_bounds__(256) k_fft_pass(FftPass ps, int TB, const InC 
     const C2<T> *tw = reinterpret_cast<const C2<T> *>(ps.tw);
     int L = N;
     for (int st = 0; st < ps.nrad; ++st) {
-        const int r = ps.rad[st];
-        const int S = L / r;
-        const int per_line = N / r;
-        const int stride_tw = N / L;
-        for (int w = tid; w < TB * per_line; w += NT) {
-            const int bl = w / per_line, j = w % per_line;
-            const int g = j / S, nn = j % S;
-            C2<T> *base = buf + bl * LS + g * L + nn;
-            C2<T> x[8];
-            for (int t = 0; t < r; ++t) x[t] = base[t * S];
-            switch (r) {
-                case 2: dft2<T>(x); break;
-                case 3: dft3<T>(x, ps.sign); break;
-                case 4: dft4<T>(x, ps.sign); break;
-                case 5: dft5<T>(x, ps.sign); break;
-                default: dft8<T>(x, ps.sign); break;
-            }
-            base[0] = x[0];
-            for (int u = 1; u < r; ++u) {
-                C2<T> wv = tw[(int)(((int64_t)nn * u * stride_tw) % N)];
-                if (ps.sign < 0) wv.y = -wv.y;
-                base[u * S] = mul<T>(x[u], wv);
-            }
+        switch (ps.rad[st]) {
+            case 2: dif_stage<T, 2>(buf, LS, TB, N, L, ps.sign, tw); L /= 2; break;
+            case 3: dif_stage<T, 3>(buf, LS, TB, N, L, ps.sign, tw); L /= 3; break;
+            case 4: dif_stage<T, 4>(buf, LS, TB, N, L, ps.sign, tw); L /= 4; break;
+            case 5: dif_stage<T, 5>(buf, LS, TB, N, L, ps.sign, tw); L /= 5; break;
+            default: dif_stage<T, 8>(buf, LS, TB, N, L, ps.sign, tw); L /= 8; break;
         }
         __syncthreads();
-        L = S;
     }
 
     // ---- store the output window (digit-reversed slots), optional scale on output
     const bool out_elem_fast = (ps.out_se == 1);
-    for (int idx = tid; idx < TB * ps.L_out; idx += NT) {
-        int bl, e;
-        if (out_elem_fast) { bl = idx / ps.L_out; e = idx % ps.L_out; } else { bl = idx % TB; e = idx / TB; }
-        if (bl >= nlines) continue;
-        const int64_t inner = inner0 + bl;
-        int pos = (e + ps.out_first) % N;
-        if (pos < 0) pos += N;
-        const C2<T> v = buf[bl * LS + ps.rev[pos]];
-        double vx = (double)v.x, vy = (double)v.y;
-        if (scale_on_output) {
-            double f = 1.0;
-            if (ps.elem_scale) f *= ps.elem_scale[e];
-            if (ps.line_scale) f *= ps.line_scale[outer * ps.nb_inner + inner];
-            vx *= f; vy *= f;
+    for (int it = 0; it < (out_elem_fast ? TB : 1); ++it) {
+        for (int k = out_elem_fast ? tid : (tid >> lgTB); k < ps.L_out; k += out_elem_fast ? NT : pos_step) {
+            const int bl = out_elem_fast ? it : bl_fast;
+            if (bl >= nlines) continue;
+            const int e = k;
+            const int64_t inner = inner0 + bl;
+            const int pos = wrapN(e + ps.out_first, N);
+            const C2<T> v = buf[bl * LS + __ldg(ps.rev + pos)];
+            if (sizeof(OutC) == sizeof(C2<T>) && !(scale_on_output && (ps.elem_scale || ps.line_scale))) {
+                OutC o;
+                o.x = v.x;
+                o.y = v.y;
+                out[outer * ps.out_so + inner * ps.out_si + (int64_t)e * ps.out_se] = o;
+                continue;
+            }
+            double vx = (double)v.x, vy = (double)v.y;
+            if (scale_on_output) {
+                double f = 1.0;
+                if (ps.elem_scale) f *= ps.elem_scale[e];
+                if (ps.line_scale) f *= ps.line_scale[outer * ps.nb_inner + inner];
+                vx *= f; vy *= f;
+            }
+            OutC o;
+            o.x = (decltype(o.x))vx;
+            o.y = (decltype(o.y))vy;
+            out[outer * ps.out_so + inner * ps.out_si + (int64_t)e * ps.out_se] = o;
         }
-        OutC o;
-        o.x = (decltype(o.x))vx;
-        o.y = (decltype(o.y))vy;
-        out[outer * ps.out_so + inner * ps.out_si + (int64_t)e * ps.out_se] = o;
     }
 }
 
-int lines_per_tile(int N) {
-    int tb = 4096 / N;
-    if (tb < 8) tb = 8;
-    if (tb > 64) tb = 64;
-    return tb;
+// lines per tile: a power of two in [8, 64] with about 4096 elements per tile
+int lines_per_tile(int N, int &lg) {
+    lg = 3;
+    while (lg < 6 && (1 << (lg + 1)) * N <= 4096) ++lg;
+    return 1 << lg;
 }
 
 template <typename T, typename InC, typename OutC, int MODE>
 cudaError_t run_pass(sgl_plan *p, FftPass ps, const void *in, void *out, ZetaSrc zs, int scale_on_output) {
-    const int TB = lines_per_tile(ps.N);
+    int lgTB = 0;
+    const int TB = lines_per_tile(ps.N, lgTB);
     const size_t smem = (size_t)TB * (ps.N + 1) * sizeof(C2<T>);
     auto kern = k_fft_pass<T, InC, OutC, MODE>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     const int64_t tiles = ps.nb_outer * ((ps.nb_inner + TB - 1) / TB);
     if (tiles <= 0) return cudaSuccess;
-    kern<<<(unsigned)tiles, 256, smem, p->stream>>>(ps, TB, (const InC *)in, (OutC *)out, zs, scale_on_output);
+    kern<<<(unsigned)tiles, 256, smem, p->stream>>>(ps, TB, lgTB, (const InC *)in, (OutC *)out, zs, scale_on_output);
     p->launches += 1;
     return cudaGetLastError();
 }

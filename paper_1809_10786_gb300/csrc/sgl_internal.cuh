@@ -13,8 +13,6 @@ namespace sgl {
 constexpr double kPi = 3.14159265358979323846;
 constexpr int kMaxQ = 16;          // 2q taps per axis must fit one warp
 constexpr int kMaxRadices = 16;
-constexpr int kItemPoints = 8;     // points per interpolation work item (one column bin)
-
 // Spatial bins: a column bin holds the points of one (i0, i1) cell column and one chunk of
 // S2 = 33 - 2q cells on the azimuthal axis, so the taps of all its points cover one warp's
 // 32 lanes on that axis and share their (2q)^2 rows.  C0 x C1 columns form a super-bin.
@@ -86,9 +84,6 @@ struct Buffers {
     int *bin_of, *rank_of;     // per input point
     int *bin_count, *bin_off;  // [nbins]
     int *scan_tmp;             // block sums
-    int *item_count, *item_off; // per bin: interpolation work items and their prefix sum
-    int2 *items;               // (first sorted point, count <= kItemPoints) per work item
-    int *n_items;              // total work items (device)
     // host-IO staging
     double *io_xyz, *io_coef, *io_vals, *io_grad;
 };
@@ -117,7 +112,6 @@ struct sgl_plan {
     sgl::Axis ax[3];
     sgl::BinGeom bins;
     int64_t nbins;
-    int64_t max_items;
     int64_t work_bytes;
     bool points_set;
     sgl::Buffers b;

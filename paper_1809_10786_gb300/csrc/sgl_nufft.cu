@@ -152,7 +152,9 @@ __device__ __forceinline__ void unpack_cells(float w, int &c0, int &c1, int &c2)
     c2 = (v >> 20) & 1023;
 }
 
-template <int WIN, int G>
+// N2T: the axis-2 length (the row stride) as a compile-time constant (0: read it from g) -- with
+// it the unrolled row loads use immediate offsets instead of per-load address arithmetic
+template <int WIN, int G, bool LIN1, int N2T>
 __global__ void __launch_bounds__(256) k_interp32(NGeom g, int64_t M, const float4 *__restrict__ pts, const int *__restrict__ perm,
                                                   const float2 *__restrict__ grid, double2 *__restrict__ vals) {
     const int lane = threadIdx.x & 31, gl = lane & (G - 1);
@@ -160,14 +162,16 @@ __global__ void __launch_bounds__(256) k_interp32(NGeom g, int64_t M, const floa
     const float qf = (float)q;
     const float par0 = (float)g.par[0], par1 = (float)g.par[1], par2 = (float)g.par[2];
     const float nrm0 = (float)g.norm[0], nrm1 = (float)g.norm[1], nrm2 = (float)g.norm[2];
-    const int64_t s1 = g.N[2], s0 = (int64_t)g.rows[1] * g.N[2];
+    const int64_t s1 = N2T ? N2T : g.N[2], s0 = (int64_t)g.rows[1] * s1;
+    // warps sweep the bin-sorted points in grid-stride order (consecutive warps: neighbouring points)
     constexpr int PPW = 32 / G;
     const int64_t warp0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / 32;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) / 32;
+    const int64_t end = M;
     for (int64_t base = warp0 * PPW; base < M; base += nwarps * PPW) {
         const int64_t i = base + lane / G;
         const bool live = i < M;
-        const float4 pt = pts[live ? i : M - 1];
+        const float4 pt = pts[live ? i : end - 1];
         int c0, c1, c2;
         unpack_cells(pt.w, c0, c1, c2);
         const int a0 = c0 - q + 1, a1 = c1 - q + 1, a2 = c2 - q + 1;
@@ -176,23 +180,23 @@ __global__ void __launch_bounds__(256) k_interp32(NGeom g, int64_t M, const floa
         const float w0_own = tap ? window<WIN, float>(pt.x + off, qf, par0, nrm0) : 0.f;
         const float w1_own = tap ? window<WIN, float>(pt.y + off, qf, par1, nrm1) : 0.f;
         const float w2 = tap ? window<WIN, float>(pt.z + off, qf, par2, nrm2) : 0.f;
-        const int col = tap ? wrap_index(a2 + gl, g.N[2]) : 0;
+        const int col = tap ? wrap_index(a2 + gl, (int)s1) : 0;
         float2 w1p[G];
-        int off1[G];
 #pragma unroll
         for (int b = 0; b < G; ++b) {
             const float w = __shfl_sync(0xffffffffu, w1_own, b, G);
             w1p[b] = make_float2(w, w);
-            off1[b] = (b < q2) ? row_of(a1 + b, g.first[1], g.rows[1], g.N[1]) * (int)s1 + col : col;
         }
+        // LIN1: windowed axis 1, rows a1 + b stored contiguously from row a1 - first
+        const int64_t r1base = LIN1 ? (int64_t)(a1 - g.first[1]) * s1 + col : col;
         float2 acc = make_float2(0.f, 0.f);
         for (int a = 0; a < q2; ++a) {
             const float w0 = __shfl_sync(0xffffffffu, w0_own, a, G);
-            const float2 *rowp = grid + row_of(a0 + a, g.first[0], g.rows[0], g.N[0]) * s0;
+            const float2 *rowp = grid + row_of(a0 + a, g.first[0], g.rows[0], g.N[0]) * s0 + r1base;
             float2 rs = make_float2(0.f, 0.f);
 #pragma unroll
             for (int b = 0; b < G; ++b)
-                if (b < q2) rs = ffma2(w1p[b], __ldg(rowp + off1[b]), rs);
+                if (b < q2) rs = ffma2(w1p[b], __ldg(rowp + (LIN1 ? b * s1 : row_of(a1 + b, g.first[1], g.rows[1], g.N[1]) * s1)), rs);
             acc = ffma2(make_float2(w0, w0), rs, acc);
         }
         float x = acc.x * w2, y = acc.y * w2;
@@ -207,8 +211,10 @@ __global__ void __launch_bounds__(256) k_interp32(NGeom g, int64_t M, const floa
 
 // FP32 window-derivative interpolation: s, ds/du0, ds/du1 in one sweep of the rows, ds/du2 from
 // psi' on the lanes, then the chain rule in FP32 (sincospi of the torus coordinates).
-template <int WIN, int G>
-__global__ void __launch_bounds__(256) k_grad32(NGeom g, int64_t M, const float4 *__restrict__ pts, const int *__restrict__ perm,
+// N2T: the axis-2 length (the row stride) as a compile-time constant (0: read it from g) -- with
+// it the unrolled row loads use immediate offsets instead of per-load address arithmetic
+template <int WIN, int G, bool LIN1, int N2T>
+__global__ void __launch_bounds__(256, 3) k_grad32(NGeom g, int64_t M, const float4 *__restrict__ pts, const int *__restrict__ perm,
                                                 const unsigned long long *__restrict__ r2max, const float2 *__restrict__ grid,
                                                 const double2 *__restrict__ gout, double *__restrict__ gxyz) {
     const int lane = threadIdx.x & 31, gl = lane & (G - 1);
@@ -216,17 +222,19 @@ __global__ void __launch_bounds__(256) k_grad32(NGeom g, int64_t M, const float4
     const float qf = (float)q;
     const float par0 = (float)g.par[0], par1 = (float)g.par[1], par2 = (float)g.par[2];
     const float nrm0 = (float)g.norm[0], nrm1 = (float)g.norm[1], nrm2 = (float)g.norm[2];
-    const int64_t s1 = g.N[2], s0 = (int64_t)g.rows[1] * g.N[2];
+    const int64_t s1 = N2T ? N2T : g.N[2], s0 = (int64_t)g.rows[1] * s1;
     double rhod = sqrt(__longlong_as_double((long long)*r2max)) * (1.0 + 0x1p-20);
     if (!(rhod > 0.0)) rhod = 1.0;
     const float rho = (float)rhod;
+    // warps sweep the bin-sorted points in grid-stride order (consecutive warps: neighbouring points)
     constexpr int PPW = 32 / G;
     const int64_t warp0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / 32;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) / 32;
+    const int64_t end = M;
     for (int64_t base = warp0 * PPW; base < M; base += nwarps * PPW) {
         const int64_t i = base + lane / G;
         const bool live = i < M;
-        const float4 pt = pts[live ? i : M - 1];
+        const float4 pt = pts[live ? i : end - 1];
         int c0, c1, c2;
         unpack_cells(pt.w, c0, c1, c2);
         const int a0 = c0 - q + 1, a1 = c1 - q + 1, a2 = c2 - q + 1;
@@ -239,27 +247,26 @@ __global__ void __launch_bounds__(256) k_grad32(NGeom g, int64_t M, const float4
         const float d1_own = tap ? window_deriv<WIN, float>(x1, qf, par1, nrm1) : 0.f;
         const float w2 = tap ? window<WIN, float>(x2, qf, par2, nrm2) : 0.f;
         const float d2 = tap ? window_deriv<WIN, float>(x2, qf, par2, nrm2) : 0.f;
-        const int col = tap ? wrap_index(a2 + gl, g.N[2]) : 0;
+        const int col = tap ? wrap_index(a2 + gl, (int)s1) : 0;
         float2 w1p[G], d1p[G];
-        int off1[G];
 #pragma unroll
         for (int b = 0; b < G; ++b) {
             const float w = __shfl_sync(0xffffffffu, w1_own, b, G);
             const float d = __shfl_sync(0xffffffffu, d1_own, b, G);
             w1p[b] = make_float2(w, w);
             d1p[b] = make_float2(d, d);
-            off1[b] = (b < q2) ? row_of(a1 + b, g.first[1], g.rows[1], g.N[1]) * (int)s1 + col : col;
         }
+        const int64_t r1base = LIN1 ? (int64_t)(a1 - g.first[1]) * s1 + col : col;
         float2 af = make_float2(0.f, 0.f), ad0 = af, ad1 = af;
         for (int a = 0; a < q2; ++a) {
             const float w0 = __shfl_sync(0xffffffffu, w0_own, a, G);
             const float d0 = __shfl_sync(0xffffffffu, d0_own, a, G);
-            const float2 *rowp = grid + row_of(a0 + a, g.first[0], g.rows[0], g.N[0]) * s0;
+            const float2 *rowp = grid + row_of(a0 + a, g.first[0], g.rows[0], g.N[0]) * s0 + r1base;
             float2 rs = make_float2(0.f, 0.f), rd = rs;
 #pragma unroll
             for (int b = 0; b < G; ++b)
                 if (b < q2) {
-                    const float2 v = __ldg(rowp + off1[b]);
+                    const float2 v = __ldg(rowp + (LIN1 ? b * s1 : row_of(a1 + b, g.first[1], g.rows[1], g.N[1]) * s1));
                     rs = ffma2(w1p[b], v, rs);
                     rd = ffma2(d1p[b], v, rd);
                 }
@@ -335,10 +342,11 @@ __device__ __forceinline__ void write_point_gradient(const NGeom &g, double rho,
 template <typename T, int WIN, int Q2MAX, int C1>
 struct SpreadSmem {
     static constexpr int PCH = 64;
-    static constexpr int T1MAX = (C1 + Q2MAX - 1 + 1) & ~1;   // rounded up to even: pairs load as 128 bits
+    static constexpr int PAD = sizeof(T) == 4 ? 4 : 2;         // 128-bit weight loads
+    static constexpr int T1MAX = (C1 + Q2MAX - 1 + PAD - 1) / PAD * PAD;
     C2<T> y[PCH];
     T w0[PCH][Q2MAX];
-    C2<T> w1[PCH][T1MAX];     // (w1, w1) pairs
+    T w1[PCH][T1MAX];         // axis-1 weights on the tile rows (0 off the point's taps)
     T w2[PCH][32];
     int ta0[PCH];
 };
@@ -393,9 +401,7 @@ __global__ void __launch_bounds__(32 * (C0 + Q2MAX - 1)) k_spread_slab(NGeom g, 
             } else if (e < Q2MAX + T1MAX) {
                 const int tb = e - Q2MAX;
                 const int rel = tb - (c1 - sb1 * C1);      // tap index of row tb for this point
-                const T w = (rel >= 0 && rel < q2 && tb < T1) ? window<WIN, T>(f1 + (T)(q - 1 - rel), qT, par1, nrm1) : (T)0;
-                sm.w1[p][tb].x = w;
-                sm.w1[p][tb].y = w;
+                sm.w1[p][tb] = (rel >= 0 && rel < q2 && tb < T1) ? window<WIN, T>(f1 + (T)(q - 1 - rel), qT, par1, nrm1) : (T)0;
             } else if (e < Q2MAX + T1MAX + 32) {
                 const int L = e - Q2MAX - T1MAX;
                 const int rel = cbase + L - (c2 - q + 1);
@@ -418,15 +424,17 @@ __global__ void __launch_bounds__(32 * (C0 + Q2MAX - 1)) k_spread_slab(NGeom g, 
             if constexpr (sizeof(T) == 4) {
                 const float4 *w1v = reinterpret_cast<const float4 *>(&sm.w1[p][0]);
 #pragma unroll
-                for (int h = 0; h < T1MAX / 2; ++h) {
+                for (int h = 0; h < T1MAX / 4; ++h) {
                     const float4 w = w1v[h];
-                    acc[2 * h] = ffma2(make_float2(w.x, w.y), z, acc[2 * h]);
-                    acc[2 * h + 1] = ffma2(make_float2(w.z, w.w), z, acc[2 * h + 1]);
+                    acc[4 * h].x = fmaf(w.x, z.x, acc[4 * h].x);         acc[4 * h].y = fmaf(w.x, z.y, acc[4 * h].y);
+                    acc[4 * h + 1].x = fmaf(w.y, z.x, acc[4 * h + 1].x); acc[4 * h + 1].y = fmaf(w.y, z.y, acc[4 * h + 1].y);
+                    acc[4 * h + 2].x = fmaf(w.z, z.x, acc[4 * h + 2].x); acc[4 * h + 2].y = fmaf(w.z, z.y, acc[4 * h + 2].y);
+                    acc[4 * h + 3].x = fmaf(w.w, z.x, acc[4 * h + 3].x); acc[4 * h + 3].y = fmaf(w.w, z.y, acc[4 * h + 3].y);
                 }
             } else {
 #pragma unroll
                 for (int tb = 0; tb < T1MAX; ++tb) {
-                    const T w = sm.w1[p][tb].x;
+                    const double w = sm.w1[p][tb];
                     acc[tb].x = fma(w, z.x, acc[tb].x);
                     acc[tb].y = fma(w, z.y, acc[tb].y);
                 }
@@ -464,13 +472,15 @@ __global__ void __launch_bounds__(256) k_interp64(NGeom g, int64_t M, const doub
     const int q = g.q, q2 = 2 * q;
     const double qd = (double)q;
     const int64_t s1 = g.N[2], s0 = (int64_t)g.rows[1] * g.N[2];
+    // warps sweep the bin-sorted points in grid-stride order (consecutive warps: neighbouring points)
     constexpr int PPW = 32 / G;
     const int64_t warp0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / 32;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) / 32;
+    const int64_t end = M;
     for (int64_t base = warp0 * PPW; base < M; base += nwarps * PPW) {
         const int64_t i = base + lane / G;
         const bool live = i < M;
-        const int64_t ii = live ? i : M - 1;
+        const int64_t ii = live ? i : end - 1;
         const double u0 = u_sorted[3 * ii], u1 = u_sorted[3 * ii + 1], u2 = u_sorted[3 * ii + 2];
         const int a0 = cell_clamped(u0, g.cmax0) - q + 1, a1 = cell_clamped(u1, g.cmax1) - q + 1;
         const int a2 = min(max((int)floor(u2), 0), g.N[2] - 1) - q + 1;
@@ -523,13 +533,15 @@ __global__ void __launch_bounds__(256) k_grad64(NGeom g, int64_t M, const double
     const int64_t s1 = g.N[2], s0 = (int64_t)g.rows[1] * g.N[2];
     double rho = sqrt(__longlong_as_double((long long)*r2max)) * (1.0 + 0x1p-20);
     if (!(rho > 0.0)) rho = 1.0;
+    // warps sweep the bin-sorted points in grid-stride order (consecutive warps: neighbouring points)
     constexpr int PPW = 32 / G;
     const int64_t warp0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / 32;
     const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) / 32;
+    const int64_t end = M;
     for (int64_t base = warp0 * PPW; base < M; base += nwarps * PPW) {
         const int64_t i = base + lane / G;
         const bool live = i < M;
-        const int64_t ii = live ? i : M - 1;
+        const int64_t ii = live ? i : end - 1;
         const double u0 = u_sorted[3 * ii], u1 = u_sorted[3 * ii + 1], u2 = u_sorted[3 * ii + 2];
         const int a0 = cell_clamped(u0, g.cmax0) - q + 1, a1 = cell_clamped(u1, g.cmax1) - q + 1;
         const int a2 = min(max((int)floor(u2), 0), g.N[2] - 1) - q + 1;
@@ -601,6 +613,7 @@ NGeom make_geom(const sgl_plan *p) {
     return g;
 }
 
+// blocks of 256 threads for a grid-stride sweep over the points
 int nufft_blocks(int64_t M, int G) {
     const int64_t ppb = 256 / G;                 // points per block per sweep
     int64_t b = (M + ppb - 1) / ppb;
@@ -615,9 +628,20 @@ cudaError_t interp_t(sgl_plan *p, double2 *vals) {
     if constexpr (sizeof(T) == 4) {
         const float2 *gridf = (const float2 *)p->b.bufA;
         const int q2 = 2 * p->q;
-        if (q2 <= 8) k_interp32<WIN, 8><<<nufft_blocks(p->M, 8), 256, 0, p->stream>>>(g, p->M, p->b.pts32, p->b.perm, gridf, vals);
-        else if (q2 <= 16) k_interp32<WIN, 16><<<nufft_blocks(p->M, 16), 256, 0, p->stream>>>(g, p->M, p->b.pts32, p->b.perm, gridf, vals);
-        else k_interp32<WIN, 32><<<nufft_blocks(p->M, 32), 256, 0, p->stream>>>(g, p->M, p->b.pts32, p->b.perm, gridf, vals);
+        const bool lin = p->ax[1].rows < p->ax[1].N;
+        const int n2 = p->ax[2].N;
+#define SGL_INTERP32(GG, LL, NN) k_interp32<WIN, GG, LL, NN><<<nufft_blocks(p->M, GG), 256, 0, p->stream>>>(g, p->M, p->b.pts32, p->b.perm, gridf, vals)
+#define SGL_INTERP32_N(GG)                                                      \
+        if (lin && n2 == 128) SGL_INTERP32(GG, true, 128);                      \
+        else if (lin && n2 == 256) SGL_INTERP32(GG, true, 256);                 \
+        else if (lin && n2 == 512) SGL_INTERP32(GG, true, 512);                 \
+        else if (lin) SGL_INTERP32(GG, true, 0);                                \
+        else SGL_INTERP32(GG, false, 0);
+        if (q2 <= 8) { SGL_INTERP32_N(8) }
+        else if (q2 <= 16) { SGL_INTERP32_N(16) }
+        else { if (lin) SGL_INTERP32(32, true, 0); else SGL_INTERP32(32, false, 0); }
+#undef SGL_INTERP32_N
+#undef SGL_INTERP32
         p->launches += 1;
         return cudaGetLastError();
     } else {
@@ -666,12 +690,20 @@ cudaError_t grad_t(sgl_plan *p, const double2 *gout, double *gxyz) {
     const int q2 = 2 * p->q;
     if constexpr (sizeof(T) == 4) {
         const float2 *gridf = (const float2 *)p->b.bufA;
-        if (q2 <= 8)
-            k_grad32<WIN, 8><<<nufft_blocks(p->M, 8), 256, 0, p->stream>>>(g, p->M, p->b.pts32, p->b.perm, p->b.r2max, gridf, gout, gxyz);
-        else if (q2 <= 16)
-            k_grad32<WIN, 16><<<nufft_blocks(p->M, 16), 256, 0, p->stream>>>(g, p->M, p->b.pts32, p->b.perm, p->b.r2max, gridf, gout, gxyz);
-        else
-            k_grad32<WIN, 32><<<nufft_blocks(p->M, 32), 256, 0, p->stream>>>(g, p->M, p->b.pts32, p->b.perm, p->b.r2max, gridf, gout, gxyz);
+        const bool lin = p->ax[1].rows < p->ax[1].N;
+        const int n2 = p->ax[2].N;
+#define SGL_GRAD32(GG, LL, NN) k_grad32<WIN, GG, LL, NN><<<nufft_blocks(p->M, GG), 256, 0, p->stream>>>(g, p->M, p->b.pts32, p->b.perm, p->b.r2max, gridf, gout, gxyz)
+#define SGL_GRAD32_N(GG)                                                        \
+        if (lin && n2 == 128) SGL_GRAD32(GG, true, 128);                        \
+        else if (lin && n2 == 256) SGL_GRAD32(GG, true, 256);                   \
+        else if (lin && n2 == 512) SGL_GRAD32(GG, true, 512);                   \
+        else if (lin) SGL_GRAD32(GG, true, 0);                                  \
+        else SGL_GRAD32(GG, false, 0);
+        if (q2 <= 8) { SGL_GRAD32_N(8) }
+        else if (q2 <= 16) { SGL_GRAD32_N(16) }
+        else { if (lin) SGL_GRAD32(32, true, 0); else SGL_GRAD32(32, false, 0); }
+#undef SGL_GRAD32_N
+#undef SGL_GRAD32
     } else {
         const double2 *gridd = (const double2 *)p->b.bufA;
         if (q2 <= 8)

@@ -170,21 +170,6 @@ __global__ void k_scatter_points(int64_t M, const double *__restrict__ u_tmp, co
     }
 }
 
-// work items for interpolation: each nonempty column bin is cut into pieces of <= kItemPoints points
-__global__ void k_item_count(const int *__restrict__ cnt, int64_t n, int *__restrict__ item_count) {
-    for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < n; b += (int64_t)gridDim.x * blockDim.x)
-        item_count[b] = (cnt[b] + kItemPoints - 1) / kItemPoints;
-}
-
-__global__ void k_item_fill(const int *__restrict__ cnt, const int *__restrict__ off, const int *__restrict__ item_count,
-                            const int *__restrict__ item_off, int64_t n, int2 *__restrict__ items, int *__restrict__ n_items) {
-    for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < n; b += (int64_t)gridDim.x * blockDim.x) {
-        const int c = cnt[b], k = item_count[b], o = item_off[b], first = off[b];
-        for (int j = 0; j < k; ++j) items[o + j] = make_int2(first + j * kItemPoints, min(kItemPoints, c - j * kItemPoints));
-        if (b == n - 1) *n_items = o + k;
-    }
-}
-
 void scan(const int *cnt, int64_t n, int *tmp, int *off, cudaStream_t s) {
     const int nblk = (int)((n + kScanBlock - 1) / kScanBlock);
     k_scan_block_totals<<<nblk, kThreads, 0, s>>>(cnt, n, tmp);
@@ -222,11 +207,7 @@ cudaError_t launch_points(sgl_plan *p, const double *xyz, int64_t M) {
         scan(b.bin_count, p->nbins, b.scan_tmp, b.bin_off, s);
         k_scatter_points<<<grid_blocks(M, kThreads), kThreads, 0, s>>>(M, b.u_tmp, b.bin_of, b.rank_of, b.bin_off, g, b.u_sorted,
                                                                        b.pts32, b.perm);
-        k_item_count<<<grid_blocks(p->nbins, kThreads), kThreads, 0, s>>>(b.bin_count, p->nbins, b.item_count);
-        scan(b.item_count, p->nbins, b.scan_tmp, b.item_off, s);
-        k_item_fill<<<grid_blocks(p->nbins, kThreads), kThreads, 0, s>>>(b.bin_count, b.bin_off, b.item_count, b.item_off,
-                                                                          p->nbins, b.items, b.n_items);
-        p->launches += 10;
+        p->launches += 5;
     }
     return cudaGetLastError();
 }
