@@ -219,6 +219,30 @@ sgl_status sgl_trig_coeffs_noalloc(int B, const double *xyz_dev, int64_t M, cons
 /* Synchronize the plan's stream and report deferred device errors (non-finite points). */
 sgl_status sgl_sync(sgl_plan *plan);
 
+/*
+ * Batches: n independent transforms, instance i with bandwidth B[i] and at most
+ * M_max[i] points, all with the same precision, window, q and sigma, issued together
+ * on one stream (Def. of the NDSGLFT applied per instance).  The instances run in
+ * stream order and share the FFT work buffers (sized for the largest instance).
+ * With sgl_batch_use_graph(b, 1) a batch forward or adjoint is captured into a CUDA
+ * graph the first time and replayed while the pointer arrays and point counts are the
+ * same as at capture (a change recaptures).  Pointer arrays are host arrays of n
+ * device pointers, with the per-instance layouts of sgl_forward / sgl_adjoint.
+ * SGL_FLAG_PROFILE is not accepted for batches.
+ */
+typedef struct sgl_batch sgl_batch;
+sgl_status sgl_batch_create(sgl_batch **out, int n, const int *B, const int64_t *M_max, int precision, int window,
+                            int q, double sigma, unsigned flags, void *cuda_stream);
+void sgl_batch_destroy(sgl_batch *batch);
+sgl_status sgl_batch_use_graph(sgl_batch *batch, int enable);
+sgl_status sgl_batch_set_points(sgl_batch *batch, const double *const *xyz_dev, const int64_t *M);
+sgl_status sgl_batch_forward(sgl_batch *batch, const double *const *coef_dev, double *const *vals_dev);
+sgl_status sgl_batch_adjoint(sgl_batch *batch, const double *const *vals_dev, double *const *coef_dev);
+/* n, graph replays so far, device bytes owned (any output may be NULL) */
+sgl_status sgl_batch_info(const sgl_batch *batch, int *n, int64_t *graph_launches, int64_t *workspace_bytes);
+/* synchronize the stream and report deferred device errors of any instance */
+sgl_status sgl_batch_sync(sgl_batch *batch);
+
 /* Message of the last failing call on this thread ("" if none). */
 const char *sgl_last_error(void);
 

@@ -75,6 +75,20 @@ def load_library(build_if_missing=True):
             f = getattr(lib, name)
             f.restype = ctypes.c_int
             f.argtypes = args
+        pp = ctypes.POINTER(ctypes.c_void_p)
+        lib.sgl_batch_create.restype = ctypes.c_int
+        lib.sgl_batch_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                         ctypes.POINTER(i64), ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                         ctypes.c_uint, vp]
+        lib.sgl_batch_destroy.restype = None
+        lib.sgl_batch_destroy.argtypes = [vp]
+        for name, args in [("sgl_batch_use_graph", [vp, ctypes.c_int]), ("sgl_batch_set_points", [vp, pp, ctypes.POINTER(i64)]),
+                           ("sgl_batch_forward", [vp, pp, pp]), ("sgl_batch_adjoint", [vp, pp, pp]),
+                           ("sgl_batch_info", [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(i64), ctypes.POINTER(i64)]),
+                           ("sgl_batch_sync", [vp])]:
+            f = getattr(lib, name)
+            f.restype = ctypes.c_int
+            f.argtypes = args
         lib.sgl_stage_name.restype = ctypes.c_char_p
         lib.sgl_stage_name.argtypes = [ctypes.c_int]
         _LIB = lib
@@ -225,6 +239,74 @@ class Plan:
 
     def sync(self):
         _check(self.lib.sgl_sync(self._h))
+
+
+class BatchPlan:
+    """Many independent transforms issued together (sgl_batch_*): instance i has bandwidth
+    Bs[i] and at most M_maxs[i] points; optional CUDA-graph capture of whole batch calls."""
+
+    def __init__(self, Bs, M_maxs, precision=PREC_FP64, window=WIN_KB, q=8, sigma=2.0, device=None):
+        if not torch.cuda.is_available():
+            raise SGLError(3, "no CUDA device: the NFSGLFT runs only on the GPU")
+        self.lib = load_library()
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else torch.device(device).index or 0)
+        self.Bs = [int(b) for b in Bs]
+        self.n = len(self.Bs)
+        M_maxs = [int(m) for m in M_maxs]
+        self._h = ctypes.c_void_p()
+        with torch.cuda.device(self.device):
+            st = self.lib.sgl_batch_create(ctypes.byref(self._h), self.n, (ctypes.c_int * self.n)(*self.Bs),
+                                           (ctypes.c_int64 * self.n)(*M_maxs), int(precision), int(window), int(q),
+                                           float(sigma), 0, _stream_handle(self.device))
+        _check(st)
+        self.Ms = [0] * self.n
+        self._keep = []
+
+    def close(self):
+        if self._h:
+            self.lib.sgl_batch_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def use_graph(self, enable=True):
+        _check(self.lib.sgl_batch_use_graph(self._h, 1 if enable else 0))
+
+    def _ptrs(self, tensors):
+        return (ctypes.c_void_p * self.n)(*[t.data_ptr() for t in tensors])
+
+    def set_points(self, xyz_list):
+        xs = [_dev_tensor(x, torch.float64, (x.shape[0], 3), "xyz", self.device) for x in xyz_list]
+        Ms = [x.shape[0] for x in xs]
+        _check(self.lib.sgl_batch_set_points(self._h, self._ptrs(xs), (ctypes.c_int64 * self.n)(*Ms)))
+        self.Ms = Ms
+        self._keep = xs
+
+    def forward(self, coef_list, out_list=None):
+        cs = [_dev_tensor(c, torch.complex128, (num_coeffs(B),), "coef", self.device) for c, B in zip(coef_list, self.Bs)]
+        if out_list is None:
+            out_list = [torch.empty(M, dtype=torch.complex128, device=self.device) for M in self.Ms]
+        _check(self.lib.sgl_batch_forward(self._h, self._ptrs(cs), self._ptrs(out_list)))
+        return out_list
+
+    def adjoint(self, vals_list, out_list=None):
+        vs = [_dev_tensor(v, torch.complex128, (M,), "vals", self.device) for v, M in zip(vals_list, self.Ms)]
+        if out_list is None:
+            out_list = [torch.empty(num_coeffs(B), dtype=torch.complex128, device=self.device) for B in self.Bs]
+        _check(self.lib.sgl_batch_adjoint(self._h, self._ptrs(vs), self._ptrs(out_list)))
+        return out_list
+
+    def info(self):
+        n, gl, wb = ctypes.c_int(), ctypes.c_int64(), ctypes.c_int64()
+        _check(self.lib.sgl_batch_info(self._h, ctypes.byref(n), ctypes.byref(gl), ctypes.byref(wb)))
+        return {"n": n.value, "graph_launches": gl.value, "workspace_bytes": wb.value}
+
+    def sync(self):
+        _check(self.lib.sgl_batch_sync(self._h))
 
 
 NOALLOC_MAX_B = 32

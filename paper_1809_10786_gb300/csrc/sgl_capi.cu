@@ -7,6 +7,8 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -178,6 +180,20 @@ void polar_matrices(int B, std::vector<double> &P) {
     }
 }
 
+// P_m depends on B only: computed once per B per process and reused by every plan
+const std::vector<double> &cached_polar_matrices(int B) {
+    static std::mutex mu;
+    static std::map<int, std::vector<double>> cache;
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = cache.find(B);
+    if (it == cache.end()) {
+        std::vector<double> P;
+        polar_matrices(B, P);
+        it = cache.emplace(B, std::move(P)).first;
+    }
+    return it->second;
+}
+
 struct DevAlloc {
     std::vector<void *> ptrs;
     int64_t bytes = 0;
@@ -241,8 +257,14 @@ int64_t sgl_num_coeffs(int B) {
 
 const char *sgl_last_error(void) { return g_last_error.c_str(); }
 
-sgl_status sgl_plan_create(sgl_plan **out, int B, int64_t M_max, int precision, int window, int q, double sigma,
-                           unsigned flags, void *cuda_stream) {
+}  // extern "C"
+
+namespace sgl {
+
+// Plan creation.  shared (optional): FFT work buffers owned by a batch, used instead of the
+// plan's own when both are large enough (only the plan's own buffers are freed with it).
+sgl_status plan_create_impl(sgl_plan **out, int B, int64_t M_max, int precision, int window, int q, double sigma,
+                            unsigned flags, void *cuda_stream, const SharedWork *shared) {
     if (!out) return set_error(SGL_ERR_ARG, "out is NULL");
     *out = nullptr;
     if (B < 1 || B > 128) return set_error(SGL_ERR_ARG, "B must be in [1, 128]");
@@ -316,7 +338,10 @@ sgl_status sgl_plan_create(sgl_plan **out, int B, int64_t M_max, int precision, 
     ALLOC(b.beta, (size_t)(2 * B - 1) * (K0 + 1) * B);
     ALLOC(b.zeta, (size_t)(K0 + 1) * (K1 + 1) * W);
     ALLOC(b.linescale, (size_t)(W * W));
-    {
+    if (shared && shared->bufA && shared->bufB && shared->bytesA >= nA * csz && shared->bytesB >= bytesB) {
+        b.bufA = shared->bufA; b.bufB = shared->bufB;
+        b.bufA_bytes = shared->bytesA; b.bufB_bytes = shared->bytesB;
+    } else {
         unsigned char *pa = nullptr, *pb = nullptr;
         ALLOC(pa, nA * csz);
         ALLOC(pb, bytesB);
@@ -353,8 +378,7 @@ sgl_status sgl_plan_create(sgl_plan **out, int B, int64_t M_max, int precision, 
     if (flags & SGL_FLAG_PROFILE) p->prof = new (std::nothrow) Profiler();
 
     // ---- host precompute (FP64) and upload
-    std::vector<double> P;
-    polar_matrices(B, P);
+    const std::vector<double> &P = cached_polar_matrices(B);
     std::vector<double> costab(8 * B);
     for (int m = 0; m < 8 * B; ++m) costab[m] = (double)cosl((long double)m * 3.14159265358979323846264338327950288L / (4.0L * B));
     std::vector<double> dec[3];
@@ -396,6 +420,31 @@ sgl_status sgl_plan_create(sgl_plan **out, int B, int64_t M_max, int precision, 
     if ((e = cudaStreamSynchronize(p->stream)) != cudaSuccess) return fail(SGL_ERR_CUDA, std::string("plan upload: ") + cudaGetErrorString(e));
     *out = p;
     return ok();
+}
+
+// FFT work-buffer sizes (bytes) a plan with these parameters needs.
+sgl_status plan_work_sizes(int B, int precision, int q, double sigma, size_t *bytesA, size_t *bytesB) {
+    if (B < 1 || B > 128 || q < 1 || q > kMaxQ || !(sigma >= 1.5 && sigma <= 4.0)) return set_error(SGL_ERR_ARG, "invalid plan parameters");
+    const int nsz[3] = {4 * B, 2 * B, 2 * B};
+    int N[3], rows[3];
+    for (int d = 0; d < 3; ++d) {
+        N[d] = next_fft_size(sigma * nsz[d]);
+        rows[d] = (d < 2 && N[d] / 2 + 2 * q + 1 <= N[d]) ? N[d] / 2 + 2 * q + 1 : N[d];
+    }
+    const int64_t W = 2 * (B - 1) + 1;
+    const size_t csz = precision == SGL_FP32_MIXED ? sizeof(float2) : sizeof(double2);
+    *bytesA = std::max<size_t>((size_t)rows[0] * W * W, (size_t)rows[0] * rows[1] * N[2]) * csz;
+    *bytesB = std::max<size_t>((size_t)rows[0] * rows[1] * W * csz, (size_t)(2 * (2 * B - 2) + 1) * W * W * sizeof(double2));
+    return SGL_OK;
+}
+
+}  // namespace sgl
+
+extern "C" {
+
+sgl_status sgl_plan_create(sgl_plan **out, int B, int64_t M_max, int precision, int window, int q, double sigma,
+                           unsigned flags, void *cuda_stream) {
+    return plan_create_impl(out, B, M_max, precision, window, q, sigma, flags, cuda_stream, nullptr);
 }
 
 void sgl_plan_destroy(sgl_plan *plan) {

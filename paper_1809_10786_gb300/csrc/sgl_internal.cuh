@@ -119,6 +119,15 @@ struct sgl_plan {
 
 namespace sgl {
 
+// FFT work buffers shared by the plans of a batch (the plans run one after another on one stream).
+struct SharedWork {
+    void *bufA, *bufB;
+    size_t bytesA, bytesB;
+};
+sgl_status plan_create_impl(sgl_plan **out, int B, int64_t M_max, int precision, int window, int q, double sigma,
+                            unsigned flags, void *cuda_stream, const SharedWork *shared);
+sgl_status plan_work_sizes(int B, int precision, int q, double sigma, size_t *bytesA, size_t *bytesB);
+
 // ---- launchers (all asynchronous on plan->stream); return cudaGetLastError() ----
 cudaError_t launch_points(sgl_plan *p, const double *xyz, int64_t M);
 cudaError_t launch_radial_matrices(sgl_plan *p);

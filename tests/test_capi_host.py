@@ -69,3 +69,18 @@ def test_null_plan_is_rejected(lib):
 
 def test_out_pointer_required(lib):
     assert lib.sgl_plan_create(None, 8, 10, 0, 0, 8, 2.0, 0, None) == 1
+
+
+def test_batch_create_rejects_bad_arguments_without_cuda(lib):
+    h = ctypes.c_void_p(5)
+    Bs = (ctypes.c_int * 2)(8, 12)
+    Ms = (ctypes.c_int64 * 2)(10, 20)
+    assert lib.sgl_batch_create(ctypes.byref(h), 0, Bs, Ms, 0, 0, 8, 2.0, 0, None) == 1
+    assert h.value is None
+    assert lib.sgl_batch_create(ctypes.byref(h), 2, None, Ms, 0, 0, 8, 2.0, 0, None) == 1
+    bad = (ctypes.c_int * 2)(8, 0)
+    assert lib.sgl_batch_create(ctypes.byref(h), 2, bad, Ms, 0, 0, 8, 2.0, 0, None) == 1
+    assert "instance 1" in lib.sgl_last_error().decode()
+    assert lib.sgl_batch_create(ctypes.byref(h), 2, Bs, Ms, 0, 0, 8, 2.0, 2, None) == 1     # profiling flag
+    assert lib.sgl_batch_forward(None, None, None) == 1
+    lib.sgl_batch_destroy(None)

@@ -1,0 +1,74 @@
+"""Batched transforms (marked gpu): a batch gives the same results as one plan per
+instance, with and without CUDA-graph replay, and the 256-instance workload (B uniform
+in 8..48, M log-uniform in [1e3, 1e5]) matches the oracle on sampled outputs."""
+import numpy as np
+import pytest
+import torch
+
+import paper_1809_10786_gb300 as sgl
+from paper_1809_10786_gb300 import inputs
+from oracle import direct
+
+pytestmark = pytest.mark.gpu
+DEV = torch.device("cuda", 0)
+
+
+def gpu(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+
+
+def instances(specs, seed):
+    cs = [inputs.coefficients(B, seed + 10 * i) for i, (B, M) in enumerate(specs)]
+    xs = [inputs.points_gaussian(M, seed + 10 * i + 1) for i, (B, M) in enumerate(specs)]
+    ys = [inputs.values(M, seed + 10 * i + 2) for i, (B, M) in enumerate(specs)]
+    return cs, xs, ys
+
+
+@pytest.mark.parametrize("prec", [sgl.PREC_FP64, sgl.PREC_FP32_MIXED])
+def test_batch_matches_single_plans_and_graph_replay(prec):
+    specs = [(8, 900), (13, 1500), (21, 40), (37, 3000), (8, 1), (16, 700)]
+    cs, xs, ys = instances(specs, 8100)
+    bp = sgl.BatchPlan([B for B, _ in specs], [M for _, M in specs], precision=prec, q=6)
+    bp.set_points([gpu(x) for x in xs])
+    f_b = [t.cpu().numpy() for t in bp.forward([gpu(c) for c in cs])]
+    a_b = [t.cpu().numpy() for t in bp.adjoint([gpu(y) for y in ys])]
+    for i, (B, M) in enumerate(specs):
+        p = sgl.Plan(B, M, precision=prec, q=6)
+        p.set_points(gpu(xs[i]))
+        f = p.forward(gpu(cs[i])).cpu().numpy()
+        a = p.adjoint(gpu(ys[i])).cpu().numpy()
+        assert np.array_equal(f_b[i], f)
+        # spreading adds with atomics: the order (and FP32 rounding) differs from run to run
+        tol = 1e-12 if prec == sgl.PREC_FP64 else 1e-5
+        assert np.abs(a_b[i] - a).max() <= tol * max(np.abs(a).max(), 1e-300)
+    # graph mode: capture once, replay, same numbers; new pointers recapture
+    bp.use_graph(True)
+    ct = [gpu(c) for c in cs]
+    outs = [torch.empty(M, dtype=torch.complex128, device=DEV) for _, M in specs]
+    for _ in range(3):
+        bp.forward(ct, outs)
+    torch.cuda.synchronize()
+    for i in range(len(specs)):
+        assert np.array_equal(outs[i].cpu().numpy(), f_b[i])
+    assert bp.info()["graph_launches"] == 3
+    f_new = [t.cpu().numpy() for t in bp.forward(ct)]
+    for i in range(len(specs)):
+        assert np.array_equal(f_new[i], f_b[i])
+    bp.sync()
+
+
+@pytest.mark.parametrize("prec,tol", [(sgl.PREC_FP64, 1e-10), (sgl.PREC_FP32_MIXED, 1e-4)])
+def test_256_instance_workload_sampled(prec, tol):
+    specs = inputs.batch_instances(256, inputs.seed_for(3))
+    cs, xs, ys = instances(specs, inputs.seed_for(3, 1))
+    bp = sgl.BatchPlan([B for B, _ in specs], [M for _, M in specs], precision=prec, q=8)
+    bp.set_points([gpu(x) for x in xs])
+    bp.use_graph(True)
+    fs = [t.cpu().numpy() for t in bp.forward([gpu(c) for c in cs])]
+    bp.sync()
+    rng = np.random.default_rng(3)
+    for i in rng.choice(256, 12, replace=False):
+        B, M = specs[i]
+        idx = np.sort(rng.choice(M, min(M, 40), replace=False))
+        ref, _ = direct.forward(B, xs[i][idx], cs[i])
+        assert np.abs(fs[i][idx] - ref).max() <= tol * np.abs(ref).max(), (i, B, M)
