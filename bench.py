@@ -242,6 +242,37 @@ def run_ours(args):
         del plan
         torch.cuda.empty_cache()
 
+    # ---- the FP32-mixed path at the workload's other window cutoffs (same step, value only)
+    by_q = {}
+    if not args.no_extra_q:
+        for qq in (4, 6):
+            plan = sgl.Plan(B, M, precision=sgl.PREC_FP32_MIXED, window=sgl.WIN_KB, q=qq, sigma=2.0, device=dev)
+
+            qout = {}
+
+            def qstep():
+                plan.set_points(x)
+                qout["f"] = plan.forward(c)
+                sd.allreduce_coefficients(plan.adjoint(y))
+                plan.grad_points(c, g)
+
+            for _ in range(args.warmup):
+                qstep()
+            barrier()
+            evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+            for k in range(args.steps):
+                flush.zero_()
+                evs[k][0].record()
+                qstep()
+                evs[k][1].record()
+            barrier()
+            ms = sd.max_over_ranks(sum(a.elapsed_time(b) for a, b in evs), dev)
+            by_q[qq] = {"value": round(world * M / (ms / args.steps * 1e-3) / 1e6, 4), "ms_per_step": round(ms / args.steps, 4)}
+            keep["fp32_mixed_q%d" % qq] = {"f": qout["f"].detach().cpu().numpy()}
+            plan.close()
+            del plan
+            torch.cuda.empty_cache()
+
     # ---- end to end through the C-ABI with host buffers (copies inside the timed region)
     e2e = None
     if not args.no_e2e:
@@ -300,11 +331,15 @@ def run_ours(args):
                      "ms_per_step": round(results["fp64"]["ms_per_step"], 4),
                      "gpu_launches": results["fp64"]["gpu_launches"], "stages": results["fp64"]["stages"]},
             "stages_fp32_mixed": head["stages"],
+            "fp32_mixed_other_cutoffs": by_q,
             "e2e": e2e}
 
     # ---- CPU baseline (oracle on the host cores, rank 0, N = 1) and the measured error on its sample
     if rank == 0 and world == 1 and not args.no_cpu:
         base, err = cpu_baseline(args, x_h, c_h, y_h, g_h, keep, dev)
+        for qq in by_q:
+            if ("fp32_mixed_q%d" % qq) in err:
+                by_q[qq]["forward_error"] = err["fp32_mixed_q%d" % qq]["forward"]
         line["cpu_baseline"] = base
         line["error_vs_oracle"] = err
     if rank == 0:
@@ -346,6 +381,9 @@ def cpu_baseline(args, x_h, c_h, y_h, g_h, keep, dev):
         ea = np.abs(a - a_ref).max() / np.abs(a_ref).max()
         err[prec_name] = {"forward": float(ef), "adjoint": float(ea), "grad": float(eg),
                           "measure": "max |gpu - oracle| / max |oracle| on the sample"}
+    for key in sorted(k for k in keep if k.startswith("fp32_mixed_q")):
+        ef = np.abs(keep[key]["f"][idx] - f_ref).max() / np.abs(f_ref).max()
+        err[key] = {"forward": float(ef), "measure": "max |gpu - oracle| / max |oracle| on the sample"}
     return base, err
 
 
@@ -359,7 +397,7 @@ def run_reference(args):
     from oracle import direct
     from paper_1809_10786_gb300 import inputs
 
-    S = args.cpu_sample
+    S = args.ref_sample
     B = args.B
     c = inputs.coefficients(B, inputs.seed_for(2))
     x = inputs.points_gaussian(S, inputs.seed_for(2, 1))
@@ -400,9 +438,11 @@ def main():
     ap.add_argument("--B", type=int, default=64)
     ap.add_argument("--M", type=int, default=1_000_000)
     ap.add_argument("--q", type=int, default=8)
-    ap.add_argument("--cpu-sample", type=int, default=8000)
+    ap.add_argument("--cpu-sample", type=int, default=96000)
+    ap.add_argument("--ref-sample", type=int, default=24000)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-extra-q", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")
