@@ -70,6 +70,10 @@ typedef enum {
 /* plan flags */
 #define SGL_FLAG_HOST_IO 1u   /* also allocate staging buffers for the *_host calls */
 #define SGL_FLAG_PROFILE 2u   /* record CUDA events around every stage (read with sgl_profile) */
+#define SGL_FLAG_SIMT 4u      /* FP32-mixed: interpolate and take gradients with the CUDA-core kernels only */
+#define SGL_FLAG_TC 8u        /* FP32-mixed: use the tensor-core (tcgen05) interpolation and gradient
+                                 kernels wherever the plan allows them (q <= 8, windowed axes 0
+                                 and 1), not only where they are the faster choice */
 
 /* stages reported by sgl_profile (index order) */
 #define SGL_NUM_STAGES 12
@@ -91,6 +95,7 @@ typedef struct {
     double sigma_eff[3];      /* N[d] / n[d] */
     int64_t workspace_bytes;  /* device bytes owned by the plan */
     int64_t kernel_launches;  /* CUDA kernels this plan has launched so far */
+    int tensor_cores;         /* bit 0: interpolation, bit 1: gradient run on the tcgen05 kernels */
 } sgl_plan_info_t;
 
 /* Nc = B(B+1)(2B+1)/6 (Sect. 1); -1 if B < 1. */

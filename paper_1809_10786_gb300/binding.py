@@ -15,7 +15,7 @@ from . import build as _build
 
 PREC_FP64, PREC_FP32_MIXED = 0, 1
 WIN_KB, WIN_GAUSS = 0, 1
-FLAG_HOST_IO, FLAG_PROFILE = 1, 2
+FLAG_HOST_IO, FLAG_PROFILE, FLAG_SIMT, FLAG_TC = 1, 2, 4, 8
 NUM_STAGES = 12
 
 _STATUS = {0: "SGL_OK", 1: "SGL_ERR_ARG", 2: "SGL_ERR_ALLOC", 3: "SGL_ERR_CUDA", 4: "SGL_ERR_NONFINITE",
@@ -36,7 +36,7 @@ class PlanInfo(ctypes.Structure):
                 ("num_coeffs", ctypes.c_int64), ("M_max", ctypes.c_int64), ("M", ctypes.c_int64),
                 ("n", ctypes.c_int * 3), ("N", ctypes.c_int * 3), ("rows", ctypes.c_int * 3),
                 ("sigma_eff", ctypes.c_double * 3), ("workspace_bytes", ctypes.c_int64),
-                ("kernel_launches", ctypes.c_int64)]
+                ("kernel_launches", ctypes.c_int64), ("tensor_cores", ctypes.c_int)]
 
 
 def library_path():
@@ -124,7 +124,7 @@ class Plan:
     """One NFSGLFT plan (sgl_plan_create): bandwidth B, up to M_max points."""
 
     def __init__(self, B, M_max, precision=PREC_FP64, window=WIN_KB, q=8, sigma=2.0, host_io=False, profile=False,
-                 device=None):
+                 device=None, simt=False, tensor_cores=False):
         if not torch.cuda.is_available():
             raise SGLError(3, "no CUDA device: the NFSGLFT runs only on the GPU")
         self.lib = load_library()
@@ -134,7 +134,9 @@ class Plan:
         self._h = ctypes.c_void_p()
         with torch.cuda.device(self.device):
             st = self.lib.sgl_plan_create(ctypes.byref(self._h), self.B, self.M_max, self.precision, self.window,
-                                          self.q, self.sigma, (FLAG_HOST_IO if host_io else 0) | (FLAG_PROFILE if profile else 0),
+                                          self.q, self.sigma,
+                                          (FLAG_HOST_IO if host_io else 0) | (FLAG_PROFILE if profile else 0) | (FLAG_SIMT if simt else 0)
+                                          | (FLAG_TC if tensor_cores else 0),
                                           _stream_handle(self.device))
         _check(st)
         self.Nc = num_coeffs(self.B)
@@ -161,7 +163,8 @@ class Plan:
         return {"B": inf.B, "q": inf.q, "precision": inf.precision, "window": inf.window,
                 "num_coeffs": inf.num_coeffs, "M_max": inf.M_max, "M": inf.M, "n": list(inf.n), "N": list(inf.N),
                 "rows": list(inf.rows), "sigma_eff": list(inf.sigma_eff), "workspace_bytes": inf.workspace_bytes,
-                "kernel_launches": inf.kernel_launches}
+                "kernel_launches": inf.kernel_launches,
+                "tensor_cores": {"interp": bool(inf.tensor_cores & 1), "grad": bool(inf.tensor_cores & 2)}}
 
     def profile(self):
         """{stage: (milliseconds, timed calls)} since the last call (plan made with profile=True)."""
@@ -245,7 +248,8 @@ class BatchPlan:
     """Many independent transforms issued together (sgl_batch_*): instance i has bandwidth
     Bs[i] and at most M_maxs[i] points; optional CUDA-graph capture of whole batch calls."""
 
-    def __init__(self, Bs, M_maxs, precision=PREC_FP64, window=WIN_KB, q=8, sigma=2.0, device=None):
+    def __init__(self, Bs, M_maxs, precision=PREC_FP64, window=WIN_KB, q=8, sigma=2.0, device=None, simt=False,
+                 tensor_cores=False):
         if not torch.cuda.is_available():
             raise SGLError(3, "no CUDA device: the NFSGLFT runs only on the GPU")
         self.lib = load_library()
@@ -257,7 +261,8 @@ class BatchPlan:
         with torch.cuda.device(self.device):
             st = self.lib.sgl_batch_create(ctypes.byref(self._h), self.n, (ctypes.c_int * self.n)(*self.Bs),
                                            (ctypes.c_int64 * self.n)(*M_maxs), int(precision), int(window), int(q),
-                                           float(sigma), 0, _stream_handle(self.device))
+                                           float(sigma), (FLAG_SIMT if simt else 0) | (FLAG_TC if tensor_cores else 0),
+                                           _stream_handle(self.device))
         _check(st)
         self.Ms = [0] * self.n
         self._keep = []

@@ -273,6 +273,8 @@ sgl_status plan_create_impl(sgl_plan **out, int B, int64_t M_max, int precision,
     if (window != SGL_WIN_KB && window != SGL_WIN_GAUSS) return set_error(SGL_ERR_ARG, "unknown window");
     if (q < 1 || q > kMaxQ) return set_error(SGL_ERR_ARG, "q must be in [1, 16]");
     if (!(sigma >= 1.5 && sigma <= 4.0)) return set_error(SGL_ERR_ARG, "sigma must be in [1.5, 4]");
+    if (flags & ~(SGL_FLAG_HOST_IO | SGL_FLAG_PROFILE | SGL_FLAG_SIMT | SGL_FLAG_TC)) return set_error(SGL_ERR_ARG, "unknown flag bits");
+    if ((flags & SGL_FLAG_SIMT) && (flags & SGL_FLAG_TC)) return set_error(SGL_ERR_ARG, "SGL_FLAG_SIMT and SGL_FLAG_TC exclude each other");
 
     PlanHolder *h = new (std::nothrow) PlanHolder();
     if (!h) return set_error(SGL_ERR_ALLOC, "host allocation failed");
@@ -307,7 +309,9 @@ sgl_status plan_create_impl(sgl_plan **out, int B, int64_t M_max, int precision,
     }
     {
         BinGeom &g = p->bins;
-        g.S2 = 33 - 2 * q;
+        // FP32 plans with q <= 8: a multiple of 4, so that the tensor-core kernels' TMA boxes start
+        // 16-byte aligned (lanes from sb2 * S2 - tc_halo(q)); otherwise as wide as one warp allows
+        g.S2 = (precision == SGL_FP32_MIXED && q <= 8) ? 4 * ((32 - tc_halo(q) - q) / 4) : 33 - 2 * q;
         g.C0 = (precision == SGL_FP32_MIXED) ? 8 : 4;   // must match the spreading kernels' template sizes
         g.C1 = (precision == SGL_FP32_MIXED) ? 8 : 2;
         g.ncell[0] = p->ax[0].N / 2 + 1;
@@ -373,8 +377,14 @@ sgl_status plan_create_impl(sgl_plan **out, int B, int64_t M_max, int precision,
         ALLOC(b.io_vals, 2 * Mc);
         ALLOC(b.io_grad, 3 * Mc);
     }
+    p->tc = tc_eligible(p);
+    tc_choose(p);
+    p->tc = p->tc_interp || p->tc_grad;
+    if (p->tc) ALLOC(b.planes, (size_t)tc_plane_floats(p));
 #undef ALLOC
     p->work_bytes = A.bytes;
+    if (p->tc && (e = tc_make_tensor_map(p)) != cudaSuccess)
+        return fail(SGL_ERR_CUDA, std::string("TMA descriptor of the grid planes: ") + cudaGetErrorString(e));
     if (flags & SGL_FLAG_PROFILE) p->prof = new (std::nothrow) Profiler();
 
     // ---- host precompute (FP64) and upload
@@ -473,6 +483,7 @@ sgl_status sgl_plan_info(const sgl_plan *plan, sgl_plan_info_t *info) {
     }
     info->workspace_bytes = plan->work_bytes;
     info->kernel_launches = plan->launches;
+    info->tensor_cores = (plan->tc_interp ? 1 : 0) | (plan->tc_grad ? 2 : 0);
     return ok();
 }
 
@@ -675,6 +686,10 @@ sgl_status sgl_sync(sgl_plan *plan) {
     SGL_CUDA_TRY(cudaStreamSynchronize(plan->stream));
     int flagsv = 0;
     SGL_CUDA_TRY(cudaMemcpy(&flagsv, plan->b.dev_flags, sizeof(int), cudaMemcpyDeviceToHost));
+    if (flagsv & 2) {
+        SGL_CUDA_TRY(cudaMemset(plan->b.dev_flags, 0, sizeof(int)));
+        return set_error(SGL_ERR_TIMEOUT, "a tensor-core pipeline wait gave up (results of the last call are invalid)");
+    }
     if (flagsv & 1) {
         SGL_CUDA_TRY(cudaMemset(plan->b.dev_flags, 0, sizeof(int)));
         return set_error(SGL_ERR_NONFINITE, "a point coordinate was NaN or infinite (treated as the origin)");

@@ -86,7 +86,15 @@ struct Buffers {
     int *scan_tmp;             // block sums
     // host-IO staging
     double *io_xyz, *io_coef, *io_vals, *io_grad;
+    // tensor-core interpolation (FP32-mixed): grid as planes Re hi, Im hi, Re lo, Im lo [rows0][rows1][pitch]
+    float *planes;
 };
+
+// Tensor-core interpolation layout on the azimuthal axis: a super-bin's 32 lanes start at
+// grid index sb2 * S2 - tc_halo(q) (a multiple of 4, as a TMA box origin must be), and the
+// planes store columns -tc_halo(q) ... pitch - tc_halo(q) - 1, wrapped.
+__host__ __device__ inline int tc_halo(int q) { return 4 * ((q + 2) / 4); }
+__host__ __device__ inline int tc_pitch(int N2) { return (N2 + 32 + 3) / 4 * 4; }
 
 }  // namespace sgl
 
@@ -114,6 +122,9 @@ struct sgl_plan {
     int64_t nbins;
     int64_t work_bytes;
     bool points_set;
+    bool tc;                            // tensor-core kernels usable (planes and TMA map exist)
+    bool tc_interp, tc_grad;            // ... and chosen for the interpolation / the gradient
+    alignas(64) unsigned char tc_map[128];   // TMA descriptor of b.planes (CUtensorMap)
     sgl::Buffers b;
 };
 
@@ -141,6 +152,13 @@ cudaError_t launch_fft_adjoint(sgl_plan *p);    // grid (bufA) -> eta' full supp
 cudaError_t launch_interp(sgl_plan *p, double2 *vals);
 cudaError_t launch_spread(sgl_plan *p, const double2 *vals);
 cudaError_t launch_grad(sgl_plan *p, const double2 *gout, double *gxyz);
+// tensor-core interpolation / gradient (sgl_nufft_tc.cu)
+bool tc_eligible(const sgl_plan *p);
+void tc_choose(sgl_plan *p);
+int64_t tc_plane_floats(const sgl_plan *p);
+cudaError_t tc_make_tensor_map(sgl_plan *p);
+cudaError_t launch_interp_tc(sgl_plan *p, double2 *vals);
+cudaError_t launch_grad_tc(sgl_plan *p, const double2 *gout, double *gxyz);
 
 // explicit-pointer launchers (no plan) used by the allocation-free entry point
 cudaError_t launch_max_radius_raw(cudaStream_t s, const double *xyz, int64_t M, unsigned long long *r2max, int *flags);

@@ -8,99 +8,12 @@
 // A group of G lanes (G = 8, 16 or 32 >= 2q) handles one point: lane c owns the
 // azimuthal tap c, loops over the (2q)^2 rows (axis 0, axis 1), and the group
 // reduces with the azimuthal weights at the end.  Points are visited in bin order.
-#include "sgl_internal.cuh"
+#include "sgl_nufft_common.cuh"
 
 #include <algorithm>
 
 namespace sgl {
 namespace {
-
-template <typename T> struct CT;
-template <> struct CT<float> { using type = float2; };
-template <> struct CT<double> { using type = double2; };
-template <typename T> using C2 = typename CT<T>::type;
-
-__device__ __forceinline__ float d_exp(float x) { return expf(x); }
-__device__ __forceinline__ double d_exp(double x) { return exp(x); }
-__device__ __forceinline__ float d_expm1(float x) { return expm1f(x); }
-__device__ __forceinline__ double d_expm1(double x) { return expm1(x); }
-__device__ __forceinline__ float d_sqrt(float x) { return sqrtf(x); }
-__device__ __forceinline__ double d_sqrt(double x) { return sqrt(x); }
-
-// psi(x) and d psi / dx for |x| <= q (0 outside); peak-normalized: psi(0) = 1.
-// KB:    psi = [sinh(b s)/s] / [sinh(b q)/q],  s = sqrt(q^2 - x^2)
-//           = norm * exp(b (s - q)) * (1 - exp(-2 b s)) / s
-// Gauss: psi = exp(-x^2 / (2 lambda))
-template <int WIN, typename T>
-__device__ __forceinline__ T window(T x, T q, T par, T norm) {
-    if (fabs(x) > q) return (T)0;
-    if (WIN == SGL_WIN_KB) {
-        const T s = d_sqrt(q * q - x * x);
-        const T ratio = (s > (T)1e-6) ? -d_expm1(-(T)2 * par * s) / s : (T)2 * par;
-        return norm * d_exp(par * (s - q)) * ratio;
-    } else {
-        return d_exp(-x * x / ((T)2 * par));
-    }
-}
-
-template <int WIN, typename T>
-__device__ __forceinline__ T window_deriv(T x, T q, T par, T norm) {
-    if (fabs(x) > q) return (T)0;
-    if (WIN == SGL_WIN_KB) {
-        // d/dx [sinh(b s)/s] = -x (b s cosh(b s) - sinh(b s)) / s^3
-        const T s = d_sqrt(q * q - x * x);
-        if (s < (T)1e-4) return -x * norm * d_exp(-par * q) * ((T)2 / (T)3) * par * par * par;
-        const T em = d_exp(-(T)2 * par * s);
-        const T num = par * s * ((T)1 + em) - ((T)1 - em);
-        return -x * norm * d_exp(par * (s - q)) * num / (s * s * s);
-    } else {
-        return -x / par * d_exp(-x * x / ((T)2 * par));
-    }
-}
-
-struct NGeom {
-    int N[3], rows[3], first[3];
-    int q;
-    double par[3], norm[3];
-    // bins (see BinGeom): azimuthal chunk, columns per super-bin, super-bins per axis
-    int S2, C0, C1, nsb0, nsb1, nsb2, cmax0, cmax1;
-};
-
-__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
-    // elementwise a * b + c on a packed pair (fma.rn.f32x2)
-    unsigned long long ra = *reinterpret_cast<unsigned long long *>(&a);
-    unsigned long long rb = *reinterpret_cast<unsigned long long *>(&b);
-    unsigned long long rc = *reinterpret_cast<unsigned long long *>(&c);
-    unsigned long long rd;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(rd) : "l"(ra), "l"(rb), "l"(rc));
-    return *reinterpret_cast<float2 *>(&rd);
-}
-
-__device__ __forceinline__ int cell_clamped(double u, int cmax) { return min(max((int)floor(u), 0), cmax); }
-
-// i mod n in [0, n) for any int i
-__device__ __forceinline__ int wrap_index(int i, int n) {
-    int r = i % n;
-    return r < 0 ? r + n : r;
-}
-
-// storage row of grid index t, or -1 if a windowed axis does not store it (periodic axes wrap)
-__device__ __forceinline__ int row_checked(int t, int first, int rows, int N) {
-    if (rows == N) return wrap_index(t, N);
-    const int r = t - first;
-    return (r >= 0 && r < rows) ? r : -1;
-}
-
-// storage row of grid index t on an axis (windowed rows start at first = -q, periodic rows wrap)
-__device__ __forceinline__ int row_of(int t, int first, int rows, int N) {
-    int r = t - first;
-    if (r < 0) r += N;
-    if (r >= rows) r -= N;
-    return r;
-}
-
-__device__ __forceinline__ void atomic_add_c(float2 *p, float x, float y) { atomicAdd(&p->x, x); atomicAdd(&p->y, y); }
-__device__ __forceinline__ void atomic_add_c(double2 *p, double x, double y) { atomicAdd(&p->x, x); atomicAdd(&p->y, y); }
 
 template <typename T, int WIN, int G>
 __global__ void __launch_bounds__(256) k_spread(NGeom g, int64_t M, const double *__restrict__ u_sorted,
@@ -144,13 +57,6 @@ __global__ void __launch_bounds__(256) k_spread(NGeom g, int64_t M, const double
 // the loops (the FP64 pipe of GB300 runs at 1/64 of the FP32 rate).  G = 8/16/32 >= 2q lanes
 // serve one point: lane j evaluates the weights of tap j on each axis and shares them by
 // shuffle; the (2q)^2 rows are read once per point, lane = azimuthal tap, packed FP32 FMA.
-
-__device__ __forceinline__ void unpack_cells(float w, int &c0, int &c1, int &c2) {
-    const int v = __float_as_int(w);
-    c0 = v & 1023;
-    c1 = (v >> 10) & 1023;
-    c2 = (v >> 20) & 1023;
-}
 
 // N2T: the axis-2 length (the row stride) as a compile-time constant (0: read it from g) -- with
 // it the unrolled row loads use immediate offsets instead of per-load address arithmetic
@@ -286,28 +192,8 @@ __global__ void __launch_bounds__(256, 3) k_grad32(NGeom g, int64_t M, const flo
             v2y += __shfl_xor_sync(0xffffffffu, v2y, o);
         }
         if (live && gl == 0) {
-            // ds/dt_d = (N_d / 2 pi) ds/du_d;  t_d / pi = 2 u_d / N_d
-            const float k0 = g.N[0] * 0.15915494309189535f, k1 = g.N[1] * 0.15915494309189535f, k2 = g.N[2] * 0.15915494309189535f;
-            const float h0 = 2.f * ((float)c0 + pt.x) / g.N[0], h1 = 2.f * ((float)c1 + pt.y) / g.N[1], h2 = 2.f * ((float)c2 + pt.z) / g.N[2];
-            float st0, ct0h, sth, st1, ct1, sp, cp;
-            sincospif(h0, &st0, &ct0h);
-            sincospif(0.5f * h0, &sth, &ct0h);          // cos(t0 / 2)
-            sincospif(h1, &st1, &ct1);
-            sincospif(h2, &sp, &cp);
-            const float r = rho * ct0h * ct0h;            // r = rho (1 + cos t0) / 2
-            const float dt0dr = (st0 > 0.f) ? -2.f / (rho * st0) : 0.f;
-            const float ir = (r > 0.f) ? 1.f / r : 0.f;
-            const float irs = (r > 0.f && st1 > 0.f) ? 1.f / (r * st1) : 0.f;
-            const float er[3] = {st1 * cp, st1 * sp, ct1}, et[3] = {ct1 * cp, ct1 * sp, -st1}, ep[3] = {-sp, cp, 0.f};
             const int dst = perm[i];
-            const double2 gv = gout[dst];
-            const float gx = (float)gv.x, gy = (float)gv.y;
-            const float A = k0 * dt0dr, Bq = k1 * ir, Cq = k2 * irs;
-            for (int d = 0; d < 3; ++d) {
-                const float vx = A * v0x * er[d] + Bq * v1x * et[d] + Cq * v2x * ep[d];
-                const float vy = A * v0y * er[d] + Bq * v1y * et[d] + Cq * v2y * ep[d];
-                gxyz[3 * (int64_t)dst + d] = (double)(gx * vx + gy * vy);     // Re(conj(g) v)
-            }
+            grad_chain32(g, rho, c0, c1, c2, pt.x, pt.y, pt.z, v0x, v0y, v1x, v1y, v2x, v2y, gout[dst], gxyz + 3 * (int64_t)dst);
         }
     }
 }
@@ -592,27 +478,6 @@ __global__ void __launch_bounds__(256) k_grad64(NGeom g, int64_t M, const double
     }
 }
 
-NGeom make_geom(const sgl_plan *p) {
-    NGeom g{};
-    for (int d = 0; d < 3; ++d) {
-        g.N[d] = p->ax[d].N;
-        g.rows[d] = p->ax[d].rows;
-        g.first[d] = p->ax[d].first;
-        g.par[d] = p->ax[d].wpar;
-        g.norm[d] = (p->window == SGL_WIN_KB) ? p->q / (-expm1(-2.0 * p->ax[d].wpar * p->q)) : 1.0;
-    }
-    g.q = p->q;
-    g.S2 = p->bins.S2;
-    g.C0 = p->bins.C0;
-    g.C1 = p->bins.C1;
-    g.nsb0 = p->bins.nsb[0];
-    g.nsb1 = p->bins.nsb[1];
-    g.nsb2 = p->bins.nsb[2];
-    g.cmax0 = p->ax[0].N / 2;
-    g.cmax1 = p->ax[1].N / 2;
-    return g;
-}
-
 // blocks of 256 threads for a grid-stride sweep over the points
 int nufft_blocks(int64_t M, int G) {
     const int64_t ppb = 256 / G;                 // points per block per sweep
@@ -721,6 +586,7 @@ cudaError_t grad_t(sgl_plan *p, const double2 *gout, double *gxyz) {
 
 cudaError_t launch_interp(sgl_plan *p, double2 *vals) {
     if (p->M == 0) return cudaSuccess;
+    if (p->tc_interp) return launch_interp_tc(p, vals);
     const bool f32 = p->prec == SGL_FP32_MIXED, kb = p->window == SGL_WIN_KB;
     if (f32) return kb ? interp_t<float, SGL_WIN_KB>(p, vals) : interp_t<float, SGL_WIN_GAUSS>(p, vals);
     return kb ? interp_t<double, SGL_WIN_KB>(p, vals) : interp_t<double, SGL_WIN_GAUSS>(p, vals);
@@ -735,6 +601,7 @@ cudaError_t launch_spread(sgl_plan *p, const double2 *vals) {
 
 cudaError_t launch_grad(sgl_plan *p, const double2 *gout, double *gxyz) {
     if (p->M == 0) return cudaSuccess;
+    if (p->tc_grad) return launch_grad_tc(p, gout, gxyz);
     const bool f32 = p->prec == SGL_FP32_MIXED, kb = p->window == SGL_WIN_KB;
     if (f32) return kb ? grad_t<float, SGL_WIN_KB>(p, gout, gxyz) : grad_t<float, SGL_WIN_GAUSS>(p, gout, gxyz);
     return kb ? grad_t<double, SGL_WIN_KB>(p, gout, gxyz) : grad_t<double, SGL_WIN_GAUSS>(p, gout, gxyz);

@@ -1,0 +1,162 @@
+// sgl_nufft_common.cuh -- window functions, grid geometry and index helpers shared by the
+// interpolation / spreading kernels (SIMT in sgl_nufft.cu, tensor-core in sgl_nufft_tc.cu).
+#pragma once
+
+#include "sgl_internal.cuh"
+
+namespace sgl {
+namespace {
+
+template <typename T> struct CT;
+template <> struct CT<float> { using type = float2; };
+template <> struct CT<double> { using type = double2; };
+template <typename T> using C2 = typename CT<T>::type;
+
+__device__ __forceinline__ float d_exp(float x) { return expf(x); }
+__device__ __forceinline__ double d_exp(double x) { return exp(x); }
+__device__ __forceinline__ float d_expm1(float x) { return expm1f(x); }
+__device__ __forceinline__ double d_expm1(double x) { return expm1(x); }
+__device__ __forceinline__ float d_sqrt(float x) { return sqrtf(x); }
+__device__ __forceinline__ double d_sqrt(double x) { return sqrt(x); }
+
+// psi(x) and d psi / dx for |x| <= q (0 outside); peak-normalized: psi(0) = 1.
+// KB:    psi = [sinh(b s)/s] / [sinh(b q)/q],  s = sqrt(q^2 - x^2)
+//           = norm * exp(b (s - q)) * (1 - exp(-2 b s)) / s
+// Gauss: psi = exp(-x^2 / (2 lambda))
+template <int WIN, typename T>
+__device__ __forceinline__ T window(T x, T q, T par, T norm) {
+    if (fabs(x) > q) return (T)0;
+    if (WIN == SGL_WIN_KB) {
+        const T s = d_sqrt(q * q - x * x);
+        const T ratio = (s > (T)1e-6) ? -d_expm1(-(T)2 * par * s) / s : (T)2 * par;
+        return norm * d_exp(par * (s - q)) * ratio;
+    } else {
+        return d_exp(-x * x / ((T)2 * par));
+    }
+}
+
+template <int WIN, typename T>
+__device__ __forceinline__ T window_deriv(T x, T q, T par, T norm) {
+    if (fabs(x) > q) return (T)0;
+    if (WIN == SGL_WIN_KB) {
+        // d/dx [sinh(b s)/s] = -x (b s cosh(b s) - sinh(b s)) / s^3
+        const T s = d_sqrt(q * q - x * x);
+        if (s < (T)1e-4) return -x * norm * d_exp(-par * q) * ((T)2 / (T)3) * par * par * par;
+        const T em = d_exp(-(T)2 * par * s);
+        const T num = par * s * ((T)1 + em) - ((T)1 - em);
+        return -x * norm * d_exp(par * (s - q)) * num / (s * s * s);
+    } else {
+        return -x / par * d_exp(-x * x / ((T)2 * par));
+    }
+}
+
+struct NGeom {
+    int N[3], rows[3], first[3];
+    int q;
+    double par[3], norm[3];
+    // bins (see BinGeom): azimuthal chunk, columns per super-bin, super-bins per axis
+    int S2, C0, C1, nsb0, nsb1, nsb2, cmax0, cmax1;
+};
+
+__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
+    // elementwise a * b + c on a packed pair (fma.rn.f32x2)
+    unsigned long long ra = *reinterpret_cast<unsigned long long *>(&a);
+    unsigned long long rb = *reinterpret_cast<unsigned long long *>(&b);
+    unsigned long long rc = *reinterpret_cast<unsigned long long *>(&c);
+    unsigned long long rd;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(rd) : "l"(ra), "l"(rb), "l"(rc));
+    return *reinterpret_cast<float2 *>(&rd);
+}
+
+__device__ __forceinline__ int cell_clamped(double u, int cmax) { return min(max((int)floor(u), 0), cmax); }
+
+// i mod n in [0, n) for any int i
+__device__ __forceinline__ int wrap_index(int i, int n) {
+    int r = i % n;
+    return r < 0 ? r + n : r;
+}
+
+// storage row of grid index t, or -1 if a windowed axis does not store it (periodic axes wrap)
+__device__ __forceinline__ int row_checked(int t, int first, int rows, int N) {
+    if (rows == N) return wrap_index(t, N);
+    const int r = t - first;
+    return (r >= 0 && r < rows) ? r : -1;
+}
+
+// storage row of grid index t on an axis (windowed rows start at first = -q, periodic rows wrap)
+__device__ __forceinline__ int row_of(int t, int first, int rows, int N) {
+    int r = t - first;
+    if (r < 0) r += N;
+    if (r >= rows) r -= N;
+    return r;
+}
+
+__device__ __forceinline__ void atomic_add_c(float2 *p, float x, float y) { atomicAdd(&p->x, x); atomicAdd(&p->y, y); }
+__device__ __forceinline__ void atomic_add_c(double2 *p, double x, double y) { atomicAdd(&p->x, x); atomicAdd(&p->y, y); }
+
+__device__ __forceinline__ void unpack_cells(float w, int &c0, int &c1, int &c2) {
+    const int v = __float_as_int(w);
+    c0 = v & 1023;
+    c1 = (v >> 10) & 1023;
+    c2 = (v >> 20) & 1023;
+}
+
+inline NGeom make_geom(const sgl_plan *p) {
+    NGeom g{};
+    for (int d = 0; d < 3; ++d) {
+        g.N[d] = p->ax[d].N;
+        g.rows[d] = p->ax[d].rows;
+        g.first[d] = p->ax[d].first;
+        g.par[d] = p->ax[d].wpar;
+        g.norm[d] = (p->window == SGL_WIN_KB) ? p->q / (-expm1(-2.0 * p->ax[d].wpar * p->q)) : 1.0;
+    }
+    g.q = p->q;
+    g.S2 = p->bins.S2;
+    g.C0 = p->bins.C0;
+    g.C1 = p->bins.C1;
+    g.nsb0 = p->bins.nsb[0];
+    g.nsb1 = p->bins.nsb[1];
+    g.nsb2 = p->bins.nsb[2];
+    g.cmax0 = p->ax[0].N / 2;
+    g.cmax1 = p->ax[1].N / 2;
+    return g;
+}
+
+// Chain rule in FP32 for one point: from the window-derivative sums v_d = ds/du_d (complex) to
+// Re(conj(g) grad_x s), written as three doubles.  t_d = 2 pi u_d / N_d are the torus angles
+// (r = rho (1 + cos t0) / 2, theta = t1, phi = t2); sincospi of t_d / pi keeps it in FP32.
+__device__ __forceinline__ void grad_chain32(const NGeom &g, float rho, int c0, int c1, int c2, float f0, float f1, float f2,
+                                             float v0x, float v0y, float v1x, float v1y, float v2x, float v2y, double2 gv,
+                                             double *out) {
+    // ds/dt_d = (N_d / 2 pi) ds/du_d;  t_d / pi = 2 u_d / N_d
+    const float k0 = g.N[0] * 0.15915494309189535f, k1 = g.N[1] * 0.15915494309189535f, k2 = g.N[2] * 0.15915494309189535f;
+    const float h0 = 2.f * ((float)c0 + f0) / g.N[0], h1 = 2.f * ((float)c1 + f1) / g.N[1], h2 = 2.f * ((float)c2 + f2) / g.N[2];
+    float st0, ct0h, sth, st1, ct1, sp, cp;
+    sincospif(h0, &st0, &ct0h);
+    sincospif(0.5f * h0, &sth, &ct0h);          // cos(t0 / 2)
+    sincospif(h1, &st1, &ct1);
+    sincospif(h2, &sp, &cp);
+    const float r = rho * ct0h * ct0h;            // r = rho (1 + cos t0) / 2
+    const float dt0dr = (st0 > 0.f) ? -2.f / (rho * st0) : 0.f;
+    const float ir = (r > 0.f) ? 1.f / r : 0.f;
+    const float irs = (r > 0.f && st1 > 0.f) ? 1.f / (r * st1) : 0.f;
+    const float er[3] = {st1 * cp, st1 * sp, ct1}, et[3] = {ct1 * cp, ct1 * sp, -st1}, ep[3] = {-sp, cp, 0.f};
+    const float gx = (float)gv.x, gy = (float)gv.y;
+    const float A = k0 * dt0dr, Bq = k1 * ir, Cq = k2 * irs;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        const float vx = A * v0x * er[d] + Bq * v1x * et[d] + Cq * v2x * ep[d];
+        const float vy = A * v0y * er[d] + Bq * v1y * et[d] + Cq * v2y * ep[d];
+        out[d] = (double)(gx * vx + gy * vy);     // Re(conj(g) v)
+    }
+}
+
+// rho = max |x| (1 + 2^-20) from the bit pattern of max |x|^2 (1 if no point is away from the origin)
+__device__ __forceinline__ float rho_from_r2max(const unsigned long long *r2max) {
+    double rhod = sqrt(__longlong_as_double((long long)*r2max)) * (1.0 + 0x1p-20);
+    if (!(rhod > 0.0)) rhod = 1.0;
+    return (float)rhod;
+}
+
+}  // namespace
+}  // namespace sgl

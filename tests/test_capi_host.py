@@ -60,6 +60,15 @@ def test_plan_create_rejects_bad_arguments_without_cuda(lib, args, word):
     assert word in lib.sgl_last_error().decode()
 
 
+@pytest.mark.parametrize("flags,word", [(16, "flag"), (4 | 8, "SGL_FLAG_SIMT")])
+def test_plan_create_rejects_bad_flags_without_cuda(lib, flags, word):
+    h = ctypes.c_void_p(123)
+    st = lib.sgl_plan_create(ctypes.byref(h), 8, 10, 1, 0, 8, 2.0, flags, None)
+    assert st == 1
+    assert h.value is None
+    assert word in lib.sgl_last_error().decode()
+
+
 def test_null_plan_is_rejected(lib):
     assert lib.sgl_forward(None, None, None) == 1
     assert lib.sgl_set_points(None, None, 0) == 1

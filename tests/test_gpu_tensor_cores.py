@@ -1,0 +1,131 @@
+"""Tensor-core (tcgen05) interpolation and gradient of FP32-mixed plans (marked gpu).
+
+FP32-mixed plans with q <= 8 and windowed axes 0 and 1 run the windowed interpolation and
+the window-derivative gradient as slab products on the tensor cores (3xTF32 split, FP32
+accumulation).  Checked here against the oracle's direct sums (same envelopes as the
+CUDA-core kernels) and against the CUDA-core kernels of the same plan type (SGL_FLAG_SIMT),
+on inputs that span many super-bins, super-bins with several 128-point chunks, a ragged
+last chunk, both windows and several cutoffs.
+"""
+import numpy as np
+import pytest
+import torch
+
+import paper_1809_10786_gb300 as sgl
+from paper_1809_10786_gb300 import inputs
+from oracle import direct
+
+pytestmark = pytest.mark.gpu
+DEV = torch.device("cuda", 0)
+
+
+def rel(a, b):
+    return float(np.abs(a - b).max() / np.abs(b).max())
+
+
+def gpu(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+
+
+def clustered(M, seed, centre=(0.3, -0.2, 0.1), width=0.05):
+    """Points packed into a few grid cells: super-bins with several 128-point chunks."""
+    rng = np.random.default_rng(seed)
+    return np.asarray(centre) + width * rng.standard_normal((M, 3))
+
+
+def well_conditioned(x, rho):
+    """Points away from the origin and the polar axis (t0 and theta away from 0 and pi)."""
+    r = np.linalg.norm(x, axis=1)
+    sin_theta = np.hypot(x[:, 0], x[:, 1]) / np.maximum(r, 1e-300)
+    return (r > 0.05 * rho) & (r < 0.95 * rho) & (sin_theta > 0.1)
+
+
+def pair(B, M, q, win, x):
+    tc = sgl.Plan(B, M, precision=sgl.PREC_FP32_MIXED, window=win, q=q, device=DEV, tensor_cores=True)
+    ref = sgl.Plan(B, M, precision=sgl.PREC_FP32_MIXED, window=win, q=q, device=DEV, simt=True)
+    for p in (tc, ref):
+        p.set_points(gpu(x))
+    return tc, ref
+
+
+# bounds: the FP32 envelope of the CUDA-core kernels at q >= 4 (gradients: FP32 rounding
+# amplified by the chain rule, about 1e-3 relative at these sizes); at q = 2 the window
+# approximation error itself (about 3e-4 for the Kaiser-Bessel window, sigma = 2) dominates
+@pytest.mark.parametrize("B,M,q,win,bound,gbound", [
+    (16, 3001, 8, sgl.WIN_KB, 5e-6, 3e-3),
+    (20, 2500, 6, sgl.WIN_KB, 5e-6, 3e-3),
+    (24, 4099, 4, sgl.WIN_KB, 2e-5, 3e-3),
+    (16, 1777, 2, sgl.WIN_KB, 2e-3, 5e-2),
+    (16, 2000, 8, sgl.WIN_GAUSS, 5e-6, 3e-3),
+])
+def test_tc_forward_and_gradient_match_oracle(B, M, q, win, bound, gbound):
+    c = inputs.coefficients(B, 8100 + B)
+    x = inputs.points_gaussian(M, 8101 + B)
+    g = inputs.complex_normal(M, 8102 + B)
+    tc, ref = pair(B, M, q, win, x)
+    assert tc.info()["tensor_cores"] == {"interp": True, "grad": True}
+    assert ref.info()["tensor_cores"] == {"interp": False, "grad": False}
+    f = tc.forward(gpu(c)).cpu().numpy()
+    gx = tc.grad_points(gpu(c), gpu(g)).cpu().numpy()
+    tc.sync()
+    f_simt = ref.forward(gpu(c)).cpu().numpy()
+    gx_simt = ref.grad_points(gpu(c), gpu(g)).cpu().numpy()
+    f_ref, _ = direct.forward(B, x, c)
+    g_ref, _ = direct.grad_points(B, x, c, g)
+    # forward: the two FP32 kernels agree to FP32 rounding, and both sit in the envelope
+    assert rel(f, f_simt) <= 2e-6
+    assert rel(f, f_ref) <= bound
+    # gradient: the chain rule's 1/(r sin theta) amplifies FP32 rounding near the axis and the
+    # origin differently for the two summation orders, so each is held to the oracle instead
+    # (and at q = 2 the window's approximation error itself is amplified by dt0/dr = -2 / (rho
+    # sin t0) near the origin, so the oracle comparison takes the well-conditioned points)
+    ok = well_conditioned(x, tc.rho())
+    e_tc, e_simt = rel(gx[ok], g_ref[ok]), rel(gx_simt[ok], g_ref[ok])
+    assert e_tc <= gbound, (e_tc, e_simt)
+    assert e_tc <= 3 * e_simt + 1e-6, (e_tc, e_simt)
+    assert rel(gx, gx_simt) <= 1e-3
+
+
+def test_tc_dense_super_bins_and_ragged_chunks():
+    # ~6000 points in a few cells: several 128-point chunks per super-bin, ragged last chunks
+    B, M = 16, 6007
+    c = inputs.coefficients(B, 8200)
+    x = clustered(M, 8201)
+    g = inputs.complex_normal(M, 8202)
+    tc, ref = pair(B, M, 8, sgl.WIN_KB, x)
+    f = tc.forward(gpu(c)).cpu().numpy()
+    gx = tc.grad_points(gpu(c), gpu(g)).cpu().numpy()
+    tc.sync()
+    assert rel(f, ref.forward(gpu(c)).cpu().numpy()) <= 2e-6
+    gx_simt = ref.grad_points(gpu(c), gpu(g)).cpu().numpy()
+    idx = inputs.subset(M, 300, 8203)
+    f_ref, _ = direct.forward(B, x[idx], c)
+    g_ref, _ = direct.grad_points(B, x[idx], c, g[idx])
+    assert rel(f[idx], f_ref) <= 5e-6
+    assert rel(gx[idx], g_ref) <= 1e-3
+    assert rel(gx[idx], g_ref) <= 3 * rel(gx_simt[idx], g_ref) + 1e-6
+
+
+@pytest.mark.parametrize("M", [1, 127, 128, 129])
+def test_tc_small_point_counts(M):
+    B = 12
+    c = inputs.coefficients(B, 8300 + M)
+    x = inputs.points_gaussian(M, 8301 + M)
+    tc, ref = pair(B, M, 8, sgl.WIN_KB, x)
+    f = tc.forward(gpu(c)).cpu().numpy()
+    tc.sync()
+    f_ref, _ = direct.forward(B, x, c)
+    assert rel(f, ref.forward(gpu(c)).cpu().numpy()) <= 2e-6
+    assert rel(f, f_ref) <= 5e-6
+
+
+def test_tc_is_used_only_where_eligible():
+    # FP64 plans, q > 8 and grids whose axis 1 is not windowed stay on the CUDA-core kernels
+    none = {"interp": False, "grad": False}
+    f32 = sgl.PREC_FP32_MIXED
+    assert sgl.Plan(16, 10, precision=sgl.PREC_FP64, device=DEV, tensor_cores=True).info()["tensor_cores"] == none
+    assert sgl.Plan(16, 10, precision=f32, q=9, device=DEV, tensor_cores=True).info()["tensor_cores"] == none
+    assert sgl.Plan(8, 10, precision=f32, q=8, device=DEV, tensor_cores=True).info()["tensor_cores"] == none
+    # default choice: the faster kernel per operation (tensor cores for the interpolation at q >= 7)
+    assert sgl.Plan(16, 10, precision=f32, q=8, device=DEV).info()["tensor_cores"] == {"interp": True, "grad": False}
+    assert sgl.Plan(16, 10, precision=f32, q=4, device=DEV).info()["tensor_cores"] == none
