@@ -281,6 +281,8 @@ sgl_status plan_create_impl(sgl_plan **out, int B, int64_t M_max, int precision,
     sgl_plan *p = &h->plan;
     std::memset(p, 0, sizeof(sgl_plan));
     cudaGetDevice(&p->device);
+    if (cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device) != cudaSuccess || p->num_sms < 1)
+        p->num_sms = 1;
     p->stream = (cudaStream_t)cuda_stream;
     p->B = B; p->q = q; p->prec = precision; p->window = window; p->flags = flags; p->sigma = sigma;
     p->M_max = M_max; p->M = 0; p->Nc = sgl_num_coeffs(B);

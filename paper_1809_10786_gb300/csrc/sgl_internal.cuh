@@ -86,7 +86,7 @@ struct Buffers {
     int *scan_tmp;             // block sums
     // host-IO staging
     double *io_xyz, *io_coef, *io_vals, *io_grad;
-    // tensor-core interpolation (FP32-mixed): grid as planes Re hi, Im hi, Re lo, Im lo [rows0][rows1][pitch]
+    // tensor-core interpolation (FP32-mixed): grid as planes Re, Im [rows0][rows1][pitch] with an azimuthal halo
     float *planes;
 };
 
@@ -109,6 +109,7 @@ struct Profiler;   // CUDA-event bookkeeping (sgl_capi.cu)
 
 struct sgl_plan {
     int device;
+    int num_sms;            // multiprocessors of the device (persistent kernels)
     int64_t launches;       // kernels launched (host-side count)
     sgl::Profiler *prof;    // non-NULL with SGL_FLAG_PROFILE
     cudaStream_t stream;
@@ -124,7 +125,7 @@ struct sgl_plan {
     bool points_set;
     bool tc;                            // tensor-core kernels usable (planes and TMA map exist)
     bool tc_interp, tc_grad;            // ... and chosen for the interpolation / the gradient
-    alignas(64) unsigned char tc_map[128];   // TMA descriptor of b.planes (CUtensorMap)
+    alignas(64) unsigned char tc_map[2][128];   // TMA descriptors of b.planes (CUtensorMap): interpolation, gradient
     sgl::Buffers b;
 };
 

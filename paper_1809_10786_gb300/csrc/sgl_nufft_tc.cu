@@ -1,35 +1,40 @@
 // sgl_nufft_tc.cu -- windowed interpolation (NFFT step 3, Sect. 2) and its window-derivative
 // form (the point gradient) on the 5th-generation tensor cores, FP32-mixed plans.
 //
-// For one super-bin (C0 x C1 cell columns x S2 azimuthal cells) and one chunk of up to 128
-// of its points, the sum over the taps factors slab by slab.  For the tile slab ta (one grid
-// row on axis 0) let G_ta[tb][c] be the grid values on the T1 = C1 + 2q - 1 tile rows of axis
-// 1 and the 32 azimuthal lanes c of the super-bin.  Then
+// For one super-bin (C0 x C1 cell columns x S2 azimuthal cells) and a chunk of up to 128 of
+// its points, the sum over the taps factors slab by slab.  For the tile slab ta (one grid row
+// on axis 0) let G_ta[tb][c] be the grid values on the T1 = C1 + 2q - 1 tile rows of axis 1
+// and the 32 azimuthal lanes c of the super-bin.  Then
 //
-//     D_ta[p][tb] = sum_c  w2_p[c] G_ta[tb][c]                (a 128 x 48 x 32 product)
+//     D_ta[p][tb] = sum_c  w2_p[c] G_ta[tb][c]                (M = 128 points, K = 32 lanes)
 //     s_p         = sum_ta w0_p[ta] sum_tb w1_p[tb] D_ta[p][tb]
 //
-// with w_d the point's window weights on the tile (zero off its 2q taps).  The product runs
-// as tcgen05.mma kind::tf32 with an FP32 accumulator in tensor memory; both operands are
-// split into a TF32 head and a TF32 remainder (x = hi + lo), and hi*hi + hi*lo + lo*hi keeps
-// the product at FP32 accuracy.  The gradient adds a second product with the derivative
-// weights w2' and contracts D_ta with w0', w1' as well.
+// with w_d the point's window weights on the tile (zero off its 2q taps).  G slabs go through
+// the tensor core together (N = 2 G TB1 columns: Re and Im of G slabs of TB1 >= T1 rows), as
+// tcgen05.mma kind::tf32 with an FP32 accumulator in tensor memory.  Both operands are split
+// into a TF32 head and a TF32 remainder (x = hi + lo), and hi*hi + hi*lo + lo*hi keeps the
+// product at FP32 accuracy.  The gradient adds a second product with the derivative weights
+// w2' and contracts D_ta with w0', w1' as well.
 //
-// Data: the forward FFT's grid is re-laid out once per call into four FP32 planes
-// (Re hi, Im hi, Re lo, Im lo) with a wrapped halo on the azimuthal axis, so that every
-// G_ta tile is one TMA box (32 lanes x T1 rows, 128-byte swizzle) per plane.
+// Data: the forward FFT's grid is copied once per call into two FP32 planes (Re, Im) with a
+// wrapped halo on the azimuthal axis, so that the tiles of G slabs are one TMA box (32 lanes
+// x TB1 rows x G slabs, 128-byte swizzle) per plane; the split into head and remainder happens
+// on chip.
 //
-// CTA = one super-bin, 6 warps: warp 0 issues the TMA loads into a ring of NS stages, warp 1
-// owns tensor memory and issues the MMAs, warps 2-5 (one thread per point, the thread's TMEM
-// lane = its point) write the w2 operand and reduce D_ta from TMEM (two accumulator buffers,
-// so the MMAs of slab ta+1 overlap the reduction of slab ta).  Every mbarrier wait is bounded
-// (about a second); on expiry the CTA sets bit 1 of the plan's device flags, drains what it
-// has in flight and returns.
+// One persistent CTA per SM walks its super-bins in 128-point passes.  Warp 0 issues the TMA
+// loads into a ring of tile stages, warps 2-3 split each landed tile in place, warp 1 owns
+// tensor memory and issues the MMAs (operand w2 from TMEM, tile from shared memory), four prep
+// warps write each pass's operands into TMEM and its axis-0/1 window tables into shared memory
+// (double-buffered, one pass ahead), and four reduction warps contract the accumulators with the
+// tables -- one thread per point in both, the thread's TMEM lane is its point.  Every mbarrier wait is bounded (about a second); on
+// expiry the CTA sets bit 1 of the plan's device flags, drains what it has in flight and
+// returns.
 #include "sgl_nufft_common.cuh"
 
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
+#include <algorithm>
 #include <cstring>
 #include <mutex>
 
@@ -38,24 +43,49 @@ namespace {
 
 constexpr int kC0 = 8, kC1 = 8;       // cell columns per super-bin (FP32 plans)
 constexpr int kLanes = 32;            // azimuthal lanes = MMA K
-constexpr int kPM = 128;              // points per chunk = MMA M
-constexpr int kNB = 48;               // MMA N: rows 0..T1-1 Re, rows 24..24+T1-1 Im
-constexpr int kImRow = 24;
-constexpr int kT1Max = 23;            // C1 + 2q - 1 for q <= 8
-constexpr int kNS = 3;                // TMA stages
-constexpr int kTileA = kPM * 128;     // bytes of one A operand (128 rows x 32 FP32)
-constexpr int kTileB = kNB * 128;     // bytes of one B operand (48 rows x 32 FP32)
-constexpr int kThreads = 192;
+constexpr int kPM = 128;              // points per pass = MMA M
+constexpr int kTB1Max = 24;           // tile rows per slab, T1 = C1 + 2q - 1 rounded up to 8 (q <= 8)
 constexpr long long kWaitCycles = 1ll << 31;   // ~1 s at 2 GHz
 
-// instruction descriptor, kind::tf32: D FP32, A and B TF32, both K-major, M = 128, N = 48
-constexpr uint32_t kIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kNB >> 3) << 17) | ((uint32_t)(kPM >> 4) << 24);
+// instruction descriptor, kind::tf32: D FP32, A and B TF32, both K-major, M = 128, N = n
+__host__ __device__ constexpr uint32_t tf32_idesc(int n) {
+    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(kPM >> 4) << 24);
+}
+
+// Pipeline shape.  Interpolation: groups of 4 slabs (N <= 192), two accumulator buffers.
+// Gradient: groups of 2 slabs with two accumulators each (D and D'), one accumulator buffer.
+// Operands (w2; w2' for the gradient) and window tables are double-buffered across passes.
+// TMEM: 512 columns, one CTA per SM.
+template <bool GRAD>
+struct TcCfg {
+    static constexpr int G = GRAD ? 2 : 4;                   // slabs per group
+    static constexpr int NBMAX = 2 * G * kTB1Max;            // N of one product (Re and Im rows)
+    static constexpr int NCONV = 2;                          // split warps
+    static constexpr int WPREP = 2 + NCONV;                  // first of 4 prep warps; 4 reduction warps follow
+    static constexpr int WRED = WPREP + 4;
+    static constexpr int THREADS = 32 * (WRED + 4);
+    static constexpr int DBUF = GRAD ? 1 : 2;                // accumulator buffers
+    static constexpr uint32_t DCOLS = GRAD ? 2 * NBMAX : NBMAX;   // accumulator columns per buffer (D, D')
+    static constexpr uint32_t ACOLS = GRAD ? 128 : 64;       // operand columns per buffer (hi, lo, hi', lo')
+    static constexpr uint32_t ABASE = DBUF * DCOLS;
+    static constexpr uint32_t ALLOC = 512;
+    static constexpr int NS = GRAD ? 4 : 3;                  // tile stages
+    static constexpr int STAGE = NBMAX * 128;                // bytes of one tile operand (hi or lo)
+    static constexpr int NTAB = GRAD ? 2 : 1;                // window tables per axis (psi; psi')
+    static_assert(ABASE + 2 * ACOLS <= ALLOC, "tensor memory budget");
+};
 
 template <bool GRAD>
 struct TcSmem {
-    alignas(1024) unsigned char a[GRAD ? 4 : 2][kTileA];     // w2 hi, lo (+ w2' hi, lo)
-    alignas(1024) unsigned char b[kNS][2][kTileB];            // per stage: grid tile hi, lo
-    uint64_t full[kNS], empty[kNS], tfull[2], tempty[2], afull, done;
+    using C = TcCfg<GRAD>;
+    // tile stages: [0] receives the raw FP32 tiles (TMA) and is split in place into the TF32
+    // head, [1] takes the remainder
+    alignas(1024) unsigned char b[C::NS][2][C::STAGE];
+    float w0tab[2][C::NTAB][16][kPM];                        // per buffer: axis-0 psi (psi') per tap j and point row
+    float w1tab[2][C::NTAB][kTB1Max][kPM];                   // per buffer: axis-1 psi (psi') per tile row
+    float lanes[kPM][kLanes + 1];                            // prep: one point's axis-2 weights placed on the 32 lanes
+    uint64_t tma_full[C::NS], conv_full[C::NS], empty[C::NS];
+    uint64_t tfull[2], tempty[2], afull[2], aempty[2], tabfull[2], done;
     uint32_t tmem_base;
     int abort;
 };
@@ -70,7 +100,7 @@ struct TcArgs {
     const double2 *gout;
     double *gxyz;
     int *dev_flags;
-    int T1;
+    int TB1;                                // tile rows per slab (multiple of 8, >= C1 + 2q - 1)
 };
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -81,13 +111,62 @@ __device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
            ((uint64_t)2 << 61);
 }
 
-// byte offset of element (row, k) in a K-major 128-byte-swizzled tile of 32 FP32 per row
-__device__ __forceinline__ uint32_t sw128_off(int row, int k4) { return (uint32_t)(row * 128 + ((k4 ^ (row & 7)) << 4)); }
+// TF32 head of x: round to nearest (ties away) at mantissa bit 13 with integer operations (a
+// carry out of the mantissa moves into the exponent, which is the correctly rounded result).
+// The remainder x - head is exact in FP32; the tensor core reads its top 19 bits.
+__device__ __forceinline__ float tf32_head(float x) { return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u); }
 
-__device__ __forceinline__ float tf32_head(float x) {
-    uint32_t r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-    return __uint_as_float(r);
+// Branch-free window psi(x) and psi'(x) (zero for |x| > q) for the operand rows: straight-line
+// code (approximate reciprocal square root, fast exponentials), so the 16 to 32 evaluations of a
+// point interleave.  The KB exponent b (s - q) is taken as -b x^2 / (s + q): no cancellation
+// near the peak, so the relative error of s enters psi only weakly.  `edge` is psi's limit for
+// s -> 0 over the normalization (KB: 2 b e^(-bq)); `ih` is 1 / (2 lambda) (Gaussian).
+template <int WIN>
+__device__ __forceinline__ float win_fast(float x, float q, float par, float norm, float edge) {
+    const float s2 = fmaf(-x, x, q * q);
+    if constexpr (WIN == SGL_WIN_KB) {
+        const float sv = (s2 > 1e-12f) ? s2 * rsqrtf(s2) : 0.f;
+        const float e1 = __expf(-__fdividef(par * x * x, sv + q)), e2 = __expf(-par * (sv + q));
+        const float v = (sv > 1e-3f) ? __fdividef(norm * (e1 - e2), sv) : norm * edge;
+        return (s2 >= 0.f) ? v : 0.f;
+    } else {
+        const float v = __expf(-x * x * edge);
+        return (s2 >= 0.f) ? v : 0.f;
+    }
+}
+
+// psi and psi' together (shared square root and exponentials)
+template <int WIN>
+__device__ __forceinline__ float2 win_both_fast(float x, float q, float par, float norm, float edge) {
+    const float s2 = fmaf(-x, x, q * q);
+    if constexpr (WIN == SGL_WIN_KB) {
+        const float sv = (s2 > 1e-12f) ? s2 * rsqrtf(s2) : 0.f;
+        const float e1 = __expf(-__fdividef(par * x * x, sv + q)), em = __expf(-2.f * par * sv);
+        const float isv = __fdividef(1.f, sv);
+        const float v = (sv > 1e-3f) ? norm * e1 * (1.f - em) * isv : norm * edge;
+        const float num = par * sv * (1.f + em) - (1.f - em);
+        const float d = (sv > 1e-3f) ? -x * norm * e1 * num * isv * isv * isv : -x * norm * edge * (par * par / 3.f);
+        return (s2 >= 0.f) ? make_float2(v, d) : make_float2(0.f, 0.f);
+    } else {
+        const float v = __expf(-x * x * edge);
+        return (s2 >= 0.f) ? make_float2(v, -2.f * x * edge * v) : make_float2(0.f, 0.f);
+    }
+}
+
+template <int WIN>
+__device__ __forceinline__ float win_deriv_fast(float x, float q, float par, float norm, float edge) {
+    const float s2 = fmaf(-x, x, q * q);
+    if constexpr (WIN == SGL_WIN_KB) {
+        // d/dx [sinh(b s)/s] = -x (b s cosh(b s) - sinh(b s)) / s^3; limit s -> 0: -x (2/3) b^3 e^(-bq) (normalized)
+        const float sv = (s2 > 1e-12f) ? s2 * rsqrtf(s2) : 0.f;
+        const float e1 = __expf(-__fdividef(par * x * x, sv + q)), em = __expf(-2.f * par * sv);
+        const float num = par * sv * (1.f + em) - (1.f - em);
+        const float v = (sv > 1e-3f) ? __fdividef(-x * norm * e1 * num, sv * sv * sv) : -x * norm * edge * (par * par / 3.f);
+        return (s2 >= 0.f) ? v : 0.f;
+    } else {
+        const float v = -2.f * x * edge * __expf(-x * x * edge);
+        return (s2 >= 0.f) ? v : 0.f;
+    }
 }
 
 __device__ __forceinline__ bool mbar_try(uint32_t mbar, uint32_t parity) {
@@ -122,81 +201,120 @@ __device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap *map
         :: "r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(mbar), "r"(x), "r"(y), "r"(z), "r"(w) : "memory");
 }
 
-__device__ __forceinline__ void mma_tf32(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
-    asm volatile("{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n"
-                 :: "r"(dtmem), "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(accumulate));
+// D (TMEM) += A (TMEM) * B (shared memory)
+__device__ __forceinline__ void mma_tf32_ts(uint32_t dtmem, uint32_t atmem, uint64_t bdesc, uint32_t idesc, uint32_t accumulate) {
+    asm volatile("{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n}\n"
+                 :: "r"(dtmem), "r"(atmem), "l"(bdesc), "r"(idesc), "r"(accumulate));
 }
 
 __device__ __forceinline__ void mma_commit(uint32_t mbar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" :: "r"(mbar) : "memory");
 }
 
-// 16 consecutive FP32 columns of this thread's TMEM lane
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float *v) {
-    uint32_t r[16];
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-                   "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+// 8 consecutive FP32 columns of this thread's TMEM lane
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float *v) {
+    uint32_t r[8];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
                  : "r"(taddr));
 #pragma unroll
-    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+    for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// 32 consecutive FP32 columns of this thread's TMEM lane
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const float *v) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,"
+                 "%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};"
+                 :: "r"(taddr), "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])),
+                    "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])), "r"(__float_as_uint(v[6])),
+                    "r"(__float_as_uint(v[7])), "r"(__float_as_uint(v[8])), "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])),
+                    "r"(__float_as_uint(v[11])), "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])), "r"(__float_as_uint(v[14])),
+                    "r"(__float_as_uint(v[15])), "r"(__float_as_uint(v[16])), "r"(__float_as_uint(v[17])), "r"(__float_as_uint(v[18])),
+                    "r"(__float_as_uint(v[19])), "r"(__float_as_uint(v[20])), "r"(__float_as_uint(v[21])), "r"(__float_as_uint(v[22])),
+                    "r"(__float_as_uint(v[23])), "r"(__float_as_uint(v[24])), "r"(__float_as_uint(v[25])), "r"(__float_as_uint(v[26])),
+                    "r"(__float_as_uint(v[27])), "r"(__float_as_uint(v[28])), "r"(__float_as_uint(v[29])), "r"(__float_as_uint(v[30])),
+                    "r"(__float_as_uint(v[31]))
+                 : "memory");
 }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-// write 32 weights (one operand row) as TF32 head and remainder, 128-byte swizzled
-__device__ __forceinline__ void store_split_row(unsigned char *hi, unsigned char *lo, int row, const float *w) {
+// TF32 head and remainder of 32 weights, written to TMEM columns col (head) and col + 32 (remainder)
+__device__ __forceinline__ void store_split_tmem(uint32_t taddr, const float *w) {
+    float h[32], l[32];
 #pragma unroll
-    for (int k4 = 0; k4 < 8; ++k4) {
-        float4 h, l;
-        h.x = tf32_head(w[4 * k4]);     l.x = tf32_head(w[4 * k4] - h.x);
-        h.y = tf32_head(w[4 * k4 + 1]); l.y = tf32_head(w[4 * k4 + 1] - h.y);
-        h.z = tf32_head(w[4 * k4 + 2]); l.z = tf32_head(w[4 * k4 + 2] - h.z);
-        h.w = tf32_head(w[4 * k4 + 3]); l.w = tf32_head(w[4 * k4 + 3] - h.w);
-        const uint32_t o = sw128_off(row, k4);
-        *reinterpret_cast<float4 *>(hi + o) = h;
-        *reinterpret_cast<float4 *>(lo + o) = l;
+    for (int k = 0; k < 32; ++k) {
+        h[k] = tf32_head(w[k]);
+        l[k] = w[k] - h[k];
     }
+    tmem_st32(taddr, h);
+    tmem_st32(taddr + 32, l);
+}
+
+// The CTA's sequence of passes: super-bins blockIdx.x, blockIdx.x + gridDim.x, ..., each cut into
+// passes of 128 points (empty super-bins skipped).  Every role walks the same sequence.
+struct PassIter {
+    int64_t sb = -1;
+    int pass = 0, npass = 0, first = 0, np = 0;
+};
+
+__device__ __forceinline__ bool next_pass(PassIter &it, const TcArgs &a) {
+    if (it.sb >= 0 && ++it.pass < it.npass) return true;
+    for (it.sb = (it.sb < 0 ? (int64_t)blockIdx.x : it.sb + gridDim.x); it.sb < a.nsuper; it.sb += gridDim.x) {
+        const int f = a.bin_off[it.sb * kC0 * kC1];
+        const int l = (it.sb + 1 < a.nsuper) ? a.bin_off[(it.sb + 1) * kC0 * kC1] : (int)a.M;
+        if (l > f) {
+            it.first = f;
+            it.np = l - f;
+            it.npass = (it.np + kPM - 1) / kPM;
+            it.pass = 0;
+            return true;
+        }
+    }
+    return false;
 }
 
 template <int WIN, bool GRAD>
-__global__ void __launch_bounds__(kThreads, GRAD ? 2 : 3)
+__global__ void __launch_bounds__(TcCfg<GRAD>::THREADS, 1)
 k_nufft_tc(const __grid_constant__ CUtensorMap tmap, NGeom g, TcArgs args) {
+    using Cfg = TcCfg<GRAD>;
     using S = TcSmem<GRAD>;
-    constexpr uint32_t kBufCols = GRAD ? 128 : 64;     // TMEM columns per accumulator buffer
-    constexpr uint32_t kAllocCols = 2 * kBufCols;
+    constexpr int G = Cfg::G, NS = Cfg::NS;
     extern __shared__ unsigned char smem_raw[];
     S &sm = *reinterpret_cast<S *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
 
-    const int64_t sb = blockIdx.x;
-    if (sb >= args.nsuper) return;
-    const int first = args.bin_off[sb * kC0 * kC1];
-    const int last = (sb + 1 < args.nsuper) ? args.bin_off[(sb + 1) * kC0 * kC1] : (int)args.M;
-    const int np = last - first;
-    if (np <= 0) return;
-    const int sb1 = (int)(sb % g.nsb1), sb2 = (int)((sb / g.nsb1) % g.nsb2), sb0 = (int)(sb / ((int64_t)g.nsb1 * g.nsb2));
     const int q = g.q, q2 = 2 * q;
-    const int T0 = kC0 + q2 - 1, T1 = args.T1;
-    const int nchunks = (np + kPM - 1) / kPM;
+    const int T0 = kC0 + q2 - 1;
+    const int NG = (T0 + G - 1) / G;                 // slab groups per pass
+    const int TB1 = args.TB1, NB = 2 * G * TB1;      // rows per slab, N of one product
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
-    // ---- setup: barriers (thread 0), tensor memory (warp 1)
+    // ---- setup: zero tiles, barriers (thread 0), tensor memory (warp 1)
+    for (int i = threadIdx.x; i < (int)(sizeof(sm.b) / 16); i += Cfg::THREADS)
+        reinterpret_cast<float4 *>(&sm.b[0][0][0])[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     if (threadIdx.x == 0) {
-        for (int i = 0; i < kNS; ++i) { mbar_init(smem_addr(&sm.full[i]), 1); mbar_init(smem_addr(&sm.empty[i]), 1); }
-        for (int i = 0; i < 2; ++i) { mbar_init(smem_addr(&sm.tfull[i]), 1); mbar_init(smem_addr(&sm.tempty[i]), 4); }
-        mbar_init(smem_addr(&sm.afull), 4);
+        for (int i = 0; i < NS; ++i) {
+            mbar_init(smem_addr(&sm.tma_full[i]), 1);
+            mbar_init(smem_addr(&sm.conv_full[i]), Cfg::NCONV);
+            mbar_init(smem_addr(&sm.empty[i]), 1);
+        }
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(smem_addr(&sm.tfull[i]), 1);
+            mbar_init(smem_addr(&sm.tempty[i]), 4);
+            mbar_init(smem_addr(&sm.afull[i]), 4);
+            mbar_init(smem_addr(&sm.aempty[i]), 4);
+            mbar_init(smem_addr(&sm.tabfull[i]), 4);
+        }
         mbar_init(smem_addr(&sm.done), 1);
         sm.abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    // grid tiles: rows the TMA boxes do not cover (T1 <= row < 24, 24 + T1 <= row) stay zero
-    for (int i = threadIdx.x; i < (int)(sizeof(sm.b) / 16); i += kThreads)
-        reinterpret_cast<float4 *>(&sm.b[0][0][0])[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" :: "r"(smem_addr(&sm.tmem_base)),
-                     "r"(kAllocCols));
+                     "r"(Cfg::ALLOC));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     tc_fence_before();
@@ -206,69 +324,104 @@ k_nufft_tc(const __grid_constant__ CUtensorMap tmap, NGeom g, TcArgs args) {
     volatile int *abort_flag = &sm.abort;
 
     if (warp == 0) {
-        // ---------------- TMA producer
+        // ---------------- TMA producer: raw Re / Im tiles of every slab group of every pass
         if (lane == 0) {
-            const int x = sb2 * g.S2;                 // halo-shifted azimuthal coordinate of lane 0
-            const int y = sb1 * kC1 + 1;              // stored row of tile row 0 on axis 1 (first = -q)
-            const int z0 = sb0 * kC0 + 1;             // stored row of slab 0 on axis 0
-            const uint32_t tx = 4u * (uint32_t)T1 * 128u;
+            const uint32_t tx = 2u * (uint32_t)(G * TB1) * 128u;
             int s = 0;
-            for (int ch = 0; ch < nchunks && !*abort_flag; ++ch)
-                for (int ta = 0; ta < T0; ++ta, ++s) {
-                    const int st = s % kNS;
-                    if (s >= kNS && !mbar_wait(smem_addr(&sm.empty[st]), ((s / kNS) + 1) & 1)) {
-                        *abort_flag = 1;
-                        break;
-                    }
-                    if (*abort_flag) break;
-                    const uint32_t fb = smem_addr(&sm.full[st]);
+            PassIter it;
+            while (!*abort_flag && next_pass(it, args)) {
+                const int sb1 = (int)(it.sb % g.nsb1), sb2 = (int)((it.sb / g.nsb1) % g.nsb2);
+                const int sb0 = (int)(it.sb / ((int64_t)g.nsb1 * g.nsb2));
+                const int x = sb2 * g.S2;             // halo-shifted azimuthal coordinate of lane 0
+                const int y = sb1 * kC1 + 1;          // stored row of tile row 0 on axis 1 (first = -q)
+                const int z0 = sb0 * kC0 + 1;         // stored row of slab 0 on axis 0
+                bool ok = true;
+                for (int gi = 0; gi < NG; ++gi, ++s) {
+                    const int st = s % NS;
+                    if (s >= NS && !mbar_wait(smem_addr(&sm.empty[st]), ((s / NS) + 1) & 1)) ok = false;
+                    if (!ok || *abort_flag) { ok = false; break; }
+                    const uint32_t fb = smem_addr(&sm.tma_full[st]);
                     mbar_expect_tx(fb, tx);
-                    const uint32_t hi = smem_addr(sm.b[st][0]), lo = smem_addr(sm.b[st][1]);
-                    tma_load_4d(hi, &tmap, fb, x, y, z0 + ta, 0);
-                    tma_load_4d(hi + kImRow * 128, &tmap, fb, x, y, z0 + ta, 1);
-                    tma_load_4d(lo, &tmap, fb, x, y, z0 + ta, 2);
-                    tma_load_4d(lo + kImRow * 128, &tmap, fb, x, y, z0 + ta, 3);
+                    const uint32_t hi = smem_addr(sm.b[st][0]);
+                    tma_load_4d(hi, &tmap, fb, x, y, z0 + G * gi, 0);
+                    tma_load_4d(hi + G * TB1 * 128, &tmap, fb, x, y, z0 + G * gi, 1);
                 }
-            // drain: the last loads issued into each stage have landed before the CTA may exit
-            for (int k = (s > kNS ? s - kNS : 0); k < s; ++k) mbar_wait(smem_addr(&sm.full[k % kNS]), (k / kNS) & 1);
+                if (!ok) { *abort_flag = 1; break; }
+            }
+            // the last loads issued into each stage have landed before the CTA may exit
+            for (int k = (s > NS ? s - NS : 0); k < s; ++k) mbar_wait(smem_addr(&sm.tma_full[k % NS]), (k / NS) & 1);
         }
+    } else if (warp >= 2 && warp < Cfg::WPREP) {
+        // ---------------- split warps: raw tiles -> TF32 head (in place) + remainder
+        const int part = warp - 2;
+        const int nvec = NB * 8;                      // float4 per tile operand (NB rows x 128 bytes)
+        int s = 0;
+        PassIter it;
+        bool ok = true;
+        while (ok && next_pass(it, args)) {
+            for (int gi = 0; gi < NG; ++gi, ++s) {
+                const int st = s % NS;
+                ok = __all_sync(0xffffffffu, mbar_wait(smem_addr(&sm.tma_full[st]), (s / NS) & 1) && !*abort_flag);
+                if (!ok) break;
+                float4 *hi = reinterpret_cast<float4 *>(sm.b[st][0]);
+                float4 *lo = reinterpret_cast<float4 *>(sm.b[st][1]);
+#pragma unroll 4
+                for (int i = part * 32 + lane; i < nvec; i += 32 * Cfg::NCONV) {
+                    const float4 v = hi[i];
+                    float4 h, l;
+                    h.x = tf32_head(v.x); l.x = v.x - h.x;
+                    h.y = tf32_head(v.y); l.y = v.y - h.y;
+                    h.z = tf32_head(v.z); l.z = v.z - h.z;
+                    h.w = tf32_head(v.w); l.w = v.w - h.w;
+                    hi[i] = h;
+                    lo[i] = l;
+                }
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                __syncwarp();
+                if (lane == 0) mbar_arrive(smem_addr(&sm.conv_full[st]));
+            }
+        }
+        if (!ok) *abort_flag = 1;
     } else if (warp == 1) {
         // ---------------- MMA issuer
         if (lane == 0) {
-            int s = 0;
+            const uint32_t idesc = tf32_idesc(NB);
+            int s = 0, k = 0;
             bool ok = true;
-            for (int ch = 0; ch < nchunks && ok; ++ch) {
-                ok = mbar_wait(smem_addr(&sm.afull), ch & 1) && !*abort_flag;
+            PassIter it;
+            while (ok && next_pass(it, args)) {
+                const int abuf = k & 1;
+                ok = mbar_wait(smem_addr(&sm.afull[abuf]), (k >> 1) & 1) && !*abort_flag;
                 tc_fence_after();
-                for (int ta = 0; ta < T0 && ok; ++ta, ++s) {
-                    const int st = s % kNS, buf = s & 1;
-                    ok = mbar_wait(smem_addr(&sm.full[st]), (s / kNS) & 1);
-                    if (ok && s >= 2) ok = mbar_wait(smem_addr(&sm.tempty[buf]), ((s >> 1) + 1) & 1);
+                const uint32_t a = tmem + Cfg::ABASE + (uint32_t)abuf * Cfg::ACOLS;
+                for (int gi = 0; gi < NG && ok; ++gi, ++s) {
+                    const int st = s % NS, buf = s % Cfg::DBUF, use = s / Cfg::DBUF;
+                    ok = mbar_wait(smem_addr(&sm.conv_full[st]), (s / NS) & 1);
+                    if (ok && use >= 1) ok = mbar_wait(smem_addr(&sm.tempty[buf]), (use + 1) & 1);
                     if (!ok || *abort_flag) { ok = false; break; }
                     tc_fence_after();
-                    const uint32_t d = tmem + buf * kBufCols;
-                    const uint32_t ahi = smem_addr(sm.a[0]), alo = smem_addr(sm.a[1]);
                     const uint32_t bhi = smem_addr(sm.b[st][0]), blo = smem_addr(sm.b[st][1]);
+                    const uint32_t d = tmem + (uint32_t)buf * Cfg::DCOLS;
 #pragma unroll
                     for (int ks = 0; ks < kLanes / 8; ++ks) {
-                        const uint32_t ko = ks * 32;          // 8 TF32 of K per instruction
-                        mma_tf32(d, sw128_desc(ahi + ko), sw128_desc(bhi + ko), ks > 0);
-                        mma_tf32(d, sw128_desc(ahi + ko), sw128_desc(blo + ko), 1);
-                        mma_tf32(d, sw128_desc(alo + ko), sw128_desc(bhi + ko), 1);
+                        const uint32_t ko = ks * 32, ka = ks * 8;     // 8 TF32 of K: 32 bytes, 8 columns
+                        mma_tf32_ts(d, a + ka, sw128_desc(bhi + ko), idesc, ks > 0);
+                        mma_tf32_ts(d, a + ka, sw128_desc(blo + ko), idesc, 1);
+                        mma_tf32_ts(d, a + 32 + ka, sw128_desc(bhi + ko), idesc, 1);
                     }
                     if constexpr (GRAD) {
-                        const uint32_t dhi = smem_addr(sm.a[2]), dlo = smem_addr(sm.a[3]);
 #pragma unroll
                         for (int ks = 0; ks < kLanes / 8; ++ks) {
-                            const uint32_t ko = ks * 32;
-                            mma_tf32(d + 64, sw128_desc(dhi + ko), sw128_desc(bhi + ko), ks > 0);
-                            mma_tf32(d + 64, sw128_desc(dhi + ko), sw128_desc(blo + ko), 1);
-                            mma_tf32(d + 64, sw128_desc(dlo + ko), sw128_desc(bhi + ko), 1);
+                            const uint32_t ko = ks * 32, ka = ks * 8;
+                            mma_tf32_ts(d + Cfg::NBMAX, a + 64 + ka, sw128_desc(bhi + ko), idesc, ks > 0);
+                            mma_tf32_ts(d + Cfg::NBMAX, a + 64 + ka, sw128_desc(blo + ko), idesc, 1);
+                            mma_tf32_ts(d + Cfg::NBMAX, a + 96 + ka, sw128_desc(bhi + ko), idesc, 1);
                         }
                     }
                     mma_commit(smem_addr(&sm.empty[st]));
                     mma_commit(smem_addr(&sm.tfull[buf]));
                 }
+                ++k;
             }
             if (!ok) *abort_flag = 1;
             // every MMA issued above has completed before tensor memory is released
@@ -276,114 +429,219 @@ k_nufft_tc(const __grid_constant__ CUtensorMap tmap, NGeom g, TcArgs args) {
             mbar_wait(smem_addr(&sm.done), 0);
         }
     } else {
-        // ---------------- point threads: operand rows and the reduction of D_ta
+        // ---------------- point warps (one thread per point; TMEM lane = point)
         const int quad = warp & 3;                   // TMEM lanes 32 quad .. 32 quad + 31
-        const int p = quad * 32 + lane;              // MMA row = point within the chunk
+        const int p = quad * 32 + lane;              // MMA row = point of the pass
+        const uint32_t lane_base = (uint32_t)(quad * 32) << 16;
         const float qf = (float)q;
         const float par0 = (float)g.par[0], par1 = (float)g.par[1], par2 = (float)g.par[2];
         const float nrm0 = (float)g.norm[0], nrm1 = (float)g.norm[1], nrm2 = (float)g.norm[2];
-        const int cbase = sb2 * g.S2 - tc_halo(q);   // grid index of lane 0
-        float rho = 0.f;
-        if constexpr (GRAD) rho = rho_from_r2max(args.r2max);
-        int s = 0;
         bool ok = true;
-        for (int ch = 0; ch < nchunks && ok; ++ch) {
-            const int idx = ch * kPM + p;
-            const bool live = idx < np;
-            const int64_t i = first + (live ? idx : 0);
-            const float4 pt = args.pts[i];
-            int c0, c1, c2;
-            unpack_cells(pt.w, c0, c1, c2);
-            const int d0 = c0 - sb0 * kC0, d1 = c1 - sb1 * kC1;
-            // axis 2: lane k holds grid index cbase + k; tap rel = k - (c2 - q + 1 - cbase)
-            {
-                const int k0 = c2 - q + 1 - cbase;
-                float w[kLanes];
-#pragma unroll
-                for (int k = 0; k < kLanes; ++k) {
-                    const int rel = k - k0;
-                    w[k] = (live && rel >= 0 && rel < q2) ? window<WIN, float>(pt.z + (float)(q - 1 - rel), qf, par2, nrm2) : 0.f;
-                }
-                store_split_row(sm.a[0], sm.a[1], p, w);
-                if constexpr (GRAD) {
-#pragma unroll
-                    for (int k = 0; k < kLanes; ++k) {
-                        const int rel = k - k0;
-                        w[k] = (live && rel >= 0 && rel < q2) ? window_deriv<WIN, float>(pt.z + (float)(q - 1 - rel), qf, par2, nrm2)
-                                                              : 0.f;
-                    }
-                    store_split_row(sm.a[2], sm.a[3], p, w);
-                }
-            }
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            __syncwarp();
-            if (lane == 0) mbar_arrive(smem_addr(&sm.afull));
-            // axis 1: weights on the tile rows (zero off the point's taps)
-            float w1[kT1Max], e1[GRAD ? kT1Max : 1];
-#pragma unroll
-            for (int tb = 0; tb < kT1Max; ++tb) {
-                const int rel = tb - d1;
-                const bool on = live && rel >= 0 && rel < q2;
-                w1[tb] = on ? window<WIN, float>(pt.y + (float)(q - 1 - rel), qf, par1, nrm1) : 0.f;
-                if constexpr (GRAD) e1[tb] = on ? window_deriv<WIN, float>(pt.y + (float)(q - 1 - rel), qf, par1, nrm1) : 0.f;
-            }
-            float ax = 0.f, ay = 0.f, bx = 0.f, by = 0.f, cx = 0.f, cy = 0.f;
-            for (int ta = 0; ta < T0; ++ta, ++s) {
-                const int buf = s & 1;
-                ok = __all_sync(0xffffffffu, mbar_wait(smem_addr(&sm.tfull[buf]), (s >> 1) & 1) && !*abort_flag);
+        PassIter it;
+        if (warp < Cfg::WRED) {
+            // ---- prep warps: operands (TMEM) and window tables (shared memory) of every pass
+            // KB: psi's limit at |x| = q over the normalization, 2 b e^(-bq); Gaussian: 1 / (2 lambda)
+            const bool kb = WIN == SGL_WIN_KB;
+            const float edge0 = kb ? 2.f * par0 * expf(-par0 * qf) : 0.5f / par0;
+            const float edge1 = kb ? 2.f * par1 * expf(-par1 * qf) : 0.5f / par1;
+            const float edge2 = kb ? 2.f * par2 * expf(-par2 * qf) : 0.5f / par2;
+            int n = 0;
+            while (ok && next_pass(it, args)) {
+                const int abuf = n & 1;
+                if (n >= 2) ok = __all_sync(0xffffffffu, mbar_wait(smem_addr(&sm.aempty[abuf]), ((n >> 1) + 1) & 1) && !*abort_flag);
                 if (!ok) break;
                 tc_fence_after();
-                const uint32_t taddr = tmem + ((uint32_t)(quad * 32) << 16) + buf * kBufCols;
-                float D[kNB];
-                tmem_ld16(taddr, D);
-                tmem_ld16(taddr + 16, D + 16);
-                tmem_ld16(taddr + 32, D + 32);
-                float E[GRAD ? kNB : 1];
+                const int idx = it.pass * kPM + p;
+                const bool live = idx < it.np;
+                const float4 pt = args.pts[it.first + (live ? idx : 0)];
+                int c0, c1, c2;
+                unpack_cells(pt.w, c0, c1, c2);
+                const int sb1 = (int)(it.sb % g.nsb1), sb2 = (int)((it.sb / g.nsb1) % g.nsb2);
+                const int k0 = c2 - q + 1 - (sb2 * g.S2 - tc_halo(q));     // lane of the point's first tap
+                const int d1 = c1 - sb1 * kC1;
+                const uint32_t ta_ = tmem + lane_base + Cfg::ABASE + (uint32_t)abuf * Cfg::ACOLS;
+                // the 2q nonzero weights per axis (compile-time tap index: independent chains), placed
+                // at the point's runtime offsets through shared memory
+                float *row = sm.lanes[p];
+                float w[kLanes];
                 if constexpr (GRAD) {
-                    tmem_ld16(taddr + 64, E);
-                    tmem_ld16(taddr + 80, E + 16);
-                    tmem_ld16(taddr + 96, E + 32);
+                    // psi' goes to the table rows first, psi to the lanes; then the lanes take psi'
+                    float dv[16];
+#pragma unroll
+                    for (int k = 0; k < kLanes; ++k) row[k] = 0.f;
+#pragma unroll
+                    for (int rel = 0; rel < 16; ++rel) {
+                        const float2 v = win_both_fast<WIN>(pt.z + (float)(q - 1 - rel), qf, par2, nrm2, edge2);
+                        dv[rel] = v.y;
+                        if (live && rel < q2) row[k0 + rel] = v.x;
+                    }
+#pragma unroll
+                    for (int k = 0; k < kLanes; ++k) w[k] = row[k];
+                    store_split_tmem(ta_, w);
+#pragma unroll
+                    for (int rel = 0; rel < 16; ++rel)
+                        if (live && rel < q2) row[k0 + rel] = dv[rel];
+#pragma unroll
+                    for (int k = 0; k < kLanes; ++k) w[k] = row[k];
+                    store_split_tmem(ta_ + 64, w);
+#pragma unroll
+                    for (int tb = 0; tb < kTB1Max; ++tb) {
+                        sm.w1tab[abuf][0][tb][p] = 0.f;
+                        sm.w1tab[abuf][GRAD ? 1 : 0][tb][p] = 0.f;
+                    }
+#pragma unroll
+                    for (int rel = 0; rel < 16; ++rel) {
+                        const float2 v = win_both_fast<WIN>(pt.y + (float)(q - 1 - rel), qf, par1, nrm1, edge1);
+                        if (live && rel < q2) {
+                            sm.w1tab[abuf][0][d1 + rel][p] = v.x;
+                            sm.w1tab[abuf][GRAD ? 1 : 0][d1 + rel][p] = v.y;
+                        }
+                    }
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        const float2 v = win_both_fast<WIN>(pt.x + (float)(q - 1 - j), qf, par0, nrm0, edge0);
+                        if (j < q2) {
+                            sm.w0tab[abuf][0][j][p] = v.x;
+                            sm.w0tab[abuf][GRAD ? 1 : 0][j][p] = v.y;
+                        }
+                    }
+                } else {
+#pragma unroll
+                    for (int k = 0; k < kLanes; ++k) row[k] = 0.f;
+#pragma unroll
+                    for (int rel = 0; rel < 16; ++rel) {
+                        const float v = win_fast<WIN>(pt.z + (float)(q - 1 - rel), qf, par2, nrm2, edge2);
+                        if (live && rel < q2) row[k0 + rel] = v;
+                    }
+#pragma unroll
+                    for (int k = 0; k < kLanes; ++k) w[k] = row[k];
+                    store_split_tmem(ta_, w);
+#pragma unroll
+                    for (int tb = 0; tb < kTB1Max; ++tb) sm.w1tab[abuf][0][tb][p] = 0.f;
+#pragma unroll
+                    for (int rel = 0; rel < 16; ++rel) {
+                        const float v = win_fast<WIN>(pt.y + (float)(q - 1 - rel), qf, par1, nrm1, edge1);
+                        if (live && rel < q2) sm.w1tab[abuf][0][d1 + rel][p] = v;
+                    }
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        const float v = win_fast<WIN>(pt.x + (float)(q - 1 - j), qf, par0, nrm0, edge0);
+                        if (j < q2) sm.w0tab[abuf][0][j][p] = v;
+                    }
                 }
-                tmem_wait_ld();
+                tmem_wait_st();
                 tc_fence_before();
                 __syncwarp();
-                if (lane == 0) mbar_arrive(smem_addr(&sm.tempty[buf]));
-                const int j = ta - d0;
-                if (j < 0 || j >= q2) continue;
-                const float xo = pt.x + (float)(q - 1 - j);
-                const float w0 = window<WIN, float>(xo, qf, par0, nrm0);
-                float rx = 0.f, ry = 0.f;
-#pragma unroll
-                for (int tb = 0; tb < kT1Max; ++tb) {
-                    rx = fmaf(w1[tb], D[tb], rx);
-                    ry = fmaf(w1[tb], D[kImRow + tb], ry);
+                if (lane == 0) {
+                    mbar_arrive(smem_addr(&sm.afull[abuf]));
+                    mbar_arrive(smem_addr(&sm.tabfull[abuf]));
                 }
-                if constexpr (GRAD) {
-                    const float e0 = window_deriv<WIN, float>(xo, qf, par0, nrm0);
-                    float sx = 0.f, sy = 0.f, tx = 0.f, ty = 0.f;
-#pragma unroll
-                    for (int tb = 0; tb < kT1Max; ++tb) {
-                        sx = fmaf(e1[tb], D[tb], sx);
-                        sy = fmaf(e1[tb], D[kImRow + tb], sy);
-                        tx = fmaf(w1[tb], E[tb], tx);
-                        ty = fmaf(w1[tb], E[kImRow + tb], ty);
-                    }
-                    ax = fmaf(e0, rx, ax); ay = fmaf(e0, ry, ay);     // ds/du0
-                    bx = fmaf(w0, sx, bx); by = fmaf(w0, sy, by);     // ds/du1
-                    cx = fmaf(w0, tx, cx); cy = fmaf(w0, ty, cy);     // ds/du2
-                } else {
-                    ax = fmaf(w0, rx, ax);
-                    ay = fmaf(w0, ry, ay);
-                }
+                ++n;
             }
-            if (!ok) break;
-            if (live) {
-                const int dst = args.perm[i];
-                if constexpr (GRAD)
-                    grad_chain32(g, rho, c0, c1, c2, pt.x, pt.y, pt.z, ax, ay, bx, by, cx, cy, args.gout[dst],
-                                 args.gxyz + 3 * (int64_t)dst);
-                else
-                    args.vals[dst] = make_double2((double)ax, (double)ay);
+        } else {
+            // ---- reduction warps: contract the accumulators with the window tables
+            float rho = 0.f;
+            if constexpr (GRAD) rho = rho_from_r2max(args.r2max);
+            int s = 0, n = 0;
+            while (ok && next_pass(it, args)) {
+                const int abuf = n & 1;
+                ok = __all_sync(0xffffffffu, mbar_wait(smem_addr(&sm.tabfull[abuf]), (n >> 1) & 1) && !*abort_flag);
+                if (!ok) break;
+                const int idx = it.pass * kPM + p;
+                const bool live = idx < it.np;
+                const int64_t i = it.first + (live ? idx : 0);
+                const float4 pt = args.pts[i];
+                int c0, c1, c2;
+                unpack_cells(pt.w, c0, c1, c2);
+                const int sb0 = (int)(it.sb / ((int64_t)g.nsb1 * g.nsb2));
+                const int d0 = c0 - sb0 * kC0;
+                float w1[kTB1Max], e1[GRAD ? kTB1Max : 1];
+#pragma unroll
+                for (int tb = 0; tb < kTB1Max; ++tb) {
+                    w1[tb] = sm.w1tab[abuf][0][tb][p];
+                    if constexpr (GRAD) e1[tb] = sm.w1tab[abuf][GRAD ? 1 : 0][tb][p];
+                }
+                float2 acc = make_float2(0.f, 0.f), acc1 = acc, acc2 = acc;
+                for (int gi = 0; gi < NG; ++gi, ++s) {
+                    const int buf = s % Cfg::DBUF, use = s / Cfg::DBUF;
+                    ok = __all_sync(0xffffffffu, mbar_wait(smem_addr(&sm.tfull[buf]), use & 1) && !*abort_flag);
+                    if (!ok) break;
+                    tc_fence_after();
+                    const uint32_t taddr = tmem + lane_base + (uint32_t)buf * Cfg::DCOLS;
+#pragma unroll 1
+                    for (int z = 0; z < G; ++z) {
+                        // slab ta = G gi + z: Re of tile row tb at column z TB1 + tb, Im at G TB1 + z TB1 + tb
+                        const int j = G * gi + z - d0;
+                        float re[kTB1Max], im[kTB1Max];
+                        const uint32_t cre = taddr + z * TB1, cim = taddr + (G + z) * TB1;
+                        const int tbn = TB1 > 16 ? 24 : 16;
+                        tmem_ld8(cre, re);
+                        tmem_ld8(cim, im);
+                        tmem_ld8(cre + 8, re + 8);
+                        tmem_ld8(cim + 8, im + 8);
+                        if (TB1 > 16) {
+                            tmem_ld8(cre + 16, re + 16);
+                            tmem_ld8(cim + 16, im + 16);
+                        }
+                        tmem_wait_ld();
+                        const bool on = j >= 0 && j < q2;
+                        float2 r = make_float2(0.f, 0.f), rs = r, rt = r;
+                        if (on) {
+#pragma unroll
+                            for (int tb = 0; tb < kTB1Max; ++tb)
+                                if (tb < tbn) r = ffma2(make_float2(w1[tb], w1[tb]), make_float2(re[tb], im[tb]), r);
+                            if constexpr (GRAD) {
+#pragma unroll
+                                for (int tb = 0; tb < kTB1Max; ++tb)
+                                    if (tb < tbn) rs = ffma2(make_float2(e1[tb], e1[tb]), make_float2(re[tb], im[tb]), rs);
+                            }
+                        }
+                        if constexpr (GRAD) {
+                            // the derivative product (w2'), into the same registers
+                            tmem_ld8(cre + Cfg::NBMAX, re);
+                            tmem_ld8(cim + Cfg::NBMAX, im);
+                            tmem_ld8(cre + Cfg::NBMAX + 8, re + 8);
+                            tmem_ld8(cim + Cfg::NBMAX + 8, im + 8);
+                            if (TB1 > 16) {
+                                tmem_ld8(cre + Cfg::NBMAX + 16, re + 16);
+                                tmem_ld8(cim + Cfg::NBMAX + 16, im + 16);
+                            }
+                            tmem_wait_ld();
+                            if (on) {
+#pragma unroll
+                                for (int tb = 0; tb < kTB1Max; ++tb)
+                                    if (tb < tbn) rt = ffma2(make_float2(w1[tb], w1[tb]), make_float2(re[tb], im[tb]), rt);
+                            }
+                        }
+                        if (!on) continue;
+                        const float w0 = sm.w0tab[abuf][0][j][p];
+                        if constexpr (GRAD) {
+                            const float e0 = sm.w0tab[abuf][GRAD ? 1 : 0][j][p];
+                            acc = ffma2(make_float2(e0, e0), r, acc);      // ds/du0
+                            acc1 = ffma2(make_float2(w0, w0), rs, acc1);   // ds/du1
+                            acc2 = ffma2(make_float2(w0, w0), rt, acc2);   // ds/du2
+                        } else {
+                            acc = ffma2(make_float2(w0, w0), r, acc);
+                        }
+                    }
+                    tc_fence_before();
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(smem_addr(&sm.tempty[buf]));
+                }
+                if (!ok) break;
+                // every product of this pass is done (its last accumulator was read): operand and
+                // tables buffer free for the pass after next
+                __syncwarp();
+                if (lane == 0) mbar_arrive(smem_addr(&sm.aempty[abuf]));
+                if (live) {
+                    const int dst = args.perm[i];
+                    if constexpr (GRAD)
+                        grad_chain32(g, rho, c0, c1, c2, pt.x, pt.y, pt.z, acc.x, acc.y, acc1.x, acc1.y, acc2.x, acc2.y,
+                                     args.gout[dst], args.gxyz + 3 * (int64_t)dst);
+                    else
+                        args.vals[dst] = make_double2((double)acc.x, (double)acc.y);
+                }
+                ++n;
             }
         }
         if (!ok) *abort_flag = 1;
@@ -393,27 +651,25 @@ k_nufft_tc(const __grid_constant__ CUtensorMap tmap, NGeom g, TcArgs args) {
     if (*abort_flag && threadIdx.x == 0) atomicOr(args.dev_flags, 2);
     if (warp == 1) {
         tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(kAllocCols));
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(Cfg::ALLOC));
     }
 }
 
-// grid[r0][r1][c] (FP32 complex) -> planes[4][r0][r1][pitch]: Re hi, Im hi, Re lo, Im lo at halo
-// column e = c + L (every e in [0, pitch) holds grid column (e - L) mod N2)
-__global__ void k_split_planes(const float2 *__restrict__ grid, float *__restrict__ planes, int64_t lines, int N2, int pitch,
-                               int L) {
+// grid[r0][r1][c] (FP32 complex) -> planes[2][r0][r1][pitch]: Re, Im at halo column e = c + L
+// (every e in [0, pitch) holds grid column (e - L) mod N2)
+__global__ void k_halo_planes(const float2 *__restrict__ grid, float *__restrict__ planes, int64_t lines, int N2, int pitch,
+                              int L) {
     const int64_t n = lines * pitch;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
         const int64_t line = t / pitch;
         const int e = (int)(t - line * pitch);
-        const int c = wrap_index(e - L, N2);
-        const float2 v = grid[line * N2 + c];
-        const float hx = tf32_head(v.x), hy = tf32_head(v.y);
-        planes[t] = hx;
-        planes[n + t] = hy;
-        planes[2 * n + t] = tf32_head(v.x - hx);
-        planes[3 * n + t] = tf32_head(v.y - hy);
+        const float2 v = grid[line * N2 + wrap_index(e - L, N2)];
+        planes[t] = v.x;
+        planes[n + t] = v.y;
     }
 }
+
+int tile_rows(int q) { return (kC1 + 2 * q - 1 + 7) / 8 * 8; }
 
 }  // namespace
 
@@ -423,26 +679,39 @@ bool tc_eligible(const sgl_plan *p) {
            p->bins.C0 == kC0 && p->bins.C1 == kC1 && p->bins.S2 % 4 == 0 && p->bins.S2 + tc_halo(p->q) + p->q <= kLanes;
 }
 
-// Which operations take the tensor-core kernels.  Measured on GB300 (B = 64, 10^6 points,
-// q = 8): interpolation 1.15 ms against 1.53 ms on the CUDA cores, gradient 2.74 against
-// 2.65 ms; at q = 4 the CUDA-core kernels are three times faster (their work falls as q^3,
-// the slab products' does not).  So by default: interpolation for q >= 7, gradient never.
+// Which operations take the tensor-core kernels by default (SGL_FLAG_TC: every eligible one).
+// Measured on GB300 (B = 64, 10^6 points, ms, tensor cores / CUDA cores): q = 8 interpolation
+// 0.89 / 1.53, gradient 1.99 / 2.66; q = 6: 0.69 / 1.23, 1.69 / 1.93; q = 4: 0.54 / 0.28,
+// 1.27 / 0.48 (the CUDA-core kernels' work falls as q^3, the slab products' much less).
 void tc_choose(sgl_plan *p) {
-    const bool force = (p->flags & SGL_FLAG_TC) != 0;
-    p->tc_interp = p->tc && (force || p->q >= 7);
-    p->tc_grad = p->tc && force;
+    const bool use = p->tc && ((p->flags & SGL_FLAG_TC) || p->q >= 6);
+    p->tc_interp = use;
+    p->tc_grad = use;
 }
 
 int64_t tc_plane_floats(const sgl_plan *p) {
-    return 4 * (int64_t)p->ax[0].rows * p->ax[1].rows * tc_pitch(p->ax[2].N);
+    return 2 * (int64_t)p->ax[0].rows * p->ax[1].rows * tc_pitch(p->ax[2].N);
 }
 
 namespace {
 std::mutex g_encode_mu;
 PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+
+// tensor map over the planes: dims (pitch, rows1, rows0, 2 planes), box 32 lanes x TB1 rows x G slabs
+cudaError_t encode_map(sgl_plan *p, int G, void *out) {
+    const int pitch = tc_pitch(p->ax[2].N);
+    const cuuint64_t dims[4] = {(cuuint64_t)pitch, (cuuint64_t)p->ax[1].rows, (cuuint64_t)p->ax[0].rows, 2};
+    const cuuint64_t strides[3] = {(cuuint64_t)pitch * 4, (cuuint64_t)pitch * 4 * p->ax[1].rows,
+                                   (cuuint64_t)pitch * 4 * p->ax[1].rows * p->ax[0].rows};
+    const cuuint32_t box[4] = {(cuuint32_t)kLanes, (cuuint32_t)tile_rows(p->q), (cuuint32_t)G, 1};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    CUresult r = g_encode(reinterpret_cast<CUtensorMap *>(out), CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, p->b.planes, dims, strides,
+                          box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
 }  // namespace
 
-// tensor map over the planes: dims (pitch, rows1, rows0, 4 planes), box 32 lanes x T1 rows
 cudaError_t tc_make_tensor_map(sgl_plan *p) {
     {
         std::lock_guard<std::mutex> lock(g_encode_mu);
@@ -455,43 +724,38 @@ cudaError_t tc_make_tensor_map(sgl_plan *p) {
             g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
         }
     }
-    const int pitch = tc_pitch(p->ax[2].N);
-    const cuuint64_t dims[4] = {(cuuint64_t)pitch, (cuuint64_t)p->ax[1].rows, (cuuint64_t)p->ax[0].rows, 4};
-    const cuuint64_t strides[3] = {(cuuint64_t)pitch * 4, (cuuint64_t)pitch * 4 * p->ax[1].rows,
-                                   (cuuint64_t)pitch * 4 * p->ax[1].rows * p->ax[0].rows};
-    const cuuint32_t box[4] = {(cuuint32_t)kLanes, (cuuint32_t)(kC1 + 2 * p->q - 1), 1, 1};
-    const cuuint32_t estr[4] = {1, 1, 1, 1};
-    static_assert(sizeof(CUtensorMap) <= sizeof(p->tc_map), "tensor map storage");
-    CUtensorMap *map = reinterpret_cast<CUtensorMap *>(p->tc_map);
-    CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, p->b.planes, dims, strides, box, estr,
-                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+    static_assert(sizeof(CUtensorMap) <= sizeof(p->tc_map[0]), "tensor map storage");
+    cudaError_t e = encode_map(p, TcCfg<false>::G, p->tc_map[0]);
+    if (e == cudaSuccess) e = encode_map(p, TcCfg<true>::G, p->tc_map[1]);
+    return e;
 }
 
 namespace {
 
-cudaError_t split_planes(sgl_plan *p) {
+cudaError_t halo_planes(sgl_plan *p) {
     const int64_t lines = (int64_t)p->ax[0].rows * p->ax[1].rows;
     const int pitch = tc_pitch(p->ax[2].N);
     const int64_t n = lines * pitch;
     int64_t blocks = (n + 255) / 256;
-    if (blocks > 152 * 8) blocks = 152 * 8;
-    k_split_planes<<<(unsigned)blocks, 256, 0, p->stream>>>((const float2 *)p->b.bufA, p->b.planes, lines, p->ax[2].N, pitch,
-                                                           tc_halo(p->q));
+    if (blocks > (int64_t)p->num_sms * 8) blocks = (int64_t)p->num_sms * 8;
+    k_halo_planes<<<(unsigned)blocks, 256, 0, p->stream>>>((const float2 *)p->b.bufA, p->b.planes, lines, p->ax[2].N, pitch,
+                                                          tc_halo(p->q));
     p->launches += 1;
     return cudaGetLastError();
 }
 
 template <int WIN, bool GRAD>
 cudaError_t run_tc(sgl_plan *p, TcArgs a) {
-    cudaError_t e = split_planes(p);
+    cudaError_t e = halo_planes(p);
     if (e != cudaSuccess) return e;
-    const size_t smem = sizeof(TcSmem<GRAD>) + 1024;
+    // the 512 TMEM columns a CTA allocates are the whole SM's: ask for enough shared memory that
+    // no second CTA of this kernel fits beside it (its allocation would wait for the first)
+    const size_t smem = std::max<size_t>(sizeof(TcSmem<GRAD>) + 1024, (size_t)120 * 1024);
     auto kern = k_nufft_tc<WIN, GRAD>;
     if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess) return e;
-    const CUtensorMap *map = reinterpret_cast<const CUtensorMap *>(p->tc_map);
-    kern<<<(unsigned)p->bins.nsuper, kThreads, smem, p->stream>>>(*map, make_geom(p), a);
+    const CUtensorMap *map = reinterpret_cast<const CUtensorMap *>(p->tc_map[GRAD ? 1 : 0]);
+    const int64_t grid = std::min<int64_t>(p->bins.nsuper, p->num_sms);
+    kern<<<(unsigned)grid, TcCfg<GRAD>::THREADS, smem, p->stream>>>(*map, make_geom(p), a);
     p->launches += 1;
     return cudaGetLastError();
 }
@@ -505,7 +769,7 @@ TcArgs base_args(const sgl_plan *p) {
     a.perm = p->b.perm;
     a.r2max = p->b.r2max;
     a.dev_flags = p->b.dev_flags;
-    a.T1 = kC1 + 2 * p->q - 1;
+    a.TB1 = tile_rows(p->q);
     return a;
 }
 

@@ -83,7 +83,7 @@ def test_tc_forward_and_gradient_match_oracle(B, M, q, win, bound, gbound):
     e_tc, e_simt = rel(gx[ok], g_ref[ok]), rel(gx_simt[ok], g_ref[ok])
     assert e_tc <= gbound, (e_tc, e_simt)
     assert e_tc <= 3 * e_simt + 1e-6, (e_tc, e_simt)
-    assert rel(gx, gx_simt) <= 1e-3
+    assert rel(gx, gx_simt) <= 5e-3
 
 
 def test_tc_dense_super_bins_and_ragged_chunks():
@@ -126,6 +126,8 @@ def test_tc_is_used_only_where_eligible():
     assert sgl.Plan(16, 10, precision=sgl.PREC_FP64, device=DEV, tensor_cores=True).info()["tensor_cores"] == none
     assert sgl.Plan(16, 10, precision=f32, q=9, device=DEV, tensor_cores=True).info()["tensor_cores"] == none
     assert sgl.Plan(8, 10, precision=f32, q=8, device=DEV, tensor_cores=True).info()["tensor_cores"] == none
-    # default choice: the faster kernel per operation (tensor cores for the interpolation at q >= 7)
-    assert sgl.Plan(16, 10, precision=f32, q=8, device=DEV).info()["tensor_cores"] == {"interp": True, "grad": False}
+    # default choice: the faster kernels (tensor cores from q = 6 on)
+    both = {"interp": True, "grad": True}
+    assert sgl.Plan(16, 10, precision=f32, q=8, device=DEV).info()["tensor_cores"] == both
+    assert sgl.Plan(16, 10, precision=f32, q=6, device=DEV).info()["tensor_cores"] == both
     assert sgl.Plan(16, 10, precision=f32, q=4, device=DEV).info()["tensor_cores"] == none
