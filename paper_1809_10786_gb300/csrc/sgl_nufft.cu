@@ -225,6 +225,14 @@ __device__ __forceinline__ void write_point_gradient(const NGeom &g, double rho,
 // warp w owns tile slab a = w (one grid row on axis 0) and keeps the sums for all T1 rows of
 // axis 1 and its 32 azimuthal lanes in registers while it sweeps every point of the super-bin;
 // each tile cell is then added to the grid once (atomically: neighbouring tiles overlap).
+// window value for the spreading staging: FP32 takes the branch-free evaluation, FP64 the
+// reference form
+template <int WIN, typename T>
+__device__ __forceinline__ T win_value(T x, T q, T par, T norm) {
+    if constexpr (sizeof(T) == 4) return window_pair32<WIN>(x, q, par, norm).x;
+    else return window<WIN, T>(x, q, par, norm);
+}
+
 template <typename T, int WIN, int Q2MAX, int C1>
 struct SpreadSmem {
     static constexpr int PCH = 64;
@@ -282,16 +290,17 @@ __global__ void __launch_bounds__(32 * (C0 + Q2MAX - 1)) k_spread_slab(NGeom g, 
                 c2 = min(max((int)floor(u2), 0), g.N[2] - 1);
                 f0 = u0 - c0; f1 = u1 - c1; f2 = u2 - c2;
             }
+            // window values (FP32: the branch-free, well-conditioned evaluation)
             if (e < Q2MAX) {
-                sm.w0[p][e] = (e < q2) ? window<WIN, T>(f0 + (T)(q - 1 - e), qT, par0, nrm0) : (T)0;
+                sm.w0[p][e] = (e < q2) ? win_value<WIN, T>(f0 + (T)(q - 1 - e), qT, par0, nrm0) : (T)0;
             } else if (e < Q2MAX + T1MAX) {
                 const int tb = e - Q2MAX;
                 const int rel = tb - (c1 - sb1 * C1);      // tap index of row tb for this point
-                sm.w1[p][tb] = (rel >= 0 && rel < q2 && tb < T1) ? window<WIN, T>(f1 + (T)(q - 1 - rel), qT, par1, nrm1) : (T)0;
+                sm.w1[p][tb] = (rel >= 0 && rel < q2 && tb < T1) ? win_value<WIN, T>(f1 + (T)(q - 1 - rel), qT, par1, nrm1) : (T)0;
             } else if (e < Q2MAX + T1MAX + 32) {
                 const int L = e - Q2MAX - T1MAX;
                 const int rel = cbase + L - (c2 - q + 1);
-                sm.w2[p][L] = (rel >= 0 && rel < q2) ? window<WIN, T>(f2 + (T)(q - 1 - rel), qT, par2, nrm2) : (T)0;
+                sm.w2[p][L] = (rel >= 0 && rel < q2) ? win_value<WIN, T>(f2 + (T)(q - 1 - rel), qT, par2, nrm2) : (T)0;
             } else {
                 const double2 y = vals[perm[pi]];
                 sm.y[p].x = (T)y.x;
@@ -312,10 +321,10 @@ __global__ void __launch_bounds__(32 * (C0 + Q2MAX - 1)) k_spread_slab(NGeom g, 
 #pragma unroll
                 for (int h = 0; h < T1MAX / 4; ++h) {
                     const float4 w = w1v[h];
-                    acc[4 * h].x = fmaf(w.x, z.x, acc[4 * h].x);         acc[4 * h].y = fmaf(w.x, z.y, acc[4 * h].y);
-                    acc[4 * h + 1].x = fmaf(w.y, z.x, acc[4 * h + 1].x); acc[4 * h + 1].y = fmaf(w.y, z.y, acc[4 * h + 1].y);
-                    acc[4 * h + 2].x = fmaf(w.z, z.x, acc[4 * h + 2].x); acc[4 * h + 2].y = fmaf(w.z, z.y, acc[4 * h + 2].y);
-                    acc[4 * h + 3].x = fmaf(w.w, z.x, acc[4 * h + 3].x); acc[4 * h + 3].y = fmaf(w.w, z.y, acc[4 * h + 3].y);
+                    acc[4 * h] = ffma2(make_float2(w.x, w.x), z, acc[4 * h]);
+                    acc[4 * h + 1] = ffma2(make_float2(w.y, w.y), z, acc[4 * h + 1]);
+                    acc[4 * h + 2] = ffma2(make_float2(w.z, w.z), z, acc[4 * h + 2]);
+                    acc[4 * h + 3] = ffma2(make_float2(w.w, w.w), z, acc[4 * h + 3]);
                 }
             } else {
 #pragma unroll

@@ -158,5 +158,33 @@ __device__ __forceinline__ float rho_from_r2max(const unsigned long long *r2max)
     return (float)rhod;
 }
 
+
+// psi(x) and psi'(x) in FP32 for |x| <= q (zero outside), well-conditioned and branch-free
+// (straight-line code, so the 16 taps of a point interleave): the Kaiser-Bessel exponent
+// b (s - q) is evaluated as -b x^2 / (s + q), which has no cancellation near the peak.
+// KB:    psi  = norm e^(b (s - q)) (1 - e^(-2 b s)) / s,   s = sqrt(q^2 - x^2)
+//        psi' = -x norm e^(b (s - q)) (b s (1 + e^(-2bs)) - (1 - e^(-2bs))) / s^3
+//        (limits s -> 0: psi -> 2 b norm e^(-bq), psi' -> -x (2/3) b^3 norm e^(-bq))
+// Gauss: psi = exp(-x^2 / (2 lambda)),  psi' = -x / lambda psi.
+template <int WIN>
+__device__ __forceinline__ float2 window_pair32(float x, float q, float par, float norm) {
+    const float s2 = fmaf(-x, x, q * q);
+    float v, d;
+    if (WIN == SGL_WIN_KB) {
+        const float sv = sqrtf(fmaxf(s2, 0.f));
+        const float e1 = expf(-__fdividef(par * x * x, sv + q));
+        const float em = expf(-2.f * par * sv), om = 1.f - em;
+        const float is = __fdividef(1.f, sv);
+        const bool tiny = sv < 1e-3f;
+        const float ebq = expf(-par * q);
+        v = tiny ? 2.f * par * norm * ebq : norm * e1 * om * is;
+        d = tiny ? -x * norm * ebq * (2.f / 3.f) * par * par * par : -x * norm * e1 * (par * sv * (1.f + em) - om) * is * is * is;
+    } else {
+        v = expf(-__fdividef(x * x, 2.f * par));
+        d = -__fdividef(x, par) * v;
+    }
+    return (s2 >= 0.f) ? make_float2(v, d) : make_float2(0.f, 0.f);
+}
+
 }  // namespace
 }  // namespace sgl
