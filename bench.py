@@ -198,10 +198,9 @@ def run_ours(args):
 
         def step():
             plan.set_points(x)
-            out["f"] = plan.forward(c)
+            out["f"], out["g"] = plan.forward_grad(c, g)      # forward values and point gradient, one pass
             a = plan.adjoint(y)
             out["a"] = sd.allreduce_coefficients(a)
-            out["g"] = plan.grad_points(c, g)
 
         for _ in range(args.warmup):
             step()
@@ -260,9 +259,8 @@ def run_ours(args):
 
             def qstep():
                 plan.set_points(x)
-                qout["f"] = plan.forward(c)
+                qout["f"], _ = plan.forward_grad(c, g)
                 sd.allreduce_coefficients(plan.adjoint(y))
-                plan.grad_points(c, g)
 
             for _ in range(args.warmup):
                 qstep()
@@ -294,9 +292,8 @@ def run_ours(args):
         go = torch.empty((M, 3), dtype=torch.float64).pin_memory()
 
         def hstep():
-            hplan.forward_host(xp, cp, fo)
+            hplan.forward_grad_host(xp, cp, gp, fo, go)
             hplan.adjoint_host(xp, yp, ao)
-            hplan.grad_points_host(xp, cp, gp, go)
 
         for _ in range(args.warmup):
             hstep()
@@ -308,9 +305,9 @@ def run_ours(args):
         el = sd.max_over_ranks(time.perf_counter() - t0, dev)
         Nc = hplan.Nc
         e2e = {"value": world * M / (el / args.steps) / 1e6, "unit": UNIT,
-               "h2d_bytes_per_step": 3 * 24 * M + 2 * 16 * Nc + 16 * M + 16 * M,
-               "d2h_bytes_per_step": 16 * M + 16 * Nc + 24 * M,
-               "path": "sgl_forward_host + sgl_adjoint_host + sgl_grad_points_host, pinned host buffers"}
+               "h2d_bytes_per_step": 2 * 24 * M + 16 * Nc + 16 * M + 16 * M,
+               "d2h_bytes_per_step": 16 * M + 24 * M + 16 * Nc,
+               "path": "sgl_forward_grad_host + sgl_adjoint_host, pinned host buffers"}
         hplan.close()
 
     head = results["fp32_mixed"]
@@ -329,7 +326,7 @@ def run_ours(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
             "data": "synthetic (seeded): coefficients U[-1/2,1/2]^2, points N(0, I/2) in |x| <= 5, values U[-1/2,1/2]^2",
             "config": {"workload": "B=64 (Nc=89440), M=1e6 points per GPU, sigma=2, Kaiser-Bessel q=8; step = set_points"
-                                   " + forward + adjoint + point gradient",
+                                   " + forward values with point gradient (sgl_forward_grad, one pass) + adjoint",
                        "B": B, "M_per_gpu": M, "q": q, "sigma": 2.0, "window": "kaiser-bessel",
                        "precision": "fp32-mixed (FFT, spreading, interpolation in FP32; conversions FP64)",
                        "parallelism": "points sharded, adjoint coefficients all-reduced" if world > 1 else "single GPU",

@@ -95,7 +95,8 @@ typedef struct {
     double sigma_eff[3];      /* N[d] / n[d] */
     int64_t workspace_bytes;  /* device bytes owned by the plan */
     int64_t kernel_launches;  /* CUDA kernels this plan has launched so far */
-    int tensor_cores;         /* bit 0: interpolation, bit 1: gradient run on the tcgen05 kernels */
+    int tensor_cores;         /* bit 0: interpolation, bit 1: gradient, bit 2: spreading run on the
+                                 tcgen05 kernels */
 } sgl_plan_info_t;
 
 /* Nc = B(B+1)(2B+1)/6 (Sect. 1); -1 if B < 1. */
@@ -174,6 +175,16 @@ sgl_status sgl_grad_points(sgl_plan *plan, const double *coef_dev, const double 
 sgl_status sgl_trig_coeffs(sgl_plan *plan, const double *coef_dev, double *eta_dev);
 
 /*
+ * Forward transform and point gradient together: vals_dev = Lambda coef (as sgl_forward) and
+ * gxyz_dev as sgl_grad_points, from one pass of the conversions, the FFT and one windowed
+ * sweep (the value is the gradient sweep's s itself), which is what a loss-and-gradient step
+ * needs.  coef_dev complex128 [Nc]; gout_dev complex128 [M]; vals_dev complex128 [M];
+ * gxyz_dev double [M][3]; all device pointers, 8-byte aligned, on the plan's stream.
+ */
+sgl_status sgl_forward_grad(sgl_plan *plan, const double *coef_dev, const double *gout_dev,
+                            double *vals_dev, double *gxyz_dev);
+
+/*
  * Host-buffer variants (need SGL_FLAG_HOST_IO): copy the inputs from host memory
  * into the plan's staging buffers, run set_points + forward (or adjoint) on the
  * plan's stream, copy the result back and synchronize the stream before returning.
@@ -186,6 +197,9 @@ sgl_status sgl_adjoint_host(sgl_plan *plan, const double *xyz_host, int64_t M,
 /* gout_host complex128 [M]; gxyz_host double [M][3] (see sgl_grad_points). */
 sgl_status sgl_grad_points_host(sgl_plan *plan, const double *xyz_host, int64_t M, const double *coef_host,
                                 const double *gout_host, double *gxyz_host);
+/* vals_host complex128 [M]; gxyz_host double [M][3] (see sgl_forward_grad). */
+sgl_status sgl_forward_grad_host(sgl_plan *plan, const double *xyz_host, int64_t M, const double *coef_host,
+                                 const double *gout_host, double *vals_host, double *gxyz_host);
 
 /*
  * Per-stage device times of a plan created with SGL_FLAG_PROFILE: synchronizes the

@@ -70,6 +70,8 @@ def load_library(build_if_missing=True):
                            ("sgl_grad_points", [vp, vp, vp, vp]), ("sgl_trig_coeffs", [vp, vp, vp]),
                            ("sgl_forward_host", [vp, vp, i64, vp, vp]), ("sgl_adjoint_host", [vp, vp, i64, vp, vp]),
                            ("sgl_grad_points_host", [vp, vp, i64, vp, vp, vp]),
+                           ("sgl_forward_grad", [vp, vp, vp, vp, vp]),
+                           ("sgl_forward_grad_host", [vp, vp, i64, vp, vp, vp, vp]),
                            ("sgl_profile", [vp, dp, ctypes.POINTER(i64)]), ("sgl_sync", [vp]),
                            ("sgl_trig_coeffs_noalloc", [ctypes.c_int, vp, i64, vp, vp, vp])]:
             f = getattr(lib, name)
@@ -164,7 +166,8 @@ class Plan:
                 "num_coeffs": inf.num_coeffs, "M_max": inf.M_max, "M": inf.M, "n": list(inf.n), "N": list(inf.N),
                 "rows": list(inf.rows), "sigma_eff": list(inf.sigma_eff), "workspace_bytes": inf.workspace_bytes,
                 "kernel_launches": inf.kernel_launches,
-                "tensor_cores": {"interp": bool(inf.tensor_cores & 1), "grad": bool(inf.tensor_cores & 2)}}
+                "tensor_cores": {"interp": bool(inf.tensor_cores & 1), "grad": bool(inf.tensor_cores & 2),
+                                 "spread": bool(inf.tensor_cores & 4)}}
 
     def profile(self):
         """{stage: (milliseconds, timed calls)} since the last call (plan made with profile=True)."""
@@ -215,6 +218,21 @@ class Plan:
                                         ctypes.c_void_p(out.data_ptr())))
         return out
 
+    def forward_grad(self, coef, gout, vals=None, gxyz=None):
+        """(f = Lambda coef, Re(conj(gout) grad_x f)) from one conversion, FFT and windowed sweep."""
+        coef = _dev_tensor(coef, torch.complex128, (self.Nc,), "coef", self.device)
+        gout = _dev_tensor(gout, torch.complex128, (self.M,), "gout", self.device)
+        if vals is None:
+            vals = torch.empty(self.M, dtype=torch.complex128, device=self.device)
+        if gxyz is None:
+            gxyz = torch.empty((self.M, 3), dtype=torch.float64, device=self.device)
+        vals = _dev_tensor(vals, torch.complex128, (self.M,), "vals", self.device)
+        gxyz = _dev_tensor(gxyz, torch.float64, (self.M, 3), "gxyz", self.device)
+        self._stream()
+        _check(self.lib.sgl_forward_grad(self._h, ctypes.c_void_p(coef.data_ptr()), ctypes.c_void_p(gout.data_ptr()),
+                                         ctypes.c_void_p(vals.data_ptr()), ctypes.c_void_p(gxyz.data_ptr())))
+        return vals, gxyz
+
     def trig_coeffs(self, coef):
         """eta_k on |k0| <= 2B-2, |k1|, |k2| <= B-1 as complex128 [4B-3, 2B-1, 2B-1]."""
         coef = _dev_tensor(coef, torch.complex128, (self.Nc,), "coef", self.device)
@@ -239,6 +257,11 @@ class Plan:
         _check(self.lib.sgl_grad_points_host(self._h, _host_ptr(xyz_host), int(xyz_host.shape[0]), _host_ptr(coef_host),
                                              _host_ptr(gout_host), _host_ptr(gxyz_host)))
         return gxyz_host
+
+    def forward_grad_host(self, xyz_host, coef_host, gout_host, vals_host, gxyz_host):
+        _check(self.lib.sgl_forward_grad_host(self._h, _host_ptr(xyz_host), int(xyz_host.shape[0]), _host_ptr(coef_host),
+                                              _host_ptr(gout_host), _host_ptr(vals_host), _host_ptr(gxyz_host)))
+        return vals_host, gxyz_host
 
     def sync(self):
         _check(self.lib.sgl_sync(self._h))

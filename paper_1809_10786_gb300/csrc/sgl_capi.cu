@@ -378,10 +378,11 @@ sgl_status plan_create_impl(sgl_plan **out, int B, int64_t M_max, int precision,
         ALLOC(b.io_coef, (size_t)(2 * p->Nc));
         ALLOC(b.io_vals, 2 * Mc);
         ALLOC(b.io_grad, 3 * Mc);
+        ALLOC(b.io_out, 2 * Mc);
     }
     p->tc = tc_eligible(p);
     tc_choose(p);
-    p->tc = p->tc_interp || p->tc_grad;
+    p->tc = p->tc_interp || p->tc_grad || p->tc_spread;
     if (p->tc) ALLOC(b.planes, (size_t)tc_plane_floats(p));
 #undef ALLOC
     p->work_bytes = A.bytes;
@@ -485,7 +486,7 @@ sgl_status sgl_plan_info(const sgl_plan *plan, sgl_plan_info_t *info) {
     }
     info->workspace_bytes = plan->work_bytes;
     info->kernel_launches = plan->launches;
-    info->tensor_cores = (plan->tc_interp ? 1 : 0) | (plan->tc_grad ? 2 : 0);
+    info->tensor_cores = (plan->tc_interp ? 1 : 0) | (plan->tc_grad ? 2 : 0) | (plan->tc_spread ? 4 : 0);
     return ok();
 }
 
@@ -597,7 +598,22 @@ sgl_status sgl_grad_points(sgl_plan *plan, const double *coef_dev, const double 
     if (sgl_status s = coef_to_zeta(plan, coef_dev)) return s;
     if (sgl_status s = zeta_to_grid(plan)) return s;
     StageScope sc(plan, ST_GRAD);
-    return launch_status(launch_grad(plan, (const double2 *)gout_dev, gxyz_dev), "gradient interpolation");
+    return launch_status(launch_grad(plan, (const double2 *)gout_dev, gxyz_dev, nullptr), "gradient interpolation");
+}
+
+sgl_status sgl_forward_grad(sgl_plan *plan, const double *coef_dev, const double *gout_dev, double *vals_dev,
+                            double *gxyz_dev) {
+    if (sgl_status s = check_plan(plan)) return s;
+    if (!plan->points_set) return set_error(SGL_ERR_STATE, "sgl_set_points has not been called");
+    if (!coef_dev || !aligned8(coef_dev)) return set_error(SGL_ERR_ARG, "coef must be a non-NULL, 8-byte aligned device pointer");
+    if (plan->M > 0 && (!gout_dev || !gxyz_dev || !vals_dev || !aligned8(gout_dev) || !aligned8(gxyz_dev) || !aligned8(vals_dev)))
+        return set_error(SGL_ERR_ARG, "gout, vals and gxyz must be non-NULL, 8-byte aligned device pointers");
+    if (plan->M == 0) return ok();
+    if (sgl_status s = coef_to_zeta(plan, coef_dev)) return s;
+    if (sgl_status s = zeta_to_grid(plan)) return s;
+    StageScope sc(plan, ST_GRAD);
+    return launch_status(launch_grad(plan, (const double2 *)gout_dev, gxyz_dev, (double2 *)vals_dev),
+                         "gradient interpolation");
 }
 
 sgl_status sgl_trig_coeffs(sgl_plan *plan, const double *coef_dev, double *eta_dev) {
@@ -680,6 +696,27 @@ sgl_status sgl_grad_points_host(sgl_plan *plan, const double *xyz_host, int64_t 
     if (sgl_status s = sgl_set_points(plan, plan->b.io_xyz, M)) return s;
     if (sgl_status s = sgl_grad_points(plan, plan->b.io_coef, plan->b.io_vals, plan->b.io_grad)) return s;
     if (M > 0) SGL_CUDA_TRY(cudaMemcpyAsync(gxyz_host, plan->b.io_grad, sizeof(double) * 3 * M, cudaMemcpyDeviceToHost, st));
+    return sgl_sync(plan);
+}
+
+sgl_status sgl_forward_grad_host(sgl_plan *plan, const double *xyz_host, int64_t M, const double *coef_host,
+                                 const double *gout_host, double *vals_host, double *gxyz_host) {
+    if (sgl_status s = check_plan(plan)) return s;
+    if (!(plan->flags & SGL_FLAG_HOST_IO)) return set_error(SGL_ERR_STATE, "plan was created without SGL_FLAG_HOST_IO");
+    if (M < 0 || M > plan->M_max) return set_error(SGL_ERR_ARG, "M must be in [0, M_max]");
+    if (!coef_host || (M > 0 && (!xyz_host || !gout_host || !vals_host || !gxyz_host))) return set_error(SGL_ERR_ARG, "NULL host buffer");
+    cudaStream_t st = plan->stream;
+    if (M > 0) {
+        SGL_CUDA_TRY(cudaMemcpyAsync(plan->b.io_xyz, xyz_host, sizeof(double) * 3 * M, cudaMemcpyHostToDevice, st));
+        SGL_CUDA_TRY(cudaMemcpyAsync(plan->b.io_vals, gout_host, sizeof(double2) * M, cudaMemcpyHostToDevice, st));
+    }
+    SGL_CUDA_TRY(cudaMemcpyAsync(plan->b.io_coef, coef_host, sizeof(double2) * plan->Nc, cudaMemcpyHostToDevice, st));
+    if (sgl_status s = sgl_set_points(plan, plan->b.io_xyz, M)) return s;
+    if (sgl_status s = sgl_forward_grad(plan, plan->b.io_coef, plan->b.io_vals, plan->b.io_out, plan->b.io_grad)) return s;
+    if (M > 0) {
+        SGL_CUDA_TRY(cudaMemcpyAsync(vals_host, plan->b.io_out, sizeof(double2) * M, cudaMemcpyDeviceToHost, st));
+        SGL_CUDA_TRY(cudaMemcpyAsync(gxyz_host, plan->b.io_grad, sizeof(double) * 3 * M, cudaMemcpyDeviceToHost, st));
+    }
     return sgl_sync(plan);
 }
 

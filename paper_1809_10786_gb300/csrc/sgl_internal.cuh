@@ -85,7 +85,7 @@ struct Buffers {
     int *bin_count, *bin_off;  // [nbins]
     int *scan_tmp;             // block sums
     // host-IO staging
-    double *io_xyz, *io_coef, *io_vals, *io_grad;
+    double *io_xyz, *io_coef, *io_vals, *io_grad, *io_out;
     // tensor-core interpolation (FP32-mixed): grid as planes Re, Im [rows0][rows1][pitch] with an azimuthal halo
     float *planes;
 };
@@ -124,7 +124,7 @@ struct sgl_plan {
     int64_t work_bytes;
     bool points_set;
     bool tc;                            // tensor-core kernels usable (planes and TMA map exist)
-    bool tc_interp, tc_grad;            // ... and chosen for the interpolation / the gradient
+    bool tc_interp, tc_grad, tc_spread; // ... and chosen for the interpolation / gradient / spreading
     alignas(64) unsigned char tc_map[2][128];   // TMA descriptors of b.planes (CUtensorMap): interpolation, gradient
     sgl::Buffers b;
 };
@@ -152,14 +152,15 @@ cudaError_t launch_fft_forward(sgl_plan *p);    // zeta -> grid (bufA)
 cudaError_t launch_fft_adjoint(sgl_plan *p);    // grid (bufA) -> eta' full support (bufB, FP64)
 cudaError_t launch_interp(sgl_plan *p, double2 *vals);
 cudaError_t launch_spread(sgl_plan *p, const double2 *vals);
-cudaError_t launch_grad(sgl_plan *p, const double2 *gout, double *gxyz);
+cudaError_t launch_grad(sgl_plan *p, const double2 *gout, double *gxyz, double2 *vals);   // vals: NULL or the values too
 // tensor-core interpolation / gradient (sgl_nufft_tc.cu)
 bool tc_eligible(const sgl_plan *p);
 void tc_choose(sgl_plan *p);
 int64_t tc_plane_floats(const sgl_plan *p);
 cudaError_t tc_make_tensor_map(sgl_plan *p);
 cudaError_t launch_interp_tc(sgl_plan *p, double2 *vals);
-cudaError_t launch_grad_tc(sgl_plan *p, const double2 *gout, double *gxyz);
+cudaError_t launch_grad_tc(sgl_plan *p, const double2 *gout, double *gxyz, double2 *vals);
+cudaError_t launch_spread_tc(sgl_plan *p, const double2 *vals);
 
 // explicit-pointer launchers (no plan) used by the allocation-free entry point
 cudaError_t launch_max_radius_raw(cudaStream_t s, const double *xyz, int64_t M, unsigned long long *r2max, int *flags);

@@ -122,7 +122,8 @@ __global__ void __launch_bounds__(256) k_interp32(NGeom g, int64_t M, const floa
 template <int WIN, int G, bool LIN1, int N2T>
 __global__ void __launch_bounds__(256, 3) k_grad32(NGeom g, int64_t M, const float4 *__restrict__ pts, const int *__restrict__ perm,
                                                 const unsigned long long *__restrict__ r2max, const float2 *__restrict__ grid,
-                                                const double2 *__restrict__ gout, double *__restrict__ gxyz) {
+                                                const double2 *__restrict__ gout, double *__restrict__ gxyz,
+                                                double2 *__restrict__ vals) {
     const int lane = threadIdx.x & 31, gl = lane & (G - 1);
     const int q = g.q, q2 = 2 * q;
     const float qf = (float)q;
@@ -182,6 +183,7 @@ __global__ void __launch_bounds__(256, 3) k_grad32(NGeom g, int64_t M, const flo
         }
         float v0x = ad0.x * w2, v0y = ad0.y * w2, v1x = ad1.x * w2, v1y = ad1.y * w2;
         float v2x = af.x * d2, v2y = af.y * d2;
+        float sx = af.x * w2, sy = af.y * w2;          // the value s itself (forward with gradient)
 #pragma unroll
         for (int o = G / 2; o > 0; o >>= 1) {
             v0x += __shfl_xor_sync(0xffffffffu, v0x, o);
@@ -190,10 +192,15 @@ __global__ void __launch_bounds__(256, 3) k_grad32(NGeom g, int64_t M, const flo
             v1y += __shfl_xor_sync(0xffffffffu, v1y, o);
             v2x += __shfl_xor_sync(0xffffffffu, v2x, o);
             v2y += __shfl_xor_sync(0xffffffffu, v2y, o);
+            if (vals) {
+                sx += __shfl_xor_sync(0xffffffffu, sx, o);
+                sy += __shfl_xor_sync(0xffffffffu, sy, o);
+            }
         }
         if (live && gl == 0) {
             const int dst = perm[i];
             grad_chain32(g, rho, c0, c1, c2, pt.x, pt.y, pt.z, v0x, v0y, v1x, v1y, v2x, v2y, gout[dst], gxyz + 3 * (int64_t)dst);
+            if (vals) vals[dst] = make_double2((double)sx, (double)sy);
         }
     }
 }
@@ -421,7 +428,7 @@ template <int WIN, int G>
 __global__ void __launch_bounds__(256) k_grad64(NGeom g, int64_t M, const double *__restrict__ u_sorted,
                                                 const int *__restrict__ perm, const unsigned long long *__restrict__ r2max,
                                                 const double2 *__restrict__ grid, const double2 *__restrict__ gout,
-                                                double *__restrict__ gxyz) {
+                                                double *__restrict__ gxyz, double2 *__restrict__ vals) {
     const int lane = threadIdx.x & 31, gl = lane & (G - 1);
     const int q = g.q, q2 = 2 * q;
     const double qd = (double)q;
@@ -470,6 +477,7 @@ __global__ void __launch_bounds__(256) k_grad64(NGeom g, int64_t M, const double
             bx = fma(w0, sx, bx); by = fma(w0, sy, by);
         }
         double f2x = d2 * fx, f2y = d2 * fy;
+        double sx = w2 * fx, sy = w2 * fy;             // the value s itself (forward with gradient)
         ax *= w2; ay *= w2; bx *= w2; by *= w2;
 #pragma unroll
         for (int o = G / 2; o > 0; o >>= 1) {
@@ -479,10 +487,15 @@ __global__ void __launch_bounds__(256) k_grad64(NGeom g, int64_t M, const double
             by += __shfl_xor_sync(0xffffffffu, by, o);
             f2x += __shfl_xor_sync(0xffffffffu, f2x, o);
             f2y += __shfl_xor_sync(0xffffffffu, f2y, o);
+            if (vals) {
+                sx += __shfl_xor_sync(0xffffffffu, sx, o);
+                sy += __shfl_xor_sync(0xffffffffu, sy, o);
+            }
         }
         if (live && gl == 0) {
             const int dst = perm[i];
             write_point_gradient(g, rho, u0, u1, u2, ax, ay, bx, by, f2x, f2y, gout[dst], gxyz + 3 * (int64_t)dst);
+            if (vals) vals[dst] = make_double2(sx, sy);
         }
     }
 }
@@ -559,14 +572,14 @@ cudaError_t spread_t(sgl_plan *p, const double2 *vals) {
 }
 
 template <typename T, int WIN>
-cudaError_t grad_t(sgl_plan *p, const double2 *gout, double *gxyz) {
+cudaError_t grad_t(sgl_plan *p, const double2 *gout, double *gxyz, double2 *vals) {
     NGeom g = make_geom(p);
     const int q2 = 2 * p->q;
     if constexpr (sizeof(T) == 4) {
         const float2 *gridf = (const float2 *)p->b.bufA;
         const bool lin = p->ax[1].rows < p->ax[1].N;
         const int n2 = p->ax[2].N;
-#define SGL_GRAD32(GG, LL, NN) k_grad32<WIN, GG, LL, NN><<<nufft_blocks(p->M, GG), 256, 0, p->stream>>>(g, p->M, p->b.pts32, p->b.perm, p->b.r2max, gridf, gout, gxyz)
+#define SGL_GRAD32(GG, LL, NN) k_grad32<WIN, GG, LL, NN><<<nufft_blocks(p->M, GG), 256, 0, p->stream>>>(g, p->M, p->b.pts32, p->b.perm, p->b.r2max, gridf, gout, gxyz, vals)
 #define SGL_GRAD32_N(GG)                                                        \
         if (lin && n2 == 128) SGL_GRAD32(GG, true, 128);                        \
         else if (lin && n2 == 256) SGL_GRAD32(GG, true, 256);                   \
@@ -581,11 +594,11 @@ cudaError_t grad_t(sgl_plan *p, const double2 *gout, double *gxyz) {
     } else {
         const double2 *gridd = (const double2 *)p->b.bufA;
         if (q2 <= 8)
-            k_grad64<WIN, 8><<<nufft_blocks(p->M, 8), 256, 0, p->stream>>>(g, p->M, p->b.u_sorted, p->b.perm, p->b.r2max, gridd, gout, gxyz);
+            k_grad64<WIN, 8><<<nufft_blocks(p->M, 8), 256, 0, p->stream>>>(g, p->M, p->b.u_sorted, p->b.perm, p->b.r2max, gridd, gout, gxyz, vals);
         else if (q2 <= 16)
-            k_grad64<WIN, 16><<<nufft_blocks(p->M, 16), 256, 0, p->stream>>>(g, p->M, p->b.u_sorted, p->b.perm, p->b.r2max, gridd, gout, gxyz);
+            k_grad64<WIN, 16><<<nufft_blocks(p->M, 16), 256, 0, p->stream>>>(g, p->M, p->b.u_sorted, p->b.perm, p->b.r2max, gridd, gout, gxyz, vals);
         else
-            k_grad64<WIN, 32><<<nufft_blocks(p->M, 32), 256, 0, p->stream>>>(g, p->M, p->b.u_sorted, p->b.perm, p->b.r2max, gridd, gout, gxyz);
+            k_grad64<WIN, 32><<<nufft_blocks(p->M, 32), 256, 0, p->stream>>>(g, p->M, p->b.u_sorted, p->b.perm, p->b.r2max, gridd, gout, gxyz, vals);
     }
     p->launches += 1;
     return cudaGetLastError();
@@ -603,17 +616,18 @@ cudaError_t launch_interp(sgl_plan *p, double2 *vals) {
 
 cudaError_t launch_spread(sgl_plan *p, const double2 *vals) {
     if (p->M == 0) return cudaSuccess;
+    if (p->tc_spread) return launch_spread_tc(p, vals);
     const bool f32 = p->prec == SGL_FP32_MIXED, kb = p->window == SGL_WIN_KB;
     if (f32) return kb ? spread_t<float, SGL_WIN_KB>(p, vals) : spread_t<float, SGL_WIN_GAUSS>(p, vals);
     return kb ? spread_t<double, SGL_WIN_KB>(p, vals) : spread_t<double, SGL_WIN_GAUSS>(p, vals);
 }
 
-cudaError_t launch_grad(sgl_plan *p, const double2 *gout, double *gxyz) {
+cudaError_t launch_grad(sgl_plan *p, const double2 *gout, double *gxyz, double2 *vals) {
     if (p->M == 0) return cudaSuccess;
-    if (p->tc_grad) return launch_grad_tc(p, gout, gxyz);
+    if (p->tc_grad) return launch_grad_tc(p, gout, gxyz, vals);
     const bool f32 = p->prec == SGL_FP32_MIXED, kb = p->window == SGL_WIN_KB;
-    if (f32) return kb ? grad_t<float, SGL_WIN_KB>(p, gout, gxyz) : grad_t<float, SGL_WIN_GAUSS>(p, gout, gxyz);
-    return kb ? grad_t<double, SGL_WIN_KB>(p, gout, gxyz) : grad_t<double, SGL_WIN_GAUSS>(p, gout, gxyz);
+    if (f32) return kb ? grad_t<float, SGL_WIN_KB>(p, gout, gxyz, vals) : grad_t<float, SGL_WIN_GAUSS>(p, gout, gxyz, vals);
+    return kb ? grad_t<double, SGL_WIN_KB>(p, gout, gxyz, vals) : grad_t<double, SGL_WIN_GAUSS>(p, gout, gxyz, vals);
 }
 
 }  // namespace sgl

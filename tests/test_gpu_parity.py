@@ -210,3 +210,33 @@ def test_other_oversampling_factors(sigma):
     f = p.forward(gpu(c)).cpu().numpy()
     f_ref, _ = direct.forward(B, x, c)
     assert rel(f, f_ref) <= (1e-6 if sigma < 2 else 1e-10)
+
+
+@pytest.mark.parametrize("prec,simt,ftol", [(sgl.PREC_FP64, False, 1e-12), (sgl.PREC_FP32_MIXED, False, 3e-6),
+                                            (sgl.PREC_FP32_MIXED, True, 3e-6)])
+def test_forward_grad_equals_separate_calls(prec, simt, ftol):
+    # one pass gives the forward values and the point gradient of the separate calls
+    B, M = 16, 2345
+    c, x, _ = case(B, M, 9100)
+    g = inputs.complex_normal(M, 9101)
+    p = plan_for(B, M, prec=prec, x=x, simt=simt)
+    f, gx = p.forward_grad(gpu(c), gpu(g))
+    f, gx = f.cpu().numpy(), gx.cpu().numpy()
+    assert rel(f, p.forward(gpu(c)).cpu().numpy()) <= ftol
+    assert np.array_equal(gx, p.grad_points(gpu(c), gpu(g)).cpu().numpy())
+    f_ref, _ = direct.forward(B, x, c)
+    assert rel(f, f_ref) <= (1e-10 if prec == sgl.PREC_FP64 else 5e-6)
+
+
+def test_forward_grad_host_buffers():
+    B, M = 10, 700
+    c, x, _ = case(B, M, 9200)
+    g = inputs.complex_normal(M, 9201)
+    p = plan_for(B, M, host_io=True)
+    vals = np.empty(M, dtype=np.complex128)
+    gxyz = np.empty((M, 3))
+    p.forward_grad_host(np.ascontiguousarray(x), c, g, vals, gxyz)
+    p.set_points(gpu(x))
+    f_dev, g_dev = p.forward_grad(gpu(c), gpu(g))
+    assert np.allclose(vals, f_dev.cpu().numpy(), rtol=0, atol=1e-13 * np.abs(vals).max())
+    assert np.allclose(gxyz, g_dev.cpu().numpy(), rtol=0, atol=1e-12 * np.abs(gxyz).max())

@@ -63,8 +63,8 @@ def test_tc_forward_and_gradient_match_oracle(B, M, q, win, bound, gbound):
     x = inputs.points_gaussian(M, 8101 + B)
     g = inputs.complex_normal(M, 8102 + B)
     tc, ref = pair(B, M, q, win, x)
-    assert tc.info()["tensor_cores"] == {"interp": True, "grad": True}
-    assert ref.info()["tensor_cores"] == {"interp": False, "grad": False}
+    assert tc.info()["tensor_cores"] == {"interp": True, "grad": True, "spread": True}
+    assert ref.info()["tensor_cores"] == {"interp": False, "grad": False, "spread": False}
     f = tc.forward(gpu(c)).cpu().numpy()
     gx = tc.grad_points(gpu(c), gpu(g)).cpu().numpy()
     tc.sync()
@@ -86,6 +86,28 @@ def test_tc_forward_and_gradient_match_oracle(B, M, q, win, bound, gbound):
     assert rel(gx, gx_simt) <= 5e-3
 
 
+@pytest.mark.parametrize("B,M,q,win,bound", [
+    (16, 3001, 8, sgl.WIN_KB, 5e-6),
+    (20, 2500, 6, sgl.WIN_KB, 5e-6),
+    (24, 4099, 4, sgl.WIN_KB, 2e-5),
+    (16, 2000, 8, sgl.WIN_GAUSS, 5e-6),
+])
+def test_tc_adjoint_matches_oracle(B, M, q, win, bound):
+    y = inputs.values(M, 8150 + B)
+    x = inputs.points_gaussian(M, 8151 + B)
+    tc, ref = pair(B, M, q, win, x)
+    a = tc.adjoint(gpu(y)).cpu().numpy()
+    tc.sync()
+    a_simt = ref.adjoint(gpu(y)).cpu().numpy()
+    a_ref, _ = direct.adjoint(B, x, y)
+    assert rel(a, a_simt) <= 2e-5
+    assert rel(a, a_ref) <= bound + 2e-5
+    # the adjoint pair stays an adjoint pair to FP32 rounding
+    c = inputs.coefficients(B, 8152 + B)
+    f = tc.forward(gpu(c)).cpu().numpy()
+    assert abs(np.vdot(y, f) - np.vdot(a, c)) <= 1e-5 * np.linalg.norm(f) * np.linalg.norm(y)
+
+
 def test_tc_dense_super_bins_and_ragged_chunks():
     # ~6000 points in a few cells: several 128-point chunks per super-bin, ragged last chunks
     B, M = 16, 6007
@@ -104,6 +126,9 @@ def test_tc_dense_super_bins_and_ragged_chunks():
     assert rel(f[idx], f_ref) <= 5e-6
     assert rel(gx[idx], g_ref) <= 1e-3
     assert rel(gx[idx], g_ref) <= 3 * rel(gx_simt[idx], g_ref) + 1e-6
+    # spreading with several 32-point chunks per super-bin
+    y = inputs.values(M, 8204)
+    assert rel(tc.adjoint(gpu(y)).cpu().numpy(), ref.adjoint(gpu(y)).cpu().numpy()) <= 2e-5
 
 
 @pytest.mark.parametrize("M", [1, 127, 128, 129])
@@ -121,13 +146,13 @@ def test_tc_small_point_counts(M):
 
 def test_tc_is_used_only_where_eligible():
     # FP64 plans, q > 8 and grids whose axis 1 is not windowed stay on the CUDA-core kernels
-    none = {"interp": False, "grad": False}
+    none = {"interp": False, "grad": False, "spread": False}
     f32 = sgl.PREC_FP32_MIXED
     assert sgl.Plan(16, 10, precision=sgl.PREC_FP64, device=DEV, tensor_cores=True).info()["tensor_cores"] == none
     assert sgl.Plan(16, 10, precision=f32, q=9, device=DEV, tensor_cores=True).info()["tensor_cores"] == none
     assert sgl.Plan(8, 10, precision=f32, q=8, device=DEV, tensor_cores=True).info()["tensor_cores"] == none
     # default choice: the faster kernels (tensor cores from q = 6 on)
-    both = {"interp": True, "grad": True}
+    both = {"interp": True, "grad": True, "spread": False}
     assert sgl.Plan(16, 10, precision=f32, q=8, device=DEV).info()["tensor_cores"] == both
     assert sgl.Plan(16, 10, precision=f32, q=6, device=DEV).info()["tensor_cores"] == both
     assert sgl.Plan(16, 10, precision=f32, q=4, device=DEV).info()["tensor_cores"] == none
