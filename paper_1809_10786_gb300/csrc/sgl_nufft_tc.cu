@@ -25,8 +25,8 @@
 // loads into a ring of tile stages, warps 2-3 split each landed tile in place, warp 1 owns
 // tensor memory and issues the MMAs (operand w2 from TMEM, tile from shared memory), four prep
 // warps write each pass's operands into TMEM and its axis-0/1 window tables into shared memory
-// (double-buffered, one pass ahead), and four reduction warps contract the accumulators with the
-// tables -- one thread per point in both, the thread's TMEM lane is its point.  Every mbarrier wait is bounded (about a second); on
+// (one pass ahead), and eight reduction warps (two per lane quadrant, alternate slabs) contract the
+// accumulators with the tables -- one thread per point, the thread's TMEM lane is its point.  Every mbarrier wait is bounded (about a second); on
 // expiry the CTA sets bit 1 of the plan's device flags, drains what it has in flight and
 // returns.
 #include "sgl_nufft_common.cuh"
@@ -52,27 +52,30 @@ __host__ __device__ constexpr uint32_t tf32_idesc(int n) {
     return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(kPM >> 4) << 24);
 }
 
-// Pipeline shape.  Interpolation: groups of 4 slabs (N <= 192), two accumulator buffers.
-// Gradient: groups of 2 slabs with two accumulators each (D and D'), one accumulator buffer.
-// Operands (w2; w2' for the gradient) and window tables are double-buffered across passes.
-// TMEM: 512 columns, one CTA per SM.
+// Pipeline shape.  Interpolation: groups of 4 slabs (N <= 192), two operand buffers (w2).
+// Gradient: groups of 2 slabs with two accumulators each (D and D', N <= 96), one operand buffer
+// (w2, w2').  Accumulators double-buffered across groups.  TMEM: 512 columns, one CTA per SM.
+// Eight reduction warps: two per TMEM lane quadrant, taking alternate slabs of each group.
 template <bool GRAD>
 struct TcCfg {
     static constexpr int G = GRAD ? 2 : 4;                   // slabs per group
     static constexpr int NBMAX = 2 * G * kTB1Max;            // N of one product (Re and Im rows)
     static constexpr int NCONV = 2;                          // split warps
-    static constexpr int WPREP = 2 + NCONV;                  // first of 4 prep warps; 4 reduction warps follow
-    static constexpr int WRED = WPREP + 4;
-    static constexpr int THREADS = 32 * (WRED + 4);
-    static constexpr int DBUF = GRAD ? 1 : 2;                // accumulator buffers
+    static constexpr int WPREP = 2 + NCONV;                  // first of 4 prep warps
+    static constexpr int WRED = WPREP + 4;                   // first of 8 reduction warps
+    static constexpr int NRED = 8;
+    static constexpr int THREADS = 32 * (WRED + NRED);
+    static constexpr int DBUF = 2;                           // accumulator buffers
     static constexpr uint32_t DCOLS = GRAD ? 2 * NBMAX : NBMAX;   // accumulator columns per buffer (D, D')
+    static constexpr int ABUF = GRAD ? 1 : 2;                // operand (and window table) buffers
     static constexpr uint32_t ACOLS = GRAD ? 128 : 64;       // operand columns per buffer (hi, lo, hi', lo')
     static constexpr uint32_t ABASE = DBUF * DCOLS;
     static constexpr uint32_t ALLOC = 512;
     static constexpr int NS = GRAD ? 4 : 3;                  // tile stages
     static constexpr int STAGE = NBMAX * 128;                // bytes of one tile operand (hi or lo)
     static constexpr int NTAB = GRAD ? 2 : 1;                // window tables per axis (psi; psi')
-    static_assert(ABASE + 2 * ACOLS <= ALLOC, "tensor memory budget");
+    static constexpr int NXCH = GRAD ? 8 : 2;                // partial sums one reduction warp hands to its partner
+    static_assert(ABASE + ABUF * ACOLS <= ALLOC, "tensor memory budget");
 };
 
 template <bool GRAD>
@@ -84,8 +87,9 @@ struct TcSmem {
     float w0tab[2][C::NTAB][16][kPM];                        // per buffer: axis-0 psi (psi') per tap j and point row
     float w1tab[2][C::NTAB][kTB1Max][kPM];                   // per buffer: axis-1 psi (psi') per tile row
     float lanes[kPM][kLanes + 1];                            // prep: one point's axis-2 weights placed on the 32 lanes
+    float xch[2][C::NXCH][kPM];                              // reduction: second warp's partial sums per point
     uint64_t tma_full[C::NS], conv_full[C::NS], empty[C::NS];
-    uint64_t tfull[2], tempty[2], afull[2], aempty[2], tabfull[2], done;
+    uint64_t tfull[2], tempty[2], afull[2], aempty[2], tabfull[2], xfull[2], xfree[2], done;
     uint32_t tmem_base;
     int abort;
 };
@@ -304,10 +308,12 @@ k_nufft_tc(const __grid_constant__ CUtensorMap tmap, NGeom g, TcArgs args) {
         }
         for (int i = 0; i < 2; ++i) {
             mbar_init(smem_addr(&sm.tfull[i]), 1);
-            mbar_init(smem_addr(&sm.tempty[i]), 4);
+            mbar_init(smem_addr(&sm.tempty[i]), Cfg::NRED);
             mbar_init(smem_addr(&sm.afull[i]), 4);
-            mbar_init(smem_addr(&sm.aempty[i]), 4);
+            mbar_init(smem_addr(&sm.aempty[i]), Cfg::NRED);
             mbar_init(smem_addr(&sm.tabfull[i]), 4);
+            mbar_init(smem_addr(&sm.xfull[i]), 4);
+            mbar_init(smem_addr(&sm.xfree[i]), 4);
         }
         mbar_init(smem_addr(&sm.done), 1);
         sm.abort = 0;
@@ -391,8 +397,8 @@ k_nufft_tc(const __grid_constant__ CUtensorMap tmap, NGeom g, TcArgs args) {
             bool ok = true;
             PassIter it;
             while (ok && next_pass(it, args)) {
-                const int abuf = k & 1;
-                ok = mbar_wait(smem_addr(&sm.afull[abuf]), (k >> 1) & 1) && !*abort_flag;
+                const int abuf = k % Cfg::ABUF;
+                ok = mbar_wait(smem_addr(&sm.afull[abuf]), (k / Cfg::ABUF) & 1) && !*abort_flag;
                 tc_fence_after();
                 const uint32_t a = tmem + Cfg::ABASE + (uint32_t)abuf * Cfg::ACOLS;
                 for (int gi = 0; gi < NG && ok; ++gi, ++s) {
@@ -448,8 +454,8 @@ k_nufft_tc(const __grid_constant__ CUtensorMap tmap, NGeom g, TcArgs args) {
             const float edge2 = kb ? 2.f * par2 * expf(-par2 * qf) : 0.5f / par2;
             int n = 0;
             while (ok && next_pass(it, args)) {
-                const int abuf = n & 1;
-                if (n >= 2) ok = __all_sync(0xffffffffu, mbar_wait(smem_addr(&sm.aempty[abuf]), ((n >> 1) + 1) & 1) && !*abort_flag);
+                const int abuf = n % Cfg::ABUF, use = n / Cfg::ABUF;
+                if (use >= 1) ok = __all_sync(0xffffffffu, mbar_wait(smem_addr(&sm.aempty[abuf]), (use + 1) & 1) && !*abort_flag);
                 if (!ok) break;
                 tc_fence_after();
                 const int idx = it.pass * kPM + p;
@@ -543,10 +549,11 @@ k_nufft_tc(const __grid_constant__ CUtensorMap tmap, NGeom g, TcArgs args) {
             // ---- reduction warps: contract the accumulators with the window tables
             float rho = 0.f;
             if constexpr (GRAD) rho = rho_from_r2max(args.r2max);
+            const int half = (warp - Cfg::WRED) >> 2;     // this warp takes slabs z = half, half + 2, ... of a group
             int s = 0, n = 0;
             while (ok && next_pass(it, args)) {
-                const int abuf = n & 1;
-                ok = __all_sync(0xffffffffu, mbar_wait(smem_addr(&sm.tabfull[abuf]), (n >> 1) & 1) && !*abort_flag);
+                const int abuf = n % Cfg::ABUF, use = n / Cfg::ABUF;
+                ok = __all_sync(0xffffffffu, mbar_wait(smem_addr(&sm.tabfull[abuf]), use & 1) && !*abort_flag);
                 if (!ok) break;
                 const int idx = it.pass * kPM + p;
                 const bool live = idx < it.np;
@@ -570,7 +577,7 @@ k_nufft_tc(const __grid_constant__ CUtensorMap tmap, NGeom g, TcArgs args) {
                     tc_fence_after();
                     const uint32_t taddr = tmem + lane_base + (uint32_t)buf * Cfg::DCOLS;
 #pragma unroll 1
-                    for (int z = 0; z < G; ++z) {
+                    for (int z = half; z < G; z += 2) {
                         // slab ta = G gi + z: Re of tile row tb at column z TB1 + tb, Im at G TB1 + z TB1 + tb
                         const int j = G * gi + z - d0;
                         float re[kTB1Max], im[kTB1Max];
@@ -632,17 +639,50 @@ k_nufft_tc(const __grid_constant__ CUtensorMap tmap, NGeom g, TcArgs args) {
                 }
                 if (!ok) break;
                 // every product of this pass is done (its last accumulator was read): operand and
-                // tables buffer free for the pass after next
+                // tables buffer free for the next pass that uses it
                 __syncwarp();
                 if (lane == 0) mbar_arrive(smem_addr(&sm.aempty[abuf]));
-                if (live) {
-                    const int dst = args.perm[i];
+                // partner warps (same lane quadrant) combine their partial sums; the half-0 warp writes
+                const int xs = n & 1;
+                if (half == 1) {
+                    if (n >= 2) ok = __all_sync(0xffffffffu, mbar_wait(smem_addr(&sm.xfree[xs]), ((n >> 1) + 1) & 1) && !*abort_flag);
+                    if (!ok) break;
+                    sm.xch[xs][0][p] = acc.x;
+                    sm.xch[xs][1][p] = acc.y;
                     if constexpr (GRAD) {
-                        grad_chain32(g, rho, c0, c1, c2, pt.x, pt.y, pt.z, acc.x, acc.y, acc1.x, acc1.y, acc2.x, acc2.y,
-                                     args.gout[dst], args.gxyz + 3 * (int64_t)dst);
-                        if (args.gvals) args.gvals[dst] = make_double2((double)accv.x, (double)accv.y);
-                    } else
-                        args.vals[dst] = make_double2((double)acc.x, (double)acc.y);
+                        sm.xch[xs][2 % Cfg::NXCH][p] = acc1.x;
+                        sm.xch[xs][3 % Cfg::NXCH][p] = acc1.y;
+                        sm.xch[xs][4 % Cfg::NXCH][p] = acc2.x;
+                        sm.xch[xs][5 % Cfg::NXCH][p] = acc2.y;
+                        sm.xch[xs][6 % Cfg::NXCH][p] = accv.x;
+                        sm.xch[xs][7 % Cfg::NXCH][p] = accv.y;
+                    }
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(smem_addr(&sm.xfull[xs]));
+                } else {
+                    ok = __all_sync(0xffffffffu, mbar_wait(smem_addr(&sm.xfull[xs]), (n >> 1) & 1) && !*abort_flag);
+                    if (!ok) break;
+                    acc.x += sm.xch[xs][0][p];
+                    acc.y += sm.xch[xs][1][p];
+                    if constexpr (GRAD) {
+                        acc1.x += sm.xch[xs][2 % Cfg::NXCH][p];
+                        acc1.y += sm.xch[xs][3 % Cfg::NXCH][p];
+                        acc2.x += sm.xch[xs][4 % Cfg::NXCH][p];
+                        acc2.y += sm.xch[xs][5 % Cfg::NXCH][p];
+                        accv.x += sm.xch[xs][6 % Cfg::NXCH][p];
+                        accv.y += sm.xch[xs][7 % Cfg::NXCH][p];
+                    }
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive(smem_addr(&sm.xfree[xs]));
+                    if (live) {
+                        const int dst = args.perm[i];
+                        if constexpr (GRAD) {
+                            grad_chain32(g, rho, c0, c1, c2, pt.x, pt.y, pt.z, acc.x, acc.y, acc1.x, acc1.y, acc2.x, acc2.y,
+                                         args.gout[dst], args.gxyz + 3 * (int64_t)dst);
+                            if (args.gvals) args.gvals[dst] = make_double2((double)accv.x, (double)accv.y);
+                        } else
+                            args.vals[dst] = make_double2((double)acc.x, (double)acc.y);
+                    }
                 }
                 ++n;
             }
