@@ -279,6 +279,43 @@ def run_ours(args):
             del plan
             torch.cuda.empty_cache()
 
+    # ---- inverse transform (iNFSGLFT) in the setup of the paper's last test (Sect. 8): Cartesian
+    # grid G_N, N = 50 (M = 125000), kappa = 5, B = 8 and B = 16, CGNR from the mid-point rule, FP64;
+    # errors as the paper measures them: max |c - c_true| and max |c - c_true| / |c_true|
+    inverse_line = None
+    if not args.no_inverse and rank == 0:
+        Ni, kap = 50, 5.0
+        tt = kap * (2.0 * np.arange(Ni) / Ni - 1.0)
+        X, Y, Z = np.meshgrid(tt, tt, tt, indexing="ij")
+        xg = np.stack([X.ravel(), Y.ravel(), Z.ravel()], axis=1)
+        Mi = xg.shape[0]
+        wts = torch.from_numpy((2.0 * kap / Ni) ** 3 * np.exp(-np.sum(xg * xg, axis=1))).to(dev)
+        inverse_line = {"setup": "Sect. 8 last test: Cartesian grid G_N, N=50 (M=125000), kappa=5, KB q=8, sigma=2, FP64; "
+                                 "CGNR (sgl_inverse) from the mid-point rule (sgl_midpoint_guess); samples from the FP64 "
+                                 "forward transform of seeded random coefficients U[-1/2,1/2]^2"}
+        for Bi, iters in ((8, 200), (16, 20)):
+            ip = sgl.Plan(Bi, Mi, precision=sgl.PREC_FP64, window=sgl.WIN_KB, q=8, sigma=2.0, device=dev)
+            ip.set_points(torch.from_numpy(xg).to(dev))
+            c_true = torch.from_numpy(inputs.coefficients(Bi, inputs.seed_for(5))).to(dev)
+            f_in = ip.forward(c_true)
+            c0 = ip.midpoint_guess(f_in, wts)
+            ip.inverse(f_in, coef0=c0, iters=2)          # warm-up (work vectors)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            ci, resi, ki = ip.inverse(f_in, coef0=c0, iters=iters, method="cgnr")
+            torch.cuda.synchronize()
+            el = time.perf_counter() - t0
+
+            def errs(c):
+                d = (c - c_true).abs()
+                return [float(d.max()), float((d / c_true.abs()).max())]
+            inverse_line["B=%d" % Bi] = {
+                "Nc": int(ip.Nc), "iterations": ki, "ms_per_iteration": round(el / max(ki, 1) * 1e3, 3),
+                "relative_residual": resi, "max_abs_rel_error_initial": errs(c0), "max_abs_rel_error_final": errs(ci)}
+            ip.close()
+            del ip
+            torch.cuda.empty_cache()
+
     # ---- end to end through the C-ABI with host buffers (copies inside the timed region)
     e2e = None
     if not args.no_e2e:
@@ -338,6 +375,7 @@ def run_ours(args):
                      "gpu_launches": results["fp64"]["gpu_launches"], "stages": results["fp64"]["stages"]},
             "stages_fp32_mixed": head["stages"],
             "fp32_mixed_other_cutoffs": by_q,
+            "inverse": inverse_line,
             "e2e": e2e}
 
     # ---- CPU baseline (oracle on the host cores, rank 0, N = 1) and the measured error on its sample
@@ -449,6 +487,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extra-q", action="store_true")
+    ap.add_argument("--no-inverse", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")

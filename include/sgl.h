@@ -185,6 +185,31 @@ sgl_status sgl_forward_grad(sgl_plan *plan, const double *coef_dev, const double
                             double *vals_dev, double *gxyz_dev);
 
 /*
+ * Inverse transform (iNFSGLFT; Sect. 7, end, after the iNFFT of Sect. 2): SGL Fourier
+ * coefficients from the M samples vals_dev[i] = f(x_i) at the plan's points, by conjugate
+ * gradients on the normal equations with one sgl_forward and one sgl_adjoint per iteration:
+ *   method 1 CGNR (normal equations of the first kind; least squares, for M >= Nc),
+ *   method 2 CGNE (second kind; minimum-norm solution, for M < Nc),
+ *   method 0 picks CGNR if M >= Nc, else CGNE.
+ * coef_dev complex128 [Nc]: the initial guess on entry (zeros, or sgl_midpoint_guess), the
+ * last iterate on return.  Stops after `iters` iterations or once ||f - Lambda c|| <= tol ||f||.
+ * residual_out (host, may be NULL): the final ||f - Lambda c|| / ||f||; iters_out (host, may
+ * be NULL): iterations done.  Synchronizes the stream (the step sizes are formed on the host in
+ * extended precision from device-reduced norms).  The first call allocates four work vectors
+ * (2 M_max + 2 Nc complex128), owned by the plan.
+ */
+sgl_status sgl_inverse(sgl_plan *plan, const double *vals_dev, double *coef_dev, int iters, double tol,
+                       int method, double *residual_out, int *iters_out);
+
+/*
+ * Quadrature initial guess for sgl_inverse: coef_dev = Lambda^H (w .* vals), i.e. the rule
+ * sum_i w_i f(x_i) conj(H_nlm(x_i)) for the inner product that makes the H_nlm orthonormal
+ * (the paper's last test, Sect. 8: the mid-point rule on a Cartesian grid, w_i = h^3 e^{-|x_i|^2}).
+ * weights_dev double [M]; vals_dev complex128 [M]; coef_dev complex128 [Nc] (device).
+ */
+sgl_status sgl_midpoint_guess(sgl_plan *plan, const double *vals_dev, const double *weights_dev, double *coef_dev);
+
+/*
  * Host-buffer variants (need SGL_FLAG_HOST_IO): copy the inputs from host memory
  * into the plan's staging buffers, run set_points + forward (or adjoint) on the
  * plan's stream, copy the result back and synchronize the stream before returning.

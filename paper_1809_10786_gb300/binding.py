@@ -71,6 +71,9 @@ def load_library(build_if_missing=True):
                            ("sgl_forward_host", [vp, vp, i64, vp, vp]), ("sgl_adjoint_host", [vp, vp, i64, vp, vp]),
                            ("sgl_grad_points_host", [vp, vp, i64, vp, vp, vp]),
                            ("sgl_forward_grad", [vp, vp, vp, vp, vp]),
+                           ("sgl_inverse", [vp, vp, vp, ctypes.c_int, ctypes.c_double, ctypes.c_int, dp,
+                                            ctypes.POINTER(ctypes.c_int)]),
+                           ("sgl_midpoint_guess", [vp, vp, vp, vp]),
                            ("sgl_forward_grad_host", [vp, vp, i64, vp, vp, vp, vp]),
                            ("sgl_profile", [vp, dp, ctypes.POINTER(i64)]), ("sgl_sync", [vp]),
                            ("sgl_trig_coeffs_noalloc", [ctypes.c_int, vp, i64, vp, vp, vp])]:
@@ -232,6 +235,30 @@ class Plan:
         _check(self.lib.sgl_forward_grad(self._h, ctypes.c_void_p(coef.data_ptr()), ctypes.c_void_p(gout.data_ptr()),
                                          ctypes.c_void_p(vals.data_ptr()), ctypes.c_void_p(gxyz.data_ptr())))
         return vals, gxyz
+
+    def inverse(self, vals, coef0=None, iters=100, tol=0.0, method="auto"):
+        """iNFSGLFT: coefficients from samples at the plan's points by CGNR / CGNE.
+        Returns (coef, relative residual ||f - Lambda c|| / ||f||, iterations done)."""
+        vals = _dev_tensor(vals, torch.complex128, (self.M,), "vals", self.device)
+        coef = (torch.zeros(self.Nc, dtype=torch.complex128, device=self.device) if coef0 is None else
+                _dev_tensor(coef0, torch.complex128, (self.Nc,), "coef0", self.device).clone())
+        m = {"auto": 0, "cgnr": 1, "cgne": 2}[method]
+        res = ctypes.c_double(0.0)
+        done = ctypes.c_int(0)
+        self._stream()
+        _check(self.lib.sgl_inverse(self._h, ctypes.c_void_p(vals.data_ptr()), ctypes.c_void_p(coef.data_ptr()), int(iters),
+                                    float(tol), m, ctypes.byref(res), ctypes.byref(done)))
+        return coef, res.value, done.value
+
+    def midpoint_guess(self, vals, weights):
+        """Lambda^H (weights * vals): the quadrature initial guess of the inverse transform."""
+        vals = _dev_tensor(vals, torch.complex128, (self.M,), "vals", self.device)
+        weights = _dev_tensor(weights, torch.float64, (self.M,), "weights", self.device)
+        out = torch.empty(self.Nc, dtype=torch.complex128, device=self.device)
+        self._stream()
+        _check(self.lib.sgl_midpoint_guess(self._h, ctypes.c_void_p(vals.data_ptr()), ctypes.c_void_p(weights.data_ptr()),
+                                           ctypes.c_void_p(out.data_ptr())))
+        return out
 
     def trig_coeffs(self, coef):
         """eta_k on |k0| <= 2B-2, |k1|, |k2| <= B-1 as complex128 [4B-3, 2B-1, 2B-1]."""

@@ -373,6 +373,11 @@ sgl_status plan_create_impl(sgl_plan **out, int B, int64_t M_max, int precision,
     ALLOC(b.bin_count, (size_t)p->nbins);
     ALLOC(b.bin_off, (size_t)p->nbins);
     ALLOC(b.scan_tmp, (size_t)(p->nbins / 2048 + 2));
+    ALLOC(b.piece_cnt, (size_t)(4 * p->bins.nsuper));
+    ALLOC(b.piece_off, (size_t)(4 * p->bins.nsuper));
+    ALLOC(b.work[0], (size_t)work_list_cap(Mc, p->bins.nsuper, kTcPass));
+    ALLOC(b.work[1], (size_t)work_list_cap(Mc, p->bins.nsuper, spread_chunk(precision)));
+    ALLOC(b.work_len, 2);
     if (flags & SGL_FLAG_HOST_IO) {
         ALLOC(b.io_xyz, 3 * Mc);
         ALLOC(b.io_coef, (size_t)(2 * p->Nc));
@@ -465,6 +470,7 @@ void sgl_plan_destroy(sgl_plan *plan) {
     PlanHolder *h = holder_of(plan);
     cudaStreamSynchronize(plan->stream);
     delete plan->prof;
+    inverse_work_free(plan);
     h->alloc.release();
     delete h;
 }

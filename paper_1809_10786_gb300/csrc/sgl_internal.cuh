@@ -25,6 +25,25 @@ struct BinGeom {
     int64_t nsuper;     // nsb0 * nsb2 * nsb1
 };
 
+// Work lists over the super-bins, rebuilt by every set_points: each entry (super-bin, first
+// sorted point, points, 0) is one piece of at most P points of one super-bin, the full pieces
+// of all super-bins first, then the remainders, so that equal pieces are scheduled before the
+// smaller ones and no super-bin's point count bounds a kernel's run time.  List 0 has pieces of
+// kTcPass points (a pass of the tensor-core kernels), list 1 of spread_chunk(prec) points (a
+// CTA of the CUDA-core spreading kernel).
+constexpr int kTcPass = 128;
+#ifndef SGL_SPREAD_CHUNK32
+#define SGL_SPREAD_CHUNK32 1024
+#endif
+#ifndef SGL_SPREAD_CHUNK64
+#define SGL_SPREAD_CHUNK64 128
+#endif
+__host__ __device__ inline int spread_chunk(int prec) { return prec == SGL_FP64 ? SGL_SPREAD_CHUNK64 : SGL_SPREAD_CHUNK32; }
+// capacity of a list of pieces of P points for M points in nsuper super-bins
+__host__ __device__ inline int64_t work_list_cap(int64_t M, int64_t nsuper, int P) {
+    return (M < nsuper ? M : nsuper) + M / P + 1;
+}
+
 // Sets the thread-local message returned by sgl_last_error() and returns code.
 sgl_status set_error(sgl_status code, const std::string &msg);
 
@@ -84,6 +103,9 @@ struct Buffers {
     int *bin_of, *rank_of;     // per input point
     int *bin_count, *bin_off;  // [nbins]
     int *scan_tmp;             // block sums
+    int *piece_cnt, *piece_off;// [4 nsuper] full and remainder pieces per super-bin, both lists, and their scan
+    int4 *work[2];             // work lists (see kTcPass): tensor-core passes, spreading chunks
+    int *work_len;             // [2] entries in each list (written on the device)
     // host-IO staging
     double *io_xyz, *io_coef, *io_vals, *io_grad, *io_out;
     // tensor-core interpolation (FP32-mixed): grid as planes Re, Im [rows0][rows1][pitch] with an azimuthal halo
@@ -105,6 +127,8 @@ enum Stage {
 };
 static_assert(ST_COUNT == SGL_NUM_STAGES, "stage list and SGL_NUM_STAGES disagree");
 struct Profiler;   // CUDA-event bookkeeping (sgl_capi.cu)
+struct InverseWork;   // work vectors of the inverse transform (sgl_inverse.cu)
+void inverse_work_free(sgl_plan *p);
 }  // namespace sgl
 
 struct sgl_plan {
@@ -112,6 +136,7 @@ struct sgl_plan {
     int num_sms;            // multiprocessors of the device (persistent kernels)
     int64_t launches;       // kernels launched (host-side count)
     sgl::Profiler *prof;    // non-NULL with SGL_FLAG_PROFILE
+    sgl::InverseWork *inv;  // allocated by the first sgl_inverse / sgl_midpoint_guess
     cudaStream_t stream;
     int B, q, prec, window;
     unsigned flags;

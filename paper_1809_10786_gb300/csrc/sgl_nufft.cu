@@ -228,10 +228,12 @@ __device__ __forceinline__ void write_point_gradient(const NGeom &g, double rho,
     }
 }
 
-// Spreading by super-bins.  One CTA per super-bin (C0 x C1 columns x one azimuthal chunk);
+// Spreading by super-bins.  One CTA per entry of the spreading work list: up to
+// spread_chunk(prec) sorted points of one super-bin (C0 x C1 columns x one azimuthal chunk);
 // warp w owns tile slab a = w (one grid row on axis 0) and keeps the sums for all T1 rows of
-// axis 1 and its 32 azimuthal lanes in registers while it sweeps every point of the super-bin;
-// each tile cell is then added to the grid once (atomically: neighbouring tiles overlap).
+// axis 1 and its 32 azimuthal lanes in registers while it sweeps the entry's points; each tile
+// cell is then added to the grid once (atomically: neighbouring tiles, and the other entries of
+// a crowded super-bin, overlap it).
 // window value for the spreading staging: FP32 takes the branch-free evaluation, FP64 the
 // reference form
 template <int WIN, typename T>
@@ -253,8 +255,8 @@ struct SpreadSmem {
 };
 
 template <typename T, int WIN, int Q2MAX, int C0, int C1>
-__global__ void __launch_bounds__(32 * (C0 + Q2MAX - 1)) k_spread_slab(NGeom g, const int *__restrict__ bin_off, int64_t M,
-                                                                       int64_t nsuper, const double *__restrict__ u_sorted,
+__global__ void __launch_bounds__(32 * (C0 + Q2MAX - 1)) k_spread_slab(NGeom g, const int4 *__restrict__ work,
+                                                                       const int *__restrict__ work_len, const double *__restrict__ u_sorted,
                                                                        const float4 *__restrict__ pts32, const int *__restrict__ perm,
                                                                        const double2 *__restrict__ vals, C2<T> *__restrict__ grid) {
     using S = SpreadSmem<T, WIN, Q2MAX, C1>;
@@ -263,11 +265,10 @@ __global__ void __launch_bounds__(32 * (C0 + Q2MAX - 1)) k_spread_slab(NGeom g, 
     const int lane = threadIdx.x & 31, ta = threadIdx.x >> 5;
     const int q = g.q, q2 = 2 * q;
     const T qT = (T)q;
-    const int64_t sb = blockIdx.x;
-    if (sb >= nsuper) return;
-    const int first = bin_off[sb * C0 * C1];
-    const int last = (sb + 1 < nsuper) ? bin_off[(sb + 1) * C0 * C1] : (int)M;
-    if (first >= last) return;
+    if ((int)blockIdx.x >= __ldg(work_len)) return;
+    const int4 piece = __ldg(work + blockIdx.x);
+    const int64_t sb = piece.x;
+    const int first = piece.y, last = piece.y + piece.z;
     const int sb1 = (int)(sb % g.nsb1), sb2 = (int)((sb / g.nsb1) % g.nsb2), sb0 = (int)(sb / ((int64_t)g.nsb1 * g.nsb2));
     const int ta_org = sb0 * C0 - q + 1, tb_org = sb1 * C1 - q + 1, cbase = sb2 * g.S2 - q + 1;
     const int T1 = C1 + q2 - 1;
@@ -360,6 +361,119 @@ __global__ void __launch_bounds__(32 * (C0 + Q2MAX - 1)) k_spread_slab(NGeom g, 
                 atomicAdd(&cell->x, acc[tb].x);
                 atomicAdd(&cell->y, acc[tb].y);
             }
+        }
+    }
+}
+
+// FP64 spreading.  The FP64 pipe is the bound (1/64 of the FP32 rate), so no lane may spend a
+// DFMA on a zero weight: warp w owns tile slab a = w as above, but each half-warp h keeps the
+// tile rows tb = 2i + h of axis 1, and lane l of a half the two azimuthal cells l and l + 16 of
+// the 32-cell tile.  A point's 2q <= 16 taps on axis 2 start at tile cell s (its cell within the
+// chunk), so [s, s + 2q) meets exactly one of each lane's two cells -- l if l >= s, else l + 16 --
+// and the lane updates that accumulator (chosen by selects, on the integer pipe).
+template <int Q2MAX, int C1>
+struct Spread64Smem {
+    static constexpr int PCH = 64;
+    static constexpr int T1 = C1 + Q2MAX - 1;     // tile rows on axis 1 at the largest q
+    static constexpr int RH = (T1 + 1) / 2;        // rows per half-warp
+    double2 y[PCH];
+    double w0[PCH][Q2MAX];
+    double w1[PCH][2 * RH];   // axis-1 weights on the tile rows (0 off the point's taps)
+    double w2[PCH][32];       // axis-2 weights on the 32 tile cells (0 off the point's taps)
+    int ta0[PCH];             // the point's first slab within the tile (axis 0)
+    int s2[PCH];              // the point's first tile cell on axis 2
+};
+
+template <int WIN, int Q2MAX, int C0, int C1>
+__global__ void __launch_bounds__(32 * (C0 + Q2MAX - 1)) k_spread_slab64(NGeom g, const int4 *__restrict__ work,
+                                                                         const int *__restrict__ work_len,
+                                                                         const double *__restrict__ u_sorted,
+                                                                         const int *__restrict__ perm, const double2 *__restrict__ vals,
+                                                                         double2 *__restrict__ grid) {
+    using S = Spread64Smem<Q2MAX, C1>;
+    constexpr int PCH = S::PCH, RH = S::RH, T1P = 2 * RH;
+    constexpr int E = Q2MAX + T1P + 32 + 1;      // staged values per point
+    __shared__ __align__(16) S sm;
+    const int lane = threadIdx.x & 31, ta = threadIdx.x >> 5, half = lane >> 4, l16 = lane & 15;
+    const int q = g.q, q2 = 2 * q;
+    const double qd = (double)q;
+    if ((int)blockIdx.x >= __ldg(work_len)) return;
+    const int4 piece = __ldg(work + blockIdx.x);
+    const int64_t sb = piece.x;
+    const int first = piece.y, last = piece.y + piece.z;
+    const int sb1 = (int)(sb % g.nsb1), sb2 = (int)((sb / g.nsb1) % g.nsb2), sb0 = (int)(sb / ((int64_t)g.nsb1 * g.nsb2));
+    const int ta_org = sb0 * C0 - q + 1, tb_org = sb1 * C1 - q + 1, cbase = sb2 * g.S2 - q + 1;
+    const int T1 = C1 + q2 - 1;
+    double2 lo[RH], hi[RH];
+#pragma unroll
+    for (int i = 0; i < RH; ++i) { lo[i] = make_double2(0.0, 0.0); hi[i] = make_double2(0.0, 0.0); }
+    for (int cs = first; cs < last; cs += PCH) {
+        const int np = min(PCH, last - cs);
+        __syncthreads();
+        for (int t = threadIdx.x; t < np * E; t += blockDim.x) {
+            const int p = t / E, e = t % E;
+            const int64_t pi = cs + p;
+            const double u0 = u_sorted[3 * pi], u1 = u_sorted[3 * pi + 1], u2 = u_sorted[3 * pi + 2];
+            const int c0 = cell_clamped(u0, g.cmax0), c1 = cell_clamped(u1, g.cmax1);
+            const int c2 = min(max((int)floor(u2), 0), g.N[2] - 1);
+            if (e < Q2MAX) {
+                sm.w0[p][e] = (e < q2) ? window<WIN, double>(u0 - c0 + (double)(q - 1 - e), qd, g.par[0], g.norm[0]) : 0.0;
+            } else if (e < Q2MAX + T1P) {
+                const int tb = e - Q2MAX;
+                const int rel = tb - (c1 - sb1 * C1);
+                sm.w1[p][tb] = (rel >= 0 && rel < q2 && tb < T1)
+                                   ? window<WIN, double>(u1 - c1 + (double)(q - 1 - rel), qd, g.par[1], g.norm[1]) : 0.0;
+            } else if (e < Q2MAX + T1P + 32) {
+                const int L = e - Q2MAX - T1P;
+                const int rel = cbase + L - (c2 - q + 1);
+                sm.w2[p][L] = (rel >= 0 && rel < q2) ? window<WIN, double>(u2 - c2 + (double)(q - 1 - rel), qd, g.par[2], g.norm[2])
+                                                     : 0.0;
+            } else {
+                sm.y[p] = vals[perm[pi]];
+                sm.ta0[p] = c0 - sb0 * C0;
+                sm.s2[p] = c2 - q + 1 - cbase;
+            }
+        }
+        __syncthreads();
+        for (int p = 0; p < np; ++p) {
+            const int j = ta - sm.ta0[p];
+            if (j < 0 || j >= q2) continue;
+            const bool up = l16 < sm.s2[p];
+            const double wz = sm.w0[p][j] * sm.w2[p][up ? l16 + 16 : l16];
+            const double2 y = sm.y[p];
+            const double zx = y.x * wz, zy = y.y * wz;
+#pragma unroll
+            for (int i = 0; i < RH; ++i) {
+                const double w = sm.w1[p][2 * i + half];
+                double tx = up ? hi[i].x : lo[i].x, ty = up ? hi[i].y : lo[i].y;
+                tx = fma(w, zx, tx);
+                ty = fma(w, zy, ty);
+                hi[i].x = up ? tx : hi[i].x;
+                hi[i].y = up ? ty : hi[i].y;
+                lo[i].x = up ? lo[i].x : tx;
+                lo[i].y = up ? lo[i].y : ty;
+            }
+        }
+    }
+    if (ta >= C0 + q2 - 1) return;
+    const int64_t s1 = g.N[2], s0 = (int64_t)g.rows[1] * g.N[2];
+    const int r0 = row_checked(ta_org + ta, g.first[0], g.rows[0], g.N[0]);
+    if (r0 < 0) return;                 // slab outside the stored rows: no point reaches it
+    const int clo = wrap_index(cbase + l16, g.N[2]), chi = wrap_index(cbase + l16 + 16, g.N[2]);
+    double2 *rowp = grid + r0 * s0;
+#pragma unroll
+    for (int i = 0; i < RH; ++i) {
+        const int tb = 2 * i + half;
+        const int r1 = (tb < T1) ? row_checked(tb_org + tb, g.first[1], g.rows[1], g.N[1]) : -1;
+        if (r1 < 0) continue;
+        double2 *row = rowp + r1 * s1;
+        if (lo[i].x != 0.0 || lo[i].y != 0.0) {
+            atomicAdd(&row[clo].x, lo[i].x);
+            atomicAdd(&row[clo].y, lo[i].y);
+        }
+        if (hi[i].x != 0.0 || hi[i].y != 0.0) {
+            atomicAdd(&row[chi].x, hi[i].x);
+            atomicAdd(&row[chi].y, hi[i].y);
         }
     }
 }
@@ -546,8 +660,20 @@ template <typename T, int WIN, int Q2MAX, int C0, int C1>
 cudaError_t spread_slab_t(sgl_plan *p, const NGeom &g, const double2 *vals) {
     if (g.C0 != C0 || g.C1 != C1) return cudaErrorInvalidConfiguration;
     const int threads = 32 * (C0 + 2 * p->q - 1);
-    k_spread_slab<T, WIN, Q2MAX, C0, C1><<<(unsigned)p->bins.nsuper, threads, 0, p->stream>>>(
-        g, p->b.bin_off, p->M, p->bins.nsuper, p->b.u_sorted, p->b.pts32, p->b.perm, vals, (C2<T> *)p->b.bufA);
+    const int64_t blocks = work_list_cap(p->M, p->bins.nsuper, spread_chunk(p->prec));   // entries past work_len[1] return
+    k_spread_slab<T, WIN, Q2MAX, C0, C1><<<(unsigned)blocks, threads, 0, p->stream>>>(
+        g, p->b.work[1], p->b.work_len + 1, p->b.u_sorted, p->b.pts32, p->b.perm, vals, (C2<T> *)p->b.bufA);
+    p->launches += 1;
+    return cudaGetLastError();
+}
+
+template <int WIN, int Q2MAX, int C0, int C1>
+cudaError_t spread_slab64_t(sgl_plan *p, const NGeom &g, const double2 *vals) {
+    if (g.C0 != C0 || g.C1 != C1 || g.S2 + 2 * p->q - 1 > 32) return cudaErrorInvalidConfiguration;
+    const int threads = 32 * (C0 + 2 * p->q - 1);
+    const int64_t blocks = work_list_cap(p->M, p->bins.nsuper, spread_chunk(p->prec));   // entries past work_len[1] return
+    k_spread_slab64<WIN, Q2MAX, C0, C1><<<(unsigned)blocks, threads, 0, p->stream>>>(
+        g, p->b.work[1], p->b.work_len + 1, p->b.u_sorted, p->b.perm, vals, (double2 *)p->b.bufA);
     p->launches += 1;
     return cudaGetLastError();
 }
@@ -559,8 +685,8 @@ cudaError_t spread_t(sgl_plan *p, const double2 *vals) {
         if (p->q <= 4) return spread_slab_t<T, WIN, 8, 8, 8>(p, g, vals);
         if (p->q <= 8) return spread_slab_t<T, WIN, 16, 8, 8>(p, g, vals);
     } else {
-        if (p->q <= 4) return spread_slab_t<T, WIN, 8, 4, 2>(p, g, vals);
-        if (p->q <= 8) return spread_slab_t<T, WIN, 16, 4, 2>(p, g, vals);
+        if (p->q <= 4) return spread_slab64_t<WIN, 8, 4, 2>(p, g, vals);
+        if (p->q <= 8) return spread_slab64_t<WIN, 16, 4, 2>(p, g, vals);
     }
     C2<T> *grid = (C2<T> *)p->b.bufA;
     const int q2 = 2 * p->q;

@@ -95,8 +95,9 @@ struct TcSmem {
 };
 
 struct TcArgs {
-    const int *bin_off;
-    int64_t M, nsuper;
+    const int4 *passes;                     // work list of passes (super-bin, first point, points)
+    const int *npasses;                     // its length (device)
+    int64_t M;
     const float4 *pts;
     const int *perm;
     double2 *vals;                          // interpolation output
@@ -258,27 +259,24 @@ __device__ __forceinline__ void store_split_tmem(uint32_t taddr, const float *w)
     tmem_st32(taddr + 32, l);
 }
 
-// The CTA's sequence of passes: super-bins blockIdx.x, blockIdx.x + gridDim.x, ..., each cut into
-// passes of 128 points (empty super-bins skipped).  Every role walks the same sequence.
+// The CTA's sequence of passes: entries blockIdx.x, blockIdx.x + gridDim.x, ... of the pass work
+// list (at most 128 points of one super-bin each, full passes first), so every CTA gets the same
+// number of full passes to within one.  Every role walks the same sequence.
+static_assert(kPM == kTcPass, "pass size and work-list piece size disagree");
 struct PassIter {
     int64_t sb = -1;
-    int pass = 0, npass = 0, first = 0, np = 0;
+    int k = -1, pass = 0, first = 0, np = 0;
 };
 
 __device__ __forceinline__ bool next_pass(PassIter &it, const TcArgs &a) {
-    if (it.sb >= 0 && ++it.pass < it.npass) return true;
-    for (it.sb = (it.sb < 0 ? (int64_t)blockIdx.x : it.sb + gridDim.x); it.sb < a.nsuper; it.sb += gridDim.x) {
-        const int f = a.bin_off[it.sb * kC0 * kC1];
-        const int l = (it.sb + 1 < a.nsuper) ? a.bin_off[(it.sb + 1) * kC0 * kC1] : (int)a.M;
-        if (l > f) {
-            it.first = f;
-            it.np = l - f;
-            it.npass = (it.np + kPM - 1) / kPM;
-            it.pass = 0;
-            return true;
-        }
-    }
-    return false;
+    it.k = (it.k < 0) ? (int)blockIdx.x : it.k + (int)gridDim.x;
+    if (it.k >= __ldg(a.npasses)) return false;
+    const int4 e = __ldg(a.passes + it.k);
+    it.sb = e.x;
+    it.first = e.y;
+    it.np = e.z;
+    it.pass = 0;
+    return true;
 }
 
 template <int WIN, bool GRAD>
@@ -1109,7 +1107,7 @@ cudaError_t run_tc(sgl_plan *p, TcArgs a) {
     auto kern = k_nufft_tc<WIN, GRAD>;
     if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess) return e;
     const CUtensorMap *map = reinterpret_cast<const CUtensorMap *>(p->tc_map[GRAD ? 1 : 0]);
-    const int64_t grid = std::min<int64_t>(p->bins.nsuper, p->num_sms);
+    const int64_t grid = std::min<int64_t>(work_list_cap(p->M, p->bins.nsuper, kTcPass), p->num_sms);
     kern<<<(unsigned)grid, TcCfg<GRAD>::THREADS, smem, p->stream>>>(*map, make_geom(p), a);
     p->launches += 1;
     return cudaGetLastError();
@@ -1117,9 +1115,9 @@ cudaError_t run_tc(sgl_plan *p, TcArgs a) {
 
 TcArgs base_args(const sgl_plan *p) {
     TcArgs a{};
-    a.bin_off = p->b.bin_off;
+    a.passes = p->b.work[0];
+    a.npasses = p->b.work_len;
     a.M = p->M;
-    a.nsuper = p->bins.nsuper;
     a.pts = p->b.pts32;
     a.perm = p->b.perm;
     a.r2max = p->b.r2max;

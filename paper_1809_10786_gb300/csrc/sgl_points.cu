@@ -170,6 +170,48 @@ __global__ void k_scatter_points(int64_t M, const double *__restrict__ u_tmp, co
     }
 }
 
+// Work lists (one thread per super-bin): counts of full pieces and of remainders, laid out as
+// [full 0][rem 0][full 1][rem 1], nsuper each, so that one exclusive scan of the whole array
+// orders every list's full pieces before its remainders.
+__global__ void k_piece_count(const int *__restrict__ bin_off, int64_t nsuper, int bins_per_super, int64_t M, int P0,
+                              int P1, int *__restrict__ cnt) {
+    for (int64_t sb = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; sb < nsuper; sb += (int64_t)gridDim.x * blockDim.x) {
+        const int f = bin_off[sb * bins_per_super];
+        const int l = (sb + 1 < nsuper) ? bin_off[(sb + 1) * bins_per_super] : (int)M;
+        const int n = l - f;
+        cnt[sb] = n / P0;
+        cnt[nsuper + sb] = (n % P0) ? 1 : 0;
+        cnt[2 * nsuper + sb] = n / P1;
+        cnt[3 * nsuper + sb] = (n % P1) ? 1 : 0;
+    }
+}
+
+__global__ void k_piece_fill(const int *__restrict__ bin_off, int64_t nsuper, int bins_per_super, int64_t M, int P0, int P1,
+                             const int *__restrict__ cnt, const int *__restrict__ off, int4 *__restrict__ list0,
+                             int4 *__restrict__ list1, int *__restrict__ len) {
+    const int len0 = off[2 * nsuper];                 // entries of list 0 (they precede list 1 in the scan)
+    for (int64_t sb = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; sb < nsuper; sb += (int64_t)gridDim.x * blockDim.x) {
+        const int f = bin_off[sb * bins_per_super];
+        const int l = (sb + 1 < nsuper) ? bin_off[(sb + 1) * bins_per_super] : (int)M;
+        for (int k = 0; k < 2; ++k) {
+            const int P = k ? P1 : P0;
+            int4 *list = k ? list1 : list0;
+            const int base = k ? len0 : 0;
+            const int nfull = cnt[2 * k * nsuper + sb];
+            const int o = off[2 * k * nsuper + sb] - base;
+            for (int j = 0; j < nfull; ++j) list[o + j] = make_int4((int)sb, f + j * P, P, 0);
+            if (cnt[(2 * k + 1) * nsuper + sb]) {
+                const int r = off[(2 * k + 1) * nsuper + sb] - base;
+                list[r] = make_int4((int)sb, f + nfull * P, l - f - nfull * P, 0);
+            }
+        }
+        if (sb == 0) {
+            len[0] = len0;
+            len[1] = off[4 * nsuper - 1] + cnt[4 * nsuper - 1] - len0;
+        }
+    }
+}
+
 void scan(const int *cnt, int64_t n, int *tmp, int *off, cudaStream_t s) {
     const int nblk = (int)((n + kScanBlock - 1) / kScanBlock);
     k_scan_block_totals<<<nblk, kThreads, 0, s>>>(cnt, n, tmp);
@@ -207,7 +249,15 @@ cudaError_t launch_points(sgl_plan *p, const double *xyz, int64_t M) {
         scan(b.bin_count, p->nbins, b.scan_tmp, b.bin_off, s);
         k_scatter_points<<<grid_blocks(M, kThreads), kThreads, 0, s>>>(M, b.u_tmp, b.bin_of, b.rank_of, b.bin_off, g, b.u_sorted,
                                                                        b.pts32, b.perm);
-        p->launches += 5;
+        const int64_t ns = p->bins.nsuper;
+        const int bps = p->bins.C0 * p->bins.C1, P1 = spread_chunk(p->prec);
+        k_piece_count<<<grid_blocks(ns, kThreads), kThreads, 0, s>>>(b.bin_off, ns, bps, M, kTcPass, P1, b.piece_cnt);
+        scan(b.piece_cnt, 4 * ns, b.scan_tmp, b.piece_off, s);
+        k_piece_fill<<<grid_blocks(ns, kThreads), kThreads, 0, s>>>(b.bin_off, ns, bps, M, kTcPass, P1, b.piece_cnt, b.piece_off,
+                                                                    b.work[0], b.work[1], b.work_len);
+        p->launches += 10;
+    } else if ((e = cudaMemsetAsync(b.work_len, 0, 2 * sizeof(int), s)) != cudaSuccess) {
+        return e;
     }
     return cudaGetLastError();
 }
