@@ -192,7 +192,8 @@ def run_ours(args):
 
     results = {}
     keep = {}
-    for prec_name, prec in (("fp32_mixed", sgl.PREC_FP32_MIXED), ("fp64", sgl.PREC_FP64)):
+    precs = (("fp32_mixed", sgl.PREC_FP32_MIXED),) + (() if args.no_fp64 else (("fp64", sgl.PREC_FP64),))
+    for prec_name, prec in precs:
         plan = sgl.Plan(B, M, precision=prec, window=sgl.WIN_KB, q=q, sigma=2.0, profile=True, device=dev)
         out = {}
 
@@ -370,9 +371,9 @@ def run_ours(args):
                        "l2": "256 MiB write between timed steps (flush), inputs and grid exceed L2 in total"},
             "gpu_launches": head["gpu_launches"],
             "roofline": roofline, "clocks": head["clocks"],
-            "fp64": {"value": round(results["fp64"]["value"], 4), "unit": UNIT,
-                     "ms_per_step": round(results["fp64"]["ms_per_step"], 4),
-                     "gpu_launches": results["fp64"]["gpu_launches"], "stages": results["fp64"]["stages"]},
+            "fp64": None if "fp64" not in results else {
+                "value": round(results["fp64"]["value"], 4), "unit": UNIT, "ms_per_step": round(results["fp64"]["ms_per_step"], 4),
+                "gpu_launches": results["fp64"]["gpu_launches"], "stages": results["fp64"]["stages"]},
             "stages_fp32_mixed": head["stages"],
             "fp32_mixed_other_cutoffs": by_q,
             "inverse": inverse_line,
@@ -412,6 +413,8 @@ def cpu_baseline(args, x_h, c_h, y_h, g_h, keep, dev):
             "sample": "%d of the %d points (forward + adjoint + point gradient, direct sum, FP64); %.1f s" % (S, args.M, el)}
     err = {}
     for prec_name, prec in (("fp32_mixed", sgl.PREC_FP32_MIXED), ("fp64", sgl.PREC_FP64)):
+        if prec_name not in keep:
+            continue
         k = keep[prec_name]
         ef = np.abs(k["f"][idx] - f_ref).max() / np.abs(f_ref).max()
         eg = np.abs(k["g"][idx] - g_ref).max() / np.abs(g_ref).max()
@@ -488,6 +491,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extra-q", action="store_true")
     ap.add_argument("--no-inverse", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison run (profiling captures)")
     args = ap.parse_args()
     if args.warmup < 3:
         raise SystemExit("--warmup must be >= 3")

@@ -178,6 +178,10 @@ cudaError_t launch_fft_adjoint(sgl_plan *p);    // grid (bufA) -> eta' full supp
 cudaError_t launch_interp(sgl_plan *p, double2 *vals);
 cudaError_t launch_spread(sgl_plan *p, const double2 *vals);
 cudaError_t launch_grad(sgl_plan *p, const double2 *gout, double *gxyz, double2 *vals);   // vals: NULL or the values too
+// FP64 kernels (sgl_nufft64.cu), called by the three above for FP64 plans
+cudaError_t launch_interp64(sgl_plan *p, double2 *vals);
+cudaError_t launch_spread64(sgl_plan *p, const double2 *vals);
+cudaError_t launch_grad64(sgl_plan *p, const double2 *gout, double *gxyz, double2 *vals);
 // tensor-core interpolation / gradient (sgl_nufft_tc.cu)
 bool tc_eligible(const sgl_plan *p);
 void tc_choose(sgl_plan *p);

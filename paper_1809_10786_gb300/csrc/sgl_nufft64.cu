@@ -1,0 +1,350 @@
+// sgl_nufft64.cu -- FP64 windowed interpolation (NFFT step 3, Sect. 2), its adjoint
+// (spreading) and the window-derivative interpolation of the point gradient, binary64
+// throughout (grid coordinates, window values, products and sums).
+//
+//   s(t) = sum_{l : |u_d - l_d| <= q} alpha_l prod_d psi_d(u_d - l_d),   u_d = N_d t_d / (2 pi)
+//
+// Taps per axis: l = floor(u) - q + 1 ... floor(u) + q (2q taps).  The FP64 pipe of GB300 runs
+// at 1/64 of the FP32 rate, so it bounds every kernel here.
+#include "sgl_nufft_common.cuh"
+
+namespace sgl {
+namespace {
+
+// Chain rule from ds/du_d to Re(conj(g) grad_x f) for one point (FP64), written by one lane.
+__device__ __forceinline__ void write_point_gradient(const NGeom &g, double rho, double u0, double u1, double u2,
+                                                     double a0x, double a0y, double a1x, double a1y, double a2x, double a2y,
+                                                     double2 gv, double *outp) {
+    const double twopi = 2.0 * kPi;
+    const double g0x = a0x * (g.N[0] / twopi), g0y = a0y * (g.N[0] / twopi);
+    const double g1x = a1x * (g.N[1] / twopi), g1y = a1y * (g.N[1] / twopi);
+    const double g2x = a2x * (g.N[2] / twopi), g2y = a2y * (g.N[2] / twopi);
+    const double t0 = twopi * u0 / g.N[0], t1 = twopi * u1 / g.N[1], t2 = twopi * u2 / g.N[2];
+    const double ch = cos(0.5 * t0);
+    const double r = rho * ch * ch;                 // r = rho (1 + cos t0) / 2
+    const double st0 = sin(t0), st1 = sin(t1), ct1 = cos(t1), sp = sin(t2), cp = cos(t2);
+    const double dt0dr = (st0 > 0.0) ? -2.0 / (rho * st0) : 0.0;
+    const double ir = (r > 0.0) ? 1.0 / r : 0.0;
+    const double irs = (r > 0.0 && st1 > 0.0) ? 1.0 / (r * st1) : 0.0;
+    const double er[3] = {st1 * cp, st1 * sp, ct1}, et[3] = {ct1 * cp, ct1 * sp, -st1}, ep[3] = {-sp, cp, 0.0};
+    for (int d = 0; d < 3; ++d) {
+        const double vx = g0x * dt0dr * er[d] + g1x * ir * et[d] + g2x * irs * ep[d];
+        const double vy = g0y * dt0dr * er[d] + g1y * ir * et[d] + g2y * irs * ep[d];
+        outp[d] = gv.x * vx + gv.y * vy;           // Re(conj(g) v)
+    }
+}
+
+// FP64 spreading.  The FP64 pipe is the bound (1/64 of the FP32 rate), so no lane may spend a
+// DFMA on a zero weight: warp w owns tile slab a = w as above, but each half-warp h keeps the
+// tile rows tb = 2i + h of axis 1, and lane l of a half the two azimuthal cells l and l + 16 of
+// the 32-cell tile.  A point's 2q <= 16 taps on axis 2 start at tile cell s (its cell within the
+// chunk), so [s, s + 2q) meets exactly one of each lane's two cells -- l if l >= s, else l + 16 --
+// and the lane updates that accumulator (chosen by selects, on the integer pipe).
+template <int Q2MAX, int C1>
+struct Spread64Smem {
+    static constexpr int PCH = 64;
+    static constexpr int T1 = C1 + Q2MAX - 1;     // tile rows on axis 1 at the largest q
+    static constexpr int RH = (T1 + 1) / 2;        // rows per half-warp
+    double2 y[PCH];
+    double w0[PCH][Q2MAX];
+    double w1[PCH][2 * RH];   // axis-1 weights on the tile rows (0 off the point's taps)
+    double w2[PCH][32];       // axis-2 weights on the 32 tile cells (0 off the point's taps)
+    int ta0[PCH];             // the point's first slab within the tile (axis 0)
+    int s2[PCH];              // the point's first tile cell on axis 2
+};
+
+template <int WIN, int Q2MAX, int C0, int C1>
+__global__ void __launch_bounds__(32 * (C0 + Q2MAX - 1)) k_spread_slab64(NGeom g, const int4 *__restrict__ work,
+                                                                         const int *__restrict__ work_len,
+                                                                         const double *__restrict__ u_sorted,
+                                                                         const int *__restrict__ perm, const double2 *__restrict__ vals,
+                                                                         double2 *__restrict__ grid) {
+    using S = Spread64Smem<Q2MAX, C1>;
+    constexpr int PCH = S::PCH, RH = S::RH, T1P = 2 * RH;
+    constexpr int E = Q2MAX + T1P + 32 + 1;      // staged values per point
+    __shared__ __align__(16) S sm;
+    const int lane = threadIdx.x & 31, ta = threadIdx.x >> 5, half = lane >> 4, l16 = lane & 15;
+    const int q = g.q, q2 = 2 * q;
+    const double qd = (double)q;
+    if ((int)blockIdx.x >= __ldg(work_len)) return;
+    const int4 piece = __ldg(work + blockIdx.x);
+    const int64_t sb = piece.x;
+    const int first = piece.y, last = piece.y + piece.z;
+    const int sb1 = (int)(sb % g.nsb1), sb2 = (int)((sb / g.nsb1) % g.nsb2), sb0 = (int)(sb / ((int64_t)g.nsb1 * g.nsb2));
+    const int ta_org = sb0 * C0 - q + 1, tb_org = sb1 * C1 - q + 1, cbase = sb2 * g.S2 - q + 1;
+    const int T1 = C1 + q2 - 1;
+    double2 lo[RH], hi[RH];
+#pragma unroll
+    for (int i = 0; i < RH; ++i) { lo[i] = make_double2(0.0, 0.0); hi[i] = make_double2(0.0, 0.0); }
+    for (int cs = first; cs < last; cs += PCH) {
+        const int np = min(PCH, last - cs);
+        __syncthreads();
+        for (int t = threadIdx.x; t < np * E; t += blockDim.x) {
+            const int p = t / E, e = t % E;
+            const int64_t pi = cs + p;
+            const double u0 = u_sorted[3 * pi], u1 = u_sorted[3 * pi + 1], u2 = u_sorted[3 * pi + 2];
+            const int c0 = cell_clamped(u0, g.cmax0), c1 = cell_clamped(u1, g.cmax1);
+            const int c2 = min(max((int)floor(u2), 0), g.N[2] - 1);
+            if (e < Q2MAX) {
+                sm.w0[p][e] = (e < q2) ? window<WIN, double>(u0 - c0 + (double)(q - 1 - e), qd, g.par[0], g.norm[0]) : 0.0;
+            } else if (e < Q2MAX + T1P) {
+                const int tb = e - Q2MAX;
+                const int rel = tb - (c1 - sb1 * C1);
+                sm.w1[p][tb] = (rel >= 0 && rel < q2 && tb < T1)
+                                   ? window<WIN, double>(u1 - c1 + (double)(q - 1 - rel), qd, g.par[1], g.norm[1]) : 0.0;
+            } else if (e < Q2MAX + T1P + 32) {
+                const int L = e - Q2MAX - T1P;
+                const int rel = cbase + L - (c2 - q + 1);
+                sm.w2[p][L] = (rel >= 0 && rel < q2) ? window<WIN, double>(u2 - c2 + (double)(q - 1 - rel), qd, g.par[2], g.norm[2])
+                                                     : 0.0;
+            } else {
+                sm.y[p] = vals[perm[pi]];
+                sm.ta0[p] = c0 - sb0 * C0;
+                sm.s2[p] = c2 - q + 1 - cbase;
+            }
+        }
+        __syncthreads();
+        for (int p = 0; p < np; ++p) {
+            const int j = ta - sm.ta0[p];
+            if (j < 0 || j >= q2) continue;
+            const bool up = l16 < sm.s2[p];
+            const double wz = sm.w0[p][j] * sm.w2[p][up ? l16 + 16 : l16];
+            const double2 y = sm.y[p];
+            const double zx = y.x * wz, zy = y.y * wz;
+#pragma unroll
+            for (int i = 0; i < RH; ++i) {
+                const double w = sm.w1[p][2 * i + half];
+                double tx = up ? hi[i].x : lo[i].x, ty = up ? hi[i].y : lo[i].y;
+                tx = fma(w, zx, tx);
+                ty = fma(w, zy, ty);
+                hi[i].x = up ? tx : hi[i].x;
+                hi[i].y = up ? ty : hi[i].y;
+                lo[i].x = up ? lo[i].x : tx;
+                lo[i].y = up ? lo[i].y : ty;
+            }
+        }
+    }
+    if (ta >= C0 + q2 - 1) return;
+    const int64_t s1 = g.N[2], s0 = (int64_t)g.rows[1] * g.N[2];
+    const int r0 = row_checked(ta_org + ta, g.first[0], g.rows[0], g.N[0]);
+    if (r0 < 0) return;                 // slab outside the stored rows: no point reaches it
+    const int clo = wrap_index(cbase + l16, g.N[2]), chi = wrap_index(cbase + l16 + 16, g.N[2]);
+    double2 *rowp = grid + r0 * s0;
+#pragma unroll
+    for (int i = 0; i < RH; ++i) {
+        const int tb = 2 * i + half;
+        const int r1 = (tb < T1) ? row_checked(tb_org + tb, g.first[1], g.rows[1], g.N[1]) : -1;
+        if (r1 < 0) continue;
+        double2 *row = rowp + r1 * s1;
+        if (lo[i].x != 0.0 || lo[i].y != 0.0) {
+            atomicAdd(&row[clo].x, lo[i].x);
+            atomicAdd(&row[clo].y, lo[i].y);
+        }
+        if (hi[i].x != 0.0 || hi[i].y != 0.0) {
+            atomicAdd(&row[chi].x, hi[i].x);
+            atomicAdd(&row[chi].y, hi[i].y);
+        }
+    }
+}
+
+// FP64 path: same lane layout as the FP32 kernels, binary64 throughout (coordinates from the
+// double grid coordinates); lane j evaluates tap j's weights once and shares them by shuffle.
+template <int WIN, int G>
+__global__ void __launch_bounds__(256) k_interp64(NGeom g, int64_t M, const double *__restrict__ u_sorted,
+                                                  const int *__restrict__ perm, const double2 *__restrict__ grid,
+                                                  double2 *__restrict__ vals) {
+    const int lane = threadIdx.x & 31, gl = lane & (G - 1);
+    const int q = g.q, q2 = 2 * q;
+    const double qd = (double)q;
+    const int64_t s1 = g.N[2], s0 = (int64_t)g.rows[1] * g.N[2];
+    // warps sweep the bin-sorted points in grid-stride order (consecutive warps: neighbouring points)
+    constexpr int PPW = 32 / G;
+    const int64_t warp0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / 32;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) / 32;
+    const int64_t end = M;
+    for (int64_t base = warp0 * PPW; base < M; base += nwarps * PPW) {
+        const int64_t i = base + lane / G;
+        const bool live = i < M;
+        const int64_t ii = live ? i : end - 1;
+        const double u0 = u_sorted[3 * ii], u1 = u_sorted[3 * ii + 1], u2 = u_sorted[3 * ii + 2];
+        const int a0 = cell_clamped(u0, g.cmax0) - q + 1, a1 = cell_clamped(u1, g.cmax1) - q + 1;
+        const int a2 = min(max((int)floor(u2), 0), g.N[2] - 1) - q + 1;
+        const bool tap = gl < q2;
+        const double w0_own = tap ? window<WIN, double>(u0 - (a0 + gl), qd, g.par[0], g.norm[0]) : 0.0;
+        const double w1_own = tap ? window<WIN, double>(u1 - (a1 + gl), qd, g.par[1], g.norm[1]) : 0.0;
+        const double w2 = tap ? window<WIN, double>(u2 - (a2 + gl), qd, g.par[2], g.norm[2]) : 0.0;
+        const int col = tap ? wrap_index(a2 + gl, g.N[2]) : 0;
+        double w1[G];
+        int off1[G];
+#pragma unroll
+        for (int b = 0; b < G; ++b) {
+            w1[b] = __shfl_sync(0xffffffffu, w1_own, b, G);
+            off1[b] = (b < q2) ? row_of(a1 + b, g.first[1], g.rows[1], g.N[1]) * (int)s1 + col : col;
+        }
+        double ax = 0.0, ay = 0.0;
+        for (int a = 0; a < q2; ++a) {
+            const double w0 = __shfl_sync(0xffffffffu, w0_own, a, G);
+            const double2 *rowp = grid + row_of(a0 + a, g.first[0], g.rows[0], g.N[0]) * s0;
+            double rx = 0.0, ry = 0.0;
+#pragma unroll
+            for (int b = 0; b < G; ++b)
+                if (b < q2) {
+                    const double2 v = __ldg(rowp + off1[b]);
+                    rx = fma(w1[b], v.x, rx);
+                    ry = fma(w1[b], v.y, ry);
+                }
+            ax = fma(w0, rx, ax);
+            ay = fma(w0, ry, ay);
+        }
+        ax *= w2;
+        ay *= w2;
+#pragma unroll
+        for (int o = G / 2; o > 0; o >>= 1) {
+            ax += __shfl_xor_sync(0xffffffffu, ax, o);
+            ay += __shfl_xor_sync(0xffffffffu, ay, o);
+        }
+        if (live && gl == 0) vals[perm[i]] = make_double2(ax, ay);
+    }
+}
+
+template <int WIN, int G>
+__global__ void __launch_bounds__(256) k_grad64(NGeom g, int64_t M, const double *__restrict__ u_sorted,
+                                                const int *__restrict__ perm, const unsigned long long *__restrict__ r2max,
+                                                const double2 *__restrict__ grid, const double2 *__restrict__ gout,
+                                                double *__restrict__ gxyz, double2 *__restrict__ vals) {
+    const int lane = threadIdx.x & 31, gl = lane & (G - 1);
+    const int q = g.q, q2 = 2 * q;
+    const double qd = (double)q;
+    const int64_t s1 = g.N[2], s0 = (int64_t)g.rows[1] * g.N[2];
+    double rho = sqrt(__longlong_as_double((long long)*r2max)) * (1.0 + 0x1p-20);
+    if (!(rho > 0.0)) rho = 1.0;
+    // warps sweep the bin-sorted points in grid-stride order (consecutive warps: neighbouring points)
+    constexpr int PPW = 32 / G;
+    const int64_t warp0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / 32;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) / 32;
+    const int64_t end = M;
+    for (int64_t base = warp0 * PPW; base < M; base += nwarps * PPW) {
+        const int64_t i = base + lane / G;
+        const bool live = i < M;
+        const int64_t ii = live ? i : end - 1;
+        const double u0 = u_sorted[3 * ii], u1 = u_sorted[3 * ii + 1], u2 = u_sorted[3 * ii + 2];
+        const int a0 = cell_clamped(u0, g.cmax0) - q + 1, a1 = cell_clamped(u1, g.cmax1) - q + 1;
+        const int a2 = min(max((int)floor(u2), 0), g.N[2] - 1) - q + 1;
+        const bool tap = gl < q2;
+        const double x0 = u0 - (a0 + gl), x1 = u1 - (a1 + gl), x2 = u2 - (a2 + gl);
+        const double w0_own = tap ? window<WIN, double>(x0, qd, g.par[0], g.norm[0]) : 0.0;
+        const double d0_own = tap ? window_deriv<WIN, double>(x0, qd, g.par[0], g.norm[0]) : 0.0;
+        const double w1_own = tap ? window<WIN, double>(x1, qd, g.par[1], g.norm[1]) : 0.0;
+        const double d1_own = tap ? window_deriv<WIN, double>(x1, qd, g.par[1], g.norm[1]) : 0.0;
+        const double w2 = tap ? window<WIN, double>(x2, qd, g.par[2], g.norm[2]) : 0.0;
+        const double d2 = tap ? window_deriv<WIN, double>(x2, qd, g.par[2], g.norm[2]) : 0.0;
+        const int col = tap ? wrap_index(a2 + gl, g.N[2]) : 0;
+        double fx = 0, fy = 0, ax = 0, ay = 0, bx = 0, by = 0;
+        for (int a = 0; a < q2; ++a) {
+            const double w0 = __shfl_sync(0xffffffffu, w0_own, a, G);
+            const double dw0 = __shfl_sync(0xffffffffu, d0_own, a, G);
+            const double2 *rowp = grid + row_of(a0 + a, g.first[0], g.rows[0], g.N[0]) * s0 + col;
+            double rx = 0, ry = 0, sx = 0, sy = 0;
+#pragma unroll
+            for (int b = 0; b < G; ++b) {
+                const double w1 = __shfl_sync(0xffffffffu, w1_own, b, G);
+                const double d1 = __shfl_sync(0xffffffffu, d1_own, b, G);
+                if (b < q2) {
+                    const double2 v = __ldg(rowp + row_of(a1 + b, g.first[1], g.rows[1], g.N[1]) * s1);
+                    rx = fma(w1, v.x, rx); ry = fma(w1, v.y, ry);
+                    sx = fma(d1, v.x, sx); sy = fma(d1, v.y, sy);
+                }
+            }
+            fx = fma(w0, rx, fx); fy = fma(w0, ry, fy);
+            ax = fma(dw0, rx, ax); ay = fma(dw0, ry, ay);
+            bx = fma(w0, sx, bx); by = fma(w0, sy, by);
+        }
+        double f2x = d2 * fx, f2y = d2 * fy;
+        double sx = w2 * fx, sy = w2 * fy;             // the value s itself (forward with gradient)
+        ax *= w2; ay *= w2; bx *= w2; by *= w2;
+#pragma unroll
+        for (int o = G / 2; o > 0; o >>= 1) {
+            ax += __shfl_xor_sync(0xffffffffu, ax, o);
+            ay += __shfl_xor_sync(0xffffffffu, ay, o);
+            bx += __shfl_xor_sync(0xffffffffu, bx, o);
+            by += __shfl_xor_sync(0xffffffffu, by, o);
+            f2x += __shfl_xor_sync(0xffffffffu, f2x, o);
+            f2y += __shfl_xor_sync(0xffffffffu, f2y, o);
+            if (vals) {
+                sx += __shfl_xor_sync(0xffffffffu, sx, o);
+                sy += __shfl_xor_sync(0xffffffffu, sy, o);
+            }
+        }
+        if (live && gl == 0) {
+            const int dst = perm[i];
+            write_point_gradient(g, rho, u0, u1, u2, ax, ay, bx, by, f2x, f2y, gout[dst], gxyz + 3 * (int64_t)dst);
+            if (vals) vals[dst] = make_double2(sx, sy);
+        }
+    }
+}
+
+
+template <int WIN>
+cudaError_t interp64_t(sgl_plan *p, double2 *vals) {
+    const NGeom g = make_geom(p);
+    const double2 *gridd = (const double2 *)p->b.bufA;
+    const int q2 = 2 * p->q;
+    if (q2 <= 8) k_interp64<WIN, 8><<<nufft_blocks(p->M, 8), 256, 0, p->stream>>>(g, p->M, p->b.u_sorted, p->b.perm, gridd, vals);
+    else if (q2 <= 16) k_interp64<WIN, 16><<<nufft_blocks(p->M, 16), 256, 0, p->stream>>>(g, p->M, p->b.u_sorted, p->b.perm, gridd, vals);
+    else k_interp64<WIN, 32><<<nufft_blocks(p->M, 32), 256, 0, p->stream>>>(g, p->M, p->b.u_sorted, p->b.perm, gridd, vals);
+    p->launches += 1;
+    return cudaGetLastError();
+}
+
+template <int WIN, int Q2MAX, int C0, int C1>
+cudaError_t spread_slab64_t(sgl_plan *p, const NGeom &g, const double2 *vals) {
+    if (g.C0 != C0 || g.C1 != C1 || g.S2 + 2 * p->q - 1 > 32) return cudaErrorInvalidConfiguration;
+    const int threads = 32 * (C0 + 2 * p->q - 1);
+    const int64_t blocks = work_list_cap(p->M, p->bins.nsuper, spread_chunk(p->prec));   // entries past work_len[1] return
+    k_spread_slab64<WIN, Q2MAX, C0, C1><<<(unsigned)blocks, threads, 0, p->stream>>>(
+        g, p->b.work[1], p->b.work_len + 1, p->b.u_sorted, p->b.perm, vals, (double2 *)p->b.bufA);
+    p->launches += 1;
+    return cudaGetLastError();
+}
+
+template <int WIN>
+cudaError_t spread64_t(sgl_plan *p, const double2 *vals) {
+    const NGeom g = make_geom(p);
+    if (p->q <= 4) return spread_slab64_t<WIN, 8, 4, 2>(p, g, vals);
+    if (p->q <= 8) return spread_slab64_t<WIN, 16, 4, 2>(p, g, vals);
+    double2 *grid = (double2 *)p->b.bufA;
+    k_spread<double, WIN, 32><<<nufft_blocks(p->M, 32), 256, 0, p->stream>>>(g, p->M, p->b.u_sorted, p->b.perm, vals, grid);
+    p->launches += 1;
+    return cudaGetLastError();
+}
+
+template <int WIN>
+cudaError_t grad64_t(sgl_plan *p, const double2 *gout, double *gxyz, double2 *vals) {
+    const NGeom g = make_geom(p);
+    const double2 *gridd = (const double2 *)p->b.bufA;
+    const int q2 = 2 * p->q;
+    if (q2 <= 8)
+        k_grad64<WIN, 8><<<nufft_blocks(p->M, 8), 256, 0, p->stream>>>(g, p->M, p->b.u_sorted, p->b.perm, p->b.r2max, gridd, gout, gxyz, vals);
+    else if (q2 <= 16)
+        k_grad64<WIN, 16><<<nufft_blocks(p->M, 16), 256, 0, p->stream>>>(g, p->M, p->b.u_sorted, p->b.perm, p->b.r2max, gridd, gout, gxyz, vals);
+    else
+        k_grad64<WIN, 32><<<nufft_blocks(p->M, 32), 256, 0, p->stream>>>(g, p->M, p->b.u_sorted, p->b.perm, p->b.r2max, gridd, gout, gxyz, vals);
+    p->launches += 1;
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_interp64(sgl_plan *p, double2 *vals) {
+    return p->window == SGL_WIN_KB ? interp64_t<SGL_WIN_KB>(p, vals) : interp64_t<SGL_WIN_GAUSS>(p, vals);
+}
+
+cudaError_t launch_spread64(sgl_plan *p, const double2 *vals) {
+    return p->window == SGL_WIN_KB ? spread64_t<SGL_WIN_KB>(p, vals) : spread64_t<SGL_WIN_GAUSS>(p, vals);
+}
+
+cudaError_t launch_grad64(sgl_plan *p, const double2 *gout, double *gxyz, double2 *vals) {
+    return p->window == SGL_WIN_KB ? grad64_t<SGL_WIN_KB>(p, gout, gxyz, vals) : grad64_t<SGL_WIN_GAUSS>(p, gout, gxyz, vals);
+}
+
+}  // namespace sgl

@@ -186,5 +186,52 @@ __device__ __forceinline__ float2 window_pair32(float x, float q, float par, flo
     return (s2 >= 0.f) ? make_float2(v, d) : make_float2(0.f, 0.f);
 }
 
+// Point-parallel spreading for 2q > 16 (both precisions): G lanes per point, atomic adds per tap.
+template <typename T, int WIN, int G>
+__global__ void __launch_bounds__(256) k_spread(NGeom g, int64_t M, const double *__restrict__ u_sorted,
+                                                const int *__restrict__ perm, const double2 *__restrict__ vals,
+                                                C2<T> *__restrict__ grid) {
+    const int lane = threadIdx.x & 31;
+    const int gl = lane % G;
+    const int q2 = 2 * g.q;
+    const T qT = (T)g.q;
+    const int64_t ppw = 32 / G;
+    const int64_t warp0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / 32;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) / 32;
+    const int64_t s1 = g.N[2], s0 = (int64_t)g.rows[1] * g.N[2];
+    for (int64_t base = warp0 * ppw; base < M; base += nwarps * ppw) {
+        const int64_t i = base + lane / G;
+        if (i >= M || gl >= q2) continue;
+        const double u0 = u_sorted[3 * i], u1 = u_sorted[3 * i + 1], u2 = u_sorted[3 * i + 2];
+        const int a0 = (int)floor(u0) - g.q + 1, a1 = (int)floor(u1) - g.q + 1, a2 = (int)floor(u2) - g.q + 1;
+        const double2 y = vals[perm[i]];
+        const T w2 = window<WIN, T>((T)(u2 - (a2 + gl)), qT, (T)g.par[2], (T)g.norm[2]);
+        const T yx = (T)y.x * w2, yy = (T)y.y * w2;
+        int c = a2 + gl;
+        if (c < 0) c += g.N[2];
+        if (c >= g.N[2]) c -= g.N[2];
+        for (int a = 0; a < q2; ++a) {
+            const T w0 = window<WIN, T>((T)(u0 - (a0 + a)), qT, (T)g.par[0], (T)g.norm[0]);
+            const int r0 = row_of(a0 + a, g.first[0], g.rows[0], g.N[0]);
+            C2<T> *rowp = grid + r0 * s0 + c;
+            for (int b = 0; b < q2; ++b) {
+                const T w = w0 * window<WIN, T>((T)(u1 - (a1 + b)), qT, (T)g.par[1], (T)g.norm[1]);
+                const int r1 = row_of(a1 + b, g.first[1], g.rows[1], g.N[1]);
+                atomic_add_c(rowp + r1 * s1, w * yx, w * yy);
+            }
+        }
+    }
+}
+
+// blocks of 256 threads for a grid-stride sweep over the points
+int nufft_blocks(int64_t M, int G) {
+    const int64_t ppb = 256 / G;                 // points per block per sweep
+    int64_t b = (M + ppb - 1) / ppb;
+    if (b > 152 * 16) b = 152 * 16;
+    if (b < 1) b = 1;
+    return (int)b;
+}
+
+
 }  // namespace
 }  // namespace sgl
