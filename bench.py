@@ -113,7 +113,10 @@ def stage_work(info, M, q, prec):
                + rows0 * W * W * cs + (2 * K0 + 1) * W * W * 16)
     radial = 4 * sum((K0 + 1) * (2 * l + 1) * (B - l) for l in range(B))
     polar = 4 * (K0 + 1) * (K1 + 1) * sum(B - abs(m) for m in range(-(B - 1), B))
-    alu = "fp32" if prec == "fp32_mixed" else "fp64"
+    # FP64 plans run the three windowed loops in double-float arithmetic unless native: a
+    # double-float multiply-add is 12 FP32-pipe instructions, so its ceiling is the FP32 peak / 12
+    # in flops of the binary64 algorithm ("df")
+    alu = {"fp32_mixed": "fp32", "fp64": "df", "fp64_native": "fp64"}[prec]
     # interpolation / gradient on the tensor cores (3xTF32 slab products): the algorithmic flops
     # stay the windowed sums' own; the peak is the TF32 one
     tc = info.get("tensor_cores", {})
@@ -192,9 +195,11 @@ def run_ours(args):
 
     results = {}
     keep = {}
-    precs = (("fp32_mixed", sgl.PREC_FP32_MIXED),) + (() if args.no_fp64 else (("fp64", sgl.PREC_FP64),))
-    for prec_name, prec in precs:
-        plan = sgl.Plan(B, M, precision=prec, window=sgl.WIN_KB, q=q, sigma=2.0, profile=True, device=dev)
+    precs = (("fp32_mixed", sgl.PREC_FP32_MIXED, False),) + (
+        () if args.no_fp64 else (("fp64", sgl.PREC_FP64, False), ("fp64_native", sgl.PREC_FP64, True)))
+    for prec_name, prec, native in precs:
+        plan = sgl.Plan(B, M, precision=prec, window=sgl.WIN_KB, q=q, sigma=2.0, profile=True, device=dev,
+                        native_fp64=native)
         out = {}
 
         def step():
@@ -234,7 +239,7 @@ def run_ours(args):
                 achieved, peak, unit = amount / (per_launch_ms * 1e-3) / 1e9, hbm_peak, "GB/s"
             else:
                 achieved = amount / (per_launch_ms * 1e-3) / 1e12
-                peak, unit = {"fp32": fp32_peak, "fp64": fp64_peak, "tf32": tf32_peak}[kind], "TFLOP/s"
+                peak, unit = {"fp32": fp32_peak, "fp64": fp64_peak, "tf32": tf32_peak, "df": fp32_peak / 12}[kind], "TFLOP/s"
             bound = "hbm" if kind == "hbm" else ("tensor" if kind == "tf32" else "alu")
             table[name] = {"ms": round(per_launch_ms, 4), "share": None, "bound": bound,
                            "alu": None if kind == "hbm" else kind, "achieved": round(achieved, 3), "peak": round(peak, 2),
@@ -373,7 +378,15 @@ def run_ours(args):
             "roofline": roofline, "clocks": head["clocks"],
             "fp64": None if "fp64" not in results else {
                 "value": round(results["fp64"]["value"], 4), "unit": UNIT, "ms_per_step": round(results["fp64"]["ms_per_step"], 4),
+                "precision": "FP64 plan (binary64 everywhere but the windowed loops, which run in double-float "
+                             "arithmetic: FP32 pairs with error-free products and sums)",
                 "gpu_launches": results["fp64"]["gpu_launches"], "stages": results["fp64"]["stages"]},
+            "fp64_native": None if "fp64_native" not in results else {
+                "value": round(results["fp64_native"]["value"], 4), "unit": UNIT,
+                "ms_per_step": round(results["fp64_native"]["ms_per_step"], 4),
+                "precision": "FP64 plan with SGL_FLAG_NATIVE_FP64 (binary64 windowed loops)",
+                "gpu_launches": results["fp64_native"]["gpu_launches"],
+                "stages": {k: v["ms"] for k, v in results["fp64_native"]["stages"].items()}},
             "stages_fp32_mixed": head["stages"],
             "fp32_mixed_other_cutoffs": by_q,
             "inverse": inverse_line,
@@ -412,14 +425,16 @@ def cpu_baseline(args, x_h, c_h, y_h, g_h, keep, dev):
     base = {"value": round(S / el / 1e6, 8), "unit": UNIT, "cores": threads, "kind": "oracle",
             "sample": "%d of the %d points (forward + adjoint + point gradient, direct sum, FP64); %.1f s" % (S, args.M, el)}
     err = {}
-    for prec_name, prec in (("fp32_mixed", sgl.PREC_FP32_MIXED), ("fp64", sgl.PREC_FP64)):
+    for prec_name, prec, native in (("fp32_mixed", sgl.PREC_FP32_MIXED, False), ("fp64", sgl.PREC_FP64, False),
+                                    ("fp64_native", sgl.PREC_FP64, True)):
         if prec_name not in keep:
             continue
         k = keep[prec_name]
         ef = np.abs(k["f"][idx] - f_ref).max() / np.abs(f_ref).max()
         eg = np.abs(k["g"][idx] - g_ref).max() / np.abs(g_ref).max()
         # adjoint on the sample alone: same plan type, values zero outside the sample
-        plan = sgl.Plan(args.B, args.M, precision=prec, window=sgl.WIN_KB, q=args.q, sigma=2.0, device=dev)
+        plan = sgl.Plan(args.B, args.M, precision=prec, window=sgl.WIN_KB, q=args.q, sigma=2.0, device=dev,
+                        native_fp64=native)
         plan.set_points(torch.from_numpy(x_h).to(dev))
         ym = np.zeros_like(y_h)
         ym[idx] = y_h[idx]

@@ -74,6 +74,12 @@ typedef enum {
 #define SGL_FLAG_TC 8u        /* FP32-mixed: use the tensor-core (tcgen05) interpolation and gradient
                                  kernels wherever the plan allows them (q <= 8, windowed axes 0
                                  and 1), not only where they are the faster choice */
+#define SGL_FLAG_NATIVE_FP64 16u  /* FP64: run interpolation, gradient and spreading in binary64
+                                 arithmetic.  Without it these three loops use double-float
+                                 arithmetic (pairs of FP32 numbers with error-free products and
+                                 sums, relative rounding of order 2^-48 per operation; window
+                                 values, reductions and everything else stay binary64), which
+                                 runs several times faster on the FP32 pipes */
 
 /* stages reported by sgl_profile (index order) */
 #define SGL_NUM_STAGES 12

@@ -273,7 +273,8 @@ sgl_status plan_create_impl(sgl_plan **out, int B, int64_t M_max, int precision,
     if (window != SGL_WIN_KB && window != SGL_WIN_GAUSS) return set_error(SGL_ERR_ARG, "unknown window");
     if (q < 1 || q > kMaxQ) return set_error(SGL_ERR_ARG, "q must be in [1, 16]");
     if (!(sigma >= 1.5 && sigma <= 4.0)) return set_error(SGL_ERR_ARG, "sigma must be in [1.5, 4]");
-    if (flags & ~(SGL_FLAG_HOST_IO | SGL_FLAG_PROFILE | SGL_FLAG_SIMT | SGL_FLAG_TC)) return set_error(SGL_ERR_ARG, "unknown flag bits");
+    if (flags & ~(SGL_FLAG_HOST_IO | SGL_FLAG_PROFILE | SGL_FLAG_SIMT | SGL_FLAG_TC | SGL_FLAG_NATIVE_FP64))
+        return set_error(SGL_ERR_ARG, "unknown flag bits");
     if ((flags & SGL_FLAG_SIMT) && (flags & SGL_FLAG_TC)) return set_error(SGL_ERR_ARG, "SGL_FLAG_SIMT and SGL_FLAG_TC exclude each other");
 
     PlanHolder *h = new (std::nothrow) PlanHolder();
@@ -378,6 +379,7 @@ sgl_status plan_create_impl(sgl_plan **out, int B, int64_t M_max, int precision,
     ALLOC(b.work[0], (size_t)work_list_cap(Mc, p->bins.nsuper, kTcPass));
     ALLOC(b.work[1], (size_t)work_list_cap(Mc, p->bins.nsuper, spread_chunk(precision)));
     ALLOC(b.work_len, 2);
+    ALLOC(b.df_max, 2);
     if (flags & SGL_FLAG_HOST_IO) {
         ALLOC(b.io_xyz, 3 * Mc);
         ALLOC(b.io_coef, (size_t)(2 * p->Nc));

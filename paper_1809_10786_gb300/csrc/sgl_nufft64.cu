@@ -5,11 +5,93 @@
 //   s(t) = sum_{l : |u_d - l_d| <= q} alpha_l prod_d psi_d(u_d - l_d),   u_d = N_d t_d / (2 pi)
 //
 // Taps per axis: l = floor(u) - q + 1 ... floor(u) + q (2q taps).  The FP64 pipe of GB300 runs
-// at 1/64 of the FP32 rate, so it bounds every kernel here.
+// at 1/64 of the FP32 rate, so it bounds every binary64 kernel here.  By default the three hot
+// loops therefore run in double-float arithmetic instead: a value is the unevaluated sum hi + lo
+// of two FP32 numbers, products and sums are carried out with the error-free transformations
+// TwoProduct (Dekker; exact with a fused multiply-add) and TwoSum (Knuth), so every tap costs
+// about a dozen FP32 operations and keeps a relative rounding error of order 2^-48 (binary64:
+// 2^-53).  Window values, the final lane reductions and the chain rule stay binary64; the grid
+// is split into (hi, lo) pairs in place by one pass before the interpolation, and spreading
+// adds its double-float sums to the binary64 grid.  SGL_FLAG_NATIVE_FP64 selects the binary64
+// loops (k_interp64, k_grad64, k_spread_slab64).
 #include "sgl_nufft_common.cuh"
 
 namespace sgl {
 namespace {
+
+// ---- double-float helpers (rounded operations that the compiler may not fuse or reorder)
+__device__ __forceinline__ void df_split(double x, float &h, float &l) {
+    h = __double2float_rn(x);
+    l = __double2float_rn(x - (double)h);
+}
+
+// acc += w * v for double-float w = wh + wl, v = vh + vl.  acc is kept as a running binary32
+// sum ah (updated by TwoSum, exactly) and the accumulated rounding terms al; (double)ah +
+// (double)al is the value.
+__device__ __forceinline__ void df_fma(float &ah, float &al, float wh, float wl, float vh, float vl) {
+    const float p = __fmul_rn(wh, vh);
+    float e = fmaf(wh, vh, -p);                 // TwoProduct: wh vh = p + e exactly
+    e = fmaf(wh, vl, e);
+    e = fmaf(wl, vh, e);
+    const float s = __fadd_rn(ah, p);          // TwoSum: ah + p = s + t exactly
+    const float bv = __fsub_rn(s, ah);
+    const float t = __fadd_rn(__fsub_rn(ah, __fsub_rn(s, bv)), __fsub_rn(p, bv));
+    al = __fadd_rn(al, __fadd_rn(t, e));
+    ah = s;
+}
+
+// (ph, pl) = w * v (double-float product, unnormalized)
+__device__ __forceinline__ void df_mul(float &ph, float &pl, float wh, float wl, float vh, float vl) {
+    ph = __fmul_rn(wh, vh);
+    float e = fmaf(wh, vh, -ph);
+    e = fmaf(wh, vl, e);
+    pl = fmaf(wl, vh, e);
+}
+
+__device__ __forceinline__ double df_value(float h, float l) { return (double)h + (double)l; }
+
+// Double-float has the exponent range of binary32, and the SGL basis functions are polynomials
+// that grow like r^(2B) (they are orthonormal under the weight e^{-|x|^2}), so grids and values
+// of 1e40 and more are ordinary at moderate B.  Every double-float pass therefore works on
+// data scaled by an exact power of two: max |x| over its input (the grid, or the values to
+// spread) is reduced on the device and the pass multiplies by 2^-e on entry and by 2^e on exit,
+// with max |x| 2^-e in [1/2, 1).  (Parts below max |x| 2^-100 would lose bits; relative to the
+// sum they are below binary64's own rounding.)
+__global__ void __launch_bounds__(256) k_max_abs(const double *__restrict__ x, int64_t n, unsigned long long *__restrict__ out) {
+    __shared__ double ws[8];
+    double m = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        m = fmax(m, fabs(x[i]));
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < 8; ++w) m = fmax(m, ws[w]);
+        atomicMax(out, (unsigned long long)__double_as_longlong(m));   // non-negative doubles order as integers
+    }
+}
+
+// the exponent e of the scale for max |x| (0 when it is zero or not finite)
+__device__ __forceinline__ int df_exponent(const unsigned long long *bits) {
+    const double m = __longlong_as_double((long long)__ldg(bits));
+    int e = 0;
+    if (m > 0.0 && m <= 1.7976931348623157e308) frexp(m, &e);
+    return e;
+}
+
+// binary64 grid -> double-float grid of grid * 2^-e, in place: cell (re, im) becomes
+// (re_hi, im_hi, re_lo, im_lo)
+__global__ void __launch_bounds__(256) k_split_grid(double2 *__restrict__ grid, int64_t n, const unsigned long long *__restrict__ maxbits) {
+    float4 *out = reinterpret_cast<float4 *>(grid);
+    const double sc = ldexp(1.0, -df_exponent(maxbits));
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double2 v = grid[i];
+        float4 o;
+        df_split(v.x * sc, o.x, o.z);
+        df_split(v.y * sc, o.y, o.w);
+        out[i] = o;
+    }
+}
 
 // Chain rule from ds/du_d to Re(conj(g) grad_x f) for one point (FP64), written by one lane.
 __device__ __forceinline__ void write_point_gradient(const NGeom &g, double rho, double u0, double u1, double u2,
@@ -284,11 +366,306 @@ __global__ void __launch_bounds__(256) k_grad64(NGeom g, int64_t M, const double
 }
 
 
+// ---- double-float interpolation: same lane layout as k_interp64 (lane = azimuthal tap, the
+// (2q)^2 rows of axes 0 and 1 swept by every lane), double-float products and sums.  The axis-1
+// weights are shuffled per tap rather than kept in per-point arrays, so that four CTAs fit on an
+// SM: the loop is bound by the latency of its grid loads, not by arithmetic.
+template <int WIN, int G>
+__global__ void __launch_bounds__(256, 4) k_interp64x(NGeom g, int64_t M, const double *__restrict__ u_sorted,
+                                                   const int *__restrict__ perm, const float4 *__restrict__ grid,
+                                                   const unsigned long long *__restrict__ maxbits, double2 *__restrict__ vals) {
+    const double unscale = ldexp(1.0, df_exponent(maxbits));
+    const int lane = threadIdx.x & 31, gl = lane & (G - 1);
+    const int q = g.q, q2 = 2 * q;
+    const double qd = (double)q;
+    const int64_t s1 = g.N[2], s0 = (int64_t)g.rows[1] * g.N[2];
+    constexpr int PPW = 32 / G;
+    const int64_t warp0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / 32;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) / 32;
+    for (int64_t base = warp0 * PPW; base < M; base += nwarps * PPW) {
+        const int64_t i = base + lane / G;
+        const bool live = i < M;
+        const int64_t ii = live ? i : M - 1;
+        const double u0 = u_sorted[3 * ii], u1 = u_sorted[3 * ii + 1], u2 = u_sorted[3 * ii + 2];
+        const int a0 = cell_clamped(u0, g.cmax0) - q + 1, a1 = cell_clamped(u1, g.cmax1) - q + 1;
+        const int a2 = min(max((int)floor(u2), 0), g.N[2] - 1) - q + 1;
+        const bool tap = gl < q2;
+        float w0h_own, w0l_own, w1h_own, w1l_own;
+        df_split(tap ? window<WIN, double>(u0 - (a0 + gl), qd, g.par[0], g.norm[0]) : 0.0, w0h_own, w0l_own);
+        df_split(tap ? window<WIN, double>(u1 - (a1 + gl), qd, g.par[1], g.norm[1]) : 0.0, w1h_own, w1l_own);
+        const double w2 = tap ? window<WIN, double>(u2 - (a2 + gl), qd, g.par[2], g.norm[2]) : 0.0;
+        const int col = tap ? wrap_index(a2 + gl, g.N[2]) : 0;
+
+        float axh = 0.f, axl = 0.f, ayh = 0.f, ayl = 0.f;
+        for (int a = 0; a < q2; ++a) {
+            const float w0h = __shfl_sync(0xffffffffu, w0h_own, a, G), w0l = __shfl_sync(0xffffffffu, w0l_own, a, G);
+            const float4 *rowp = grid + row_of(a0 + a, g.first[0], g.rows[0], g.N[0]) * s0 + col;
+            float rxh = 0.f, rxl = 0.f, ryh = 0.f, ryl = 0.f;
+#pragma unroll
+            for (int b = 0; b < G; ++b) {
+                const float w1h = __shfl_sync(0xffffffffu, w1h_own, b, G), w1l = __shfl_sync(0xffffffffu, w1l_own, b, G);
+                if (b < q2) {
+                    const float4 v = __ldg(rowp + row_of(a1 + b, g.first[1], g.rows[1], g.N[1]) * s1);
+                    df_fma(rxh, rxl, w1h, w1l, v.x, v.z);
+                    df_fma(ryh, ryl, w1h, w1l, v.y, v.w);
+                }
+            }
+            df_fma(axh, axl, w0h, w0l, rxh, rxl);
+            df_fma(ayh, ayl, w0h, w0l, ryh, ryl);
+        }
+        double ax = df_value(axh, axl) * w2, ay = df_value(ayh, ayl) * w2;
+#pragma unroll
+        for (int o = G / 2; o > 0; o >>= 1) {
+            ax += __shfl_xor_sync(0xffffffffu, ax, o);
+            ay += __shfl_xor_sync(0xffffffffu, ay, o);
+        }
+        if (live && gl == 0) vals[perm[i]] = make_double2(ax * unscale, ay * unscale);
+    }
+}
+
+// ---- double-float window-derivative interpolation (values, ds/du0, ds/du1, ds/du2), layout of k_grad64
+template <int WIN, int G>
+__global__ void __launch_bounds__(256, 4) k_grad64x(NGeom g, int64_t M, const double *__restrict__ u_sorted,
+                                                 const int *__restrict__ perm, const unsigned long long *__restrict__ r2max,
+                                                 const float4 *__restrict__ grid, const unsigned long long *__restrict__ maxbits,
+                                                 const double2 *__restrict__ gout, double *__restrict__ gxyz,
+                                                 double2 *__restrict__ vals) {
+    const double unscale = ldexp(1.0, df_exponent(maxbits));
+    const int lane = threadIdx.x & 31, gl = lane & (G - 1);
+    const int q = g.q, q2 = 2 * q;
+    const double qd = (double)q;
+    const int64_t s1 = g.N[2], s0 = (int64_t)g.rows[1] * g.N[2];
+    double rho = sqrt(__longlong_as_double((long long)*r2max)) * (1.0 + 0x1p-20);
+    if (!(rho > 0.0)) rho = 1.0;
+    constexpr int PPW = 32 / G;
+    const int64_t warp0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / 32;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) / 32;
+    for (int64_t base = warp0 * PPW; base < M; base += nwarps * PPW) {
+        const int64_t i = base + lane / G;
+        const bool live = i < M;
+        const int64_t ii = live ? i : M - 1;
+        const double u0 = u_sorted[3 * ii], u1 = u_sorted[3 * ii + 1], u2 = u_sorted[3 * ii + 2];
+        const int a0 = cell_clamped(u0, g.cmax0) - q + 1, a1 = cell_clamped(u1, g.cmax1) - q + 1;
+        const int a2 = min(max((int)floor(u2), 0), g.N[2] - 1) - q + 1;
+        const bool tap = gl < q2;
+        const double x0 = u0 - (a0 + gl), x1 = u1 - (a1 + gl), x2 = u2 - (a2 + gl);
+        float w0h_own, w0l_own, d0h_own, d0l_own, w1h_own, w1l_own, d1h_own, d1l_own;
+        df_split(tap ? window<WIN, double>(x0, qd, g.par[0], g.norm[0]) : 0.0, w0h_own, w0l_own);
+        df_split(tap ? window_deriv<WIN, double>(x0, qd, g.par[0], g.norm[0]) : 0.0, d0h_own, d0l_own);
+        df_split(tap ? window<WIN, double>(x1, qd, g.par[1], g.norm[1]) : 0.0, w1h_own, w1l_own);
+        df_split(tap ? window_deriv<WIN, double>(x1, qd, g.par[1], g.norm[1]) : 0.0, d1h_own, d1l_own);
+        const double w2 = tap ? window<WIN, double>(x2, qd, g.par[2], g.norm[2]) : 0.0;
+        const double d2 = tap ? window_deriv<WIN, double>(x2, qd, g.par[2], g.norm[2]) : 0.0;
+        const int col = tap ? wrap_index(a2 + gl, g.N[2]) : 0;
+        float fxh = 0.f, fxl = 0.f, fyh = 0.f, fyl = 0.f;     // sum psi0 psi1 grid
+        float axh = 0.f, axl = 0.f, ayh = 0.f, ayl = 0.f;     // sum psi0' psi1 grid
+        float bxh = 0.f, bxl = 0.f, byh = 0.f, byl = 0.f;     // sum psi0 psi1' grid
+        for (int a = 0; a < q2; ++a) {
+            const float w0h = __shfl_sync(0xffffffffu, w0h_own, a, G), w0l = __shfl_sync(0xffffffffu, w0l_own, a, G);
+            const float d0h = __shfl_sync(0xffffffffu, d0h_own, a, G), d0l = __shfl_sync(0xffffffffu, d0l_own, a, G);
+            const float4 *rowp = grid + row_of(a0 + a, g.first[0], g.rows[0], g.N[0]) * s0 + col;
+            float rxh = 0.f, rxl = 0.f, ryh = 0.f, ryl = 0.f, sxh = 0.f, sxl = 0.f, syh = 0.f, syl = 0.f;
+#pragma unroll
+            for (int b = 0; b < G; ++b) {
+                const float w1h = __shfl_sync(0xffffffffu, w1h_own, b, G), w1l = __shfl_sync(0xffffffffu, w1l_own, b, G);
+                const float d1h = __shfl_sync(0xffffffffu, d1h_own, b, G), d1l = __shfl_sync(0xffffffffu, d1l_own, b, G);
+                if (b < q2) {
+                    const float4 v = __ldg(rowp + row_of(a1 + b, g.first[1], g.rows[1], g.N[1]) * s1);
+                    df_fma(rxh, rxl, w1h, w1l, v.x, v.z);
+                    df_fma(ryh, ryl, w1h, w1l, v.y, v.w);
+                    df_fma(sxh, sxl, d1h, d1l, v.x, v.z);
+                    df_fma(syh, syl, d1h, d1l, v.y, v.w);
+                }
+            }
+            df_fma(fxh, fxl, w0h, w0l, rxh, rxl);
+            df_fma(fyh, fyl, w0h, w0l, ryh, ryl);
+            df_fma(axh, axl, d0h, d0l, rxh, rxl);
+            df_fma(ayh, ayl, d0h, d0l, ryh, ryl);
+            df_fma(bxh, bxl, w0h, w0l, sxh, sxl);
+            df_fma(byh, byl, w0h, w0l, syh, syl);
+        }
+        const double fx = df_value(fxh, fxl) * unscale, fy = df_value(fyh, fyl) * unscale;
+        double f2x = d2 * fx, f2y = d2 * fy;
+        double sx = w2 * fx, sy = w2 * fy;             // the value s itself (forward with gradient)
+        double ax = df_value(axh, axl) * unscale * w2, ay = df_value(ayh, ayl) * unscale * w2;
+        double bx = df_value(bxh, bxl) * unscale * w2, by = df_value(byh, byl) * unscale * w2;
+#pragma unroll
+        for (int o = G / 2; o > 0; o >>= 1) {
+            ax += __shfl_xor_sync(0xffffffffu, ax, o);
+            ay += __shfl_xor_sync(0xffffffffu, ay, o);
+            bx += __shfl_xor_sync(0xffffffffu, bx, o);
+            by += __shfl_xor_sync(0xffffffffu, by, o);
+            f2x += __shfl_xor_sync(0xffffffffu, f2x, o);
+            f2y += __shfl_xor_sync(0xffffffffu, f2y, o);
+            if (vals) {
+                sx += __shfl_xor_sync(0xffffffffu, sx, o);
+                sy += __shfl_xor_sync(0xffffffffu, sy, o);
+            }
+        }
+        if (live && gl == 0) {
+            const int dst = perm[i];
+            write_point_gradient(g, rho, u0, u1, u2, ax, ay, bx, by, f2x, f2y, gout[dst], gxyz + 3 * (int64_t)dst);
+            if (vals) vals[dst] = make_double2(sx, sy);
+        }
+    }
+}
+
+// ---- double-float spreading.  The two-cells-per-lane layout of k_spread_slab64 needs more
+// registers in double-float than a CTA of C0 + 2q - 1 warps can give, so this kernel keeps one
+// azimuthal cell per lane (the 32-cell tile on the 32 lanes; a point's 2q taps leave the other
+// lanes adding zeros -- the FP32 pipe is 64 times the FP64 one, so idle lanes cost less than
+// binary64 arithmetic would) and halves the accumulators instead: the whole work piece (at most
+// spread_chunk(FP64) points) is staged once, then swept twice, for tile rows [0, RH) and
+// [RH, C1 + 2q - 1), each sweep ending with its atomic flush.
+template <int Q2MAX, int C1>
+struct Spread64xSmem {
+    static constexpr int PCH = SGL_SPREAD_CHUNK64;   // a whole work piece
+    static constexpr int T1 = C1 + Q2MAX - 1;
+    float4 y[PCH];
+    float2 w0[PCH][Q2MAX];
+    float2 w1[PCH][T1];
+    float2 w2[PCH][32];
+    int ta0[PCH];
+};
+
+template <int WIN, int Q2MAX, int C0, int C1>
+__global__ void __launch_bounds__(32 * (C0 + Q2MAX - 1)) k_spread_slab64x(NGeom g, const int4 *__restrict__ work,
+                                                                          const int *__restrict__ work_len,
+                                                                          const double *__restrict__ u_sorted,
+                                                                          const int *__restrict__ perm, const double2 *__restrict__ vals,
+                                                                          const unsigned long long *__restrict__ maxbits,
+                                                                          double2 *__restrict__ grid) {
+    using S = Spread64xSmem<Q2MAX, C1>;
+    constexpr int T1M = S::T1, RH = (T1M + 1) / 2;
+    constexpr int E = Q2MAX + T1M + 32 + 1;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    S &sm = *reinterpret_cast<S *>(smem_raw);
+    const int lane = threadIdx.x & 31, ta = threadIdx.x >> 5;
+    const int q = g.q, q2 = 2 * q;
+    const double qd = (double)q;
+    if ((int)blockIdx.x >= __ldg(work_len)) return;
+    const int vexp = df_exponent(maxbits);
+    const double vscale = ldexp(1.0, -vexp), unscale = ldexp(1.0, vexp);
+    const int4 piece = __ldg(work + blockIdx.x);
+    const int64_t sb = piece.x;
+    const int cs = piece.y, np = min(piece.z, S::PCH);
+    const int sb1 = (int)(sb % g.nsb1), sb2 = (int)((sb / g.nsb1) % g.nsb2), sb0 = (int)(sb / ((int64_t)g.nsb1 * g.nsb2));
+    const int ta_org = sb0 * C0 - q + 1, tb_org = sb1 * C1 - q + 1, cbase = sb2 * g.S2 - q + 1;
+    const int T1 = C1 + q2 - 1;
+    for (int t = threadIdx.x; t < np * E; t += blockDim.x) {
+        const int p = t / E, e = t % E;
+        const int64_t pi = cs + p;
+        const double u0 = u_sorted[3 * pi], u1 = u_sorted[3 * pi + 1], u2 = u_sorted[3 * pi + 2];
+        const int c0 = cell_clamped(u0, g.cmax0), c1 = cell_clamped(u1, g.cmax1);
+        const int c2 = min(max((int)floor(u2), 0), g.N[2] - 1);
+        if (e < Q2MAX + T1M + 32) {
+            double x, par, nrm;
+            float2 *dst;
+            bool ok;
+            if (e < Q2MAX) {
+                ok = e < q2; x = u0 - c0 + (double)(q - 1 - e); par = g.par[0]; nrm = g.norm[0]; dst = &sm.w0[p][e];
+            } else if (e < Q2MAX + T1M) {
+                const int tb = e - Q2MAX;
+                const int rel = tb - (c1 - sb1 * C1);
+                ok = rel >= 0 && rel < q2 && tb < T1; x = u1 - c1 + (double)(q - 1 - rel); par = g.par[1]; nrm = g.norm[1];
+                dst = &sm.w1[p][tb];
+            } else {
+                const int L = e - Q2MAX - T1M;
+                const int rel = cbase + L - (c2 - q + 1);
+                ok = rel >= 0 && rel < q2; x = u2 - c2 + (double)(q - 1 - rel); par = g.par[2]; nrm = g.norm[2];
+                dst = &sm.w2[p][L];
+            }
+            float h, l;
+            df_split(ok ? window<WIN, double>(x, qd, par, nrm) : 0.0, h, l);
+            *dst = make_float2(h, l);
+        } else {
+            const double2 y = vals[perm[pi]];
+            float4 v;
+            df_split(y.x * vscale, v.x, v.z);
+            df_split(y.y * vscale, v.y, v.w);
+            sm.y[p] = v;
+            sm.ta0[p] = c0 - sb0 * C0;
+        }
+    }
+    __syncthreads();
+    if (ta >= C0 + q2 - 1) return;
+    const int64_t s1 = g.N[2], s0 = (int64_t)g.rows[1] * g.N[2];
+    const int r0 = row_checked(ta_org + ta, g.first[0], g.rows[0], g.N[0]);
+    if (r0 < 0) return;                 // slab outside the stored rows: no point reaches it
+    double2 *colp = grid + r0 * s0 + wrap_index(cbase + lane, g.N[2]);
+#pragma unroll
+    for (int pass = 0; pass < 2; ++pass) {
+        float4 acc[RH];
+#pragma unroll
+        for (int r = 0; r < RH; ++r) acc[r] = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll 2
+        for (int p = 0; p < np; ++p) {
+            const int j = ta - sm.ta0[p];
+            if (j < 0 || j >= q2) continue;
+            const float2 a = sm.w0[p][j], c = sm.w2[p][lane];
+            const float4 y = sm.y[p];
+            float wzh, wzl, zxh, zxl, zyh, zyl;
+            df_mul(wzh, wzl, a.x, a.y, c.x, c.y);
+            df_mul(zxh, zxl, wzh, wzl, y.x, y.z);
+            df_mul(zyh, zyl, wzh, wzl, y.y, y.w);
+#pragma unroll
+            for (int r = 0; r < RH; ++r) {
+                const int tb = pass * RH + r;
+                if (tb < T1M) {
+                    const float2 w = sm.w1[p][tb];
+                    df_fma(acc[r].x, acc[r].y, w.x, w.y, zxh, zxl);
+                    df_fma(acc[r].z, acc[r].w, w.x, w.y, zyh, zyl);
+                }
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < RH; ++r) {
+            const int tb = pass * RH + r;
+            if (tb >= T1M || tb >= T1) continue;
+            const int r1 = row_checked(tb_org + tb, g.first[1], g.rows[1], g.N[1]);
+            if (r1 < 0) continue;
+            const double vx = df_value(acc[r].x, acc[r].y) * unscale, vy = df_value(acc[r].z, acc[r].w) * unscale;
+            if (vx != 0.0 || vy != 0.0) {
+                atomicAdd(&colp[r1 * s1].x, vx);
+                atomicAdd(&colp[r1 * s1].y, vy);
+            }
+        }
+    }
+}
+
+// max |x| of n doubles into bits (zeroed first)
+cudaError_t max_abs(sgl_plan *p, const double *x, int64_t n, unsigned long long *bits) {
+    cudaError_t e = cudaMemsetAsync(bits, 0, sizeof(unsigned long long), p->stream);
+    if (e != cudaSuccess) return e;
+    k_max_abs<<<nufft_blocks(n, 1), 256, 0, p->stream>>>(x, n, bits);
+    p->launches += 1;
+    return cudaGetLastError();
+}
+
+cudaError_t split_grid(sgl_plan *p) {
+    const int64_t n = (int64_t)p->ax[0].rows * p->ax[1].rows * p->ax[2].N;
+    cudaError_t e = max_abs(p, (const double *)p->b.bufA, 2 * n, p->b.df_max);
+    if (e != cudaSuccess) return e;
+    k_split_grid<<<nufft_blocks(n, 1), 256, 0, p->stream>>>((double2 *)p->b.bufA, n, p->b.df_max);
+    p->launches += 1;
+    return cudaGetLastError();
+}
+
 template <int WIN>
 cudaError_t interp64_t(sgl_plan *p, double2 *vals) {
     const NGeom g = make_geom(p);
     const double2 *gridd = (const double2 *)p->b.bufA;
     const int q2 = 2 * p->q;
+    if (!(p->flags & SGL_FLAG_NATIVE_FP64)) {
+        cudaError_t e = split_grid(p);
+        if (e != cudaSuccess) return e;
+        const float4 *gx = (const float4 *)p->b.bufA;
+        if (q2 <= 8) k_interp64x<WIN, 8><<<nufft_blocks(p->M, 8), 256, 0, p->stream>>>(g, p->M, p->b.u_sorted, p->b.perm, gx, p->b.df_max, vals);
+        else if (q2 <= 16) k_interp64x<WIN, 16><<<nufft_blocks(p->M, 16), 256, 0, p->stream>>>(g, p->M, p->b.u_sorted, p->b.perm, gx, p->b.df_max, vals);
+        else k_interp64x<WIN, 32><<<nufft_blocks(p->M, 32), 256, 0, p->stream>>>(g, p->M, p->b.u_sorted, p->b.perm, gx, p->b.df_max, vals);
+        p->launches += 1;
+        return cudaGetLastError();
+    }
     if (q2 <= 8) k_interp64<WIN, 8><<<nufft_blocks(p->M, 8), 256, 0, p->stream>>>(g, p->M, p->b.u_sorted, p->b.perm, gridd, vals);
     else if (q2 <= 16) k_interp64<WIN, 16><<<nufft_blocks(p->M, 16), 256, 0, p->stream>>>(g, p->M, p->b.u_sorted, p->b.perm, gridd, vals);
     else k_interp64<WIN, 32><<<nufft_blocks(p->M, 32), 256, 0, p->stream>>>(g, p->M, p->b.u_sorted, p->b.perm, gridd, vals);
@@ -296,13 +673,23 @@ cudaError_t interp64_t(sgl_plan *p, double2 *vals) {
     return cudaGetLastError();
 }
 
-template <int WIN, int Q2MAX, int C0, int C1>
+template <int WIN, int Q2MAX, int C0, int C1, bool DF>
 cudaError_t spread_slab64_t(sgl_plan *p, const NGeom &g, const double2 *vals) {
     if (g.C0 != C0 || g.C1 != C1 || g.S2 + 2 * p->q - 1 > 32) return cudaErrorInvalidConfiguration;
     const int threads = 32 * (C0 + 2 * p->q - 1);
     const int64_t blocks = work_list_cap(p->M, p->bins.nsuper, spread_chunk(p->prec));   // entries past work_len[1] return
-    k_spread_slab64<WIN, Q2MAX, C0, C1><<<(unsigned)blocks, threads, 0, p->stream>>>(
-        g, p->b.work[1], p->b.work_len + 1, p->b.u_sorted, p->b.perm, vals, (double2 *)p->b.bufA);
+    if (DF) {
+        auto kern = k_spread_slab64x<WIN, Q2MAX, C0, C1>;
+        const int smem = (int)sizeof(Spread64xSmem<Q2MAX, C1>);
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e == cudaSuccess) e = max_abs(p, (const double *)vals, 2 * p->M, p->b.df_max + 1);
+        if (e != cudaSuccess) return e;
+        kern<<<(unsigned)blocks, threads, smem, p->stream>>>(g, p->b.work[1], p->b.work_len + 1, p->b.u_sorted, p->b.perm, vals,
+                                                            p->b.df_max + 1, (double2 *)p->b.bufA);
+    } else {
+        k_spread_slab64<WIN, Q2MAX, C0, C1><<<(unsigned)blocks, threads, 0, p->stream>>>(
+            g, p->b.work[1], p->b.work_len + 1, p->b.u_sorted, p->b.perm, vals, (double2 *)p->b.bufA);
+    }
     p->launches += 1;
     return cudaGetLastError();
 }
@@ -310,8 +697,9 @@ cudaError_t spread_slab64_t(sgl_plan *p, const NGeom &g, const double2 *vals) {
 template <int WIN>
 cudaError_t spread64_t(sgl_plan *p, const double2 *vals) {
     const NGeom g = make_geom(p);
-    if (p->q <= 4) return spread_slab64_t<WIN, 8, 4, 2>(p, g, vals);
-    if (p->q <= 8) return spread_slab64_t<WIN, 16, 4, 2>(p, g, vals);
+    const bool native = p->flags & SGL_FLAG_NATIVE_FP64;
+    if (p->q <= 4) return native ? spread_slab64_t<WIN, 8, 4, 2, false>(p, g, vals) : spread_slab64_t<WIN, 8, 4, 2, true>(p, g, vals);
+    if (p->q <= 8) return native ? spread_slab64_t<WIN, 16, 4, 2, false>(p, g, vals) : spread_slab64_t<WIN, 16, 4, 2, true>(p, g, vals);
     double2 *grid = (double2 *)p->b.bufA;
     k_spread<double, WIN, 32><<<nufft_blocks(p->M, 32), 256, 0, p->stream>>>(g, p->M, p->b.u_sorted, p->b.perm, vals, grid);
     p->launches += 1;
@@ -323,6 +711,20 @@ cudaError_t grad64_t(sgl_plan *p, const double2 *gout, double *gxyz, double2 *va
     const NGeom g = make_geom(p);
     const double2 *gridd = (const double2 *)p->b.bufA;
     const int q2 = 2 * p->q;
+    if (!(p->flags & SGL_FLAG_NATIVE_FP64)) {
+        cudaError_t e = split_grid(p);
+        if (e != cudaSuccess) return e;
+        const float4 *gx = (const float4 *)p->b.bufA;
+        const unsigned long long *r2 = p->b.r2max;
+        if (q2 <= 8)
+            k_grad64x<WIN, 8><<<nufft_blocks(p->M, 8), 256, 0, p->stream>>>(g, p->M, p->b.u_sorted, p->b.perm, r2, gx, p->b.df_max, gout, gxyz, vals);
+        else if (q2 <= 16)
+            k_grad64x<WIN, 16><<<nufft_blocks(p->M, 16), 256, 0, p->stream>>>(g, p->M, p->b.u_sorted, p->b.perm, r2, gx, p->b.df_max, gout, gxyz, vals);
+        else
+            k_grad64x<WIN, 32><<<nufft_blocks(p->M, 32), 256, 0, p->stream>>>(g, p->M, p->b.u_sorted, p->b.perm, r2, gx, p->b.df_max, gout, gxyz, vals);
+        p->launches += 1;
+        return cudaGetLastError();
+    }
     if (q2 <= 8)
         k_grad64<WIN, 8><<<nufft_blocks(p->M, 8), 256, 0, p->stream>>>(g, p->M, p->b.u_sorted, p->b.perm, p->b.r2max, gridd, gout, gxyz, vals);
     else if (q2 <= 16)

@@ -52,11 +52,13 @@ def test_trig_coeffs_equal_oracle_factorization(B, M):
     assert rel(eta, ref) <= 1e-13
 
 
+@pytest.mark.parametrize("native", [False, True])
 @pytest.mark.parametrize("B,M,win,q", [(8, 1000, sgl.WIN_KB, 8), (13, 700, sgl.WIN_KB, 8), (20, 3333, sgl.WIN_KB, 8),
                                        (8, 500, sgl.WIN_GAUSS, 12), (4, 257, sgl.WIN_KB, 7)])
-def test_forward_and_adjoint_fp64(B, M, win, q):
+def test_forward_and_adjoint_fp64(B, M, win, q, native):
+    # native: binary64 hot loops; otherwise double-float (the FP64 plan's default)
     c, x, y = case(B, M, 2000 + B)
-    p = plan_for(B, M, win=win, q=q, x=x)
+    p = plan_for(B, M, win=win, q=q, x=x, native_fp64=native)
     f = p.forward(gpu(c)).cpu().numpy()
     a = p.adjoint(gpu(y)).cpu().numpy()
     f_ref, _ = direct.forward(B, x, c)
@@ -89,11 +91,12 @@ def test_fp32_mixed_error_envelope(q, bound):
     assert rel(a, a_ref) <= bound
 
 
-@pytest.mark.parametrize("prec,tol", [(sgl.PREC_FP64, 1e-9), (sgl.PREC_FP32_MIXED, 1e-3)])
-def test_grad_points_against_oracle(prec, tol):
+@pytest.mark.parametrize("prec,tol,native", [(sgl.PREC_FP64, 1e-9, False), (sgl.PREC_FP64, 1e-9, True),
+                                             (sgl.PREC_FP32_MIXED, 1e-3, False)])
+def test_grad_points_against_oracle(prec, tol, native):
     B, M = 12, 1500
     c, x, g = case(B, M, 5000)
-    p = plan_for(B, M, prec=prec, x=x)
+    p = plan_for(B, M, prec=prec, x=x, native_fp64=native)
     gx = p.grad_points(gpu(c), gpu(g)).cpu().numpy()
     ref, _ = direct.grad_points(B, x, c, g)
     assert rel(gx, ref) <= tol
@@ -240,3 +243,42 @@ def test_forward_grad_host_buffers():
     f_dev, g_dev = p.forward_grad(gpu(c), gpu(g))
     assert np.allclose(vals, f_dev.cpu().numpy(), rtol=0, atol=1e-13 * np.abs(vals).max())
     assert np.allclose(gxyz, g_dev.cpu().numpy(), rtol=0, atol=1e-12 * np.abs(gxyz).max())
+
+
+@pytest.mark.parametrize("q", [4, 8])
+def test_double_float_and_binary64_loops_agree(q):
+    # the FP64 plan's double-float hot loops (relative rounding ~2^-48 per operation) against the
+    # binary64 loops of SGL_FLAG_NATIVE_FP64 (same window, so the same approximation), on a size
+    # with many points per bin and tile; q = 4 and 8 take the two spreading-kernel sizes
+    B, M = 16, 20000
+    c, x, y = case(B, M, 5100)
+    g = y[::-1].copy()
+    out = {}
+    for native in (False, True):
+        p = plan_for(B, M, q=q, x=x, native_fp64=native)
+        f = p.forward(gpu(c)).cpu().numpy()
+        a = p.adjoint(gpu(y)).cpu().numpy()
+        fv, gx = p.forward_grad(gpu(c), gpu(g))
+        out[native] = (f, a, fv.cpu().numpy(), gx.cpu().numpy())
+        p.close()
+    for k, tol in zip(range(4), (1e-13, 1e-13, 1e-13, 1e-11)):
+        assert rel(out[False][k], out[True][k]) <= tol
+
+
+@pytest.mark.parametrize("scale", [1e-200, 1e-30, 1e40, 1e200])
+def test_fp64_plan_is_linear_over_the_whole_binary64_range(scale):
+    # the double-float loops work on power-of-two scaled data, so magnitudes far outside the
+    # binary32 range (the SGL polynomials reach 1e15 at r ~ 9 for B = 16) keep full accuracy
+    B, M = 10, 3000
+    c, x, y = case(B, M, 5200)
+    p = plan_for(B, M, x=x)
+    f1 = p.forward(gpu(c)).cpu().numpy()
+    a1 = p.adjoint(gpu(y)).cpu().numpy()
+    fs = p.forward(gpu(c * scale)).cpu().numpy()
+    as_ = p.adjoint(gpu(y * scale)).cpu().numpy()
+    _, gs = p.forward_grad(gpu(c * scale), gpu(y))
+    _, g1 = p.forward_grad(gpu(c), gpu(y))
+    assert np.isfinite(fs).all() and np.isfinite(as_).all()
+    assert rel(fs / scale, f1) <= 1e-13
+    assert rel(as_ / scale, a1) <= 1e-13
+    assert rel(gs.cpu().numpy() / scale, g1.cpu().numpy()) <= 1e-11
