@@ -216,6 +216,32 @@ sgl_status sgl_inverse(sgl_plan *plan, const double *vals_dev, double *coef_dev,
 sgl_status sgl_midpoint_guess(sgl_plan *plan, const double *vals_dev, const double *weights_dev, double *coef_dev);
 
 /*
+ * Error control.  The factorization of Lambda is exact (Sect. 7, error estimate: the final NFFT
+ * is the only approximating step), so for every coefficient vector
+ *     max_i |f(x_i) - f~(x_i)| <= bound * ||eta||_1,
+ * with eta the trigonometric coefficients of f (sgl_trig_coeffs) and bound the worst error of the
+ * windowed interpolation on a single frequency: per axis d, e_d = max over |k| <= K_d and over
+ * the fractional grid positions f = (i + 1/2) / 128, i < 128, of
+ * |1 - Psi(k)^-1 sum_taps psi(x_j) exp(-2 pi i k x_j / N_d)|,
+ * x_j = f + q - 1 - j, and bound = prod_d (1 + e_d) - 1 (the three axes' factors multiply).  This
+ * is the quantity the paper's theorem on the NFFT error bounds for the Gaussian window (aliasing
+ * plus truncation), evaluated for the plan's own window, q, oversampled grid sizes and frequency
+ * ranges.  Host computation, no GPU needed (except sgl_eta_l1).
+ *
+ * sgl_nfft_error_bound: the bound for a plan that sgl_plan_create(B, ..., window, q, sigma)
+ *   would make.  Errors: SGL_ERR_ARG for parameters sgl_plan_create rejects.
+ * sgl_plan_error_bound: the same for an existing plan.
+ * sgl_choose_cutoff: the smallest q in [1, 16] whose bound is <= tol (error-driven choice of the
+ *   cutoff for a target accuracy per unit ||eta||_1); SGL_ERR_UNSUPPORTED if none reaches tol.
+ * sgl_eta_l1: ||eta||_1 of coef_dev (complex128 [Nc], device) for the plan's current points (rho
+ *   enters eta); synchronizes the stream.  bound * ||eta||_1 bounds this transform's error.
+ */
+sgl_status sgl_nfft_error_bound(int B, int window, int q, double sigma, double *bound);
+sgl_status sgl_plan_error_bound(const sgl_plan *plan, double *bound);
+sgl_status sgl_choose_cutoff(int B, int window, double sigma, double tol, int *q);
+sgl_status sgl_eta_l1(sgl_plan *plan, const double *coef_dev, double *l1);
+
+/*
  * Host-buffer variants (need SGL_FLAG_HOST_IO): copy the inputs from host memory
  * into the plan's staging buffers, run set_points + forward (or adjoint) on the
  * plan's stream, copy the result back and synchronize the stream before returning.

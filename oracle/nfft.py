@@ -104,3 +104,47 @@ def gauss_error_bound(d, sigma, q):
     b = (3 ** d - 1) / q ** (d / 2) * (math.sqrt((2 * sigma - 1) / (2 * sigma)) + math.sqrt(2 * sigma / (2 * sigma - 1)) / (2 * math.pi)) ** d
     e = math.exp(-q * math.pi * (1 - (1 + d / (2 * sigma - 1)) / (2 * sigma)))
     return (a + b) * e
+
+
+def fft_size(target):
+    """Smallest even 2-3-5-smooth integer >= target (the plan's oversampled grid sizes)."""
+    n = math.ceil(target - 1e-9)
+    n += n % 2
+    while True:
+        m = n
+        for f in (2, 3, 5):
+            while m % f == 0:
+                m //= f
+        if m == 1:
+            return n
+        n += 2
+
+
+def single_frequency_error(N, n, K, q, window, nfrac=128):
+    """max over |k| <= K and t = 2 pi (l0 + f) / N, f = (i + 1/2) / nfrac, of |e^{ikt} - s(t)|, where
+    s is the 1-D NFFT of Sect. 2 (steps 1-3) applied to the single coefficient omega_k = 1 on a grid
+    of N = sigma n points (sigma = N / n).  By translation invariance l0 = 0 suffices."""
+    sigma = N / n
+    ks = np.arange(-K, K + 1)
+    phit = window_fourier(ks, N, sigma, q, window) / (2 * math.pi)              # step 1: beta_k = 1 / phitilde_k
+    f = (np.arange(nfrac) + 0.5) / nfrac
+    t = 2 * math.pi * f / N
+    ls = np.arange(-q, q + 2)                                                    # every l with |N t / 2 pi - l| <= q
+    # step 2: alpha_l = N^{-1} beta_k e^{2 pi i k l / N};  step 3: s(t) = sum_l alpha_l phi(t - 2 pi l / N)
+    wts = window_value(t[:, None] - 2 * math.pi * ls[None, :] / N, N, sigma, q, window)           # [f, l]
+    ph = np.exp(2j * math.pi * ks[:, None] * ls[None, :] / N)                                     # [k, l]
+    s = (ph @ wts.T) / (N * phit[:, None])                                                        # [k, f]
+    exact = np.exp(1j * ks[:, None] * t[None, :])
+    return float(np.abs(exact - s).max())
+
+
+def sgl_nfft_bound(B, q, sigma, window):
+    """Error bound of the NFSGLFT per unit ||eta||_1: the three axes' single-frequency errors
+    combined as prod (1 + e_d) - 1 (|a b c - a' b' c'| <= prod (1 + e_d) - 1 for |a| = |b| = |c| = 1,
+    |a - a'| <= e_0, ...), on the axes n = (4B, 2B, 2B), |k| <= (2B - 2, B - 1, B - 1) of Sect. 6."""
+    n = (4 * B, 2 * B, 2 * B)
+    K = (2 * B - 2, B - 1, B - 1)
+    b = 1.0
+    for d in range(3):
+        b *= 1.0 + single_frequency_error(fft_size(sigma * n[d]), n[d], K[d], q, window)
+    return b - 1.0

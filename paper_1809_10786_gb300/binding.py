@@ -74,6 +74,11 @@ def load_library(build_if_missing=True):
                            ("sgl_inverse", [vp, vp, vp, ctypes.c_int, ctypes.c_double, ctypes.c_int, dp,
                                             ctypes.POINTER(ctypes.c_int)]),
                            ("sgl_midpoint_guess", [vp, vp, vp, vp]),
+                           ("sgl_nfft_error_bound", [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_double, dp]),
+                           ("sgl_plan_error_bound", [vp, dp]),
+                           ("sgl_choose_cutoff", [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
+                                                  ctypes.POINTER(ctypes.c_int)]),
+                           ("sgl_eta_l1", [vp, vp, dp]),
                            ("sgl_forward_grad_host", [vp, vp, i64, vp, vp, vp, vp]),
                            ("sgl_profile", [vp, dp, ctypes.POINTER(i64)]), ("sgl_sync", [vp]),
                            ("sgl_trig_coeffs_noalloc", [ctypes.c_int, vp, i64, vp, vp, vp])]:
@@ -107,6 +112,20 @@ def _check(st):
 
 def num_coeffs(B):
     return int(load_library().sgl_num_coeffs(int(B)))
+
+
+def nfft_error_bound(B, window=WIN_KB, q=8, sigma=2.0):
+    """sgl_nfft_error_bound: max |f - f~| <= bound * ||eta||_1 for a plan of these parameters."""
+    b = ctypes.c_double()
+    _check(load_library().sgl_nfft_error_bound(int(B), int(window), int(q), float(sigma), ctypes.byref(b)))
+    return b.value
+
+
+def choose_cutoff(B, tol, window=WIN_KB, sigma=2.0):
+    """sgl_choose_cutoff: the smallest q whose bound per unit ||eta||_1 is <= tol."""
+    q = ctypes.c_int()
+    _check(load_library().sgl_choose_cutoff(int(B), int(window), float(sigma), float(tol), ctypes.byref(q)))
+    return q.value
 
 
 def _stream_handle(device):
@@ -249,6 +268,20 @@ class Plan:
         _check(self.lib.sgl_inverse(self._h, ctypes.c_void_p(vals.data_ptr()), ctypes.c_void_p(coef.data_ptr()), int(iters),
                                     float(tol), m, ctypes.byref(res), ctypes.byref(done)))
         return coef, res.value, done.value
+
+    def error_bound(self):
+        """sgl_plan_error_bound: max |f - f~| <= error_bound() * eta_l1(coef)."""
+        b = ctypes.c_double()
+        _check(self.lib.sgl_plan_error_bound(self._h, ctypes.byref(b)))
+        return b.value
+
+    def eta_l1(self, coef):
+        """sgl_eta_l1: ||eta||_1 of the trigonometric coefficients of coef at the current points."""
+        coef = _dev_tensor(coef, torch.complex128, (self.Nc,), "coef", self.device)
+        v = ctypes.c_double()
+        self._stream()
+        _check(self.lib.sgl_eta_l1(self._h, ctypes.c_void_p(coef.data_ptr()), ctypes.byref(v)))
+        return v.value
 
     def midpoint_guess(self, vals, weights):
         """Lambda^H (weights * vals): the quadrature initial guess of the inverse transform."""

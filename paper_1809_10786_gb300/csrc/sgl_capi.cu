@@ -116,6 +116,65 @@ double window_hat(int window, double w, double q, double par) {
     return std::sqrt(2.0 * kPi * par) * std::exp(-0.5 * par * w * w);
 }
 
+// psi(x) of the kernels on the host, peak-normalized (psi(0) = 1), zero for |x| > q:
+// KB [sinh(b s)/s] / [sinh(b q)/q], s = sqrt(q^2 - x^2); Gauss exp(-x^2 / (2 lambda))
+double window_value_host(int window, double x, double q, double par) {
+    if (std::fabs(x) > q) return 0.0;
+    if (window == SGL_WIN_KB) {
+        const double s = std::sqrt(q * q - x * x);
+        const double ratio = (s > 1e-12) ? -std::expm1(-2.0 * par * s) / s : 2.0 * par;
+        return std::exp(par * (s - q)) * ratio * q / (-std::expm1(-2.0 * par * q));
+    }
+    return std::exp(-x * x / (2.0 * par));
+}
+
+// largest error of the 1-D windowed interpolation of a single frequency |k| <= K on a grid of N
+// points (n frequencies before oversampling), over the fractional positions (i + 1/2) / 128
+double axis_error(int window, int N, int n, int K, int q) {
+    const double sig = (double)N / n;
+    const double par = (window == SGL_WIN_KB) ? kPi * (2.0 - 1.0 / sig) : sig * q / ((2.0 * sig - 1.0) * kPi);
+    constexpr int kFrac = 128;
+    double emax = 0.0;
+    std::vector<double> psi((size_t)kFrac * 2 * q);
+    for (int i = 0; i < kFrac; ++i)
+        for (int j = 0; j < 2 * q; ++j) psi[(size_t)i * 2 * q + j] = window_value_host(window, (i + 0.5) / kFrac + q - 1 - j, q, par);
+    for (int k = -K; k <= K; ++k) {
+        const double w = 2.0 * kPi * k / N;
+        const double ph = window_hat(window, w, (double)q, par);
+        for (int i = 0; i < kFrac; ++i) {
+            double re = 0.0, im = 0.0;
+            for (int j = 0; j < 2 * q; ++j) {
+                const double x = (i + 0.5) / kFrac + q - 1 - j, v = psi[(size_t)i * 2 * q + j];
+                re += v * std::cos(w * x);
+                im -= v * std::sin(w * x);
+            }
+            emax = std::max(emax, std::hypot(1.0 - re / ph, im / ph));
+        }
+    }
+    return emax;
+}
+
+// sum |eta_k| over n complex values into *acc (block sums, then one atomic add per block)
+__global__ void __launch_bounds__(256) k_abs_sum(const double2 *__restrict__ x, int64_t n, double *__restrict__ acc) {
+    __shared__ double ws[8];
+    double s = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        s += hypot(x[i].x, x[i].y);
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < 8; ++w) s += ws[w];
+        atomicAdd(acc, s);
+    }
+}
+
+double error_bound_of(int window, const int N[3], const int n[3], const int K[3], int q) {
+    double b = 1.0;
+    for (int d = 0; d < 3; ++d) b *= 1.0 + axis_error(window, N[d], n[d], K[d], q);
+    return b - 1.0;
+}
+
 // Normalized associated Legendre values Pbar_lm(x) = Q_lm P_lm(x) for 0 <= m <= l < B
 // (Condon-Shortley phase included), out[l * B + m], by the standard stable recurrences
 //   Pbar_mm = -sqrt((2m+1)/(2m)) sin Pbar_{m-1,m-1},  Pbar_{m+1,m} = sqrt(2m+3) x Pbar_mm,
@@ -380,6 +439,7 @@ sgl_status plan_create_impl(sgl_plan **out, int B, int64_t M_max, int precision,
     ALLOC(b.work[1], (size_t)work_list_cap(Mc, p->bins.nsuper, spread_chunk(precision)));
     ALLOC(b.work_len, 2);
     ALLOC(b.df_max, 2);
+    ALLOC(b.scalar, 1);
     if (flags & SGL_FLAG_HOST_IO) {
         ALLOC(b.io_xyz, 3 * Mc);
         ALLOC(b.io_coef, (size_t)(2 * p->Nc));
@@ -725,6 +785,64 @@ sgl_status sgl_forward_grad_host(sgl_plan *plan, const double *xyz_host, int64_t
         SGL_CUDA_TRY(cudaMemcpyAsync(vals_host, plan->b.io_out, sizeof(double2) * M, cudaMemcpyDeviceToHost, st));
         SGL_CUDA_TRY(cudaMemcpyAsync(gxyz_host, plan->b.io_grad, sizeof(double) * 3 * M, cudaMemcpyDeviceToHost, st));
     }
+    return sgl_sync(plan);
+}
+
+sgl_status sgl_nfft_error_bound(int B, int window, int q, double sigma, double *bound) {
+    if (!bound) return set_error(SGL_ERR_ARG, "bound must be non-NULL");
+    if (B < 1 || B > 128 || q < 1 || q > kMaxQ || !(sigma >= 1.5 && sigma <= 4.0) ||
+        (window != SGL_WIN_KB && window != SGL_WIN_GAUSS))
+        return set_error(SGL_ERR_ARG, "invalid B, window, q or sigma");
+    const int n[3] = {4 * B, 2 * B, 2 * B}, K[3] = {2 * B - 2, B - 1, B - 1};
+    int N[3];
+    for (int d = 0; d < 3; ++d) {
+        N[d] = next_fft_size(sigma * n[d]);
+        if (q >= N[d]) return set_error(SGL_ERR_ARG, "q must be smaller than every oversampled grid size");
+    }
+    *bound = error_bound_of(window, N, n, K, q);
+    return ok();
+}
+
+sgl_status sgl_plan_error_bound(const sgl_plan *plan, double *bound) {
+    if (sgl_status s = check_plan(plan)) return s;
+    if (!bound) return set_error(SGL_ERR_ARG, "bound must be non-NULL");
+    int N[3], n[3], K[3];
+    for (int d = 0; d < 3; ++d) { N[d] = plan->ax[d].N; n[d] = plan->ax[d].n; K[d] = plan->ax[d].K; }
+    *bound = error_bound_of(plan->window, N, n, K, plan->q);
+    return ok();
+}
+
+sgl_status sgl_choose_cutoff(int B, int window, double sigma, double tol, int *q) {
+    if (!q) return set_error(SGL_ERR_ARG, "q must be non-NULL");
+    if (!(tol > 0.0)) return set_error(SGL_ERR_ARG, "tol must be positive");
+    for (int qq = 1; qq <= kMaxQ; ++qq) {
+        double b = 0.0;
+        if (sgl_status s = sgl_nfft_error_bound(B, window, qq, sigma, &b)) return s;
+        if (b <= tol) {
+            *q = qq;
+            return ok();
+        }
+    }
+    return set_error(SGL_ERR_UNSUPPORTED, "no cutoff q <= 16 reaches the requested bound");
+}
+
+sgl_status sgl_eta_l1(sgl_plan *plan, const double *coef_dev, double *l1) {
+    if (sgl_status s = check_plan(plan)) return s;
+    if (!plan->points_set) return set_error(SGL_ERR_STATE, "sgl_set_points has not been called");
+    if (!coef_dev || !aligned8(coef_dev) || !l1) return set_error(SGL_ERR_ARG, "coef must be an 8-byte aligned device pointer, l1 non-NULL");
+    if (sgl_status s = coef_to_zeta(plan, coef_dev)) return s;
+    // the full eta array, (4B-3) x (2B-1) x (2B-1) complex128, in the FFT work buffer B (it holds
+    // the adjoint's eta' of the same size)
+    const int64_t n = (int64_t)(4 * plan->B - 3) * (2 * plan->B - 1) * (2 * plan->B - 1);
+    double2 *eta = (double2 *)plan->b.bufB;
+    if ((size_t)n * sizeof(double2) > plan->b.bufB_bytes) return set_error(SGL_ERR_STATE, "work buffer too small for eta");
+    if (sgl_status s = launch_status(launch_trig_export(plan, eta), "trig export")) return s;
+    SGL_CUDA_TRY(cudaMemsetAsync(plan->b.scalar, 0, sizeof(double), plan->stream));
+    const int blocks = (int)std::min<int64_t>((n + 255) / 256, 4 * 152);
+    k_abs_sum<<<blocks, 256, 0, plan->stream>>>(eta, n, plan->b.scalar);
+    plan->launches += 1;
+    SGL_CUDA_TRY(cudaGetLastError());
+    SGL_CUDA_TRY(cudaMemcpyAsync(l1, plan->b.scalar, sizeof(double), cudaMemcpyDeviceToHost, plan->stream));
     return sgl_sync(plan);
 }
 

@@ -107,6 +107,7 @@ struct Buffers {
     int4 *work[2];             // work lists (see kTcPass): tensor-core passes, spreading chunks
     int *work_len;             // [2] entries in each list (written on the device)
     unsigned long long *df_max;// [2] FP64 plans: bits of max |grid| and max |values| (scales of the double-float passes)
+    double *scalar;            // [1] device accumulator of small reductions (sgl_eta_l1)
     // host-IO staging
     double *io_xyz, *io_coef, *io_vals, *io_grad, *io_out;
     // tensor-core interpolation (FP32-mixed): grid as planes Re, Im [rows0][rows1][pitch] with an azimuthal halo

@@ -1,0 +1,95 @@
+"""Error-driven choice of the NFFT cutoff (CPU; the bound is host code).
+
+The only approximating step of the transform is the final NFFT (Sect. 7, error estimate), so
+max |f - f~| <= bound * ||eta||_1.  The library computes the bound from its own window, cutoff and
+grid; the oracle computes the same definition with its independent window pair and NFFT steps.
+Pins: agreement with the oracle; the paper's closed-form Gaussian bound (Thm. on the NFFT error)
+is never below it; on the oracle's own 3-D NFFT the measured errors stay below it.
+"""
+import ctypes
+import math
+
+import numpy as np
+import pytest
+
+from oracle import nfft
+from paper_1809_10786_gb300 import binding
+
+KB, GAUSS = 0, 1
+NAMES = {KB: "kb", GAUSS: "gauss"}
+
+
+@pytest.fixture(scope="module")
+def lib():
+    return binding.load_library()
+
+
+def c_bound(lib, B, window, q, sigma):
+    b = ctypes.c_double(-1.0)
+    assert lib.sgl_nfft_error_bound(B, window, q, ctypes.c_double(sigma), ctypes.byref(b)) == 0
+    return b.value
+
+
+@pytest.mark.parametrize("B,window,q,sigma", [(4, KB, 2, 2.0), (8, KB, 4, 2.0), (6, GAUSS, 3, 2.0),
+                                              (5, KB, 3, 1.5), (8, GAUSS, 6, 2.5), (12, KB, 5, 3.0)])
+def test_bound_equals_the_oracles_definition(lib, B, window, q, sigma):
+    ref = nfft.sgl_nfft_bound(B, q, sigma, NAMES[window])
+    assert c_bound(lib, B, window, q, sigma) == pytest.approx(ref, rel=1e-6)
+
+
+@pytest.mark.parametrize("B", [4, 8])
+def test_bound_reaches_rounding_level_at_large_cutoff(lib, B):
+    # KB at q = 8: both sides see only rounding (the window error is below 1e-13)
+    assert c_bound(lib, B, KB, 8, 2.0) <= 1e-12
+    assert nfft.sgl_nfft_bound(B, 8, 2.0, "kb") <= 1e-12
+
+
+@pytest.mark.parametrize("sigma", [2.0, 3.0])
+@pytest.mark.parametrize("q", [2, 4, 6, 8, 10])
+def test_gaussian_bound_below_the_papers_closed_form(lib, q, sigma):
+    # the theorem bounds the error of every coefficient vector by C ||w||_1, with C in closed form
+    assert c_bound(lib, 8, GAUSS, q, sigma) <= nfft.gauss_error_bound(3, sigma, q)
+
+
+def test_bound_holds_for_the_oracle_nfft():
+    # a random trigonometric polynomial on the grid sizes of the oracle's NFFT, measured error
+    # against the direct sum: below bound * ||omega||_1 (bound from the same single-frequency errors)
+    rng = np.random.default_rng(5)
+    n, sigma = (8, 6, 6), 2.0
+    for window, q in (("kb", 3), ("gauss", 4), ("kb", 5)):
+        om = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+        t = rng.uniform(0, 2 * math.pi, (300, 3))
+        approx = nfft.nfft(om, t, sigma, q, window)
+        ks = [np.arange(nj) - nj // 2 for nj in n]
+        exact = np.einsum("abc,ia,ib,ic->i", om, np.exp(1j * t[:, :1] * ks[0]), np.exp(1j * t[:, 1:2] * ks[1]),
+                          np.exp(1j * t[:, 2:] * ks[2]))
+        b = 1.0
+        for d in range(3):
+            b *= 1.0 + nfft.single_frequency_error(int(round(sigma * n[d])), n[d], n[d] // 2, q, window)
+        assert np.abs(approx - exact).max() <= (b - 1.0) * np.abs(om).sum()
+
+
+def test_bound_decreases_with_the_cutoff_and_kb_beats_gauss(lib):
+    kb = [c_bound(lib, 16, KB, q, 2.0) for q in range(2, 8)]
+    ga = [c_bound(lib, 16, GAUSS, q, 2.0) for q in range(2, 8)]
+    assert all(b < a for a, b in zip(kb, kb[1:]))
+    assert all(b < a for a, b in zip(ga, ga[1:]))
+    assert all(k < g for k, g in zip(kb, ga))
+
+
+@pytest.mark.parametrize("tol", [1e-3, 1e-6, 1e-9, 1e-12])
+def test_choose_cutoff_is_the_smallest_sufficient_q(lib, tol):
+    q = ctypes.c_int(0)
+    assert lib.sgl_choose_cutoff(32, KB, ctypes.c_double(2.0), ctypes.c_double(tol), ctypes.byref(q)) == 0
+    assert c_bound(lib, 32, KB, q.value, 2.0) <= tol
+    if q.value > 1:
+        assert c_bound(lib, 32, KB, q.value - 1, 2.0) > tol
+
+
+def test_argument_errors(lib):
+    b, q = ctypes.c_double(), ctypes.c_int()
+    assert lib.sgl_nfft_error_bound(0, KB, 4, ctypes.c_double(2.0), ctypes.byref(b)) == 1
+    assert lib.sgl_nfft_error_bound(8, 7, 4, ctypes.c_double(2.0), ctypes.byref(b)) == 1
+    assert lib.sgl_nfft_error_bound(8, KB, 17, ctypes.c_double(2.0), ctypes.byref(b)) == 1
+    assert lib.sgl_choose_cutoff(8, KB, ctypes.c_double(2.0), ctypes.c_double(0.0), ctypes.byref(q)) == 1
+    assert lib.sgl_choose_cutoff(8, GAUSS, ctypes.c_double(2.0), ctypes.c_double(1e-300), ctypes.byref(q)) == 6
