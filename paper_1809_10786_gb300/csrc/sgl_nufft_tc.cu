@@ -89,7 +89,7 @@ struct TcSmem {
     float lanes[kPM][kLanes + 1];                            // prep: one point's axis-2 weights placed on the 32 lanes
     float xch[2][C::NXCH][kPM];                              // reduction: second warp's partial sums per point
     uint64_t tma_full[C::NS], conv_full[C::NS], empty[C::NS];
-    uint64_t tfull[2], tempty[2], afull[2], aempty[2], tabfull[2], xfull[2], xfree[2], done;
+    uint64_t tfull[2], tempty[2], afull[2], aempty[2], tabfull[2], tabfree[2], xfull[2], xfree[2], done;
     uint32_t tmem_base;
     int abort;
 };
@@ -308,8 +308,9 @@ k_nufft_tc(const __grid_constant__ CUtensorMap tmap, NGeom g, TcArgs args) {
             mbar_init(smem_addr(&sm.tfull[i]), 1);
             mbar_init(smem_addr(&sm.tempty[i]), Cfg::NRED);
             mbar_init(smem_addr(&sm.afull[i]), 4);
-            mbar_init(smem_addr(&sm.aempty[i]), Cfg::NRED);
+            mbar_init(smem_addr(&sm.aempty[i]), 1);              // operand buffer read by its last MMA (commit)
             mbar_init(smem_addr(&sm.tabfull[i]), 4);
+            mbar_init(smem_addr(&sm.tabfree[i]), Cfg::NRED);     // tables read by every reduction warp
             mbar_init(smem_addr(&sm.xfull[i]), 4);
             mbar_init(smem_addr(&sm.xfree[i]), 4);
         }
@@ -426,6 +427,9 @@ k_nufft_tc(const __grid_constant__ CUtensorMap tmap, NGeom g, TcArgs args) {
                     mma_commit(smem_addr(&sm.empty[st]));
                     mma_commit(smem_addr(&sm.tfull[buf]));
                 }
+                // the operand buffer is free once this pass's products have run (the window tables
+                // have their own buffers, freed by the reduction warps)
+                if (ok) mma_commit(smem_addr(&sm.aempty[abuf]));
                 ++k;
             }
             if (!ok) *abort_flag = 1;
@@ -453,7 +457,10 @@ k_nufft_tc(const __grid_constant__ CUtensorMap tmap, NGeom g, TcArgs args) {
             int n = 0;
             while (ok && next_pass(it, args)) {
                 const int abuf = n % Cfg::ABUF, use = n / Cfg::ABUF;
+                const int tbuf = n & 1, tuse = n >> 1;        // window tables: two buffers in shared memory
                 if (use >= 1) ok = __all_sync(0xffffffffu, mbar_wait(smem_addr(&sm.aempty[abuf]), (use + 1) & 1) && !*abort_flag);
+                if (ok && tuse >= 1)
+                    ok = __all_sync(0xffffffffu, mbar_wait(smem_addr(&sm.tabfree[tbuf]), (tuse + 1) & 1) && !*abort_flag);
                 if (!ok) break;
                 tc_fence_after();
                 const int idx = it.pass * kPM + p;
@@ -491,23 +498,23 @@ k_nufft_tc(const __grid_constant__ CUtensorMap tmap, NGeom g, TcArgs args) {
                     store_split_tmem(ta_ + 64, w);
 #pragma unroll
                     for (int tb = 0; tb < kTB1Max; ++tb) {
-                        sm.w1tab[abuf][0][tb][p] = 0.f;
-                        sm.w1tab[abuf][GRAD ? 1 : 0][tb][p] = 0.f;
+                        sm.w1tab[tbuf][0][tb][p] = 0.f;
+                        sm.w1tab[tbuf][GRAD ? 1 : 0][tb][p] = 0.f;
                     }
 #pragma unroll
                     for (int rel = 0; rel < 16; ++rel) {
                         const float2 v = win_both_fast<WIN>(pt.y + (float)(q - 1 - rel), qf, par1, nrm1, edge1);
                         if (live && rel < q2) {
-                            sm.w1tab[abuf][0][d1 + rel][p] = v.x;
-                            sm.w1tab[abuf][GRAD ? 1 : 0][d1 + rel][p] = v.y;
+                            sm.w1tab[tbuf][0][d1 + rel][p] = v.x;
+                            sm.w1tab[tbuf][GRAD ? 1 : 0][d1 + rel][p] = v.y;
                         }
                     }
 #pragma unroll
                     for (int j = 0; j < 16; ++j) {
                         const float2 v = win_both_fast<WIN>(pt.x + (float)(q - 1 - j), qf, par0, nrm0, edge0);
                         if (j < q2) {
-                            sm.w0tab[abuf][0][j][p] = v.x;
-                            sm.w0tab[abuf][GRAD ? 1 : 0][j][p] = v.y;
+                            sm.w0tab[tbuf][0][j][p] = v.x;
+                            sm.w0tab[tbuf][GRAD ? 1 : 0][j][p] = v.y;
                         }
                     }
                 } else {
@@ -522,16 +529,16 @@ k_nufft_tc(const __grid_constant__ CUtensorMap tmap, NGeom g, TcArgs args) {
                     for (int k = 0; k < kLanes; ++k) w[k] = row[k];
                     store_split_tmem(ta_, w);
 #pragma unroll
-                    for (int tb = 0; tb < kTB1Max; ++tb) sm.w1tab[abuf][0][tb][p] = 0.f;
+                    for (int tb = 0; tb < kTB1Max; ++tb) sm.w1tab[tbuf][0][tb][p] = 0.f;
 #pragma unroll
                     for (int rel = 0; rel < 16; ++rel) {
                         const float v = win_fast<WIN>(pt.y + (float)(q - 1 - rel), qf, par1, nrm1, edge1);
-                        if (live && rel < q2) sm.w1tab[abuf][0][d1 + rel][p] = v;
+                        if (live && rel < q2) sm.w1tab[tbuf][0][d1 + rel][p] = v;
                     }
 #pragma unroll
                     for (int j = 0; j < 16; ++j) {
                         const float v = win_fast<WIN>(pt.x + (float)(q - 1 - j), qf, par0, nrm0, edge0);
-                        if (j < q2) sm.w0tab[abuf][0][j][p] = v;
+                        if (j < q2) sm.w0tab[tbuf][0][j][p] = v;
                     }
                 }
                 tmem_wait_st();
@@ -539,7 +546,7 @@ k_nufft_tc(const __grid_constant__ CUtensorMap tmap, NGeom g, TcArgs args) {
                 __syncwarp();
                 if (lane == 0) {
                     mbar_arrive(smem_addr(&sm.afull[abuf]));
-                    mbar_arrive(smem_addr(&sm.tabfull[abuf]));
+                    mbar_arrive(smem_addr(&sm.tabfull[tbuf]));
                 }
                 ++n;
             }
@@ -550,8 +557,8 @@ k_nufft_tc(const __grid_constant__ CUtensorMap tmap, NGeom g, TcArgs args) {
             const int half = (warp - Cfg::WRED) >> 2;     // this warp takes slabs z = half, half + 2, ... of a group
             int s = 0, n = 0;
             while (ok && next_pass(it, args)) {
-                const int abuf = n % Cfg::ABUF, use = n / Cfg::ABUF;
-                ok = __all_sync(0xffffffffu, mbar_wait(smem_addr(&sm.tabfull[abuf]), use & 1) && !*abort_flag);
+                const int tbuf = n & 1, tuse = n >> 1;
+                ok = __all_sync(0xffffffffu, mbar_wait(smem_addr(&sm.tabfull[tbuf]), tuse & 1) && !*abort_flag);
                 if (!ok) break;
                 const int idx = it.pass * kPM + p;
                 const bool live = idx < it.np;
@@ -564,8 +571,8 @@ k_nufft_tc(const __grid_constant__ CUtensorMap tmap, NGeom g, TcArgs args) {
                 float w1[kTB1Max], e1[GRAD ? kTB1Max : 1];
 #pragma unroll
                 for (int tb = 0; tb < kTB1Max; ++tb) {
-                    w1[tb] = sm.w1tab[abuf][0][tb][p];
-                    if constexpr (GRAD) e1[tb] = sm.w1tab[abuf][GRAD ? 1 : 0][tb][p];
+                    w1[tb] = sm.w1tab[tbuf][0][tb][p];
+                    if constexpr (GRAD) e1[tb] = sm.w1tab[tbuf][GRAD ? 1 : 0][tb][p];
                 }
                 float2 acc = make_float2(0.f, 0.f), acc1 = acc, acc2 = acc, accv = acc;
                 for (int gi = 0; gi < NG; ++gi, ++s) {
@@ -620,9 +627,9 @@ k_nufft_tc(const __grid_constant__ CUtensorMap tmap, NGeom g, TcArgs args) {
                             }
                         }
                         if (!on) continue;
-                        const float w0 = sm.w0tab[abuf][0][j][p];
+                        const float w0 = sm.w0tab[tbuf][0][j][p];
                         if constexpr (GRAD) {
-                            const float e0 = sm.w0tab[abuf][GRAD ? 1 : 0][j][p];
+                            const float e0 = sm.w0tab[tbuf][GRAD ? 1 : 0][j][p];
                             acc = ffma2(make_float2(e0, e0), r, acc);      // ds/du0
                             acc1 = ffma2(make_float2(w0, w0), rs, acc1);   // ds/du1
                             acc2 = ffma2(make_float2(w0, w0), rt, acc2);   // ds/du2
@@ -636,10 +643,9 @@ k_nufft_tc(const __grid_constant__ CUtensorMap tmap, NGeom g, TcArgs args) {
                     if (lane == 0) mbar_arrive(smem_addr(&sm.tempty[buf]));
                 }
                 if (!ok) break;
-                // every product of this pass is done (its last accumulator was read): operand and
-                // tables buffer free for the next pass that uses it
+                // this pass's window tables are no longer read
                 __syncwarp();
-                if (lane == 0) mbar_arrive(smem_addr(&sm.aempty[abuf]));
+                if (lane == 0) mbar_arrive(smem_addr(&sm.tabfree[tbuf]));
                 // partner warps (same lane quadrant) combine their partial sums; the half-0 warp writes
                 const int xs = n & 1;
                 if (half == 1) {
