@@ -156,16 +156,26 @@ __global__ void __launch_bounds__(256) k_fft_pass(FftPass ps, int TB, int lgTB, 
     const int nlines = (int)min((int64_t)TB, ps.nb_inner - inner0);
     const int tid = threadIdx.x, NT = blockDim.x;
 
-    // ---- load: position pos of a line holds input element e = pos - in_first (mod N), zero if e >= L_in
+    // ---- load: position pos of a line holds input element e = pos - in_first (mod N), zero if e >= L_in.
+    // Items j = tid + NT r of the TB x N tile (element-contiguous inputs: line j / N, position j % N;
+    // strided inputs: line j % TB, position j / TB, so that a warp reads consecutive lines), loaded
+    // in batches of kBatch independent loads before they go to shared memory.
     const bool in_elem_fast = (MODE == LOAD_STRIDED) && (ps.in_se == 1);
-    const int bl_fast = tid & (TB - 1), pos_step = NT >> lgTB;
-    for (int it = 0; it < (in_elem_fast ? TB : 1); ++it) {
-        for (int k = in_elem_fast ? tid : (tid >> lgTB); k < N; k += in_elem_fast ? NT : pos_step) {
-            const int bl = in_elem_fast ? it : bl_fast;
-            const int pos = k;
+    const int total = TB * N;
+    constexpr int kBatch = 8;
+    for (int j0 = 0; j0 < total; j0 += NT * kBatch) {
+        C2<T> v[kBatch];
+        int dst[kBatch];
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u) {
+            const int j = j0 + tid + NT * u;
+            int bl, pos;
+            if (in_elem_fast) { bl = j / N; pos = j - bl * N; }
+            else { bl = j & (TB - 1); pos = j >> lgTB; }
+            dst[u] = (j < total) ? bl * LS + pos : -1;
             const int e = wrapN(pos - ps.in_first, N);
-            C2<T> v = mk<T>((T)0, (T)0);
-            if (bl < nlines && e < ps.L_in) {
+            v[u] = mk<T>((T)0, (T)0);
+            if (j < total && bl < nlines && e < ps.L_in) {
                 const int64_t inner = inner0 + bl;
                 double2 d;
                 if (MODE == LOAD_ZETA) {
@@ -179,8 +189,7 @@ __global__ void __launch_bounds__(256) k_fft_pass(FftPass ps, int TB, int lgTB, 
                 } else if (sizeof(InC) == sizeof(C2<T>) && (scale_on_output || (!ps.elem_scale && !ps.line_scale))) {
                     // same precision in and out, no factor: no conversion
                     const InC x = in[outer * ps.in_so + inner * ps.in_si + (int64_t)e * ps.in_se];
-                    v = mk<T>((T)x.x, (T)x.y);
-                    buf[bl * LS + pos] = v;
+                    v[u] = mk<T>((T)x.x, (T)x.y);
                     continue;
                 } else {
                     d = to_d2(in[outer * ps.in_so + inner * ps.in_si + (int64_t)e * ps.in_se]);
@@ -191,10 +200,12 @@ __global__ void __launch_bounds__(256) k_fft_pass(FftPass ps, int TB, int lgTB, 
                     if (ps.line_scale) f *= ps.line_scale[outer * ps.nb_inner + inner];
                     d.x *= f; d.y *= f;
                 }
-                v = mk<T>((T)d.x, (T)d.y);
+                v[u] = mk<T>((T)d.x, (T)d.y);
             }
-            buf[bl * LS + pos] = v;
         }
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u)
+            if (dst[u] >= 0) buf[dst[u]] = v[u];
     }
     __syncthreads();
 
@@ -214,6 +225,7 @@ __global__ void __launch_bounds__(256) k_fft_pass(FftPass ps, int TB, int lgTB, 
 
     // ---- store the output window (digit-reversed slots), optional scale on output
     const bool out_elem_fast = (ps.out_se == 1);
+    const int bl_fast = tid & (TB - 1), pos_step = NT >> lgTB;
     for (int it = 0; it < (out_elem_fast ? TB : 1); ++it) {
         for (int k = out_elem_fast ? tid : (tid >> lgTB); k < ps.L_out; k += out_elem_fast ? NT : pos_step) {
             const int bl = out_elem_fast ? it : bl_fast;
