@@ -246,6 +246,8 @@ sgl_status sgl_eta_l1(sgl_plan *plan, const double *coef_dev, double *l1);
  * into the plan's staging buffers, run set_points + forward (or adjoint) on the
  * plan's stream, copy the result back and synchronize the stream before returning.
  * xyz_host [M][3] double; coef_host complex128 [Nc]; vals_host complex128 [M].
+ * xyz_host NULL keeps the points of the previous call (no copy, no re-binning); M must then
+ * equal their number (SGL_ERR_ARG otherwise, or if no points are set).
  */
 sgl_status sgl_forward_host(sgl_plan *plan, const double *xyz_host, int64_t M,
                             const double *coef_host, double *vals_host);

@@ -302,25 +302,36 @@ class Plan:
         _check(self.lib.sgl_trig_coeffs(self._h, ctypes.c_void_p(coef.data_ptr()), ctypes.c_void_p(out.data_ptr())))
         return out
 
+    # Host-buffer calls: numpy or pinned-CPU-tensor buffers, copies inside the call, synchronous.
+    # xyz_host None keeps the points of the previous call (no copy, no re-binning).
+    def _pts(self, xyz_host):
+        if xyz_host is None:
+            return None, self.M
+        return _host_ptr(xyz_host), int(xyz_host.shape[0])
+
     def forward_host(self, xyz_host, coef_host, vals_host):
-        """numpy or pinned-CPU-tensor buffers; copies inside the call, synchronous."""
-        _check(self.lib.sgl_forward_host(self._h, _host_ptr(xyz_host), int(xyz_host.shape[0]),
-                                         _host_ptr(coef_host), _host_ptr(vals_host)))
+        px, m = self._pts(xyz_host)
+        _check(self.lib.sgl_forward_host(self._h, px, m, _host_ptr(coef_host), _host_ptr(vals_host)))
+        self.M = m
         return vals_host
 
     def adjoint_host(self, xyz_host, vals_host, coef_host):
-        _check(self.lib.sgl_adjoint_host(self._h, _host_ptr(xyz_host), int(xyz_host.shape[0]),
-                                         _host_ptr(vals_host), _host_ptr(coef_host)))
+        px, m = self._pts(xyz_host)
+        _check(self.lib.sgl_adjoint_host(self._h, px, m, _host_ptr(vals_host), _host_ptr(coef_host)))
+        self.M = m
         return coef_host
 
     def grad_points_host(self, xyz_host, coef_host, gout_host, gxyz_host):
-        _check(self.lib.sgl_grad_points_host(self._h, _host_ptr(xyz_host), int(xyz_host.shape[0]), _host_ptr(coef_host),
-                                             _host_ptr(gout_host), _host_ptr(gxyz_host)))
+        px, m = self._pts(xyz_host)
+        _check(self.lib.sgl_grad_points_host(self._h, px, m, _host_ptr(coef_host), _host_ptr(gout_host), _host_ptr(gxyz_host)))
+        self.M = m
         return gxyz_host
 
     def forward_grad_host(self, xyz_host, coef_host, gout_host, vals_host, gxyz_host):
-        _check(self.lib.sgl_forward_grad_host(self._h, _host_ptr(xyz_host), int(xyz_host.shape[0]), _host_ptr(coef_host),
-                                              _host_ptr(gout_host), _host_ptr(vals_host), _host_ptr(gxyz_host)))
+        px, m = self._pts(xyz_host)
+        _check(self.lib.sgl_forward_grad_host(self._h, px, m, _host_ptr(coef_host), _host_ptr(gout_host), _host_ptr(vals_host),
+                                              _host_ptr(gxyz_host)))
+        self.M = m
         return vals_host, gxyz_host
 
     def sync(self):

@@ -694,15 +694,32 @@ sgl_status sgl_trig_coeffs(sgl_plan *plan, const double *coef_dev, double *eta_d
     return launch_status(launch_trig_export(plan, (double2 *)eta_dev), "trig export");
 }
 
+}  // extern "C"
+
+namespace {
+// host variants: copy the points and bin them, or (xyz_host NULL) keep the plan's current points
+sgl_status host_points(sgl_plan *plan, const double *xyz_host, int64_t M) {
+    if (!xyz_host) {
+        if (!plan->points_set || M != plan->M)
+            return set_error(SGL_ERR_ARG, "xyz_host NULL reuses the current points: they must be set and M must equal their number");
+        return SGL_OK;
+    }
+    if (M > 0)
+        SGL_CUDA_TRY(cudaMemcpyAsync(plan->b.io_xyz, xyz_host, sizeof(double) * 3 * M, cudaMemcpyHostToDevice, plan->stream));
+    return sgl_set_points(plan, plan->b.io_xyz, M);
+}
+}  // namespace
+
+extern "C" {
+
 sgl_status sgl_forward_host(sgl_plan *plan, const double *xyz_host, int64_t M, const double *coef_host, double *vals_host) {
     if (sgl_status s = check_plan(plan)) return s;
     if (!(plan->flags & SGL_FLAG_HOST_IO)) return set_error(SGL_ERR_STATE, "plan was created without SGL_FLAG_HOST_IO");
     if (M < 0 || M > plan->M_max) return set_error(SGL_ERR_ARG, "M must be in [0, M_max]");
-    if (!coef_host || (M > 0 && (!xyz_host || !vals_host))) return set_error(SGL_ERR_ARG, "NULL host buffer");
+    if (!coef_host || (M > 0 && !vals_host)) return set_error(SGL_ERR_ARG, "NULL host buffer");
     cudaStream_t st = plan->stream;
-    if (M > 0) SGL_CUDA_TRY(cudaMemcpyAsync(plan->b.io_xyz, xyz_host, sizeof(double) * 3 * M, cudaMemcpyHostToDevice, st));
+    if (sgl_status s = host_points(plan, xyz_host, M)) return s;
     SGL_CUDA_TRY(cudaMemcpyAsync(plan->b.io_coef, coef_host, sizeof(double2) * plan->Nc, cudaMemcpyHostToDevice, st));
-    if (sgl_status s = sgl_set_points(plan, plan->b.io_xyz, M)) return s;
     if (sgl_status s = sgl_forward(plan, plan->b.io_coef, plan->b.io_vals)) return s;
     if (M > 0) SGL_CUDA_TRY(cudaMemcpyAsync(vals_host, plan->b.io_vals, sizeof(double2) * M, cudaMemcpyDeviceToHost, st));
     return sgl_sync(plan);
@@ -712,13 +729,10 @@ sgl_status sgl_adjoint_host(sgl_plan *plan, const double *xyz_host, int64_t M, c
     if (sgl_status s = check_plan(plan)) return s;
     if (!(plan->flags & SGL_FLAG_HOST_IO)) return set_error(SGL_ERR_STATE, "plan was created without SGL_FLAG_HOST_IO");
     if (M < 0 || M > plan->M_max) return set_error(SGL_ERR_ARG, "M must be in [0, M_max]");
-    if (!coef_host || (M > 0 && (!xyz_host || !vals_host))) return set_error(SGL_ERR_ARG, "NULL host buffer");
+    if (!coef_host || (M > 0 && !vals_host)) return set_error(SGL_ERR_ARG, "NULL host buffer");
     cudaStream_t st = plan->stream;
-    if (M > 0) {
-        SGL_CUDA_TRY(cudaMemcpyAsync(plan->b.io_xyz, xyz_host, sizeof(double) * 3 * M, cudaMemcpyHostToDevice, st));
-        SGL_CUDA_TRY(cudaMemcpyAsync(plan->b.io_vals, vals_host, sizeof(double2) * M, cudaMemcpyHostToDevice, st));
-    }
-    if (sgl_status s = sgl_set_points(plan, plan->b.io_xyz, M)) return s;
+    if (sgl_status s = host_points(plan, xyz_host, M)) return s;
+    if (M > 0) SGL_CUDA_TRY(cudaMemcpyAsync(plan->b.io_vals, vals_host, sizeof(double2) * M, cudaMemcpyHostToDevice, st));
     if (sgl_status s = sgl_adjoint(plan, plan->b.io_vals, plan->b.io_coef)) return s;
     SGL_CUDA_TRY(cudaMemcpyAsync(coef_host, plan->b.io_coef, sizeof(double2) * plan->Nc, cudaMemcpyDeviceToHost, st));
     return sgl_sync(plan);
@@ -754,14 +768,11 @@ sgl_status sgl_grad_points_host(sgl_plan *plan, const double *xyz_host, int64_t 
     if (sgl_status s = check_plan(plan)) return s;
     if (!(plan->flags & SGL_FLAG_HOST_IO)) return set_error(SGL_ERR_STATE, "plan was created without SGL_FLAG_HOST_IO");
     if (M < 0 || M > plan->M_max) return set_error(SGL_ERR_ARG, "M must be in [0, M_max]");
-    if (!coef_host || (M > 0 && (!xyz_host || !gout_host || !gxyz_host))) return set_error(SGL_ERR_ARG, "NULL host buffer");
+    if (!coef_host || (M > 0 && (!gout_host || !gxyz_host))) return set_error(SGL_ERR_ARG, "NULL host buffer");
     cudaStream_t st = plan->stream;
-    if (M > 0) {
-        SGL_CUDA_TRY(cudaMemcpyAsync(plan->b.io_xyz, xyz_host, sizeof(double) * 3 * M, cudaMemcpyHostToDevice, st));
-        SGL_CUDA_TRY(cudaMemcpyAsync(plan->b.io_vals, gout_host, sizeof(double2) * M, cudaMemcpyHostToDevice, st));
-    }
+    if (sgl_status s = host_points(plan, xyz_host, M)) return s;
+    if (M > 0) SGL_CUDA_TRY(cudaMemcpyAsync(plan->b.io_vals, gout_host, sizeof(double2) * M, cudaMemcpyHostToDevice, st));
     SGL_CUDA_TRY(cudaMemcpyAsync(plan->b.io_coef, coef_host, sizeof(double2) * plan->Nc, cudaMemcpyHostToDevice, st));
-    if (sgl_status s = sgl_set_points(plan, plan->b.io_xyz, M)) return s;
     if (sgl_status s = sgl_grad_points(plan, plan->b.io_coef, plan->b.io_vals, plan->b.io_grad)) return s;
     if (M > 0) SGL_CUDA_TRY(cudaMemcpyAsync(gxyz_host, plan->b.io_grad, sizeof(double) * 3 * M, cudaMemcpyDeviceToHost, st));
     return sgl_sync(plan);
@@ -772,14 +783,11 @@ sgl_status sgl_forward_grad_host(sgl_plan *plan, const double *xyz_host, int64_t
     if (sgl_status s = check_plan(plan)) return s;
     if (!(plan->flags & SGL_FLAG_HOST_IO)) return set_error(SGL_ERR_STATE, "plan was created without SGL_FLAG_HOST_IO");
     if (M < 0 || M > plan->M_max) return set_error(SGL_ERR_ARG, "M must be in [0, M_max]");
-    if (!coef_host || (M > 0 && (!xyz_host || !gout_host || !vals_host || !gxyz_host))) return set_error(SGL_ERR_ARG, "NULL host buffer");
+    if (!coef_host || (M > 0 && (!gout_host || !vals_host || !gxyz_host))) return set_error(SGL_ERR_ARG, "NULL host buffer");
     cudaStream_t st = plan->stream;
-    if (M > 0) {
-        SGL_CUDA_TRY(cudaMemcpyAsync(plan->b.io_xyz, xyz_host, sizeof(double) * 3 * M, cudaMemcpyHostToDevice, st));
-        SGL_CUDA_TRY(cudaMemcpyAsync(plan->b.io_vals, gout_host, sizeof(double2) * M, cudaMemcpyHostToDevice, st));
-    }
+    if (sgl_status s = host_points(plan, xyz_host, M)) return s;
+    if (M > 0) SGL_CUDA_TRY(cudaMemcpyAsync(plan->b.io_vals, gout_host, sizeof(double2) * M, cudaMemcpyHostToDevice, st));
     SGL_CUDA_TRY(cudaMemcpyAsync(plan->b.io_coef, coef_host, sizeof(double2) * plan->Nc, cudaMemcpyHostToDevice, st));
-    if (sgl_status s = sgl_set_points(plan, plan->b.io_xyz, M)) return s;
     if (sgl_status s = sgl_forward_grad(plan, plan->b.io_coef, plan->b.io_vals, plan->b.io_out, plan->b.io_grad)) return s;
     if (M > 0) {
         SGL_CUDA_TRY(cudaMemcpyAsync(vals_host, plan->b.io_out, sizeof(double2) * M, cudaMemcpyDeviceToHost, st));

@@ -282,3 +282,24 @@ def test_fp64_plan_is_linear_over_the_whole_binary64_range(scale):
     assert rel(fs / scale, f1) <= 1e-13
     assert rel(as_ / scale, a1) <= 1e-13
     assert rel(gs.cpu().numpy() / scale, g1.cpu().numpy()) <= 1e-11
+
+
+def test_host_calls_reuse_the_points_when_xyz_is_none():
+    B, M = 8, 1500
+    c, x, y = case(B, M, 5300)
+    g = y[::-1].copy()
+    p = plan_for(B, M, host_io=True)
+    vals, gxyz = np.zeros(M, complex), np.zeros((M, 3))
+    p.forward_grad_host(np.ascontiguousarray(x), c, g, vals, gxyz)
+    a_host = np.zeros(p.Nc, complex)
+    p.adjoint_host(None, y, a_host)                 # the points of the previous call
+    f2 = np.zeros(M, complex)
+    p.forward_host(None, c, f2)
+    q = plan_for(B, M, x=x)
+    assert rel(a_host, q.adjoint(gpu(y)).cpu().numpy()) <= 1e-12
+    assert rel(f2, q.forward(gpu(c)).cpu().numpy()) <= 1e-12
+    # reusing the points with another M is an argument error (SGL_ERR_ARG = 1)
+    assert p.lib.sgl_adjoint_host(p._h, None, M - 1, y.ctypes.data, a_host.ctypes.data) == 1
+    fresh = plan_for(B, M, host_io=True)
+    with pytest.raises(sgl.SGLError):
+        fresh.adjoint_host(None, y, a_host)            # no points set yet
