@@ -62,7 +62,7 @@ class ClockSampler:
         self.proc = None
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
-                                          "-lms", "200", "-i", str(gpu_index)], stdout=subprocess.PIPE,
+                                          "-lms", "50", "-i", str(gpu_index)], stdout=subprocess.PIPE,
                                          stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.proc = None
@@ -208,12 +208,14 @@ def run_ours(args):
             a = plan.adjoint(y)
             out["a"] = sd.allreduce_coefficients(a)
 
+        # clocks are sampled from the start of the warm-up (nvidia-smi needs a moment to start)
+        # to the end of the timed steps
+        sampler = ClockSampler(local) if prec_name == "fp32_mixed" else None
         for _ in range(args.warmup):
             step()
         barrier()
         plan.profile()                                    # drop warm-up stage times
         launches0 = plan.info()["kernel_launches"]
-        sampler = ClockSampler(local) if prec_name == "fp32_mixed" else None
         evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
         barrier()
         for k in range(args.steps):
@@ -496,8 +498,8 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
-    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--B", type=int, default=64)
     ap.add_argument("--M", type=int, default=1_000_000)
