@@ -57,7 +57,9 @@ typedef enum {
 } sgl_status;
 
 typedef enum {
-    SGL_FP64 = 0,             /* every step in IEEE binary64 */
+    SGL_FP64 = 0,             /* binary64 throughout, except that interpolation, gradient and
+                                 spreading run in double-float arithmetic (FP32 pairs, relative
+                                 rounding ~2^-48) unless SGL_FLAG_NATIVE_FP64 is set */
     SGL_FP32_MIXED = 1        /* FFT, interpolation and spreading in binary32; conversions,
                                  recurrences and deconvolution factors in binary64 */
 } sgl_precision;
