@@ -154,6 +154,57 @@ double axis_error(int window, int N, int n, int K, int q) {
     return emax;
 }
 
+// psi (D = 0) and psi' (D = 1) of the kernels, peak-normalized, in extended precision (|x| <= q):
+// KB psi = norm e^{b(s-q)} (1 - e^{-2bs}) / s, norm = q / (1 - e^{-2bq}), s = sqrt(q^2 - x^2),
+//    psi' = -x 2 norm e^{-bq} (b s cosh(bs) - sinh(bs)) / s^3;  Gauss psi = e^{-x^2 / 2 lambda}, psi' = -x psi / lambda
+long double window_ld(int window, int D, long double x, long double q, long double par) {
+    if (window == SGL_WIN_KB) {
+        const long double b = par, s = sqrtl(std::max(q * q - x * x, (long double)0));
+        const long double norm = q / (-expm1l(-2 * b * q));
+        if (D == 0) return s > 0 ? norm * expl(b * (s - q)) * (-expm1l(-2 * b * s)) / s : norm * expl(-b * q) * 2 * b;
+        if (s <= 0) return -x * 2 * norm * expl(-b * q) * b * b * b / 3;
+        return -x * 2 * norm * expl(-b * q) * (b * s * coshl(b * s) - sinhl(b * s)) / (s * s * s);
+    }
+    const long double v = expl(-x * x / (2 * par));
+    return D == 0 ? v : -x * v / par;
+}
+
+// the table of every axis (layout at kWinNI): Chebyshev interpolation of degree kWinDeg on each
+// piece, rewritten as a polynomial in the offset t = x - midpoint
+void window_tables(const sgl_plan *p, std::vector<double> &tab) {
+    constexpr int n = kWinDeg + 1;
+    tab.assign(kWinTab, 0.0);
+    const long double q = p->q, h = q / kWinNI, half = h / 2;
+    const long double pi = 3.14159265358979323846264338327950288L;
+    for (int d = 0; d < 3; ++d)
+        for (int D = 0; D < 2; ++D)
+            for (int i = 0; i < kWinNI; ++i) {
+                const long double mid = (i + 0.5L) * h;
+                long double f[n], a[n], T[n][n], m[n];
+                for (int j = 0; j < n; ++j) f[j] = window_ld(p->window, D, mid + half * cosl(pi * (j + 0.5L) / n), q, p->ax[d].wpar);
+                for (int k = 0; k < n; ++k) {
+                    long double acc = 0;
+                    for (int j = 0; j < n; ++j) acc += f[j] * cosl(pi * k * (j + 0.5L) / n);
+                    a[k] = acc * 2 / n;
+                }
+                a[0] /= 2;
+                // monomial coefficients of T_k(s): T_0 = 1, T_1 = s, T_{k+1} = 2 s T_k - T_{k-1}
+                for (int k = 0; k < n; ++k)
+                    for (int c = 0; c < n; ++c) T[k][c] = 0;
+                T[0][0] = 1;
+                if (n > 1) T[1][1] = 1;
+                for (int k = 1; k + 1 < n; ++k)
+                    for (int c = 0; c < n; ++c) T[k + 1][c] = (c > 0 ? 2 * T[k][c - 1] : 0) - T[k - 1][c];
+                for (int c = 0; c < n; ++c) {
+                    m[c] = 0;
+                    for (int k = 0; k < n; ++k) m[c] += a[k] * T[k][c];
+                }
+                // s = t / half: the coefficient of t^c is m_c / half^c
+                long double sc = 1;
+                for (int c = 0; c < n; ++c, sc /= half) tab[((size_t)(d * 2 + D) * kWinNI + i) * n + c] = (double)(m[c] * sc);
+            }
+}
+
 // sum |eta_k| over n complex values into *acc (block sums, then one atomic add per block)
 __global__ void __launch_bounds__(256) k_abs_sum(const double2 *__restrict__ x, int64_t n, double *__restrict__ acc) {
     __shared__ double ws[8];
@@ -440,6 +491,7 @@ sgl_status plan_create_impl(sgl_plan **out, int B, int64_t M_max, int precision,
     ALLOC(b.work_len, 2);
     ALLOC(b.df_max, 2);
     ALLOC(b.scalar, 1);
+    ALLOC(b.wtab, (size_t)kWinTab);
     if (flags & SGL_FLAG_HOST_IO) {
         ALLOC(b.io_xyz, 3 * Mc);
         ALLOC(b.io_coef, (size_t)(2 * p->Nc));
@@ -495,6 +547,9 @@ sgl_status plan_create_impl(sgl_plan **out, int B, int64_t M_max, int precision,
     if ((e = upload(b.P, P, p->stream)) != cudaSuccess) return fail(SGL_ERR_CUDA, "upload polar matrices");
     if ((e = upload(b.costab, costab, p->stream)) != cudaSuccess) return fail(SGL_ERR_CUDA, "upload cosine table");
     if ((e = upload(b.linescale, ls, p->stream)) != cudaSuccess) return fail(SGL_ERR_CUDA, "upload line scales");
+    std::vector<double> wt;
+    window_tables(p, wt);
+    if ((e = upload(b.wtab, wt, p->stream)) != cudaSuccess) return fail(SGL_ERR_CUDA, "upload window tables");
     if ((e = cudaMemsetAsync(b.dev_flags, 0, sizeof(int), p->stream)) != cudaSuccess) return fail(SGL_ERR_CUDA, "memset");
     // the host vectors above are released on return: wait for the copies
     if ((e = cudaStreamSynchronize(p->stream)) != cudaSuccess) return fail(SGL_ERR_CUDA, std::string("plan upload: ") + cudaGetErrorString(e));

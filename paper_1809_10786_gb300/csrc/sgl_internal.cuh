@@ -32,6 +32,13 @@ struct BinGeom {
 // kTcPass points (a pass of the tensor-core kernels), list 1 of spread_chunk(prec) points (a
 // CTA of the CUDA-core spreading kernel).
 constexpr int kTcPass = 128;
+
+// Tabulated windows of the double-float FP64 kernels: psi (even) and psi' (odd) of each axis on
+// [0, q] as kWinNI pieces of degree kWinDeg in the offset from the piece's midpoint (psi is an
+// entire function of x: sinh(b s) / s is a power series in s^2 = q^2 - x^2), fitted on the host in
+// extended precision.  Layout [axis][psi, psi'][piece][coefficient, constant term first].
+constexpr int kWinNI = 64, kWinDeg = 12;
+constexpr int kWinTab = 3 * 2 * kWinNI * (kWinDeg + 1);
 #ifndef SGL_SPREAD_CHUNK32
 #define SGL_SPREAD_CHUNK32 1024
 #endif
@@ -108,6 +115,7 @@ struct Buffers {
     int *work_len;             // [2] entries in each list (written on the device)
     unsigned long long *df_max;// [2] FP64 plans: bits of max |grid| and max |values| (scales of the double-float passes)
     double *scalar;            // [1] device accumulator of small reductions (sgl_eta_l1)
+    double *wtab;              // [kWinTab] tabulated windows (FP64 plans)
     // host-IO staging
     double *io_xyz, *io_coef, *io_vals, *io_grad, *io_out;
     // tensor-core interpolation (FP32-mixed): grid as planes Re, Im [rows0][rows1][pitch] with an azimuthal halo

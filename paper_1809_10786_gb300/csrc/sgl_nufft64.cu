@@ -1,6 +1,5 @@
 // sgl_nufft64.cu -- FP64 windowed interpolation (NFFT step 3, Sect. 2), its adjoint
-// (spreading) and the window-derivative interpolation of the point gradient, binary64
-// throughout (grid coordinates, window values, products and sums).
+// (spreading) and the window-derivative interpolation of the point gradient.
 //
 //   s(t) = sum_{l : |u_d - l_d| <= q} alpha_l prod_d psi_d(u_d - l_d),   u_d = N_d t_d / (2 pi)
 //
@@ -10,10 +9,12 @@
 // of two FP32 numbers, products and sums are carried out with the error-free transformations
 // TwoProduct (Dekker; exact with a fused multiply-add) and TwoSum (Knuth), so every tap costs
 // about a dozen FP32 operations and keeps a relative rounding error of order 2^-48 (binary64:
-// 2^-53).  Window values, the final lane reductions and the chain rule stay binary64; the grid
-// is split into (hi, lo) pairs in place by one pass before the interpolation, and spreading
-// adds its double-float sums to the binary64 grid.  SGL_FLAG_NATIVE_FP64 selects the binary64
-// loops (k_interp64, k_grad64, k_spread_slab64).
+// 2^-53).  Their window values are binary64, read from per-axis polynomial tables (see kWinNI:
+// a dozen FP64 operations instead of a square root, exponentials and a division); the final lane
+// reductions and the chain rule stay binary64; the grid is split into (hi, lo) pairs in place by
+// one pass before the interpolation, and spreading adds its double-float sums to the binary64
+// grid.  SGL_FLAG_NATIVE_FP64 selects the binary64 loops (k_interp64, k_grad64, k_spread_slab64),
+// which evaluate the windows directly.
 #include "sgl_nufft_common.cuh"
 
 namespace sgl {
@@ -391,9 +392,9 @@ __global__ void __launch_bounds__(256, 4) k_interp64x(NGeom g, int64_t M, const 
         const int a2 = min(max((int)floor(u2), 0), g.N[2] - 1) - q + 1;
         const bool tap = gl < q2;
         float w0h_own, w0l_own, w1h_own, w1l_own;
-        df_split(tap ? window<WIN, double>(u0 - (a0 + gl), qd, g.par[0], g.norm[0]) : 0.0, w0h_own, w0l_own);
-        df_split(tap ? window<WIN, double>(u1 - (a1 + gl), qd, g.par[1], g.norm[1]) : 0.0, w1h_own, w1l_own);
-        const double w2 = tap ? window<WIN, double>(u2 - (a2 + gl), qd, g.par[2], g.norm[2]) : 0.0;
+        df_split(tap ? window_tab<0>(g, 0, u0 - (a0 + gl)) : 0.0, w0h_own, w0l_own);
+        df_split(tap ? window_tab<0>(g, 1, u1 - (a1 + gl)) : 0.0, w1h_own, w1l_own);
+        const double w2 = tap ? window_tab<0>(g, 2, u2 - (a2 + gl)) : 0.0;
         const int col = tap ? wrap_index(a2 + gl, g.N[2]) : 0;
 
         float axh = 0.f, axl = 0.f, ayh = 0.f, ayl = 0.f;
@@ -425,7 +426,7 @@ __global__ void __launch_bounds__(256, 4) k_interp64x(NGeom g, int64_t M, const 
 
 // ---- double-float window-derivative interpolation (values, ds/du0, ds/du1, ds/du2), layout of k_grad64
 template <int WIN, int G>
-__global__ void __launch_bounds__(256, 4) k_grad64x(NGeom g, int64_t M, const double *__restrict__ u_sorted,
+__global__ void __launch_bounds__(256, 3) k_grad64x(NGeom g, int64_t M, const double *__restrict__ u_sorted,
                                                  const int *__restrict__ perm, const unsigned long long *__restrict__ r2max,
                                                  const float4 *__restrict__ grid, const unsigned long long *__restrict__ maxbits,
                                                  const double2 *__restrict__ gout, double *__restrict__ gxyz,
@@ -450,12 +451,12 @@ __global__ void __launch_bounds__(256, 4) k_grad64x(NGeom g, int64_t M, const do
         const bool tap = gl < q2;
         const double x0 = u0 - (a0 + gl), x1 = u1 - (a1 + gl), x2 = u2 - (a2 + gl);
         float w0h_own, w0l_own, d0h_own, d0l_own, w1h_own, w1l_own, d1h_own, d1l_own;
-        df_split(tap ? window<WIN, double>(x0, qd, g.par[0], g.norm[0]) : 0.0, w0h_own, w0l_own);
-        df_split(tap ? window_deriv<WIN, double>(x0, qd, g.par[0], g.norm[0]) : 0.0, d0h_own, d0l_own);
-        df_split(tap ? window<WIN, double>(x1, qd, g.par[1], g.norm[1]) : 0.0, w1h_own, w1l_own);
-        df_split(tap ? window_deriv<WIN, double>(x1, qd, g.par[1], g.norm[1]) : 0.0, d1h_own, d1l_own);
-        const double w2 = tap ? window<WIN, double>(x2, qd, g.par[2], g.norm[2]) : 0.0;
-        const double d2 = tap ? window_deriv<WIN, double>(x2, qd, g.par[2], g.norm[2]) : 0.0;
+        df_split(tap ? window_tab<0>(g, 0, x0) : 0.0, w0h_own, w0l_own);
+        df_split(tap ? window_tab<1>(g, 0, x0) : 0.0, d0h_own, d0l_own);
+        df_split(tap ? window_tab<0>(g, 1, x1) : 0.0, w1h_own, w1l_own);
+        df_split(tap ? window_tab<1>(g, 1, x1) : 0.0, d1h_own, d1l_own);
+        const double w2 = tap ? window_tab<0>(g, 2, x2) : 0.0;
+        const double d2 = tap ? window_tab<1>(g, 2, x2) : 0.0;
         const int col = tap ? wrap_index(a2 + gl, g.N[2]) : 0;
         float fxh = 0.f, fxl = 0.f, fyh = 0.f, fyl = 0.f;     // sum psi0 psi1 grid
         float axh = 0.f, axl = 0.f, ayh = 0.f, ayl = 0.f;     // sum psi0' psi1 grid
@@ -559,24 +560,25 @@ __global__ void __launch_bounds__(32 * (C0 + Q2MAX - 1)) k_spread_slab64x(NGeom 
         const int c0 = cell_clamped(u0, g.cmax0), c1 = cell_clamped(u1, g.cmax1);
         const int c2 = min(max((int)floor(u2), 0), g.N[2] - 1);
         if (e < Q2MAX + T1M + 32) {
-            double x, par, nrm;
+            double x;
             float2 *dst;
             bool ok;
+            int d;
             if (e < Q2MAX) {
-                ok = e < q2; x = u0 - c0 + (double)(q - 1 - e); par = g.par[0]; nrm = g.norm[0]; dst = &sm.w0[p][e];
+                ok = e < q2; x = u0 - c0 + (double)(q - 1 - e); d = 0; dst = &sm.w0[p][e];
             } else if (e < Q2MAX + T1M) {
                 const int tb = e - Q2MAX;
                 const int rel = tb - (c1 - sb1 * C1);
-                ok = rel >= 0 && rel < q2 && tb < T1; x = u1 - c1 + (double)(q - 1 - rel); par = g.par[1]; nrm = g.norm[1];
+                ok = rel >= 0 && rel < q2 && tb < T1; x = u1 - c1 + (double)(q - 1 - rel); d = 1;
                 dst = &sm.w1[p][tb];
             } else {
                 const int L = e - Q2MAX - T1M;
                 const int rel = cbase + L - (c2 - q + 1);
-                ok = rel >= 0 && rel < q2; x = u2 - c2 + (double)(q - 1 - rel); par = g.par[2]; nrm = g.norm[2];
+                ok = rel >= 0 && rel < q2; x = u2 - c2 + (double)(q - 1 - rel); d = 2;
                 dst = &sm.w2[p][L];
             }
             float h, l;
-            df_split(ok ? window<WIN, double>(x, qd, par, nrm) : 0.0, h, l);
+            df_split(ok ? window_tab<0>(g, d, x) : 0.0, h, l);
             *dst = make_float2(h, l);
         } else {
             const double2 y = vals[perm[pi]];

@@ -54,9 +54,26 @@ struct NGeom {
     int N[3], rows[3], first[3];
     int q;
     double par[3], norm[3];
+    const double *wtab;        // tabulated windows (FP64 plans; see kWinNI)
+    double wh, winv;           // piece width q / kWinNI of the table, and its reciprocal
     // bins (see BinGeom): azimuthal chunk, columns per super-bin, super-bins per axis
     int S2, C0, C1, nsb0, nsb1, nsb2, cmax0, cmax1;
 };
+
+// psi (D = 0) or psi' (D = 1) of axis d from the table: the piece of |x| and its polynomial in the
+// offset from the piece's midpoint (Horner); psi is even, psi' odd; zero for |x| > q
+template <int D>
+__device__ __forceinline__ double window_tab(const NGeom &g, int d, double x) {
+    const double ax = fabs(x);
+    if (ax > (double)g.q) return 0.0;
+    const int i = min((int)(ax * g.winv), kWinNI - 1);
+    const double t = ax - (i + 0.5) * g.wh;
+    const double *c = g.wtab + ((d * 2 + D) * kWinNI + i) * (kWinDeg + 1);
+    double r = __ldg(c + kWinDeg);
+#pragma unroll
+    for (int k = kWinDeg - 1; k >= 0; --k) r = fma(r, t, __ldg(c + k));
+    return (D == 1 && x < 0.0) ? -r : r;
+}
 
 __device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
     // elementwise a * b + c on a packed pair (fma.rn.f32x2)
@@ -111,6 +128,9 @@ inline NGeom make_geom(const sgl_plan *p) {
         g.norm[d] = (p->window == SGL_WIN_KB) ? p->q / (-expm1(-2.0 * p->ax[d].wpar * p->q)) : 1.0;
     }
     g.q = p->q;
+    g.wtab = p->b.wtab;
+    g.wh = (double)p->q / kWinNI;
+    g.winv = kWinNI / (double)p->q;
     g.S2 = p->bins.S2;
     g.C0 = p->bins.C0;
     g.C1 = p->bins.C1;
