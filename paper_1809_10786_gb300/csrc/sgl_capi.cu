@@ -11,6 +11,7 @@
 #include <mutex>
 #include <new>
 #include <string>
+#include <tuple>
 #include <vector>
 
 namespace sgl {
@@ -169,40 +170,61 @@ long double window_ld(int window, int D, long double x, long double q, long doub
     return D == 0 ? v : -x * v / par;
 }
 
-// the table of every axis (layout at kWinNI): Chebyshev interpolation of degree kWinDeg on each
-// piece, rewritten as a polynomial in the offset t = x - midpoint
-void window_tables(const sgl_plan *p, std::vector<double> &tab) {
+// The table of one axis (psi and psi', layout at kWinNI): Chebyshev interpolation of degree
+// kWinDeg on each piece, rewritten as a polynomial in the offset t = x - midpoint.  Tables depend
+// only on (window, q, shape parameter) and are cached: plans of a batch share most of them.
+std::vector<double> axis_window_table(int window, int q, double par) {
     constexpr int n = kWinDeg + 1;
-    tab.assign(kWinTab, 0.0);
-    const long double q = p->q, h = q / kWinNI, half = h / 2;
+    static std::mutex mu;
+    static std::map<std::tuple<int, int, double>, std::vector<double>> cache;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        auto it = cache.find(std::make_tuple(window, q, par));
+        if (it != cache.end()) return it->second;
+    }
     const long double pi = 3.14159265358979323846264338327950288L;
-    for (int d = 0; d < 3; ++d)
-        for (int D = 0; D < 2; ++D)
-            for (int i = 0; i < kWinNI; ++i) {
-                const long double mid = (i + 0.5L) * h;
-                long double f[n], a[n], T[n][n], m[n];
-                for (int j = 0; j < n; ++j) f[j] = window_ld(p->window, D, mid + half * cosl(pi * (j + 0.5L) / n), q, p->ax[d].wpar);
-                for (int k = 0; k < n; ++k) {
-                    long double acc = 0;
-                    for (int j = 0; j < n; ++j) acc += f[j] * cosl(pi * k * (j + 0.5L) / n);
-                    a[k] = acc * 2 / n;
-                }
-                a[0] /= 2;
-                // monomial coefficients of T_k(s): T_0 = 1, T_1 = s, T_{k+1} = 2 s T_k - T_{k-1}
-                for (int k = 0; k < n; ++k)
-                    for (int c = 0; c < n; ++c) T[k][c] = 0;
-                T[0][0] = 1;
-                if (n > 1) T[1][1] = 1;
-                for (int k = 1; k + 1 < n; ++k)
-                    for (int c = 0; c < n; ++c) T[k + 1][c] = (c > 0 ? 2 * T[k][c - 1] : 0) - T[k - 1][c];
-                for (int c = 0; c < n; ++c) {
-                    m[c] = 0;
-                    for (int k = 0; k < n; ++k) m[c] += a[k] * T[k][c];
-                }
-                // s = t / half: the coefficient of t^c is m_c / half^c
-                long double sc = 1;
-                for (int c = 0; c < n; ++c, sc /= half) tab[((size_t)(d * 2 + D) * kWinNI + i) * n + c] = (double)(m[c] * sc);
+    // cos(pi k (j + 1/2) / n) (the Chebyshev nodes and the transform) and the monomial
+    // coefficients of T_k(s): T_0 = 1, T_1 = s, T_{k+1} = 2 s T_k - T_{k-1}
+    long double cs[n][n], T[n][n];
+    for (int k = 0; k < n; ++k)
+        for (int j = 0; j < n; ++j) cs[k][j] = cosl(pi * k * (j + 0.5L) / n);
+    for (int k = 0; k < n; ++k)
+        for (int c = 0; c < n; ++c) T[k][c] = 0;
+    T[0][0] = 1;
+    T[1][1] = 1;
+    for (int k = 1; k + 1 < n; ++k)
+        for (int c = 0; c < n; ++c) T[k + 1][c] = (c > 0 ? 2 * T[k][c - 1] : 0) - T[k - 1][c];
+    std::vector<double> tab((size_t)2 * kWinNI * n);
+    const long double h = (long double)q / kWinNI, half = h / 2;
+    for (int D = 0; D < 2; ++D)
+        for (int i = 0; i < kWinNI; ++i) {
+            const long double mid = (i + 0.5L) * h;
+            long double f[n], a[n];
+            for (int j = 0; j < n; ++j) f[j] = window_ld(window, D, mid + half * cs[1][j], q, par);
+            for (int k = 0; k < n; ++k) {
+                long double acc = 0;
+                for (int j = 0; j < n; ++j) acc += f[j] * cs[k][j];
+                a[k] = acc * 2 / n;
             }
+            a[0] /= 2;
+            long double sc = 1;                     // s = t / half: the coefficient of t^c is m_c / half^c
+            for (int c = 0; c < n; ++c, sc /= half) {
+                long double m = 0;
+                for (int k = c; k < n; ++k) m += a[k] * T[k][c];
+                tab[((size_t)D * kWinNI + i) * n + c] = (double)(m * sc);
+            }
+        }
+    std::lock_guard<std::mutex> lk(mu);
+    cache.emplace(std::make_tuple(window, q, par), tab);
+    return tab;
+}
+
+void window_tables(const sgl_plan *p, std::vector<double> &tab) {
+    tab.assign(kWinTab, 0.0);
+    for (int d = 0; d < 3; ++d) {
+        const std::vector<double> t = axis_window_table(p->window, p->q, p->ax[d].wpar);
+        std::copy(t.begin(), t.end(), tab.begin() + (size_t)d * t.size());
+    }
 }
 
 // sum |eta_k| over n complex values into *acc (block sums, then one atomic add per block)
@@ -425,8 +447,12 @@ sgl_status plan_create_impl(sgl_plan **out, int B, int64_t M_max, int precision,
         // FP32 plans with q <= 8: a multiple of 4, so that the tensor-core kernels' TMA boxes start
         // 16-byte aligned (lanes from sb2 * S2 - tc_halo(q)); otherwise as wide as one warp allows
         g.S2 = (precision == SGL_FP32_MIXED && q <= 8) ? 4 * ((32 - tc_halo(q) - q) / 4) : 33 - 2 * q;
-        g.C0 = (precision == SGL_FP32_MIXED) ? 8 : 4;   // must match the spreading kernels' template sizes
-        g.C1 = (precision == SGL_FP32_MIXED) ? 8 : 2;
+        // must match the spreading kernels' template sizes; FP64 double-float spreading amortizes
+        // its per-cell flush over the larger super-bin, the binary64 kernel's half-warp layout
+        // keeps 4 x 2
+        const bool native64 = precision == SGL_FP64 && (flags & SGL_FLAG_NATIVE_FP64);
+        g.C0 = native64 ? 4 : 8;
+        g.C1 = (precision == SGL_FP32_MIXED) ? 8 : (native64 ? 2 : 4);
         g.ncell[0] = p->ax[0].N / 2 + 1;
         g.ncell[1] = p->ax[1].N / 2 + 1;
         g.nsb[0] = (g.ncell[0] + g.C0 - 1) / g.C0;
@@ -547,9 +573,11 @@ sgl_status plan_create_impl(sgl_plan **out, int B, int64_t M_max, int precision,
     if ((e = upload(b.P, P, p->stream)) != cudaSuccess) return fail(SGL_ERR_CUDA, "upload polar matrices");
     if ((e = upload(b.costab, costab, p->stream)) != cudaSuccess) return fail(SGL_ERR_CUDA, "upload cosine table");
     if ((e = upload(b.linescale, ls, p->stream)) != cudaSuccess) return fail(SGL_ERR_CUDA, "upload line scales");
-    std::vector<double> wt;
-    window_tables(p, wt);
-    if ((e = upload(b.wtab, wt, p->stream)) != cudaSuccess) return fail(SGL_ERR_CUDA, "upload window tables");
+    if (precision == SGL_FP64 && !(flags & SGL_FLAG_NATIVE_FP64)) {      // read by the double-float kernels only
+        std::vector<double> wt;
+        window_tables(p, wt);
+        if ((e = upload(b.wtab, wt, p->stream)) != cudaSuccess) return fail(SGL_ERR_CUDA, "upload window tables");
+    }
     if ((e = cudaMemsetAsync(b.dev_flags, 0, sizeof(int), p->stream)) != cudaSuccess) return fail(SGL_ERR_CUDA, "memset");
     // the host vectors above are released on return: wait for the copies
     if ((e = cudaStreamSynchronize(p->stream)) != cudaSuccess) return fail(SGL_ERR_CUDA, std::string("plan upload: ") + cudaGetErrorString(e));

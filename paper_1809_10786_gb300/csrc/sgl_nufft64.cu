@@ -680,7 +680,7 @@ cudaError_t spread_slab64_t(sgl_plan *p, const NGeom &g, const double2 *vals) {
     if (g.C0 != C0 || g.C1 != C1 || g.S2 + 2 * p->q - 1 > 32) return cudaErrorInvalidConfiguration;
     const int threads = 32 * (C0 + 2 * p->q - 1);
     const int64_t blocks = work_list_cap(p->M, p->bins.nsuper, spread_chunk(p->prec));   // entries past work_len[1] return
-    if (DF) {
+    if constexpr (DF) {
         auto kern = k_spread_slab64x<WIN, Q2MAX, C0, C1>;
         const int smem = (int)sizeof(Spread64xSmem<Q2MAX, C1>);
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
@@ -700,8 +700,8 @@ template <int WIN>
 cudaError_t spread64_t(sgl_plan *p, const double2 *vals) {
     const NGeom g = make_geom(p);
     const bool native = p->flags & SGL_FLAG_NATIVE_FP64;
-    if (p->q <= 4) return native ? spread_slab64_t<WIN, 8, 4, 2, false>(p, g, vals) : spread_slab64_t<WIN, 8, 4, 2, true>(p, g, vals);
-    if (p->q <= 8) return native ? spread_slab64_t<WIN, 16, 4, 2, false>(p, g, vals) : spread_slab64_t<WIN, 16, 4, 2, true>(p, g, vals);
+    if (p->q <= 4) return native ? spread_slab64_t<WIN, 8, 4, 2, false>(p, g, vals) : spread_slab64_t<WIN, 8, 8, 4, true>(p, g, vals);
+    if (p->q <= 8) return native ? spread_slab64_t<WIN, 16, 4, 2, false>(p, g, vals) : spread_slab64_t<WIN, 16, 8, 4, true>(p, g, vals);
     double2 *grid = (double2 *)p->b.bufA;
     k_spread<double, WIN, 32><<<nufft_blocks(p->M, 32), 256, 0, p->stream>>>(g, p->M, p->b.u_sorted, p->b.perm, vals, grid);
     p->launches += 1;
