@@ -94,21 +94,37 @@ __global__ void __launch_bounds__(256) k_split_grid(double2 *__restrict__ grid, 
     }
 }
 
-// Chain rule from ds/du_d to Re(conj(g) grad_x f) for one point (FP64), written by one lane.
-__device__ __forceinline__ void write_point_gradient(const NGeom &g, double rho, double u0, double u1, double u2,
-                                                     double a0x, double a0y, double a1x, double a1y, double a2x, double a2y,
-                                                     double2 gv, double *outp) {
-    const double twopi = 2.0 * kPi;
-    const double g0x = a0x * (g.N[0] / twopi), g0y = a0y * (g.N[0] / twopi);
-    const double g1x = a1x * (g.N[1] / twopi), g1y = a1y * (g.N[1] / twopi);
-    const double g2x = a2x * (g.N[2] / twopi), g2y = a2y * (g.N[2] / twopi);
-    const double t0 = twopi * u0 / g.N[0], t1 = twopi * u1 / g.N[1], t2 = twopi * u2 / g.N[2];
-    const double ch = cos(0.5 * t0);
-    const double r = rho * ch * ch;                 // r = rho (1 + cos t0) / 2
-    const double st0 = sin(t0), st1 = sin(t1), ct1 = cos(t1), sp = sin(t2), cp = cos(t2);
-    const double dt0dr = (st0 > 0.0) ? -2.0 / (rho * st0) : 0.0;
-    const double ir = (r > 0.0) ? 1.0 / r : 0.0;
-    const double irs = (r > 0.0 && st1 > 0.0) ? 1.0 / (r * st1) : 0.0;
+// Chain rule from ds/du_d to Re(conj(g) grad_x f) for one point (FP64), called by every lane of
+// the point's group of G lanes (gl = lane within the group), written by the group's lane 0 when
+// `write`.  The transcendental functions and reciprocals are spread over lanes 0-2 of the group
+// (one sincos and one reciprocal each) and gathered by shuffle: an FP64 warp instruction costs
+// the FP64 pipe the same however few lanes are active.
+template <int G>
+__device__ __forceinline__ void point_gradient_lanes(const NGeom &g, int gl, double rho, double u0, double u1, double u2,
+                                                     double a0x, double a0y, double a1x, double a1y, double a2x,
+                                                     double a2y, bool write, double2 gv, double *outp) {
+    const int lane = threadIdx.x & 31, base = lane - gl;
+    const int sel = min(gl, 2);
+    const double ud = sel == 0 ? u0 : (sel == 1 ? u1 : u2);
+    const double t = g.tpn[sel] * ud;
+    double sn, cs;
+    sincos(sel == 0 ? 0.5 * t : t, &sn, &cs);        // lane 0: t0 / 2, lane 1: t1, lane 2: t2
+    const double sh = __shfl_sync(0xffffffffu, sn, base, 32), ch = __shfl_sync(0xffffffffu, cs, base, 32);
+    const double st1 = __shfl_sync(0xffffffffu, sn, base + 1, 32), ct1 = __shfl_sync(0xffffffffu, cs, base + 1, 32);
+    const double sp = __shfl_sync(0xffffffffu, sn, base + 2, 32), cp = __shfl_sync(0xffffffffu, cs, base + 2, 32);
+    const double st0 = 2.0 * sh * ch;                // sin t0
+    const double r = rho * ch * ch;                  // r = rho (1 + cos t0) / 2
+    // lane 0: dt0/dr = -2 / (rho sin t0); lane 1: 1 / r; lane 2: 1 / (r sin t1); zero where singular
+    const double den = sel == 0 ? rho * st0 : (sel == 1 ? r : r * st1);
+    const double num = sel == 0 ? -2.0 : 1.0;
+    const double rec = den > 0.0 ? num / den : 0.0;
+    const double dt0dr = __shfl_sync(0xffffffffu, rec, base, 32);
+    const double ir = __shfl_sync(0xffffffffu, rec, base + 1, 32);
+    const double irs = __shfl_sync(0xffffffffu, rec, base + 2, 32);
+    if (!write) return;
+    const double g0x = a0x * g.ntp[0], g0y = a0y * g.ntp[0];
+    const double g1x = a1x * g.ntp[1], g1y = a1y * g.ntp[1];
+    const double g2x = a2x * g.ntp[2], g2y = a2y * g.ntp[2];
     const double er[3] = {st1 * cp, st1 * sp, ct1}, et[3] = {ct1 * cp, ct1 * sp, -st1}, ep[3] = {-sp, cp, 0.0};
     for (int d = 0; d < 3; ++d) {
         const double vx = g0x * dt0dr * er[d] + g1x * ir * et[d] + g2x * irs * ep[d];
@@ -358,10 +374,12 @@ __global__ void __launch_bounds__(256) k_grad64(NGeom g, int64_t M, const double
                 sy += __shfl_xor_sync(0xffffffffu, sy, o);
             }
         }
-        if (live && gl == 0) {
-            const int dst = perm[i];
-            write_point_gradient(g, rho, u0, u1, u2, ax, ay, bx, by, f2x, f2y, gout[dst], gxyz + 3 * (int64_t)dst);
-            if (vals) vals[dst] = make_double2(sx, sy);
+        {
+            const bool w = live && gl == 0;
+            const int dst = w ? perm[i] : 0;
+            point_gradient_lanes<G>(g, gl, rho, u0, u1, u2, ax, ay, bx, by, f2x, f2y, w, w ? gout[dst] : make_double2(0.0, 0.0),
+                                    gxyz + 3 * (int64_t)dst);
+            if (w && vals) vals[dst] = make_double2(sx, sy);
         }
     }
 }
@@ -503,10 +521,12 @@ __global__ void __launch_bounds__(256, 3) k_grad64x(NGeom g, int64_t M, const do
                 sy += __shfl_xor_sync(0xffffffffu, sy, o);
             }
         }
-        if (live && gl == 0) {
-            const int dst = perm[i];
-            write_point_gradient(g, rho, u0, u1, u2, ax, ay, bx, by, f2x, f2y, gout[dst], gxyz + 3 * (int64_t)dst);
-            if (vals) vals[dst] = make_double2(sx, sy);
+        {
+            const bool w = live && gl == 0;
+            const int dst = w ? perm[i] : 0;
+            point_gradient_lanes<G>(g, gl, rho, u0, u1, u2, ax, ay, bx, by, f2x, f2y, w, w ? gout[dst] : make_double2(0.0, 0.0),
+                                    gxyz + 3 * (int64_t)dst);
+            if (w && vals) vals[dst] = make_double2(sx, sy);
         }
     }
 }

@@ -56,6 +56,7 @@ struct NGeom {
     double par[3], norm[3];
     const double *wtab;        // tabulated windows (FP64 plans; see kWinNI)
     double wh, winv;           // piece width q / kWinNI of the table, and its reciprocal
+    double tpn[3], ntp[3];     // 2 pi / N_d and N_d / (2 pi)
     // bins (see BinGeom): azimuthal chunk, columns per super-bin, super-bins per axis
     int S2, C0, C1, nsb0, nsb1, nsb2, cmax0, cmax1;
 };
@@ -126,6 +127,8 @@ inline NGeom make_geom(const sgl_plan *p) {
         g.first[d] = p->ax[d].first;
         g.par[d] = p->ax[d].wpar;
         g.norm[d] = (p->window == SGL_WIN_KB) ? p->q / (-expm1(-2.0 * p->ax[d].wpar * p->q)) : 1.0;
+        g.tpn[d] = 2.0 * kPi / p->ax[d].N;
+        g.ntp[d] = p->ax[d].N / (2.0 * kPi);
     }
     g.q = p->q;
     g.wtab = p->b.wtab;
