@@ -444,7 +444,7 @@ __global__ void __launch_bounds__(256, 4) k_interp64x(NGeom g, int64_t M, const 
 
 // ---- double-float window-derivative interpolation (values, ds/du0, ds/du1, ds/du2), layout of k_grad64
 template <int WIN, int G>
-__global__ void __launch_bounds__(256, 3) k_grad64x(NGeom g, int64_t M, const double *__restrict__ u_sorted,
+__global__ void __launch_bounds__(256, 4) k_grad64x(NGeom g, int64_t M, const double *__restrict__ u_sorted,
                                                  const int *__restrict__ perm, const unsigned long long *__restrict__ r2max,
                                                  const float4 *__restrict__ grid, const unsigned long long *__restrict__ maxbits,
                                                  const double2 *__restrict__ gout, double *__restrict__ gxyz,
@@ -645,7 +645,8 @@ __global__ void __launch_bounds__(32 * (C0 + Q2MAX - 1)) k_spread_slab64x(NGeom 
             const int tb = pass * RH + r;
             if (tb >= T1M || tb >= T1) continue;
             const int r1 = row_checked(tb_org + tb, g.first[1], g.rows[1], g.N[1]);
-            if (r1 < 0) continue;
+            // cells no point reached: skipped before any FP64 conversion
+            if (r1 < 0 || (acc[r].x == 0.f && acc[r].y == 0.f && acc[r].z == 0.f && acc[r].w == 0.f)) continue;
             const double vx = df_value(acc[r].x, acc[r].y) * unscale, vy = df_value(acc[r].z, acc[r].w) * unscale;
             if (vx != 0.0 || vy != 0.0) {
                 atomicAdd(&colp[r1 * s1].x, vx);
