@@ -287,6 +287,36 @@ def run_ours(args):
             del plan
             torch.cuda.empty_cache()
 
+    # ---- per call, as the transform alone is usually timed: set_points + forward, and the adjoint
+    # (same points), FP32-mixed and FP64 (value only)
+    by_call = {}
+    if not args.no_extra_q:
+        for prec_name, prec in (("fp32_mixed", sgl.PREC_FP32_MIXED), ("fp64", sgl.PREC_FP64)):
+            if prec_name == "fp64" and args.no_fp64:
+                continue
+            plan = sgl.Plan(B, M, precision=prec, window=sgl.WIN_KB, q=q, sigma=2.0, device=dev)
+            plan.set_points(x)
+            calls = {"set_points+forward": lambda: (plan.set_points(x), plan.forward(c)),
+                     "adjoint": lambda: sd.allreduce_coefficients(plan.adjoint(y))}
+            by_call[prec_name] = {}
+            for name, fn in calls.items():
+                for _ in range(args.warmup):
+                    fn()
+                barrier()
+                evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+                for k in range(args.steps):
+                    flush.zero_()
+                    evs[k][0].record()
+                    fn()
+                    evs[k][1].record()
+                barrier()
+                ms = sd.max_over_ranks(sum(a.elapsed_time(b) for a, b in evs), dev)
+                by_call[prec_name][name] = {"value": round(world * M / (ms / args.steps * 1e-3) / 1e6, 4),
+                                            "ms": round(ms / args.steps, 4)}
+            plan.close()
+            del plan
+            torch.cuda.empty_cache()
+
     # ---- inverse transform (iNFSGLFT) in the setup of the paper's last test (Sect. 8): Cartesian
     # grid G_N, N = 50 (M = 125000), kappa = 5, B = 8 and B = 16, CGNR from the mid-point rule, FP64;
     # errors as the paper measures them: max |c - c_true| and max |c - c_true| / |c_true|
@@ -393,6 +423,7 @@ def run_ours(args):
                 "stages": {k: v["ms"] for k, v in results["fp64_native"]["stages"].items()}},
             "stages_fp32_mixed": head["stages"],
             "fp32_mixed_other_cutoffs": by_q,
+            "by_call": by_call,
             "inverse": inverse_line,
             "e2e": e2e}
 
