@@ -93,3 +93,22 @@ def test_argument_errors(lib):
     assert lib.sgl_nfft_error_bound(8, KB, 17, ctypes.c_double(2.0), ctypes.byref(b)) == 1
     assert lib.sgl_choose_cutoff(8, KB, ctypes.c_double(2.0), ctypes.c_double(0.0), ctypes.byref(q)) == 1
     assert lib.sgl_choose_cutoff(8, GAUSS, ctypes.c_double(2.0), ctypes.c_double(1e-300), ctypes.byref(q)) == 6
+
+
+def test_bound_is_attained_by_the_worst_single_frequency():
+    # not vacuous: over the single coefficient vectors e_k (k on axis 0, 0 on the others), the
+    # oracle's 3-D NFFT at many points shows an error of at least half of axis 0's term of the
+    # bound (the axes at k = 0 add next to nothing), and never more than the whole bound
+    n, sigma, q, window = (8, 6, 6), 2.0, 3, "kb"
+    e0 = nfft.single_frequency_error(int(round(sigma * n[0])), n[0], n[0] // 2, q, window)
+    t = np.random.default_rng(9).uniform(0, 2 * math.pi, (4000, 3))
+    om = np.zeros(n, complex)
+    worst = 0.0
+    for k in range(-(n[0] // 2), n[0] // 2):
+        om[:] = 0
+        om[k + n[0] // 2, n[1] // 2, n[2] // 2] = 1.0
+        worst = max(worst, float(np.abs(nfft.nfft(om, t, sigma, q, window) - np.exp(1j * k * t[:, 0])).max()))
+    b = 1.0
+    for d in range(3):
+        b *= 1.0 + nfft.single_frequency_error(int(round(sigma * n[d])), n[d], n[d] // 2, q, window)
+    assert 0.5 * e0 <= worst <= b - 1.0
