@@ -228,7 +228,9 @@ sgl_status sgl_midpoint_guess(sgl_plan *plan, const double *vals_dev, const doub
  * x_j = f + q - 1 - j, and bound = prod_d (1 + e_d) - 1 (the three axes' factors multiply).  This
  * is the quantity the paper's theorem on the NFFT error bounds for the Gaussian window (aliasing
  * plus truncation), evaluated for the plan's own window, q, oversampled grid sizes and frequency
- * ranges.  Host computation, no GPU needed (except sgl_eta_l1).
+ * ranges.  It bounds the approximation in exact arithmetic, with the maximum over f taken on
+ * the 128 sampled positions; the rounding of the plan's precision comes on top (FP32-mixed:
+ * about 1e-7 relative).  Host computation, no GPU needed (except sgl_eta_l1).
  *
  * sgl_nfft_error_bound: the bound for a plan that sgl_plan_create(B, ..., window, q, sigma)
  *   would make.  Errors: SGL_ERR_ARG for parameters sgl_plan_create rejects.
