@@ -119,6 +119,7 @@ sgl_status sgl_batch_create(sgl_batch **out, int n, const int *B, const int64_t 
     if (n < 1 || n > 65536) return sgl::set_error(SGL_ERR_ARG, "n must be in [1, 65536]");
     if (!B || !M_max) return sgl::set_error(SGL_ERR_ARG, "B and M_max arrays must not be NULL");
     if (flags & SGL_FLAG_PROFILE) return sgl::set_error(SGL_ERR_ARG, "batches do not take SGL_FLAG_PROFILE");
+    if (flags & SGL_FLAG_OVERLAP_POINTS) return sgl::set_error(SGL_ERR_ARG, "batches do not take SGL_FLAG_OVERLAP_POINTS");
     sgl_batch *b = new (std::nothrow) sgl_batch();
     if (!b) return sgl::set_error(SGL_ERR_ALLOC, "host allocation failed");
     b->n = n;

@@ -38,22 +38,50 @@ struct Profiler {
     }
 };
 
-// RAII scope: records a start event on construction and an end event on destruction.
+// RAII scope: records a start event on construction and an end event on destruction, on the
+// plan's stream or on the stream the stage runs on.
 struct StageScope {
     sgl_plan *p;
     int stage;
+    cudaStream_t s;
     cudaEvent_t a = nullptr;
-    StageScope(sgl_plan *pl, int st) : p(pl), stage(st) {
-        if (p->prof) { a = p->prof->take(); cudaEventRecord(a, p->stream); }
+    StageScope(sgl_plan *pl, int st) : StageScope(pl, st, pl->stream) {}
+    StageScope(sgl_plan *pl, int st, cudaStream_t str) : p(pl), stage(st), s(str) {
+        if (p->prof) { a = p->prof->take(); cudaEventRecord(a, s); }
     }
     ~StageScope() {
         if (p->prof && a) {
             cudaEvent_t b = p->prof->take();
-            cudaEventRecord(b, p->stream);
+            cudaEventRecord(b, s);
             p->prof->open.push_back({a, b, stage});
         }
     }
 };
+
+bool capturing(cudaStream_t s) {
+    cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+    return cudaStreamIsCapturing(s, &st) == cudaSuccess && st != cudaStreamCaptureStatusNone;
+}
+
+// Orders the plan's stream after the binning forked by the last sgl_set_points.  Inside a stream
+// capture the wait becomes an external-event node of the graph (the binning ran outside it).
+cudaError_t join_points(sgl_plan *p) {
+    if (!p->bins_pending) return cudaSuccess;
+    const bool cap = capturing(p->stream);
+    cudaError_t e = cudaStreamWaitEvent(p->stream, p->ev_bins, cap ? cudaEventWaitExternal : 0);
+    if (e == cudaSuccess && !cap) p->bins_pending = false;   // a captured wait orders only the graph
+    return e;
+}
+
+void release_side(sgl_plan *p) {
+    if (p->side) cudaStreamSynchronize(p->side);
+    if (p->ev_fork) cudaEventDestroy(p->ev_fork);
+    if (p->ev_bins) cudaEventDestroy(p->ev_bins);
+    if (p->side) cudaStreamDestroy(p->side);
+    p->side = nullptr;
+    p->ev_fork = p->ev_bins = nullptr;
+    p->bins_pending = false;
+}
 
 sgl_status set_error(sgl_status code, const std::string &msg) {
     g_last_error = msg;
@@ -405,7 +433,7 @@ sgl_status plan_create_impl(sgl_plan **out, int B, int64_t M_max, int precision,
     if (window != SGL_WIN_KB && window != SGL_WIN_GAUSS) return set_error(SGL_ERR_ARG, "unknown window");
     if (q < 1 || q > kMaxQ) return set_error(SGL_ERR_ARG, "q must be in [1, 16]");
     if (!(sigma >= 1.5 && sigma <= 4.0)) return set_error(SGL_ERR_ARG, "sigma must be in [1.5, 4]");
-    if (flags & ~(SGL_FLAG_HOST_IO | SGL_FLAG_PROFILE | SGL_FLAG_SIMT | SGL_FLAG_TC | SGL_FLAG_NATIVE_FP64))
+    if (flags & ~(SGL_FLAG_HOST_IO | SGL_FLAG_PROFILE | SGL_FLAG_SIMT | SGL_FLAG_TC | SGL_FLAG_NATIVE_FP64 | SGL_FLAG_OVERLAP_POINTS))
         return set_error(SGL_ERR_ARG, "unknown flag bits");
     if ((flags & SGL_FLAG_SIMT) && (flags & SGL_FLAG_TC)) return set_error(SGL_ERR_ARG, "SGL_FLAG_SIMT and SGL_FLAG_TC exclude each other");
 
@@ -423,6 +451,7 @@ sgl_status plan_create_impl(sgl_plan **out, int B, int64_t M_max, int precision,
     const int nsz[3] = {4 * B, 2 * B, 2 * B};
     const int Ksz[3] = {p->K0, p->K1, p->K1};
     auto fail = [&](sgl_status st, const std::string &m) {
+        release_side(p);
         h->alloc.release();
         delete p->prof;
         delete h;
@@ -579,6 +608,12 @@ sgl_status plan_create_impl(sgl_plan **out, int B, int64_t M_max, int precision,
         if ((e = upload(b.wtab, wt, p->stream)) != cudaSuccess) return fail(SGL_ERR_CUDA, "upload window tables");
     }
     if ((e = cudaMemsetAsync(b.dev_flags, 0, sizeof(int), p->stream)) != cudaSuccess) return fail(SGL_ERR_CUDA, "memset");
+    if ((flags & SGL_FLAG_OVERLAP_POINTS) && !shared) {   // the plans of a batch bin on the batch stream
+        e = cudaStreamCreateWithFlags(&p->side, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_bins, cudaEventDisableTiming);
+        if (e != cudaSuccess) return fail(SGL_ERR_CUDA, std::string("binning stream: ") + cudaGetErrorString(e));
+    }
     // the host vectors above are released on return: wait for the copies
     if ((e = cudaStreamSynchronize(p->stream)) != cudaSuccess) return fail(SGL_ERR_CUDA, std::string("plan upload: ") + cudaGetErrorString(e));
     *out = p;
@@ -613,7 +648,9 @@ sgl_status sgl_plan_create(sgl_plan **out, int B, int64_t M_max, int precision, 
 void sgl_plan_destroy(sgl_plan *plan) {
     if (!plan) return;
     PlanHolder *h = holder_of(plan);
+    join_points(plan);
     cudaStreamSynchronize(plan->stream);
+    release_side(plan);
     delete plan->prof;
     inverse_work_free(plan);
     h->alloc.release();
@@ -645,10 +682,28 @@ sgl_status sgl_set_points(sgl_plan *plan, const double *xyz_dev, int64_t M) {
     if (sgl_status s = check_plan(plan)) return s;
     if (M < 0 || M > plan->M_max) return set_error(SGL_ERR_ARG, "M must be in [0, M_max]");
     if (M > 0 && (!xyz_dev || !aligned8(xyz_dev))) return set_error(SGL_ERR_ARG, "xyz must be a non-NULL, 8-byte aligned device pointer");
-    cudaError_t e;
-    {
-        StageScope sc(plan, ST_POINTS);
-        e = launch_points(plan, xyz_dev, M);
+    // rho on the plan's stream (after the previous binning, which still reads it).  With
+    // SGL_FLAG_OVERLAP_POINTS the binning then runs on the plan's binning stream, after everything
+    // already on the plan's stream, so that it overlaps the conversions and the FFT of the next
+    // forward; it reads a copy of the points in plan memory (u_sorted is rewritten only by its
+    // own scatter), so the caller may reuse xyz in stream order.  In a stream capture it stays
+    // on the plan's stream.
+    cudaError_t e = join_points(plan);
+    const bool fork = plan->side && !capturing(plan->stream);
+    if (e == cudaSuccess) {
+        StageScope sc(plan, ST_POINTS);   // from rho to the end of the binning
+        e = launch_points_rho(plan, xyz_dev, M, fork ? plan->b.u_sorted : nullptr);
+        if (e == cudaSuccess && fork) {
+            e = cudaEventRecord(plan->ev_fork, plan->stream);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(plan->side, plan->ev_fork, 0);
+            if (e == cudaSuccess) {
+                plan->bins_pending = true;
+                sc.s = plan->side;
+            }
+        }
+        if (e == cudaSuccess)
+            e = launch_points_bins(plan, fork ? plan->b.u_sorted : xyz_dev, M, fork ? plan->side : plan->stream);
+        if (e == cudaSuccess && fork) e = cudaEventRecord(plan->ev_bins, plan->side);
     }
     if (e != cudaSuccess) return launch_status(e, "set_points");
     {
@@ -703,6 +758,7 @@ sgl_status sgl_forward(sgl_plan *plan, const double *coef_dev, double *vals_dev)
     if (plan->M == 0) return ok();
     if (sgl_status s = coef_to_zeta(plan, coef_dev)) return s;
     if (sgl_status s = zeta_to_grid(plan)) return s;
+    SGL_CUDA_TRY(join_points(plan));
     StageScope sc(plan, ST_INTERP);
     return launch_status(launch_interp(plan, (double2 *)vals_dev), "interpolation");
 }
@@ -718,7 +774,8 @@ sgl_status sgl_adjoint(sgl_plan *plan, const double *vals_dev, double *coef_dev)
     }
     const Axis &A0 = plan->ax[0], &A1 = plan->ax[1], &A2 = plan->ax[2];
     const size_t csz = plan->prec == SGL_FP32_MIXED ? sizeof(float2) : sizeof(double2);
-    cudaError_t e;
+    cudaError_t e = join_points(plan);
+    if (e != cudaSuccess) return launch_status(e, "spreading");
     {
         StageScope sc(plan, ST_SPREAD);
         e = cudaMemsetAsync(plan->b.bufA, 0, (size_t)A0.rows * A1.rows * A2.N * csz, plan->stream);
@@ -748,6 +805,7 @@ sgl_status sgl_grad_points(sgl_plan *plan, const double *coef_dev, const double 
     if (plan->M == 0) return ok();
     if (sgl_status s = coef_to_zeta(plan, coef_dev)) return s;
     if (sgl_status s = zeta_to_grid(plan)) return s;
+    SGL_CUDA_TRY(join_points(plan));
     StageScope sc(plan, ST_GRAD);
     return launch_status(launch_grad(plan, (const double2 *)gout_dev, gxyz_dev, nullptr), "gradient interpolation");
 }
@@ -762,6 +820,7 @@ sgl_status sgl_forward_grad(sgl_plan *plan, const double *coef_dev, const double
     if (plan->M == 0) return ok();
     if (sgl_status s = coef_to_zeta(plan, coef_dev)) return s;
     if (sgl_status s = zeta_to_grid(plan)) return s;
+    SGL_CUDA_TRY(join_points(plan));
     StageScope sc(plan, ST_GRAD);
     return launch_status(launch_grad(plan, (const double2 *)gout_dev, gxyz_dev, (double2 *)vals_dev),
                          "gradient interpolation");
@@ -829,6 +888,7 @@ const char *sgl_stage_name(int stage) {
 sgl_status sgl_profile(sgl_plan *plan, double *ms_out, int64_t *count_out) {
     if (sgl_status s = check_plan(plan)) return s;
     if (!plan->prof) return set_error(SGL_ERR_STATE, "plan was created without SGL_FLAG_PROFILE");
+    SGL_CUDA_TRY(join_points(plan));
     SGL_CUDA_TRY(cudaStreamSynchronize(plan->stream));
     double ms[ST_COUNT] = {0};
     int64_t cnt[ST_COUNT] = {0};
@@ -939,6 +999,7 @@ sgl_status sgl_eta_l1(sgl_plan *plan, const double *coef_dev, double *l1) {
 
 sgl_status sgl_sync(sgl_plan *plan) {
     if (sgl_status s = check_plan(plan)) return s;
+    SGL_CUDA_TRY(join_points(plan));
     SGL_CUDA_TRY(cudaStreamSynchronize(plan->stream));
     int flagsv = 0;
     SGL_CUDA_TRY(cudaMemcpy(&flagsv, plan->b.dev_flags, sizeof(int), cudaMemcpyDeviceToHost));

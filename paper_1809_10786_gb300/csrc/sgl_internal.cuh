@@ -148,6 +148,12 @@ struct sgl_plan {
     sgl::Profiler *prof;    // non-NULL with SGL_FLAG_PROFILE
     sgl::InverseWork *inv;  // allocated by the first sgl_inverse / sgl_midpoint_guess
     cudaStream_t stream;
+    // Binning of the points on a plan-owned stream (SGL_FLAG_OVERLAP_POINTS; NULL otherwise):
+    // sgl_set_points forks it after everything already on `stream`; the first call that reads
+    // the bins joins it.
+    cudaStream_t side;
+    cudaEvent_t ev_fork, ev_bins;
+    bool bins_pending;
     int B, q, prec, window;
     unsigned flags;
     double sigma;
@@ -176,7 +182,10 @@ sgl_status plan_create_impl(sgl_plan **out, int B, int64_t M_max, int precision,
 sgl_status plan_work_sizes(int B, int precision, int q, double sigma, size_t *bytesA, size_t *bytesB);
 
 // ---- launchers (all asynchronous on plan->stream); return cudaGetLastError() ----
-cudaError_t launch_points(sgl_plan *p, const double *xyz, int64_t M);
+// rho on plan->stream (and, with `copy` non-NULL, a copy of the points there), then the binning
+// of the points (read from xyz) on stream s
+cudaError_t launch_points_rho(sgl_plan *p, const double *xyz, int64_t M, double *copy);
+cudaError_t launch_points_bins(sgl_plan *p, const double *xyz, int64_t M, cudaStream_t s);
 cudaError_t launch_radial_matrices(sgl_plan *p);
 cudaError_t launch_radial_forward(sgl_plan *p, const double2 *coef);
 cudaError_t launch_polar_forward(sgl_plan *p);

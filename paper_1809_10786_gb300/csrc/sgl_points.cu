@@ -10,12 +10,15 @@ namespace {
 
 constexpr int kThreads = 256;
 
+// rho^2 = max |x|^2 over the finite points; with `copy` non-NULL the points are also copied there
 __global__ void k_max_radius(const double *__restrict__ xyz, int64_t M,
-                             unsigned long long *__restrict__ r2max, int *__restrict__ flags) {
+                             unsigned long long *__restrict__ r2max, int *__restrict__ flags,
+                             double *__restrict__ copy) {
     double best = 0.0;
     bool bad = false;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < M; i += (int64_t)gridDim.x * blockDim.x) {
         const double x = xyz[3 * i], y = xyz[3 * i + 1], z = xyz[3 * i + 2];
+        if (copy) { copy[3 * i] = x; copy[3 * i + 1] = y; copy[3 * i + 2] = z; }
         if (!(isfinite(x) && isfinite(y) && isfinite(z))) { bad = true; continue; }
         best = fmax(best, x * x + y * y + z * z);
     }
@@ -228,13 +231,20 @@ int grid_blocks(int64_t work, int threads) {
 
 }  // namespace
 
-cudaError_t launch_points(sgl_plan *p, const double *xyz, int64_t M) {
-    Buffers &b = p->b;
-    cudaStream_t s = p->stream;
+cudaError_t launch_points_rho(sgl_plan *p, const double *xyz, int64_t M, double *copy) {
     cudaError_t e;
-    if ((e = cudaMemsetAsync(b.r2max, 0, sizeof(unsigned long long), s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(p->b.r2max, 0, sizeof(unsigned long long), p->stream)) != cudaSuccess) return e;
+    if (M > 0) {
+        k_max_radius<<<grid_blocks(M, kThreads), kThreads, 0, p->stream>>>(xyz, M, p->b.r2max, p->b.dev_flags, copy);
+        p->launches += 1;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_points_bins(sgl_plan *p, const double *xyz, int64_t M, cudaStream_t s) {
+    Buffers &b = p->b;
+    cudaError_t e;
     if ((e = cudaMemsetAsync(b.bin_count, 0, sizeof(int) * p->nbins, s)) != cudaSuccess) return e;
-    if (M > 0) { k_max_radius<<<grid_blocks(M, kThreads), kThreads, 0, s>>>(xyz, M, b.r2max, b.dev_flags); p->launches += 1; }
     PointGeom g;
     for (int d = 0; d < 3; ++d) g.N[d] = p->ax[d].N;
     g.S2 = p->bins.S2;
@@ -263,7 +273,7 @@ cudaError_t launch_points(sgl_plan *p, const double *xyz, int64_t M) {
 }
 
 cudaError_t launch_max_radius_raw(cudaStream_t s, const double *xyz, int64_t M, unsigned long long *r2max, int *flags) {
-    if (M > 0) k_max_radius<<<grid_blocks(M, kThreads), kThreads, 0, s>>>(xyz, M, r2max, flags);
+    if (M > 0) k_max_radius<<<grid_blocks(M, kThreads), kThreads, 0, s>>>(xyz, M, r2max, flags, nullptr);
     return cudaGetLastError();
 }
 

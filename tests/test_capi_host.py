@@ -60,7 +60,7 @@ def test_plan_create_rejects_bad_arguments_without_cuda(lib, args, word):
     assert word in lib.sgl_last_error().decode()
 
 
-@pytest.mark.parametrize("flags,word", [(32, "flag"), (1 << 31, "flag"), (4 | 8, "SGL_FLAG_SIMT")])
+@pytest.mark.parametrize("flags,word", [(64, "flag"), (1 << 31, "flag"), (4 | 8, "SGL_FLAG_SIMT")])
 def test_plan_create_rejects_bad_flags_without_cuda(lib, flags, word):
     h = ctypes.c_void_p(123)
     st = lib.sgl_plan_create(ctypes.byref(h), 8, 10, 1, 0, 8, 2.0, flags, None)
@@ -91,5 +91,7 @@ def test_batch_create_rejects_bad_arguments_without_cuda(lib):
     assert lib.sgl_batch_create(ctypes.byref(h), 2, bad, Ms, 0, 0, 8, 2.0, 0, None) == 1
     assert "instance 1" in lib.sgl_last_error().decode()
     assert lib.sgl_batch_create(ctypes.byref(h), 2, Bs, Ms, 0, 0, 8, 2.0, 2, None) == 1     # profiling flag
+    assert lib.sgl_batch_create(ctypes.byref(h), 2, Bs, Ms, 0, 0, 8, 2.0, 32, None) == 1    # overlapped binning
+    assert "SGL_FLAG_OVERLAP_POINTS" in lib.sgl_last_error().decode()
     assert lib.sgl_batch_forward(None, None, None) == 1
     lib.sgl_batch_destroy(None)

@@ -1,0 +1,101 @@
+"""Stream order of the overlapped points binning, SGL_FLAG_OVERLAP_POINTS (marked gpu).
+
+With the flag, sgl_set_points computes rho on the plan's stream and bins the points on a
+plan-owned stream, so that the binning overlaps the conversions and the FFT of the next call.
+These tests check that the overlap is invisible to the caller: every call gives what a plan that
+binned the same points in plain stream order gives, the caller may overwrite the points right
+after set_points, and the stage timings still count one points stage per call.
+"""
+import numpy as np
+import pytest
+import torch
+
+import paper_1809_10786_gb300 as sgl
+from paper_1809_10786_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+DEV = torch.device("cuda", 0)
+
+
+def rel(a, b):
+    return float((a - b).abs().max() / b.abs().max())
+
+
+def gpu(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+
+
+def plan(B, M, prec=sgl.PREC_FP32_MIXED, **kw):
+    return sgl.Plan(B, M, precision=prec, window=sgl.WIN_KB, q=8, sigma=2.0, overlap_points=True, **kw)
+
+
+def batch_reference(B, M, prec, x, kind, arg):
+    """The same transform from a batch of one: its plans bin on the batch stream itself."""
+    bp = sgl.BatchPlan([B], [M], precision=prec, window=sgl.WIN_KB, q=8, sigma=2.0)
+    bp.set_points([x])
+    out = bp.forward([arg]) if kind == "forward" else bp.adjoint([arg])
+    torch.cuda.synchronize()
+    return out[0]
+
+
+@pytest.mark.parametrize("prec,tol", [(sgl.PREC_FP32_MIXED, 1e-5), (sgl.PREC_FP64, 1e-11)])
+def test_points_may_be_overwritten_right_after_set_points(prec, tol):
+    B, M = 32, 1_000_000
+    c = gpu(inputs.coefficients(B, 7100))
+    x = gpu(inputs.points_gaussian(M, 7101))
+    x0 = x.clone()
+    p = plan(B, M, prec)
+    p.set_points(x)
+    x.mul_(0.25).add_(0.5)           # the caller reuses its buffer in stream order
+    f = p.forward(c)
+    torch.cuda.synchronize()
+    assert rel(f, batch_reference(B, M, prec, x0, "forward", c)) <= tol      # stale points: O(1)
+
+
+def test_consecutive_set_points_keep_the_last_points():
+    B, M = 24, 400_000
+    c = gpu(inputs.coefficients(B, 7200))
+    y = gpu(inputs.values(M, 7201))
+    x1 = gpu(inputs.points_gaussian(M, 7202))
+    x2 = gpu(inputs.points_gaussian(M, 7203))
+    p = plan(B, M)
+    p.set_points(x1)
+    p.set_points(x2)
+    a = p.adjoint(y)                 # the adjoint straight after the binning: spreading joins it
+    f = p.forward(c)
+    torch.cuda.synchronize()
+    assert rel(a, batch_reference(B, M, sgl.PREC_FP32_MIXED, x2, "adjoint", y)) <= 1e-4
+    assert rel(f, batch_reference(B, M, sgl.PREC_FP32_MIXED, x2, "forward", c)) <= 1e-5
+
+
+def test_side_stream_plan_on_a_torch_stream_and_rho():
+    B, M = 16, 300_000
+    c = gpu(inputs.coefficients(B, 7300))
+    x = gpu(inputs.points_gaussian(M, 7301))
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())      # the inputs were made on the default stream
+    p = plan(B, M)
+    with torch.cuda.stream(s):
+        p.set_points(x)
+        rho = p.rho()                # rho is known on the plan's stream before the binning ends
+        g = torch.ones(M, dtype=torch.complex128, device=DEV)
+        f, gx = p.forward_grad(c, g)
+    s.synchronize()
+    r = float(torch.sqrt((x * x).sum(1).max()))
+    assert r <= rho <= r * (1 + 2e-6)
+    assert rel(f, batch_reference(B, M, sgl.PREC_FP32_MIXED, x, "forward", c)) <= 1e-5
+    assert torch.isfinite(gx).all()
+
+
+def test_points_stage_is_timed_once_per_set_points():
+    B, M = 16, 200_000
+    x = gpu(inputs.points_gaussian(M, 7400))
+    c = gpu(inputs.coefficients(B, 7401))
+    p = plan(B, M, profile=True)
+    for _ in range(3):
+        p.set_points(x)
+        p.forward(c)
+    st = p.profile()
+    ms, n = st["points"]
+    assert n == 3 and ms > 0.0
+    assert st["interp"][1] == 3
