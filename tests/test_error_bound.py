@@ -7,7 +7,9 @@ Pins: agreement with the oracle; the paper's closed-form Gaussian bound (Thm. on
 is never below it; on the oracle's own 3-D NFFT the measured errors stay below it.
 """
 import ctypes
+import json
 import math
+import os
 
 import numpy as np
 import pytest
@@ -49,6 +51,35 @@ def test_bound_reaches_rounding_level_at_large_cutoff(lib, B):
 def test_gaussian_bound_below_the_papers_closed_form(lib, q, sigma):
     # the theorem bounds the error of every coefficient vector by C ||w||_1, with C in closed form
     assert c_bound(lib, 8, GAUSS, q, sigma) <= nfft.gauss_error_bound(3, sigma, q)
+
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "gauss_nfft_error_constant.json")
+
+
+@pytest.mark.parametrize("case", json.load(open(GOLDEN))["cases"], ids=lambda c: "d%d-s%g-q%d" % (c["d"], c["sigma"], c["q"]))
+def test_gaussian_closed_form_equals_the_theorems_constant(case):
+    # the closed form of the theorem on the d-dimensional NFFT error, evaluated by hand (golden file)
+    assert nfft.gauss_error_bound(case["d"], case["sigma"], case["q"]) == pytest.approx(case["C"], rel=1e-13)
+
+
+@pytest.mark.parametrize("d,sigma", [(1, 2.0), (2, 2.0), (3, 2.0), (3, 3.0)])
+def test_gaussian_closed_form_decay_rate_and_prefactor_limit(d, sigma):
+    # large q: the prefactor tends to (2^d - 1) 2^d and the ratio of consecutive cutoffs to
+    # e^{-pi E}, E = 1 - (1 + d / (2 sigma - 1)) / (2 sigma) -- the exponent and the constant
+    # pinned separately from the golden values
+    E = 1.0 - (1.0 + d / (2.0 * sigma - 1.0)) / (2.0 * sigma)
+    q = 200
+    ratio = nfft.gauss_error_bound(d, sigma, q + 1) / nfft.gauss_error_bound(d, sigma, q)
+    assert math.log(ratio) == pytest.approx(-math.pi * E, abs=2e-4)
+    pref = nfft.gauss_error_bound(d, sigma, q) * math.exp(q * math.pi * E)
+    # corrections at finite q: (1 + 1/(2 pi q))^d - 1 from the first term, O(q^{-d/2}) from the second
+    tol = 1.2 * d / (2 * math.pi * q) + 1.5 * (3 ** d - 1) / ((2 ** d - 1) * 2 ** d) * q ** (-d / 2)
+    assert pref == pytest.approx((2 ** d - 1) * 2 ** d, rel=tol)
+
+
+def test_gaussian_closed_form_rejects_small_oversampling():
+    with pytest.raises(ValueError):
+        nfft.gauss_error_bound(3, 1.3, 8)
 
 
 def test_bound_holds_for_the_oracle_nfft():
