@@ -293,19 +293,25 @@ const char *sgl_stage_name(int stage);
  * same eta as sgl_trig_coeffs for the points xyz_dev (rho = max |x_i| with the same
  * 2^-20 margin) without allocating: no cudaMalloc, no cudaFree, no allocating library
  * routine.  Its scratch is one static device array sized for B <= SGL_NOALLOC_MAX_B
- * (about 4.9 MB), which every GPU that loads the library holds until process exit.
+ * (about 6.9 MB, the conversion tables of every such B included), which every GPU that
+ * loads the library holds until process exit.
  *   B: 1 <= B <= SGL_NOALLOC_MAX_B, otherwise SGL_ERR_ARG with a message naming the limit.
- *   xyz_dev [M][3] double (device, M >= 0); coef_dev complex128 [Nc] (device);
- *   eta_dev complex128 [4B-3][2B-1][2B-1] (device), layout as in sgl_trig_coeffs.
+ *   xyz_dev [M][3] double (device, M >= 0; M = 0 gives rho = 1); coef_dev complex128 [Nc]
+ *   (device); eta_dev complex128 [4B-3][2B-1][2B-1] (device), layout as in sgl_trig_coeffs.
  *   cuda_stream: the stream the work is issued on (asynchronous, like the plan calls).
  * Set-up: the first call on a device looks up the scratch array's device address on the
- * current device (once per device); make that first call before capturing a stream.
+ * current device, copies the conversion tables (built once per process in host static
+ * storage) into the array on cuda_stream and synchronizes that stream.  That first call
+ * returns SGL_ERR_STATE inside a stream capture: make it before capturing.  Later calls
+ * issue one memset and the conversion kernels only.
  * All calls share the one scratch array, which keeps the last call's contents (the
  * reduction cell is cleared by each call): calls that overlap on the GPU -- on different
  * streams, or from different host threads -- race on it and must be serialized by the caller.
  * Non-finite coordinates are left out of rho and not reported.
+ * sgl_noalloc_max_b() returns SGL_NOALLOC_MAX_B of the loaded library.
  */
 #define SGL_NOALLOC_MAX_B 32
+int sgl_noalloc_max_b(void);
 sgl_status sgl_trig_coeffs_noalloc(int B, const double *xyz_dev, int64_t M, const double *coef_dev,
                                    double *eta_dev, void *cuda_stream);
 

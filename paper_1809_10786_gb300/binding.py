@@ -99,6 +99,8 @@ def load_library(build_if_missing=True):
             f = getattr(lib, name)
             f.restype = ctypes.c_int
             f.argtypes = args
+        lib.sgl_noalloc_max_b.restype = ctypes.c_int
+        lib.sgl_noalloc_max_b.argtypes = []
         lib.sgl_stage_name.restype = ctypes.c_char_p
         lib.sgl_stage_name.argtypes = [ctypes.c_int]
         _LIB = lib
@@ -410,13 +412,15 @@ class BatchPlan:
         _check(self.lib.sgl_batch_sync(self._h))
 
 
-NOALLOC_MAX_B = 32
+def noalloc_max_b():
+    """The largest B sgl_trig_coeffs_noalloc accepts (its static scratch limit), from the library."""
+    return int(load_library().sgl_noalloc_max_b())
 
 
 def trig_coeffs_noalloc(B, xyz, coef, out=None):
     """eta for points xyz and coefficients coef without any device allocation by the library
-    (sgl_trig_coeffs_noalloc; B <= 32).  Tensors on the current CUDA device; the output
-    tensor may be passed in so that no allocation happens on this side either."""
+    (sgl_trig_coeffs_noalloc; B <= noalloc_max_b()).  Tensors on the current CUDA device; the
+    output tensor may be passed in so that no allocation happens on this side either."""
     lib = load_library()
     dev = xyz.device
     xyz = _dev_tensor(xyz, torch.float64, (xyz.shape[0], 3), "xyz", dev)
