@@ -281,8 +281,8 @@ double error_bound_of(int window, const int N[3], const int n[3], const int K[3]
 //   Pbar_mm = -sqrt((2m+1)/(2m)) sin Pbar_{m-1,m-1},  Pbar_{m+1,m} = sqrt(2m+3) x Pbar_mm,
 //   Pbar_lm = a_lm (x Pbar_{l-1,m} - b_lm Pbar_{l-2,m}),
 //   a_lm = sqrt((4l^2-1)/(l^2-m^2)),  b_lm = sqrt(((l-1)^2-m^2)/(4(l-1)^2-1)).
-void legendre_normalized(int B, double x, double sn, std::vector<double> &out) {
-    out.assign((size_t)B * B, 0.0);
+void legendre_normalized(int B, double x, double sn, double *out) {
+    std::fill(out, out + (size_t)B * B, 0.0);
     double pmm = 1.0 / std::sqrt(4.0 * kPi);
     for (int m = 0; m < B; ++m) {
         if (m > 0) pmm *= -std::sqrt((2.0 * m + 1.0) / (2.0 * m)) * sn;
@@ -296,36 +296,39 @@ void legendre_normalized(int B, double x, double sn, std::vector<double> &out) {
     }
 }
 
+}  // namespace
+
 // Polar conversion matrices (Sect. 6, spherical subtransform; Thm. on the factorization):
 // for m >= 0, kappa1 = 0..K1, l = m..B-1, with w_j = (2j+1) pi / (4B), j < 2B:
 //  m even: P[m][k][l] = (1/2B) sum_j cos(k w_j) Pbar_lm(cos w_j)       (DCT, then Chebyshev -> exponential)
 //  m odd:  eps_k = (c_k/2B) sum_j cos(k w_j) Pbar_lm(cos w_j) / sin w_j  (c_0 = 1, c_k = 2; V_B weighting)
 //          zeta_k = (1/4i) {2eps_0 - eps_2 (k=1); eps_{k-1} - eps_{k+1} (1<k<2B-2); eps_{k-1} (k >= 2B-2)}
 //          and P[m][k][l] holds the real factor 4i zeta_k / 4 (the kernels apply the -i).
-// The matrices for -m are (-1)^m times those for m.
-void polar_matrices(int B, std::vector<double> &P) {
+// The matrices for -m are (-1)^m times those for m.  Also the cosine table cos(m pi / 4B), m < 8B.
+// No heap use (the allocation-free entry point builds its tables in static storage).
+void conversion_tables(int B, double *P, double *costab, double *leg) {
+    constexpr int kMaxB2 = 2 * 128;
     const int K1 = B - 1, n2 = 2 * B;
-    P.assign((size_t)B * (K1 + 1) * B, 0.0);
-    std::vector<std::vector<double>> leg(n2);
-    std::vector<double> w(n2);
+    std::fill(P, P + (size_t)B * (K1 + 1) * B, 0.0);
+    double w[kMaxB2], eps[kMaxB2 + 2];
     for (int j = 0; j < n2; ++j) {
         w[j] = (2.0 * j + 1.0) * kPi / (4.0 * B);
-        legendre_normalized(B, std::cos(w[j]), std::sin(w[j]), leg[j]);
+        legendre_normalized(B, std::cos(w[j]), std::sin(w[j]), leg + (size_t)j * B * B);
     }
-    std::vector<double> eps(n2 + 2);
     for (int m = 0; m < B; ++m) {
         for (int l = m; l < B; ++l) {
             if (m % 2 == 0) {
                 for (int k = 0; k <= K1; ++k) {
                     long double s = 0.0L;
-                    for (int j = 0; j < n2; ++j) s += (long double)std::cos(k * w[j]) * leg[j][(size_t)l * B + m];
+                    for (int j = 0; j < n2; ++j) s += (long double)std::cos(k * w[j]) * leg[((size_t)j * B + l) * B + m];
                     P[((size_t)m * (K1 + 1) + k) * B + l] = (double)(s / n2);
                 }
             } else {
-                std::fill(eps.begin(), eps.end(), 0.0);
+                std::fill(eps, eps + n2 + 2, 0.0);
                 for (int k = 0; k < n2; ++k) {
                     long double s = 0.0L;
-                    for (int j = 0; j < n2; ++j) s += (long double)std::cos(k * w[j]) * leg[j][(size_t)l * B + m] / std::sin(w[j]);
+                    for (int j = 0; j < n2; ++j)
+                        s += (long double)std::cos(k * w[j]) * leg[((size_t)j * B + l) * B + m] / std::sin(w[j]);
                     eps[k] = (double)(s * (k == 0 ? 1.0L : 2.0L) / n2);
                 }
                 for (int k = 1; k <= K1; ++k) {
@@ -338,18 +341,26 @@ void polar_matrices(int B, std::vector<double> &P) {
             }
         }
     }
+    for (int m = 0; m < 8 * B; ++m)
+        costab[m] = (double)cosl((long double)m * 3.14159265358979323846264338327950288L / (4.0L * B));
 }
 
-// P_m depends on B only: computed once per B per process and reused by every plan
-const std::vector<double> &cached_polar_matrices(int B) {
+namespace {
+
+// P_m and the cosine table depend on B only: computed once per B per process and reused by every plan
+struct ConvTables { std::vector<double> P, costab; };
+const ConvTables &cached_conversion_tables(int B) {
     static std::mutex mu;
-    static std::map<int, std::vector<double>> cache;
+    static std::map<int, ConvTables> cache;
     std::lock_guard<std::mutex> lock(mu);
     auto it = cache.find(B);
     if (it == cache.end()) {
-        std::vector<double> P;
-        polar_matrices(B, P);
-        it = cache.emplace(B, std::move(P)).first;
+        ConvTables t;
+        t.P.resize((size_t)B * B * B);
+        t.costab.resize((size_t)8 * B);
+        std::vector<double> leg((size_t)2 * B * B * B);
+        conversion_tables(B, t.P.data(), t.costab.data(), leg.data());
+        it = cache.emplace(B, std::move(t)).first;
     }
     return it->second;
 }
@@ -524,6 +535,7 @@ sgl_status plan_create_impl(sgl_plan **out, int B, int64_t M_max, int precision,
         Axis &a = p->ax[d];
         ALLOC(a.tw_d, (size_t)a.N);
         ALLOC(a.tw_f, (size_t)a.N);
+        ALLOC(a.tw_df, (size_t)a.N);
         ALLOC(a.rev, (size_t)a.N);
         ALLOC(a.deconv, (size_t)(2 * a.K + 1));
     }
@@ -546,6 +558,7 @@ sgl_status plan_create_impl(sgl_plan **out, int B, int64_t M_max, int precision,
     ALLOC(b.work_len, 2);
     ALLOC(b.df_max, 2);
     ALLOC(b.scalar, 1);
+    ALLOC(b.sched, 4);
     ALLOC(b.wtab, (size_t)kWinTab);
     if (flags & SGL_FLAG_HOST_IO) {
         ALLOC(b.io_xyz, 3 * Mc);
@@ -565,9 +578,8 @@ sgl_status plan_create_impl(sgl_plan **out, int B, int64_t M_max, int precision,
     if (flags & SGL_FLAG_PROFILE) p->prof = new (std::nothrow) Profiler();
 
     // ---- host precompute (FP64) and upload
-    const std::vector<double> &P = cached_polar_matrices(B);
-    std::vector<double> costab(8 * B);
-    for (int m = 0; m < 8 * B; ++m) costab[m] = (double)cosl((long double)m * 3.14159265358979323846264338327950288L / (4.0L * B));
+    const ConvTables &ct = cached_conversion_tables(B);
+    const std::vector<double> &P = ct.P, &costab = ct.costab;
     std::vector<double> dec[3];
     for (int d = 0; d < 3; ++d) {
         Axis &a = p->ax[d];
@@ -576,10 +588,14 @@ sgl_status plan_create_impl(sgl_plan **out, int B, int64_t M_max, int precision,
             dec[d][k + a.K] = 1.0 / window_hat(window, 2.0 * kPi * k / a.N, (double)q, a.wpar);
         std::vector<double2> twd(a.N);
         std::vector<float2> twf(a.N);
+        std::vector<float4> twdf(a.N);
         for (int m = 0; m < a.N; ++m) {
             const long double ang = 2.0L * 3.14159265358979323846264338327950288L * m / a.N;
-            twd[m] = make_double2((double)cosl(ang), (double)sinl(ang));
+            const long double c = cosl(ang), sn = sinl(ang);
+            twd[m] = make_double2((double)c, (double)sn);
             twf[m] = make_float2((float)twd[m].x, (float)twd[m].y);
+            const float ch = (float)c, sh = (float)sn;
+            twdf[m] = make_float4(ch, (float)(c - (long double)ch), sh, (float)(sn - (long double)sh));
         }
         std::vector<int> rev(a.N);
         for (int k = 0; k < a.N; ++k) {
@@ -593,6 +609,7 @@ sgl_status plan_create_impl(sgl_plan **out, int B, int64_t M_max, int precision,
         }
         if ((e = upload(a.tw_d, twd, p->stream)) != cudaSuccess) return fail(SGL_ERR_CUDA, "upload twiddles");
         if ((e = upload(a.tw_f, twf, p->stream)) != cudaSuccess) return fail(SGL_ERR_CUDA, "upload twiddles");
+        if ((e = upload(a.tw_df, twdf, p->stream)) != cudaSuccess) return fail(SGL_ERR_CUDA, "upload twiddles");
         if ((e = upload(a.rev, rev, p->stream)) != cudaSuccess) return fail(SGL_ERR_CUDA, "upload digit reversal");
         if ((e = upload(a.deconv, dec[d], p->stream)) != cudaSuccess) return fail(SGL_ERR_CUDA, "upload deconvolution");
     }
@@ -693,24 +710,37 @@ sgl_status sgl_set_points(sgl_plan *plan, const double *xyz_dev, int64_t M) {
     if (e == cudaSuccess) {
         StageScope sc(plan, ST_POINTS);   // from rho to the end of the binning
         e = launch_points_rho(plan, xyz_dev, M, fork ? plan->b.u_sorted : nullptr);
+        bool forked = false;
         if (e == cudaSuccess && fork) {
             e = cudaEventRecord(plan->ev_fork, plan->stream);
             if (e == cudaSuccess) e = cudaStreamWaitEvent(plan->side, plan->ev_fork, 0);
             if (e == cudaSuccess) {
-                plan->bins_pending = true;
+                forked = true;
                 sc.s = plan->side;
             }
         }
         if (e == cudaSuccess)
             e = launch_points_bins(plan, fork ? plan->b.u_sorted : xyz_dev, M, fork ? plan->side : plan->stream);
         if (e == cudaSuccess && fork) e = cudaEventRecord(plan->ev_bins, plan->side);
+        // the join waits on ev_bins: only a recorded event may be waited on; after a failure past
+        // the fork, drain the side stream and leave the plan without points
+        if (e == cudaSuccess && fork) plan->bins_pending = true;
+        if (e != cudaSuccess && forked) cudaStreamSynchronize(plan->side);
     }
-    if (e != cudaSuccess) return launch_status(e, "set_points");
+    if (e != cudaSuccess) {
+        plan->points_set = false;
+        plan->M = 0;
+        return launch_status(e, "set_points");
+    }
     {
         StageScope sc(plan, ST_RADIAL_MATRIX);
         e = launch_radial_matrices(plan);
     }
-    if (e != cudaSuccess) return launch_status(e, "radial matrices");
+    if (e != cudaSuccess) {
+        plan->points_set = false;
+        plan->M = 0;
+        return launch_status(e, "radial matrices");
+    }
     plan->M = M;
     plan->points_set = true;
     return ok();

@@ -10,6 +10,15 @@
 // FFT (radices 8, 4, 2, 3, 5; output in digit-reversed slots), and writes the
 // L_out output positions (e + out_first) mod N.  The (sigma n)^{-d} scale and the
 // window deconvolution 1/phitilde_k are folded into per-element and per-line factors.
+//
+// FP32-mixed plans run their two radial-axis passes (pass A of the forward transform, pass A'
+// of the adjoint) in double-float arithmetic and the four angular passes in binary32.  The
+// radial DFT mixes every radius: its rounding error lands on all rows l0 alike, also at radii
+// r near rho where no point lies and the radial conversion matrices K_l (polynomials of degree
+// up to 2B - 2 in r) are largest, so the adjoint's K_l^T amplifies it (measured at B = 64, 10^6
+// points: a binary32 radial pass alone made the adjoint coefficients 2.4e-5 wrong relative to
+// their maximum; binary32 angular passes, whose errors stay on the rows of their own radius, and
+// binary32 spreading 2e-8 and 6e-8).
 #include "sgl_internal.cuh"
 
 #include <type_traits>
@@ -17,10 +26,58 @@
 namespace sgl {
 namespace {
 
+// Double-float scalar: the unevaluated sum h + l of two binary32 numbers.  Sums by TwoSum
+// (Knuth), products by TwoProduct (Dekker; exact with a fused multiply-add), each renormalized
+// by Fast2Sum: a relative rounding of about 2^-44 per operation, normwise through a DFT.  The
+// rounded intrinsics keep the compiler from fusing or reordering the error terms.
+struct dfl {
+    float h, l;
+    dfl() = default;
+    __host__ __device__ constexpr dfl(float hh, float ll) : h(hh), l(ll) {}
+    __host__ __device__ constexpr dfl(int v) : h((float)v), l(0.f) {}
+    __host__ __device__ constexpr dfl(float v) : h(v), l(0.f) {}
+    __host__ __device__ constexpr dfl(double v) : h((float)v), l((float)(v - (double)(float)v)) {}
+};
+struct dfl2 { dfl x, y; };
+__device__ __forceinline__ dfl fast_two_sum(float a, float b) {       // |a| >= |b| (else a rounding of b's size)
+    const float s = __fadd_rn(a, b);
+    return dfl(s, __fsub_rn(b, __fsub_rn(s, a)));
+}
+__device__ __forceinline__ dfl operator+(dfl a, dfl b) {
+    const float s = __fadd_rn(a.h, b.h);
+    const float bb = __fsub_rn(s, a.h);
+    const float e = __fadd_rn(__fsub_rn(a.h, __fsub_rn(s, bb)), __fsub_rn(b.h, bb));   // a.h + b.h = s + e exactly
+    return fast_two_sum(s, __fadd_rn(e, __fadd_rn(a.l, b.l)));
+}
+__device__ __forceinline__ dfl operator-(dfl a) { return dfl(-a.h, -a.l); }
+__device__ __forceinline__ dfl operator-(dfl a, dfl b) { return a + (-b); }
+__device__ __forceinline__ dfl operator*(dfl a, dfl b) {
+    const float p = __fmul_rn(a.h, b.h);
+    float e = fmaf(a.h, b.h, -p);                                      // a.h b.h = p + e exactly
+    e = fmaf(a.h, b.l, e);
+    e = fmaf(a.l, b.h, e);
+    return fast_two_sum(p, e);
+}
+// multiplication by a sign s = +1 or -1 (the transform direction)
+__device__ __forceinline__ dfl operator*(int s, dfl a) { return s > 0 ? a : -a; }
+__device__ __forceinline__ dfl operator*(dfl a, int s) { return s > 0 ? a : -a; }
+
 template <typename T> struct CT;
 template <> struct CT<float> { using type = float2; };
 template <> struct CT<double> { using type = double2; };
+template <> struct CT<dfl> { using type = dfl2; };
 template <typename T> using C2 = typename CT<T>::type;
+
+// a scalar of the pass arithmetic stored as the output type's scalar, and widened to binary64
+__device__ __forceinline__ float narrow_f(float v) { return v; }
+__device__ __forceinline__ float narrow_f(dfl v) { return __fadd_rn(v.h, v.l); }
+__device__ __forceinline__ double widen(float v) { return (double)v; }
+__device__ __forceinline__ double widen(double v) { return v; }
+__device__ __forceinline__ double widen(dfl v) { return (double)v.h + (double)v.l; }
+template <typename S, typename V> __device__ __forceinline__ S narrow(V v) {
+    if constexpr (sizeof(S) == 4) return narrow_f(v);
+    else return widen(v);
+}
 
 template <typename T> __device__ __forceinline__ C2<T> mk(T x, T y) { C2<T> r; r.x = x; r.y = y; return r; }
 template <typename T> __device__ __forceinline__ C2<T> add(C2<T> a, C2<T> b) { return mk<T>(a.x + b.x, a.y + b.y); }
@@ -45,7 +102,7 @@ __device__ __forceinline__ void dft8(C2<T> *x, int s) {
     C2<T> e[4] = {x[0], x[2], x[4], x[6]}, o[4] = {x[1], x[3], x[5], x[7]};
     dft4<T>(e, s);
     dft4<T>(o, s);
-    const T h = (T)0.70710678118654752440;
+    constexpr T h = T(0.70710678118654752440);
     // W8^u = e^{s 2 pi i u / 8}
     C2<T> w1 = mk<T>(h, s * h), w3 = mk<T>(-h, s * h);
     C2<T> t0 = o[0], t1 = mul<T>(o[1], w1), t2 = mul_si<T>(o[2], s), t3 = mul<T>(o[3], w3);
@@ -57,7 +114,8 @@ __device__ __forceinline__ void dft8(C2<T> *x, int s) {
 
 template <typename T>
 __device__ __forceinline__ void dft3(C2<T> *x, int s) {
-    const T c = (T)-0.5, d = (T)0.86602540378443864676 * s;   // W3 = c + i d
+    constexpr T c = T(-0.5), d0 = T(0.86602540378443864676);
+    const T d = d0 * s;                                        // W3 = c + i d
     C2<T> a = add<T>(x[1], x[2]), b = sub<T>(x[1], x[2]);
     C2<T> y0 = add<T>(x[0], a);
     C2<T> m = mk<T>(x[0].x + c * a.x, x[0].y + c * a.y);
@@ -67,8 +125,9 @@ __device__ __forceinline__ void dft3(C2<T> *x, int s) {
 
 template <typename T>
 __device__ __forceinline__ void dft5(C2<T> *x, int s) {
-    const T c1 = (T)0.30901699437494742410, c2 = (T)-0.80901699437494742410;
-    const T s1 = (T)0.95105651629515357212 * s, s2 = (T)0.58778525229247312917 * s;
+    constexpr T c1 = T(0.30901699437494742410), c2 = T(-0.80901699437494742410);
+    constexpr T s1p = T(0.95105651629515357212), s2p = T(0.58778525229247312917);
+    const T s1 = s1p * s, s2 = s2p * s;
     C2<T> a1 = add<T>(x[1], x[4]), b1 = sub<T>(x[1], x[4]);
     C2<T> a2 = add<T>(x[2], x[3]), b2 = sub<T>(x[2], x[3]);
     C2<T> y0 = add<T>(x[0], add<T>(a1, a2));
@@ -174,7 +233,7 @@ __global__ void __launch_bounds__(256) k_fft_pass(FftPass ps, int TB, int lgTB, 
             else { bl = j & (TB - 1); pos = j >> lgTB; }
             dst[u] = (j < total) ? bl * LS + pos : -1;
             const int e = wrapN(pos - ps.in_first, N);
-            v[u] = mk<T>((T)0, (T)0);
+            v[u] = mk<T>(T(0), T(0));
             if (j < total && bl < nlines && e < ps.L_in) {
                 const int64_t inner = inner0 + bl;
                 double2 d;
@@ -186,10 +245,10 @@ __global__ void __launch_bounds__(256) k_fft_pass(FftPass ps, int TB, int lgTB, 
                     const int k0 = e - zs.K0;
                     d = zs.zeta[((int64_t)abs(k0) * (zs.K1 + 1) + abs(k1)) * W + mi];
                     if (k1 < 0 && ((mi - zs.K1) & 1)) { d.x = -d.x; d.y = -d.y; }
-                } else if (sizeof(InC) == sizeof(C2<T>) && (scale_on_output || (!ps.elem_scale && !ps.line_scale))) {
-                    // same precision in and out, no factor: no conversion
+                } else if (scale_on_output || (!ps.elem_scale && !ps.line_scale)) {
+                    // no factor on the input: straight conversion to the pass arithmetic
                     const InC x = in[outer * ps.in_so + inner * ps.in_si + (int64_t)e * ps.in_se];
-                    v[u] = mk<T>((T)x.x, (T)x.y);
+                    v[u] = mk<T>(T(x.x), T(x.y));
                     continue;
                 } else {
                     d = to_d2(in[outer * ps.in_so + inner * ps.in_si + (int64_t)e * ps.in_se]);
@@ -200,7 +259,7 @@ __global__ void __launch_bounds__(256) k_fft_pass(FftPass ps, int TB, int lgTB, 
                     if (ps.line_scale) f *= ps.line_scale[outer * ps.nb_inner + inner];
                     d.x *= f; d.y *= f;
                 }
-                v[u] = mk<T>((T)d.x, (T)d.y);
+                v[u] = mk<T>(T(d.x), T(d.y));
             }
         }
 #pragma unroll
@@ -234,23 +293,19 @@ __global__ void __launch_bounds__(256) k_fft_pass(FftPass ps, int TB, int lgTB, 
             const int64_t inner = inner0 + bl;
             const int pos = wrapN(e + ps.out_first, N);
             const C2<T> v = buf[bl * LS + __ldg(ps.rev + pos)];
-            if (sizeof(OutC) == sizeof(C2<T>) && !(scale_on_output && (ps.elem_scale || ps.line_scale))) {
-                OutC o;
-                o.x = v.x;
-                o.y = v.y;
+            using S = decltype(OutC::x);
+            OutC o;
+            if (!(scale_on_output && (ps.elem_scale || ps.line_scale))) {
+                o.x = narrow<S>(v.x);
+                o.y = narrow<S>(v.y);
                 out[outer * ps.out_so + inner * ps.out_si + (int64_t)e * ps.out_se] = o;
                 continue;
             }
-            double vx = (double)v.x, vy = (double)v.y;
-            if (scale_on_output) {
-                double f = 1.0;
-                if (ps.elem_scale) f *= ps.elem_scale[e];
-                if (ps.line_scale) f *= ps.line_scale[outer * ps.nb_inner + inner];
-                vx *= f; vy *= f;
-            }
-            OutC o;
-            o.x = (decltype(o.x))vx;
-            o.y = (decltype(o.y))vy;
+            double f = 1.0;
+            if (ps.elem_scale) f *= ps.elem_scale[e];
+            if (ps.line_scale) f *= ps.line_scale[outer * ps.nb_inner + inner];
+            o.x = (S)(widen(v.x) * f);
+            o.y = (S)(widen(v.y) * f);
             out[outer * ps.out_so + inner * ps.out_si + (int64_t)e * ps.out_se] = o;
         }
     }
@@ -292,7 +347,7 @@ FftPass base_pass(const Axis &a, int sign, bool fp32) {
 template <typename T>
 cudaError_t forward_passes(sgl_plan *p) {
     const Axis &A0 = p->ax[0], &A1 = p->ax[1], &A2 = p->ax[2];
-    const bool f32 = std::is_same<T, float>::value;
+    constexpr bool f32 = std::is_same<T, float>::value;
     const int64_t W = 2 * p->K1 + 1;
     ZetaSrc zs{p->b.zeta, p->K0, p->K1};
     cudaError_t e;
@@ -303,7 +358,12 @@ cudaError_t forward_passes(sgl_plan *p) {
     a.nb_outer = 1; a.nb_inner = W * W;
     a.out_so = 0; a.out_si = 1; a.out_se = W * W;
     a.elem_scale = A0.deconv; a.line_scale = p->b.linescale;
-    if ((e = run_pass<T, double2, C2<T>, LOAD_ZETA>(p, a, nullptr, p->b.bufA, zs, 0)) != cudaSuccess) return e;
+    if constexpr (f32) {
+        a.tw = A0.tw_df;                          // radial pass in double-float (file comment)
+        if ((e = run_pass<dfl, double2, C2<T>, LOAD_ZETA>(p, a, nullptr, p->b.bufA, zs, 0)) != cudaSuccess) return e;
+    } else if ((e = run_pass<T, double2, C2<T>, LOAD_ZETA>(p, a, nullptr, p->b.bufA, zs, 0)) != cudaSuccess) {
+        return e;
+    }
     // pass B (axis 1): X0 -> X1[l0][l1 row][m]
     FftPass b = base_pass(A1, +1, f32);
     b.L_in = (int)W; b.in_first = -p->K1;
@@ -325,7 +385,7 @@ cudaError_t forward_passes(sgl_plan *p) {
 template <typename T>
 cudaError_t adjoint_passes(sgl_plan *p) {
     const Axis &A0 = p->ax[0], &A1 = p->ax[1], &A2 = p->ax[2];
-    const bool f32 = std::is_same<T, float>::value;
+    constexpr bool f32 = std::is_same<T, float>::value;
     const int64_t W = 2 * p->K1 + 1;
     ZetaSrc zs{p->b.zeta, p->K0, p->K1};
     cudaError_t e;
@@ -353,6 +413,10 @@ cudaError_t adjoint_passes(sgl_plan *p) {
     a.in_so = 0; a.in_si = 1; a.in_se = W * W;
     a.out_so = 0; a.out_si = 1; a.out_se = W * W;
     a.elem_scale = A0.deconv; a.line_scale = p->b.linescale;
+    if constexpr (f32) {
+        a.tw = A0.tw_df;                          // radial pass in double-float (file comment)
+        return run_pass<dfl, C2<T>, double2, LOAD_STRIDED>(p, a, p->b.bufA, p->b.bufB, zs, 1);
+    }
     return run_pass<T, C2<T>, double2, LOAD_STRIDED>(p, a, p->b.bufA, p->b.bufB, zs, 1);
 }
 

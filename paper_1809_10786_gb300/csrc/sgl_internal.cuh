@@ -69,6 +69,7 @@ struct Axis {
     // device tables
     double2 *tw_d;  // exp(2 pi i m / N), m < N
     float2 *tw_f;
+    float4 *tw_df;  // the same as double-float pairs (re hi, re lo, im hi, im lo)
     int *rev;       // digit-reversed slot of output index p after the DIF passes
     double *deconv; // 1 / Psihat(2 pi k / N), k = -K..K (index k + K)
 };
@@ -115,6 +116,7 @@ struct Buffers {
     int *work_len;             // [2] entries in each list (written on the device)
     unsigned long long *df_max;// [2] FP64 plans: bits of max |grid| and max |values| (scales of the double-float passes)
     double *scalar;            // [1] device accumulator of small reductions (sgl_eta_l1)
+    int *sched;                // [4] work counters of the persistent kernels (zeroed before each launch)
     double *wtab;              // [kWinTab] tabulated windows (FP64 plans)
     // host-IO staging
     double *io_xyz, *io_coef, *io_vals, *io_grad, *io_out;
@@ -209,6 +211,11 @@ cudaError_t tc_make_tensor_map(sgl_plan *p);
 cudaError_t launch_interp_tc(sgl_plan *p, double2 *vals);
 cudaError_t launch_grad_tc(sgl_plan *p, const double2 *gout, double *gxyz, double2 *vals);
 cudaError_t launch_spread_tc(sgl_plan *p, const double2 *vals);
+
+// Host tables of the conversions for bandwidth B (sgl_capi.cu): the polar matrices P [B][B][B]
+// ([m >= 0][kappa1][l]) and cos(m pi / 4B), m < 8B; leg is caller scratch of 2 B^3 doubles.  No
+// heap use.
+void conversion_tables(int B, double *P, double *costab, double *leg);
 
 // explicit-pointer launchers (no plan) used by the allocation-free entry point
 cudaError_t launch_max_radius_raw(cudaStream_t s, const double *xyz, int64_t M, unsigned long long *r2max, int *flags);

@@ -29,18 +29,22 @@ def gpu(a):
     return torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
 
 
-def plan(B, x, prec=sgl.PREC_FP64, q=8):
-    p = sgl.Plan(B, len(x), precision=prec, q=q, device=DEV)
+def plan(B, x, prec=sgl.PREC_FP64, q=8, native=False):
+    p = sgl.Plan(B, len(x), precision=prec, q=q, device=DEV, native_fp64=native)
     p.set_points(gpu(x))
     return p
 
 
-def test_cgnr_follows_the_oracle_and_reaches_least_squares():
+# later residuals: within 2 % of the oracle's with the binary64 windowed loops (transform errors
+# ~1e-15, the sensitivity above at 1e-15 is ~1e-4), 25 % with the double-float loops (errors of
+# order 1e-14, the sensitivity above at 1e-14 reaches 11 %)
+@pytest.mark.parametrize("native,later", [(True, 0.02), (False, 0.25)])
+def test_cgnr_follows_the_oracle_and_reaches_least_squares(native, later):
     B, M = 5, 500                                  # Nc = 55, cond(Lambda) ~ 150
     x = inputs.points_gaussian(M, 9305)
     L = inverse.matrix(B, x)
     f = L @ inputs.coefficients(B, 9306) + 1e-3 * inputs.complex_normal(M, 9307)
-    p = plan(B, x)
+    p = plan(B, x, native=native)
     _, res_or = inverse.cgnr(L, f, np.zeros(L.shape[1], complex), 30)
     gpu_res = []
     for it in (5, 10, 20, 30):
@@ -48,7 +52,7 @@ def test_cgnr_follows_the_oracle_and_reaches_least_squares():
         assert k == it
         gpu_res.append(r)
         # early residual norms follow the oracle's closely, later ones to the sensitivity above
-        assert r == pytest.approx(res_or[it] / res_or[0], rel=1e-6 if it == 5 else 0.25)
+        assert r == pytest.approx(res_or[it] / res_or[0], rel=1e-6 if it == 5 else later)
     assert all(b <= a * (1 + 1e-3) for a, b in zip(gpu_res, gpu_res[1:]))
     c, res, k = p.inverse(gpu(f), iters=300, tol=0.0, method="cgnr")
     c_ls = np.linalg.lstsq(L, f, rcond=None)[0]
@@ -93,7 +97,8 @@ def test_midpoint_guess_matches_the_oracle():
     assert rel(g, inverse.midpoint_guess(B, x, f, kappa, N)) <= 1e-10
 
 
-def test_paper_last_test_setup_small():
+@pytest.mark.parametrize("native,later", [(True, 0.02), (False, 0.25)])
+def test_paper_last_test_setup_small(native, later):
     # Sect. 8, last test, at a size the dense oracle handles: Cartesian grid G_N, kappa = 5,
     # exact samples of random coefficients, CGNR from the mid-point rule
     B, N, kappa = 4, 14, 5.0
@@ -101,12 +106,12 @@ def test_paper_last_test_setup_small():
     c_true = inputs.coefficients(B, 9346)
     f, _ = direct.forward(B, x, c_true)
     w = (2.0 * kappa / N) ** 3 * np.exp(-np.sum(x * x, axis=1))
-    p = plan(B, x)
+    p = plan(B, x, native=native)
     c0 = p.midpoint_guess(gpu(f), gpu(w))
     c, res, k = p.inverse(gpu(f), coef0=c0, iters=40, method="cgnr")
     L = inverse.matrix(B, x)
     c_or, res_or = inverse.cgnr(L, f, c0.cpu().numpy(), 40)
-    assert res == pytest.approx(res_or[-1] / np.linalg.norm(f), rel=0.25)      # sensitivity: module docstring
+    assert res == pytest.approx(res_or[-1] / np.linalg.norm(f), rel=later)     # sensitivity: module docstring
     assert res <= res_or[0] / np.linalg.norm(f)
     # run to convergence: the consistent system gives back the coefficients
     c, res, k = p.inverse(gpu(f), coef0=c0, iters=2000, tol=1e-10, method="cgnr")
