@@ -545,6 +545,7 @@ sgl_status plan_create_impl(sgl_plan **out, int B, int64_t M_max, int precision,
     ALLOC(b.u_tmp, 3 * Mc);
     ALLOC(b.u_sorted, 3 * Mc);
     ALLOC(b.pts32, Mc);
+    if (precision == SGL_FP32_MIXED) ALLOC(b.ys32, Mc);
     ALLOC(b.perm, Mc);
     ALLOC(b.bin_of, Mc);
     ALLOC(b.rank_of, Mc);

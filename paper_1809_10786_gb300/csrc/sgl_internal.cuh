@@ -107,6 +107,7 @@ struct Buffers {
     double *u_tmp;             // [M][3] grid coordinates, input order
     double *u_sorted;          // [M][3] grid coordinates, bin order
     float4 *pts32;             // [M] bin order: (u0 - c0, u1 - c1, u2 - c2, cells c0 | c1 << 10 | c2 << 20 as bits)
+    float2 *ys32;              // [M] bin order: the values to spread (FP32-mixed adjoint)
     int *perm;                 // sorted position -> input index
     int *bin_of, *rank_of;     // per input point
     int *bin_count, *bin_off;  // [nbins]

@@ -171,162 +171,208 @@ __global__ void __launch_bounds__(256, 3) k_grad32(NGeom g, int64_t M, const flo
     }
 }
 
-// Spreading by super-bins.  One CTA per entry of the spreading work list: up to
-// spread_chunk(prec) sorted points of one super-bin (C0 x C1 columns x one azimuthal chunk);
-// warp w owns tile slab a = w (one grid row on axis 0) and keeps the sums for all T1 rows of
-// axis 1 and its 32 azimuthal lanes in registers while it sweeps the entry's points; each tile
-// cell is then added to the grid once (atomically: neighbouring tiles, and the other entries of
-// a crowded super-bin, overlap it).
-// window value for the spreading staging: FP32 takes the branch-free evaluation, FP64 the
-// reference form
-template <int WIN, typename T>
-__device__ __forceinline__ T win_value(T x, T q, T par, T norm) {
-    if constexpr (sizeof(T) == 4) return window_pair32<WIN>(x, q, par, norm).x;
-    else return window<WIN, T>(x, q, par, norm);
-}
-
-template <typename T, int WIN, int Q2MAX, int C1>
-struct SpreadSmem {
+// FP32 spreading by super-bins, persistent.  One CTA per SM takes entries of the spreading work
+// list (at most 1024 sorted points of one super-bin: C0 x C1 = 8 x 8 cell columns x one azimuthal
+// chunk) from a device counter until the list is exhausted, and sweeps each entry in chunks of
+// PCH points.  Warp ta owns tile slab ta (one grid row of axis 0; the tile has C0 + 2q - 1 of
+// them) and keeps the sums of the C1 + Q2M - 1 tile rows of axis 1 and its 32 azimuthal lanes in
+// registers.  A point's 2q rows start at its column's row tb0 in [0, C1): rows are swept in
+// blocks of four, and the blocks wholly before tb0 = 4 or after the point's last row are left out
+// by one warp-uniform branch (every lane serves the same point).  Each tile cell is added to the
+// grid once per entry (atomically: neighbouring tiles, and the other entries of a crowded
+// super-bin, overlap it).  Point staging (window values) is double-buffered: in one iteration
+// every warp stages its share of the next chunk and then sweeps the current one, with one barrier
+// per chunk; thread 0 fetches the work one chunk further ahead.  The values come pre-gathered in
+// bin order (k_gather_sorted), so staging reads contiguous memory only.
+template <int Q2M>
+struct RsStage {
     static constexpr int PCH = 64;
-    static constexpr int PAD = sizeof(T) == 4 ? 4 : 2;         // 128-bit weight loads
-    static constexpr int T1MAX = (C1 + Q2MAX - 1 + PAD - 1) / PAD * PAD;
-    C2<T> y[PCH];
-    T w0[PCH][Q2MAX];
-    T w1[PCH][T1MAX];         // axis-1 weights on the tile rows (0 off the point's taps)
-    T w2[PCH][32];
-    int ta0[PCH];
+    static constexpr int T1P = (8 + Q2M - 1 + 3) / 4 * 4;      // tile rows padded to blocks of four
+    float w0[PCH][Q2M];       // axis-0 weights of the point's taps (slab ta0 + j)
+    float w1[PCH][T1P];       // axis-1 weights on the tile rows (0 off the point's taps)
+    float w2[PCH][32];        // azimuthal weights on the 32 lanes (0 off the point's taps)
+    float2 y[PCH];
+    int pk[PCH];              // ta0 | tb0 << 8: the point's first slab and first tile row
 };
 
-template <typename T, int WIN, int Q2MAX, int C0, int C1>
-__global__ void __launch_bounds__(32 * (C0 + Q2MAX - 1)) k_spread_slab(NGeom g, const int4 *__restrict__ work,
-                                                                       const int *__restrict__ work_len, const double *__restrict__ u_sorted,
-                                                                       const float4 *__restrict__ pts32, const int *__restrict__ perm,
-                                                                       const double2 *__restrict__ vals, C2<T> *__restrict__ grid) {
-    using S = SpreadSmem<T, WIN, Q2MAX, C1>;
-    constexpr int PCH = S::PCH, T1MAX = S::T1MAX;
-    constexpr int T1E = C1 + Q2MAX - 1;          // tile rows kept in registers (T1MAX pads the staged rows to 16 B)
-    __shared__ __align__(16) S sm;
-    const int lane = threadIdx.x & 31, ta = threadIdx.x >> 5;
-    const int q = g.q, q2 = 2 * q;
-    const T qT = (T)q;
-    if ((int)blockIdx.x >= __ldg(work_len)) return;
-    const int4 piece = __ldg(work + blockIdx.x);
-    const int64_t sb = piece.x;
-    const int first = piece.y, last = piece.y + piece.z;
-    const int sb1 = (int)(sb % g.nsb1), sb2 = (int)((sb / g.nsb1) % g.nsb2), sb0 = (int)(sb / ((int64_t)g.nsb1 * g.nsb2));
-    const int ta_org = sb0 * C0 - q + 1, tb_org = sb1 * C1 - q + 1, cbase = sb2 * g.S2 - q + 1;
-    const int T1 = C1 + q2 - 1;
-    constexpr int E = Q2MAX + T1MAX + 32 + 1;    // staged values per point
-    const T par0 = (T)g.par[0], par1 = (T)g.par[1], par2 = (T)g.par[2];
-    const T nrm0 = (T)g.norm[0], nrm1 = (T)g.norm[1], nrm2 = (T)g.norm[2];
-    C2<T> acc[T1E];
+// acc[r] += w1[r] z for the tile rows of blocks B0 .. B1 - 1 (four rows each, rows < T1E)
+template <int B0, int B1, int T1E>
+__device__ __forceinline__ void rs_rows(float2 (&acc)[T1E], const float *w1, float2 z) {
 #pragma unroll
-    for (int tb = 0; tb < T1E; ++tb) { acc[tb].x = (T)0; acc[tb].y = (T)0; }
-    for (int cs = first; cs < last; cs += PCH) {
-        const int np = min(PCH, last - cs);
-        __syncthreads();
-        for (int t = threadIdx.x; t < np * E; t += blockDim.x) {
-            const int p = t / E, e = t % E;
-            const int64_t pi = cs + p;
-            // cells and fractional coordinates (FP32: from the packed record, no FP64 work)
-            int c0, c1, c2;
-            T f0, f1, f2;
-            if constexpr (sizeof(T) == 4) {
-                const float4 pt = pts32[pi];
-                unpack_cells(pt.w, c0, c1, c2);
-                f0 = pt.x; f1 = pt.y; f2 = pt.z;
-            } else {
-                const double u0 = u_sorted[3 * pi], u1 = u_sorted[3 * pi + 1], u2 = u_sorted[3 * pi + 2];
-                c0 = cell_clamped(u0, g.cmax0);
-                c1 = cell_clamped(u1, g.cmax1);
-                c2 = min(max((int)floor(u2), 0), g.N[2] - 1);
-                f0 = u0 - c0; f1 = u1 - c1; f2 = u2 - c2;
-            }
-            // window values (FP32: the branch-free, well-conditioned evaluation), one evaluation
-            // site for the three axes: tap index rel of this element on its axis
-            if (e < Q2MAX + T1MAX + 32) {
-                T f, par, nrm, *dst;
-                int rel;
-                bool ok;
-                if (e < Q2MAX) {
-                    rel = e; ok = e < q2; f = f0; par = par0; nrm = nrm0; dst = &sm.w0[p][e];
-                } else if (e < Q2MAX + T1MAX) {
-                    const int tb = e - Q2MAX;
-                    rel = tb - (c1 - sb1 * C1);              // tap index of row tb for this point
-                    ok = rel >= 0 && rel < q2 && tb < T1; f = f1; par = par1; nrm = nrm1; dst = &sm.w1[p][tb];
-                } else {
-                    const int L = e - Q2MAX - T1MAX;
-                    rel = cbase + L - (c2 - q + 1);
-                    ok = rel >= 0 && rel < q2; f = f2; par = par2; nrm = nrm2; dst = &sm.w2[p][L];
-                }
-                *dst = ok ? win_value<WIN, T>(f + (T)(q - 1 - rel), qT, par, nrm) : (T)0;
-            } else {
-                const double2 y = vals[perm[pi]];
-                sm.y[p].x = (T)y.x;
-                sm.y[p].y = (T)y.y;
-                sm.ta0[p] = c0 - sb0 * C0;
-            }
+    for (int h = B0; h < B1; ++h) {
+        const float4 w = reinterpret_cast<const float4 *>(w1)[h];
+        if (4 * h < T1E) acc[4 * h] = ffma2(make_float2(w.x, w.x), z, acc[4 * h]);
+        if (4 * h + 1 < T1E) acc[4 * h + 1] = ffma2(make_float2(w.y, w.y), z, acc[4 * h + 1]);
+        if (4 * h + 2 < T1E) acc[4 * h + 2] = ffma2(make_float2(w.z, w.z), z, acc[4 * h + 2]);
+        if (4 * h + 3 < T1E) acc[4 * h + 3] = ffma2(make_float2(w.w, w.w), z, acc[4 * h + 3]);
+    }
+}
+
+// the values to spread in bin order, binary32
+__global__ void __launch_bounds__(256) k_gather_sorted(int64_t M, const int *__restrict__ perm, const double2 *__restrict__ vals,
+                                                       float2 *__restrict__ ys) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < M; i += (int64_t)gridDim.x * blockDim.x) {
+        const double2 y = vals[perm[i]];
+        ys[i] = make_float2((float)y.x, (float)y.y);
+    }
+}
+
+// a chunk's point records and values, copied into shared memory two chunks ahead (cp.async), so
+// that staging never waits on DRAM
+struct RsRaw {
+    float4 pt[64];
+    float2 y[64];
+};
+struct RsDesc { int sb, first, np, flags; };  // flags bit 0: last chunk of its entry; bit 1: no more work
+
+// asynchronous copies of one chunk's records (16 bytes each) and values (8 bytes each) by threads
+// 0 .. 2 np - 1, committed as one group
+__device__ __forceinline__ void rs_copy_raw(const RsDesc &d, const float4 *__restrict__ pts32, const float2 *__restrict__ ys,
+                                            RsRaw &raw) {
+    const int t = threadIdx.x;
+    if (!(d.flags & 2)) {
+        if (t < d.np) {
+            const unsigned dst = (unsigned)__cvta_generic_to_shared(&raw.pt[t]);
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(pts32 + d.first + t) : "memory");
+        } else if (t >= 64 && t < 64 + d.np) {
+            const unsigned dst = (unsigned)__cvta_generic_to_shared(&raw.y[t - 64]);
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(dst), "l"(ys + d.first + (t - 64)) : "memory");
         }
-        __syncthreads();
-        // unrolled so that the next points' shared-memory loads overlap this point's FMAs
-        // (a CTA has few warps per scheduler to hide that latency with)
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+}
+__device__ __forceinline__ void rs_copy_wait() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// thread 0 of a spreading CTA: the next chunk of the work list (cursor: super-bin, next point, end,
+// done; the entry counter is shared by all CTAs)
+__device__ __forceinline__ RsDesc rs_next_desc(int *cursor, const int4 *__restrict__ work, int nwork, int *sched) {
+    while (!cursor[3] && cursor[1] >= cursor[2]) {
+        const int e = atomicAdd(sched, 1);
+        if (e >= nwork) { cursor[3] = 1; break; }
+        const int4 piece = __ldg(work + e);
+        cursor[0] = piece.x; cursor[1] = piece.y; cursor[2] = piece.y + piece.z;
+    }
+    RsDesc d{0, 0, 0, 2};
+    if (cursor[3]) return d;
+    d.sb = cursor[0]; d.first = cursor[1]; d.np = min(64, cursor[2] - cursor[1]);
+    cursor[1] += d.np;
+    d.flags = (cursor[1] >= cursor[2]) ? 1 : 0;
+    return d;
+}
+
+// staging of one chunk (all threads of the CTA): window values of the points' taps on the tile
+template <int WIN, int Q2M>
+__device__ __forceinline__ void rs_stage(const NGeom &g, int sb, int np, const RsRaw &raw, RsStage<Q2M> &b) {
+    constexpr int C0 = 8, C1 = 8, T1P = RsStage<Q2M>::T1P;
+    constexpr int E = Q2M + T1P + 32 + 1;         // staged items per point
+    const int q = g.q, q2 = 2 * q;
+    const int sb1 = sb % g.nsb1, sb2 = (sb / g.nsb1) % g.nsb2, sb0 = sb / (g.nsb1 * g.nsb2);
+    const int cbase = sb2 * g.S2 - q + 1;
+    // the window parameters in registers (the lanes of a warp serve different axes)
+    const float par0 = g.parf[0], par1 = g.parf[1], par2 = g.parf[2];
+    const float nrm0 = g.normf[0], nrm1 = g.normf[1], nrm2 = g.normf[2];
+    // straight-line items, unrolled, so that the window evaluations of several items interleave
+#pragma unroll 4
+    for (int t = threadIdx.x; t < np * E; t += blockDim.x) {
+        const int p = t / E, e = t - p * E;
+        const float4 pt = raw.pt[p];
+        int c0, c1, c2;
+        unpack_cells(pt.w, c0, c1, c2);
+        if (e < Q2M + T1P + 32) {
+            const int ax = e < Q2M ? 0 : (e < Q2M + T1P ? 1 : 2);
+            const int L = e - (ax == 0 ? 0 : (ax == 1 ? Q2M : Q2M + T1P));   // tap (axis 0), tile row (1), lane (2)
+            const int rel = ax == 0 ? L : (ax == 1 ? L - (c1 - sb1 * C1) : cbase + L - (c2 - q + 1));
+            const float f = ax == 0 ? pt.x : (ax == 1 ? pt.y : pt.z);
+            const float par = ax == 0 ? par0 : (ax == 1 ? par1 : par2), nrm = ax == 0 ? nrm0 : (ax == 1 ? nrm1 : nrm2);
+            float *dst = ax == 0 ? &b.w0[p][L] : (ax == 1 ? &b.w1[p][L] : &b.w2[p][L]);
+            // window_pair32 is zero outside |x| <= q; an off-tap rel gives such an x or is masked
+            const float v = window_pair32<WIN>(f + (float)(q - 1 - rel), (float)q, par, nrm).x;
+            *dst = (rel >= 0 && rel < q2) ? v : 0.f;
+        } else {
+            b.y[p] = raw.y[p];
+            b.pk[p] = (c0 - sb0 * C0) | ((c1 - sb1 * C1) << 8);
+        }
+    }
+}
+
+// CTAs per SM: two where the smaller tile's registers allow (q <= 4), so that they hide each other's latency
+template <int Q2M> constexpr int rs_ctas_per_sm() { return Q2M <= 8 ? 2 : 1; }
+
+template <int WIN, int Q2M>
+__global__ void __launch_bounds__(32 * (8 + Q2M - 1), rs_ctas_per_sm<Q2M>()) k_spread_rs(NGeom g, const int4 *__restrict__ work,
+                                                                    const int *__restrict__ work_len, const float4 *__restrict__ pts32,
+                                                                    const float2 *__restrict__ ys, float2 *__restrict__ grid,
+                                                                    int *__restrict__ sched) {
+    constexpr int C0 = 8, C1 = 8, T1E = C1 + Q2M - 1, T1P = RsStage<Q2M>::T1P, NB = T1P / 4;
+    static_assert(Q2M % 4 == 0 && Q2M <= 16, "taps per axis: a multiple of 4, at most 16");
+    static_assert(RsStage<Q2M>::PCH == 64, "chunks of 64 points (two copy threads per point)");
+    __shared__ __align__(16) RsStage<Q2M> st[2];
+    __shared__ __align__(16) RsRaw raw[2];
+    __shared__ RsDesc desc[4];                    // chunks k .. k + 3 (thread 0 fills them three chunks ahead)
+    __shared__ int cursor[4];                     // thread 0's place in the work list: super-bin, next point, end, done
+    const int lane = threadIdx.x & 31, ta = threadIdx.x >> 5;
+    const int nwork = __ldg(work_len + 1);
+    if (threadIdx.x == 0) {
+        cursor[0] = cursor[1] = cursor[2] = cursor[3] = 0;
+        desc[0] = rs_next_desc(cursor, work, nwork, sched);
+        desc[1] = rs_next_desc(cursor, work, nwork, sched);
+        desc[2] = rs_next_desc(cursor, work, nwork, sched);
+    }
+    __syncthreads();
+    rs_copy_raw(desc[0], pts32, ys, raw[0]);
+    rs_copy_raw(desc[1], pts32, ys, raw[1]);
+    rs_copy_wait();
+    __syncthreads();
+    if (!(desc[0].flags & 2)) rs_stage<WIN, Q2M>(g, desc[0].sb, desc[0].np, raw[0], st[0]);
+    __syncthreads();
+    float2 acc[T1E];
+#pragma unroll
+    for (int tb = 0; tb < T1E; ++tb) acc[tb] = make_float2(0.f, 0.f);
+    for (int k = 0;; ++k) {
+        const int cur = k & 3;                    // desc[cur]: the same for every thread, so the loop ends uniformly
+        if (desc[cur].flags & 2) break;
+        if (threadIdx.x == 0) desc[(k + 3) & 3] = rs_next_desc(cursor, work, nwork, sched);   // slot last read in iteration k - 1
+        rs_copy_raw(desc[(k + 2) & 3], pts32, ys, raw[k & 1]);                                // raw[k & 1] was read in iteration k - 1
+        if (!(desc[(k + 1) & 3].flags & 2))
+            rs_stage<WIN, Q2M>(g, desc[(k + 1) & 3].sb, desc[(k + 1) & 3].np, raw[(k + 1) & 1], st[(k + 1) & 1]);
+        const RsStage<Q2M> &b = st[k & 1];
+        const int np = desc[cur].np;
+        const int q2 = 2 * g.q;
 #pragma unroll 4
         for (int p = 0; p < np; ++p) {
-            const int j = ta - sm.ta0[p];
-            if (j < 0 || j >= q2) continue;
-            const T wz = sm.w0[p][j] * sm.w2[p][lane];
-            C2<T> z;
-            z.x = sm.y[p].x * wz;
-            z.y = sm.y[p].y * wz;
-            if constexpr (sizeof(T) == 4) {
-                const float4 *w1v = reinterpret_cast<const float4 *>(&sm.w1[p][0]);
+            const int pk = b.pk[p];
+            const int j = ta - (pk & 255);
+            if ((unsigned)j >= (unsigned)q2) continue;
+            const float wz = b.w0[p][j] * b.w2[p][lane];
+            const float2 y = b.y[p];
+            const float2 z = make_float2(y.x * wz, y.y * wz);
+            // rows tb0 .. tb0 + q2 - 1 lie in blocks 0 .. NB - 2 when tb0 < 4, in blocks 1 .. NB - 1 otherwise
+            if ((pk >> 8) < 4) rs_rows<0, NB - 1, T1E>(acc, &b.w1[p][0], z);
+            else rs_rows<1, NB, T1E>(acc, &b.w1[p][0], z);
+        }
+        if (desc[cur].flags & 1) {                // the entry's last chunk: add the tile to the grid, clear it
+            const int sb = desc[cur].sb;
+            const int sb1 = sb % g.nsb1, sb2 = (sb / g.nsb1) % g.nsb2, sb0 = sb / (g.nsb1 * g.nsb2);
+            const int r0 = row_checked(sb0 * C0 - g.q + 1 + ta, g.first[0], g.rows[0], g.N[0]);
+            const int n2 = g.N[2];
+            // grid offsets fit in 32 bits (at most 1024^3 / 4 cells per plan)
+            const int base = r0 * g.rows[1] * n2 + wrap_index(sb2 * g.S2 - g.q + 1 + lane, n2);
+            const bool win1 = g.rows[1] < g.N[1];
+            int r1 = sb1 * C1 - g.q + 1 - g.first[1];   // storage row of tile row 0 (windowed axis 1)
+            const int nrow = C1 + q2 - 1;
 #pragma unroll
-                for (int h = 0; h < T1E / 4; ++h) {
-                    const float4 w = w1v[h];
-                    acc[4 * h] = ffma2(make_float2(w.x, w.x), z, acc[4 * h]);
-                    acc[4 * h + 1] = ffma2(make_float2(w.y, w.y), z, acc[4 * h + 1]);
-                    acc[4 * h + 2] = ffma2(make_float2(w.z, w.z), z, acc[4 * h + 2]);
-                    acc[4 * h + 3] = ffma2(make_float2(w.w, w.w), z, acc[4 * h + 3]);
-                }
-                constexpr int R = T1E & ~3;              // the last T1E % 4 rows
-                if constexpr (T1E % 4 >= 2) {
-                    const float2 w = *reinterpret_cast<const float2 *>(&sm.w1[p][R]);
-                    acc[R] = ffma2(make_float2(w.x, w.x), z, acc[R]);
-                    acc[R + 1] = ffma2(make_float2(w.y, w.y), z, acc[R + 1]);
-                }
-                if constexpr (T1E % 2) {
-                    const float w = sm.w1[p][T1E - 1];
-                    acc[T1E - 1] = ffma2(make_float2(w, w), z, acc[T1E - 1]);
-                }
-            } else {
-#pragma unroll
-                for (int tb = 0; tb < T1E; ++tb) {
-                    const double w = sm.w1[p][tb];
-                    acc[tb].x = fma(w, z.x, acc[tb].x);
-                    acc[tb].y = fma(w, z.y, acc[tb].y);
-                }
+            for (int tb = 0; tb < T1E; ++tb, ++r1) {
+                const float2 v = acc[tb];
+                acc[tb] = make_float2(0.f, 0.f);
+                if (r0 < 0 || tb >= nrow || (v.x == 0.f && v.y == 0.f)) continue;
+                const int rr = win1 ? r1 : wrap_index(r1 + g.first[1], g.N[1]);
+                if (rr >= 0 && rr < g.rows[1]) atomicAdd(grid + (base + rr * n2), v);
             }
         }
+        rs_copy_wait();                           // this thread's copies of chunk k + 2
+        __syncthreads();
     }
-    if (ta >= C0 + q2 - 1) return;
-    const int64_t s1 = g.N[2], s0 = (int64_t)g.rows[1] * g.N[2];
-    const int c = wrap_index(cbase + lane, g.N[2]);
-    const int r0 = row_checked(ta_org + ta, g.first[0], g.rows[0], g.N[0]);
-    if (r0 < 0) return;                 // slab outside the stored rows: no point reaches it
-    C2<T> *rowp = grid + r0 * s0 + c;
-#pragma unroll
-    for (int tb = 0; tb < T1E; ++tb) {
-        const int r1 = (tb < T1) ? row_checked(tb_org + tb, g.first[1], g.rows[1], g.N[1]) : -1;
-        if (r1 >= 0 && (acc[tb].x != (T)0 || acc[tb].y != (T)0)) {
-            C2<T> *cell = rowp + r1 * s1;
-            if constexpr (sizeof(T) == 4) {
-                atomicAdd(cell, acc[tb]);
-            } else {
-                atomicAdd(&cell->x, acc[tb].x);
-                atomicAdd(&cell->y, acc[tb].y);
-            }
-        }
-    }
+    rs_copy_wait();
 }
 
 template <typename T, int WIN>
@@ -354,14 +400,16 @@ cudaError_t interp_t(sgl_plan *p, double2 *vals) {
     }
 }
 
-template <typename T, int WIN, int Q2MAX, int C0, int C1>
-cudaError_t spread_slab_t(sgl_plan *p, const NGeom &g, const double2 *vals) {
-    if (g.C0 != C0 || g.C1 != C1) return cudaErrorInvalidConfiguration;
-    const int threads = 32 * (C0 + 2 * p->q - 1);
-    const int64_t blocks = work_list_cap(p->M, p->bins.nsuper, spread_chunk(p->prec));   // entries past work_len[1] return
-    k_spread_slab<T, WIN, Q2MAX, C0, C1><<<(unsigned)blocks, threads, 0, p->stream>>>(
-        g, p->b.work[1], p->b.work_len + 1, p->b.u_sorted, p->b.pts32, p->b.perm, vals, (C2<T> *)p->b.bufA);
-    p->launches += 1;
+template <int WIN, int Q2M>
+cudaError_t spread_rs_t(sgl_plan *p, const NGeom &g, const double2 *vals) {
+    if (g.C0 != 8 || g.C1 != 8 || 2 * p->q > Q2M || g.S2 > 33 - 2 * p->q) return cudaErrorInvalidConfiguration;
+    k_gather_sorted<<<nufft_blocks(p->M, 1), 256, 0, p->stream>>>(p->M, p->b.perm, vals, p->b.ys32);
+    cudaError_t e = cudaMemsetAsync(p->b.sched, 0, sizeof(int), p->stream);
+    if (e != cudaSuccess) return e;
+    const int threads = 32 * (8 + 2 * p->q - 1);
+    k_spread_rs<WIN, Q2M><<<p->num_sms * rs_ctas_per_sm<Q2M>(), threads, 0, p->stream>>>(g, p->b.work[1], p->b.work_len, p->b.pts32, p->b.ys32,
+                                                               (float2 *)p->b.bufA, p->b.sched);
+    p->launches += 2;
     return cudaGetLastError();
 }
 
@@ -369,8 +417,9 @@ template <typename T, int WIN>
 cudaError_t spread_t(sgl_plan *p, const double2 *vals) {
     NGeom g = make_geom(p);
     if constexpr (sizeof(T) == 4) {
-        if (p->q <= 4) return spread_slab_t<T, WIN, 8, 8, 8>(p, g, vals);
-        if (p->q <= 8) return spread_slab_t<T, WIN, 16, 8, 8>(p, g, vals);
+        if (p->q <= 4) return spread_rs_t<WIN, 8>(p, g, vals);
+        if (p->q <= 6) return spread_rs_t<WIN, 12>(p, g, vals);
+        if (p->q <= 8) return spread_rs_t<WIN, 16>(p, g, vals);
     }
     C2<T> *grid = (C2<T> *)p->b.bufA;
     const int q2 = 2 * p->q;

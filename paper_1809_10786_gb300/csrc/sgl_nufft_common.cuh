@@ -54,6 +54,7 @@ struct NGeom {
     int N[3], rows[3], first[3];
     int q;
     double par[3], norm[3];
+    float parf[3], normf[3];   // the same in binary32 (read from the parameter bank by the FP32 kernels)
     const double *wtab;        // tabulated windows (FP64 plans; see kWinNI)
     double wh, winv;           // piece width q / kWinNI of the table, and its reciprocal
     double tpn[3], ntp[3];     // 2 pi / N_d and N_d / (2 pi)
@@ -127,6 +128,8 @@ inline NGeom make_geom(const sgl_plan *p) {
         g.first[d] = p->ax[d].first;
         g.par[d] = p->ax[d].wpar;
         g.norm[d] = (p->window == SGL_WIN_KB) ? p->q / (-expm1(-2.0 * p->ax[d].wpar * p->q)) : 1.0;
+        g.parf[d] = (float)g.par[d];
+        g.normf[d] = (float)g.norm[d];
         g.tpn[d] = 2.0 * kPi / p->ax[d].N;
         g.ntp[d] = p->ax[d].N / (2.0 * kPi);
     }
