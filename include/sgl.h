@@ -112,8 +112,8 @@ typedef struct {
     double sigma_eff[3];      /* N[d] / n[d] */
     int64_t workspace_bytes;  /* device bytes owned by the plan */
     int64_t kernel_launches;  /* CUDA kernels this plan has launched so far */
-    int tensor_cores;         /* bit 0: interpolation, bit 1: gradient, bit 2: spreading run on the
-                                 tcgen05 kernels */
+    int tensor_cores;         /* bit 0: interpolation, bit 1: gradient run on the tcgen05 kernels;
+                                 bit 2 (spreading) is 0: spreading runs on the CUDA cores */
 } sgl_plan_info_t;
 
 /* Nc = B(B+1)(2B+1)/6 (Sect. 1); -1 if B < 1. */

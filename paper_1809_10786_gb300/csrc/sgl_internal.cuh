@@ -211,7 +211,6 @@ int64_t tc_plane_floats(const sgl_plan *p);
 cudaError_t tc_make_tensor_map(sgl_plan *p);
 cudaError_t launch_interp_tc(sgl_plan *p, double2 *vals);
 cudaError_t launch_grad_tc(sgl_plan *p, const double2 *gout, double *gxyz, double2 *vals);
-cudaError_t launch_spread_tc(sgl_plan *p, const double2 *vals);
 
 // Host tables of the conversions for bandwidth B (sgl_capi.cu): the polar matrices P [B][B][B]
 // ([m >= 0][kappa1][l]) and cos(m pi / 4B), m < 8B; leg is caller scratch of 2 B^3 doubles.  No

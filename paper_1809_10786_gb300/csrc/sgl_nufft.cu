@@ -467,7 +467,6 @@ cudaError_t launch_interp(sgl_plan *p, double2 *vals) {
 
 cudaError_t launch_spread(sgl_plan *p, const double2 *vals) {
     if (p->M == 0) return cudaSuccess;
-    if (p->tc_spread) return launch_spread_tc(p, vals);
     const bool f32 = p->prec == SGL_FP32_MIXED, kb = p->window == SGL_WIN_KB;
     if (!f32) return launch_spread64(p, vals);
     return kb ? spread_t<float, SGL_WIN_KB>(p, vals) : spread_t<float, SGL_WIN_GAUSS>(p, vals);

@@ -717,316 +717,6 @@ __global__ void k_halo_planes(const float2 *__restrict__ grid, float *__restrict
 }
 
 
-// ============================================================================================
-// Spreading (the adjoint of the interpolation) on the tensor cores.  For a super-bin, a group of
-// 4 slabs ta = 4 g + z and the 32 azimuthal lanes c, the tile values are an outer-product sum
-// over the super-bin's points:
-//
-//     G_{ta}[tb][c] (Re, Im) = sum_p  (w0_p[ta] w2_p[c]) (w1_p[tb] y_p)
-//                            = sum_p  A_g[(z, c)][p]   B[(ri, tb)][p]        (M = 128, N = 48, K = p)
-//
-// A_g (the slab-and-lane weights of a group) and B (the tile-row weights times the value) are
-// built per 32-point chunk (K = 32) in shared memory, split into TF32 head and remainder; the six
-// groups' accumulators (6 x 48 TMEM columns) stay in tensor memory over all chunks of a super-bin
-// and are added to the grid once, one float2 atomic per tile cell (neighbouring super-bins overlap).
-//
-// Warps: 0 MMA issuer (+ TMEM), 1-4 A builders (thread = row (z, c)), 5-6 point staging and B
-// builders (thread = row (ri, tb)), 7-10 flush (TMEM lane quadrant = warp & 3).
-// Measured (B = 64, 10^6 points, q = 8): 2.0 ms, on par with the CUDA-core spreading kernel
-// (the builders, not the products, bound it), so it is only used with SGL_FLAG_TC.
-constexpr int kSpG = 4;                  // slabs per group (M = 4 x 32 lanes)
-constexpr int kSpGroups = 6;             // groups per super-bin: 24 slabs >= C0 + 2q - 1 (q <= 8)
-constexpr int kSpN = 48;                 // N: Re rows 0..23, Im rows 24..47
-constexpr int kSpK = 32;                 // points per chunk (K)
-constexpr int kSpWA = 1, kSpNA = 4;      // A builders: warps 1..4 (slab z = w - 1)
-constexpr int kSpWS = kSpWA + kSpNA, kSpNS = 2;   // staging / B builders: warps 5..6
-constexpr int kSpWF = kSpWS + kSpNS;     // flush: warps 7..10
-constexpr int kSpThreads = 32 * (kSpWF + 4);
-constexpr uint32_t kSpIdesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(kSpN >> 3) << 17) | ((uint32_t)(kPM >> 4) << 24);
-
-struct SpSmem {
-    alignas(1024) unsigned char a[2][2][kPM * 128];          // [slot][hi, lo]: 128 rows x 32 points
-    alignas(1024) unsigned char b[2][2][kSpN * 128];         // [slot][hi, lo]: 48 rows x 32 points
-    float w0tab[2][kSpK][16];                                // [slot][point][tap]
-    float w1row[2][kSpK][kTB1Max];                           // [slot][point][tile row] (placed)
-    float w2row[2][kSpK][kLanes];                            // [slot][point][lane] (placed)
-    float2 ytab[2][kSpK];                                    // [slot][point] value (Re, Im)
-    int d0[2][kSpK];
-    uint64_t bfull[2], bempty[2], afull[2], aempty[2], dfull[kSpGroups], dfree[kSpGroups], staged[2], done;
-    uint32_t tmem_base;
-    int abort;
-};
-
-struct SpArgs {
-    const int *bin_off;
-    int64_t M, nsuper;
-    const float4 *pts;
-    const int *perm;
-    const double2 *vals;
-    float2 *grid;
-    int *dev_flags;
-};
-
-// the CTA's chunks: super-bins blockIdx.x + k gridDim.x, each cut into 32-point chunks
-struct ChunkIter {
-    int64_t sb = -1;
-    int chunk = 0, nchunk = 0, first = 0, np = 0;
-    int nsb = -1;                        // super-bins with points seen so far (index of this one)
-};
-
-__device__ __forceinline__ bool next_chunk(ChunkIter &it, const SpArgs &a) {
-    if (it.sb >= 0 && ++it.chunk < it.nchunk) return true;
-    for (it.sb = (it.sb < 0 ? (int64_t)blockIdx.x : it.sb + gridDim.x); it.sb < a.nsuper; it.sb += gridDim.x) {
-        const int f = a.bin_off[it.sb * kC0 * kC1];
-        const int l = (it.sb + 1 < a.nsuper) ? a.bin_off[(it.sb + 1) * kC0 * kC1] : (int)a.M;
-        if (l > f) {
-            it.first = f;
-            it.np = l - f;
-            it.nchunk = (it.np + kSpK - 1) / kSpK;
-            it.chunk = 0;
-            ++it.nsb;
-            return true;
-        }
-    }
-    return false;
-}
-
-// one row of a K-major, 128-byte-swizzled operand tile (32 FP32 per row) as TF32 head and remainder
-__device__ __forceinline__ void store_row_split(unsigned char *hi, unsigned char *lo, int row, const float *v) {
-#pragma unroll
-    for (int k4 = 0; k4 < 8; ++k4) {
-        float4 h, l;
-        h.x = tf32_head(v[4 * k4]);     l.x = v[4 * k4] - h.x;
-        h.y = tf32_head(v[4 * k4 + 1]); l.y = v[4 * k4 + 1] - h.y;
-        h.z = tf32_head(v[4 * k4 + 2]); l.z = v[4 * k4 + 2] - h.z;
-        h.w = tf32_head(v[4 * k4 + 3]); l.w = v[4 * k4 + 3] - h.w;
-        const uint32_t o = (uint32_t)(row * 128 + ((k4 ^ (row & 7)) << 4));
-        *reinterpret_cast<float4 *>(hi + o) = h;
-        *reinterpret_cast<float4 *>(lo + o) = l;
-    }
-}
-
-__device__ __forceinline__ void mma_tf32_ss(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
-    asm volatile("{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n"
-                 :: "r"(dtmem), "l"(adesc), "l"(bdesc), "r"(kSpIdesc), "r"(accumulate));
-}
-
-template <int WIN>
-__global__ void __launch_bounds__(kSpThreads, 1) k_spread_tc(NGeom g, SpArgs args) {
-    extern __shared__ unsigned char smem_raw[];
-    SpSmem &sm = *reinterpret_cast<SpSmem *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
-    const int q = g.q, q2 = 2 * q;
-    const int T0 = kC0 + q2 - 1, T1 = kC1 + q2 - 1;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    if (threadIdx.x == 0) {
-        for (int i = 0; i < 2; ++i) {
-            mbar_init(smem_addr(&sm.bfull[i]), kSpNS);
-            mbar_init(smem_addr(&sm.bempty[i]), 1);
-            mbar_init(smem_addr(&sm.afull[i]), kSpNA);
-            mbar_init(smem_addr(&sm.aempty[i]), 1);
-        }
-        for (int i = 0; i < kSpGroups; ++i) {
-            mbar_init(smem_addr(&sm.dfull[i]), 1);
-            mbar_init(smem_addr(&sm.dfree[i]), 4);
-        }
-        for (int i = 0; i < 2; ++i) mbar_init(smem_addr(&sm.staged[i]), kSpNS);
-        mbar_init(smem_addr(&sm.done), 1);
-        sm.abort = 0;
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    }
-    if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" :: "r"(smem_addr(&sm.tmem_base)), "r"(512));
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
-    }
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
-    const uint32_t tmem = sm.tmem_base;
-    volatile int *abort_flag = &sm.abort;
-    bool ok = true;
-    ChunkIter it;
-
-    if (warp == 0) {
-        // ---------------- MMA issuer: per chunk and group, 4 K-steps x 3 split products
-        if (lane == 0) {
-            int cc = 0;                                  // chunks issued (global)
-            while (ok && next_chunk(it, args)) {
-                const int slot = cc & 1;
-                ok = mbar_wait(smem_addr(&sm.bfull[slot]), (cc >> 1) & 1);
-                const bool firstc = it.chunk == 0, lastc = it.chunk == it.nchunk - 1;
-                const uint32_t bhi = smem_addr(sm.b[slot][0]), blo = smem_addr(sm.b[slot][1]);
-                for (int gi = 0; gi < kSpGroups && ok; ++gi) {
-                    const int st = cc * kSpGroups + gi, as = st & 1;
-                    ok = mbar_wait(smem_addr(&sm.afull[as]), (st >> 1) & 1);
-                    if (ok && firstc && it.nsb >= 1) ok = mbar_wait(smem_addr(&sm.dfree[gi]), (it.nsb + 1) & 1);
-                    if (!ok || *abort_flag) { ok = false; break; }
-                    tc_fence_after();
-                    const uint32_t d = tmem + (uint32_t)gi * kSpN;
-                    const uint32_t ahi = smem_addr(sm.a[as][0]), alo = smem_addr(sm.a[as][1]);
-#pragma unroll
-                    for (int ks = 0; ks < kSpK / 8; ++ks) {
-                        const uint32_t ko = ks * 32;
-                        mma_tf32_ss(d, sw128_desc(ahi + ko), sw128_desc(bhi + ko), (firstc && ks == 0) ? 0u : 1u);
-                        mma_tf32_ss(d, sw128_desc(ahi + ko), sw128_desc(blo + ko), 1u);
-                        mma_tf32_ss(d, sw128_desc(alo + ko), sw128_desc(bhi + ko), 1u);
-                    }
-                    mma_commit(smem_addr(&sm.aempty[as]));
-                    if (gi == kSpGroups - 1) mma_commit(smem_addr(&sm.bempty[slot]));
-                    if (lastc) mma_commit(smem_addr(&sm.dfull[gi]));
-                }
-                ++cc;
-            }
-            if (!ok) *abort_flag = 1;
-            mma_commit(smem_addr(&sm.done));
-            mbar_wait(smem_addr(&sm.done), 0);
-        }
-    } else if (warp >= kSpWA && warp < kSpWA + kSpNA) {
-        // ---------------- A builders: row (z, c) of A_g = w0_p[4 g + z] w2_p[c] over the chunk's points
-        const int z = warp - kSpWA, c = lane, row = z * 32 + c;
-        int cc = 0;
-        while (ok && next_chunk(it, args)) {
-            const int slot = cc & 1;
-            ok = __all_sync(0xffffffffu, mbar_wait(smem_addr(&sm.bfull[slot]), (cc >> 1) & 1) && !*abort_flag);
-            if (!ok) break;
-            float w2[kSpK];
-            int d0[kSpK];
-#pragma unroll
-            for (int pl = 0; pl < kSpK; ++pl) {
-                w2[pl] = sm.w2row[slot][pl][c];
-                d0[pl] = sm.d0[slot][pl];
-            }
-            for (int gi = 0; gi < kSpGroups && ok; ++gi) {
-                const int st = cc * kSpGroups + gi, as = st & 1;
-                if (st >= 2) ok = __all_sync(0xffffffffu, mbar_wait(smem_addr(&sm.aempty[as]), ((st >> 1) + 1) & 1) && !*abort_flag);
-                if (!ok) break;
-                const int ta = kSpG * gi + z;
-                float v[kSpK];
-#pragma unroll
-                for (int pl = 0; pl < kSpK; ++pl) {
-                    const int j = ta - d0[pl];
-                    v[pl] = (j >= 0 && j < q2) ? sm.w0tab[slot][pl][j] * w2[pl] : 0.f;
-                }
-                store_row_split(sm.a[as][0], sm.a[as][1], row, v);
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                __syncwarp();
-                if (lane == 0) mbar_arrive(smem_addr(&sm.afull[as]));
-            }
-            ++cc;
-        }
-    } else if (warp >= kSpWS && warp < kSpWS + kSpNS) {
-        // ---------------- staging (window values of the chunk's points) and the B operand
-        const int t = (warp - kSpWS) * 32 + lane;    // 0..63
-        const float qf = (float)q;
-        int cc = 0;
-        while (ok && next_chunk(it, args)) {
-            const int slot = cc & 1;
-            if (cc >= 2) ok = __all_sync(0xffffffffu, mbar_wait(smem_addr(&sm.bempty[slot]), ((cc >> 1) + 1) & 1) && !*abort_flag);
-            if (!ok) break;
-            const int sb1 = (int)(it.sb % g.nsb1), sb2 = (int)((it.sb / g.nsb1) % g.nsb2);
-            const int sb0 = (int)(it.sb / ((int64_t)g.nsb1 * g.nsb2));
-            // thread t: point pl = t & 31; half 0 stages axes 0 and 1, half 1 axis 2, the value and cells
-            const int pl = t & 31;
-            const int idx = it.chunk * kSpK + pl;
-            const bool live = idx < it.np;
-            const int64_t i = it.first + (live ? idx : 0);
-            const float4 pt = args.pts[i];
-            int c0, c1, c2;
-            unpack_cells(pt.w, c0, c1, c2);
-            if (t < 32) {
-                const int d1 = c1 - sb1 * kC1;
-#pragma unroll
-                for (int tb = 0; tb < kTB1Max; ++tb) sm.w1row[slot][pl][tb] = 0.f;
-#pragma unroll
-                for (int rel = 0; rel < 16; ++rel) {
-                    const float v0 = window_pair32<WIN>(pt.x + (float)(q - 1 - rel), qf, (float)g.par[0], (float)g.norm[0]).x;
-                    const float v1 = window_pair32<WIN>(pt.y + (float)(q - 1 - rel), qf, (float)g.par[1], (float)g.norm[1]).x;
-                    sm.w0tab[slot][pl][rel] = (live && rel < q2) ? v0 : 0.f;
-                    if (live && rel < q2) sm.w1row[slot][pl][d1 + rel] = v1;
-                }
-                sm.d0[slot][pl] = c0 - sb0 * kC0;
-            } else {
-                const int k0 = c2 - q + 1 - (sb2 * g.S2 - tc_halo(q));
-                float2 yv = make_float2(0.f, 0.f);
-                if (live) {
-                    const double2 y = args.vals[args.perm[i]];
-                    yv = make_float2((float)y.x, (float)y.y);
-                }
-                sm.ytab[slot][pl] = yv;
-#pragma unroll
-                for (int k = 0; k < kLanes; ++k) sm.w2row[slot][pl][k] = 0.f;
-#pragma unroll
-                for (int rel = 0; rel < 16; ++rel) {
-                    const float v2 = window_pair32<WIN>(pt.z + (float)(q - 1 - rel), qf, (float)g.par[2], (float)g.norm[2]).x;
-                    if (live && rel < q2) sm.w2row[slot][pl][k0 + rel] = v2;
-                }
-            }
-            // rendezvous of the staging warps (bounded, like every wait here)
-            __syncwarp();
-            if (lane == 0) mbar_arrive(smem_addr(&sm.staged[slot]));
-            ok = __all_sync(0xffffffffu, mbar_wait(smem_addr(&sm.staged[slot]), (cc >> 1) & 1) && !*abort_flag);
-            if (!ok) break;
-            // B row n = (ri, tb): w1_p[tb] y_p^{ri} over the chunk's points (rows >= 48: none)
-            if (t < kSpN) {
-                const int ri = t / 24, tb = t % 24;
-                float v[kSpK];
-#pragma unroll
-                for (int k = 0; k < kSpK; ++k) {
-                    const float2 y = sm.ytab[slot][k];
-                    v[k] = sm.w1row[slot][k][tb] * (ri ? y.y : y.x);
-                }
-                store_row_split(sm.b[slot][0], sm.b[slot][1], t, v);
-            }
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            __syncwarp();
-            if (lane == 0) mbar_arrive(smem_addr(&sm.bfull[slot]));
-            ++cc;
-        }
-    } else {
-        // ---------------- flush: at the end of each super-bin, the six groups' tiles into the grid
-        const int quad = warp & 3, z = quad, c = lane;      // warps 7..10: quadrants 3, 0, 1, 2
-        const uint32_t lane_base = (uint32_t)(quad * 32) << 16;
-        const int64_t s1 = g.N[2], s0 = (int64_t)g.rows[1] * g.N[2];
-        while (ok && next_chunk(it, args)) {
-            if (it.chunk != it.nchunk - 1) continue;
-            const int sb1 = (int)(it.sb % g.nsb1), sb2 = (int)((it.sb / g.nsb1) % g.nsb2);
-            const int sb0 = (int)(it.sb / ((int64_t)g.nsb1 * g.nsb2));
-            const int ta_org = sb0 * kC0 - q + 1, tb_org = sb1 * kC1 - q + 1;
-            const int col = wrap_index(sb2 * g.S2 - tc_halo(q) + c, g.N[2]);
-            for (int gi = 0; gi < kSpGroups && ok; ++gi) {
-                ok = __all_sync(0xffffffffu, mbar_wait(smem_addr(&sm.dfull[gi]), it.nsb & 1) && !*abort_flag);
-                if (!ok) break;
-                tc_fence_after();
-                float dv[kSpN];
-                const uint32_t taddr = tmem + lane_base + (uint32_t)gi * kSpN;
-#pragma unroll
-                for (int k8 = 0; k8 < kSpN / 8; ++k8) tmem_ld8(taddr + 8 * k8, dv + 8 * k8);
-                tmem_wait_ld();
-                tc_fence_before();
-                __syncwarp();
-                if (lane == 0) mbar_arrive(smem_addr(&sm.dfree[gi]));
-                const int ta = kSpG * gi + z;
-                const int r0 = (ta < T0) ? row_checked(ta_org + ta, g.first[0], g.rows[0], g.N[0]) : -1;
-                if (r0 < 0) continue;
-                float2 *rowp = args.grid + r0 * s0 + col;
-#pragma unroll
-                for (int tb = 0; tb < 24; ++tb) {
-                    const int r1 = (tb < T1) ? row_checked(tb_org + tb, g.first[1], g.rows[1], g.N[1]) : -1;
-                    const float2 v = make_float2(dv[tb], dv[24 + tb]);
-                    if (r1 >= 0 && (v.x != 0.f || v.y != 0.f)) atomicAdd(rowp + r1 * s1, v);
-                }
-            }
-        }
-    }
-    if (!ok) *abort_flag = 1;
-    tc_fence_before();
-    __syncthreads();
-    if (*abort_flag && threadIdx.x == 0) atomicOr(args.dev_flags, 2);
-    if (warp == 0) {
-        tc_fence_after();
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem), "r"(512));
-    }
-}
-
 int tile_rows(int q) { return (kC1 + 2 * q - 1 + 7) / 8 * 8; }
 
 }  // namespace
@@ -1045,7 +735,7 @@ void tc_choose(sgl_plan *p) {
     const bool use = p->tc && ((p->flags & SGL_FLAG_TC) || p->q >= 6);
     p->tc_interp = use;
     p->tc_grad = use;
-    p->tc_spread = p->tc && (p->flags & SGL_FLAG_TC);
+    p->tc_spread = false;     // spreading: the CUDA-core kernel (sgl_nufft.cu) wins in time and accuracy
 }
 
 int64_t tc_plane_floats(const sgl_plan *p) {
@@ -1138,26 +828,6 @@ cudaError_t launch_interp_tc(sgl_plan *p, double2 *vals) {
     TcArgs a = base_args(p);
     a.vals = vals;
     return p->window == SGL_WIN_KB ? run_tc<SGL_WIN_KB, false>(p, a) : run_tc<SGL_WIN_GAUSS, false>(p, a);
-}
-
-cudaError_t launch_spread_tc(sgl_plan *p, const double2 *vals) {
-    SpArgs a{};
-    a.bin_off = p->b.bin_off;
-    a.M = p->M;
-    a.nsuper = p->bins.nsuper;
-    a.pts = p->b.pts32;
-    a.perm = p->b.perm;
-    a.vals = vals;
-    a.grid = (float2 *)p->b.bufA;
-    a.dev_flags = p->b.dev_flags;
-    const size_t smem = std::max<size_t>(sizeof(SpSmem) + 1024, (size_t)120 * 1024);
-    auto kern = p->window == SGL_WIN_KB ? k_spread_tc<SGL_WIN_KB> : k_spread_tc<SGL_WIN_GAUSS>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    const int64_t grid = std::min<int64_t>(p->bins.nsuper, p->num_sms);
-    kern<<<(unsigned)grid, kSpThreads, smem, p->stream>>>(make_geom(p), a);
-    p->launches += 1;
-    return cudaGetLastError();
 }
 
 cudaError_t launch_grad_tc(sgl_plan *p, const double2 *gout, double *gxyz, double2 *vals) {

@@ -9,6 +9,7 @@ import pytest
 import torch
 
 import paper_1809_10786_gb300 as sgl
+from envelope import check
 from paper_1809_10786_gb300 import inputs
 from paper_1809_10786_gb300.autograd import ndsglft
 from oracle import direct
@@ -39,7 +40,8 @@ def masked_loss(plan, c, x, y, mask):
     return (r.real ** 2 + r.imag ** 2).sum()
 
 
-@pytest.mark.parametrize("prec,tol_c,tol_x", [(sgl.PREC_FP64, 1e-9, 1e-8), (sgl.PREC_FP32_MIXED, 1e-4, 2e-3)])
+# FP32-mixed: about 5x the measured 2.0e-7 (coefficients) and 9.5e-7 (points)
+@pytest.mark.parametrize("prec,tol_c,tol_x", [(sgl.PREC_FP64, 1e-9, 1e-8), (sgl.PREC_FP32_MIXED, 1e-6, 5e-6)])
 def test_gradients_against_oracle(workload, prec, tol_c, tol_x):
     B, M, c0, x, y, idx, mask = workload
     plan = sgl.Plan(B, M, precision=prec, q=8)
@@ -54,8 +56,8 @@ def test_gradients_against_oracle(workload, prec, tol_c, tol_x):
     r = f_sub - y[idx]
     gc_ref, _ = direct.adjoint(B, x[idx], 2 * r)
     gx_ref, _ = direct.grad_points(B, x[idx], c0, 2 * r)
-    assert np.abs(gc - gc_ref).max() <= tol_c * np.abs(gc_ref).max()
-    assert np.abs(gx[idx] - gx_ref).max() <= tol_x * np.abs(gx_ref).max()
+    check("autograd coefficients prec=%d" % prec, np.abs(gc - gc_ref).max() / np.abs(gc_ref).max(), tol_c)
+    check("autograd points prec=%d" % prec, np.abs(gx[idx] - gx_ref).max() / np.abs(gx_ref).max(), tol_x)
     others = np.setdiff1d(np.arange(M), idx)
     assert np.abs(gx[others]).max() == 0.0
 

@@ -6,6 +6,7 @@ import pytest
 import torch
 
 import paper_1809_10786_gb300 as sgl
+from envelope import check
 from paper_1809_10786_gb300 import inputs
 from oracle import direct
 
@@ -39,8 +40,8 @@ def test_batch_matches_single_plans_and_graph_replay(prec):
         a = p.adjoint(gpu(ys[i])).cpu().numpy()
         assert np.array_equal(f_b[i], f)
         # spreading adds with atomics: the order (and FP32 rounding) differs from run to run
-        tol = 1e-12 if prec == sgl.PREC_FP64 else 1e-5
-        assert np.abs(a_b[i] - a).max() <= tol * max(np.abs(a).max(), 1e-300)
+        tol = 1e-12 if prec == sgl.PREC_FP64 else 2e-7          # FP32: measured at most 3.3e-8
+        check("batch adjoint vs plan prec=%d i=%d" % (prec, i), np.abs(a_b[i] - a).max() / max(np.abs(a).max(), 1e-300), tol)
     # graph mode: capture once, replay, same numbers; new pointers recapture
     bp.use_graph(True)
     ct = [gpu(c) for c in cs]
@@ -57,7 +58,7 @@ def test_batch_matches_single_plans_and_graph_replay(prec):
     bp.sync()
 
 
-@pytest.mark.parametrize("prec,tol", [(sgl.PREC_FP64, 1e-10), (sgl.PREC_FP32_MIXED, 1e-4)])
+@pytest.mark.parametrize("prec,tol", [(sgl.PREC_FP64, 1e-10), (sgl.PREC_FP32_MIXED, 6e-6)])   # FP32: measured <= 1.2e-6
 def test_256_instance_workload_sampled(prec, tol):
     specs = inputs.batch_instances(256, inputs.seed_for(3))
     cs, xs, ys = instances(specs, inputs.seed_for(3, 1))
@@ -71,4 +72,4 @@ def test_256_instance_workload_sampled(prec, tol):
         B, M = specs[i]
         idx = np.sort(rng.choice(M, min(M, 40), replace=False))
         ref, _ = direct.forward(B, xs[i][idx], cs[i])
-        assert np.abs(fs[i][idx] - ref).max() <= tol * np.abs(ref).max(), (i, B, M)
+        check("batch 256 forward prec=%d i=%d" % (prec, i), np.abs(fs[i][idx] - ref).max() / np.abs(ref).max(), tol)

@@ -12,6 +12,7 @@ import pytest
 import torch
 
 import paper_1809_10786_gb300 as sgl
+from envelope import check
 from paper_1809_10786_gb300 import inputs
 from oracle import direct, factorization as fz
 
@@ -67,7 +68,7 @@ def test_forward_and_adjoint_fp64(B, M, win, q, native):
     assert rel(a, a_ref) <= 1e-10
 
 
-@pytest.mark.parametrize("prec,tol", [(sgl.PREC_FP64, 1e-13), (sgl.PREC_FP32_MIXED, 1e-6)])
+@pytest.mark.parametrize("prec,tol", [(sgl.PREC_FP64, 1e-13), (sgl.PREC_FP32_MIXED, 2e-8)])   # FP32: measured 4.4e-9
 def test_adjoint_identity(prec, tol):
     B, M = 16, 4000
     c, x, y = case(B, M, 3000)
@@ -75,11 +76,13 @@ def test_adjoint_identity(prec, tol):
     f = p.forward(gpu(c)).cpu().numpy()
     a = p.adjoint(gpu(y)).cpu().numpy()
     lhs, rhs = np.vdot(y, f), np.vdot(a, c)
-    assert abs(lhs - rhs) <= tol * np.linalg.norm(f) * np.linalg.norm(y)
+    check("adjoint identity B=16 prec=%d" % prec, abs(lhs - rhs) / (np.linalg.norm(f) * np.linalg.norm(y)), tol)
 
 
-@pytest.mark.parametrize("q,bound", [(4, 2e-5), (6, 5e-6), (8, 5e-6)])
-def test_fp32_mixed_error_envelope(q, bound):
+# about 5x the measured forward / adjoint errors: q = 4: 1.7e-7 / 1.1e-7; q = 6: 3.3e-7 / 1.0e-7;
+# q = 8: 5.6e-7 / 9.4e-8
+@pytest.mark.parametrize("q,bound_f,bound_a", [(4, 1e-6, 6e-7), (6, 1.7e-6, 5e-7), (8, 3e-6, 5e-7)])
+def test_fp32_mixed_error_envelope(q, bound_f, bound_a):
     B, M = 16, 3000
     c, x, y = case(B, M, 4000 + q)
     p = plan_for(B, M, prec=sgl.PREC_FP32_MIXED, q=q, x=x)
@@ -87,19 +90,19 @@ def test_fp32_mixed_error_envelope(q, bound):
     a = p.adjoint(gpu(y)).cpu().numpy()
     f_ref, _ = direct.forward(B, x, c)
     a_ref, _ = direct.adjoint(B, x, y)
-    assert rel(f, f_ref) <= bound
-    assert rel(a, a_ref) <= bound
+    check("fp32 envelope B=16 q=%d forward" % q, rel(f, f_ref), bound_f)
+    check("fp32 envelope B=16 q=%d adjoint" % q, rel(a, a_ref), bound_a)
 
 
 @pytest.mark.parametrize("prec,tol,native", [(sgl.PREC_FP64, 1e-9, False), (sgl.PREC_FP64, 1e-9, True),
-                                             (sgl.PREC_FP32_MIXED, 1e-3, False)])
+                                             (sgl.PREC_FP32_MIXED, 1e-4, False)])     # FP32: measured 1.8e-5
 def test_grad_points_against_oracle(prec, tol, native):
     B, M = 12, 1500
     c, x, g = case(B, M, 5000)
     p = plan_for(B, M, prec=prec, x=x, native_fp64=native)
     gx = p.grad_points(gpu(c), gpu(g)).cpu().numpy()
     ref, _ = direct.grad_points(B, x, c, g)
-    assert rel(gx, ref) <= tol
+    check("gradient B=12 prec=%d native=%d" % (prec, native), rel(gx, ref), tol)
 
 
 def test_grad_points_against_gpu_finite_differences():
@@ -228,7 +231,8 @@ def test_forward_grad_equals_separate_calls(prec, simt, ftol):
     assert rel(f, p.forward(gpu(c)).cpu().numpy()) <= ftol
     assert np.array_equal(gx, p.grad_points(gpu(c), gpu(g)).cpu().numpy())
     f_ref, _ = direct.forward(B, x, c)
-    assert rel(f, f_ref) <= (1e-10 if prec == sgl.PREC_FP64 else 5e-6)
+    # FP32: measured 3.8e-7 (tensor cores) and 9.1e-7 (CUDA cores)
+    check("forward_grad B=16 prec=%d simt=%d" % (prec, simt), rel(f, f_ref), 1e-10 if prec == sgl.PREC_FP64 else 5e-6)
 
 
 def test_forward_grad_host_buffers():

@@ -11,6 +11,7 @@ import pytest
 import torch
 
 import paper_1809_10786_gb300 as sgl
+from envelope import check
 from paper_1809_10786_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
@@ -38,7 +39,8 @@ def batch_reference(B, M, prec, x, kind, arg):
     return out[0]
 
 
-@pytest.mark.parametrize("prec,tol", [(sgl.PREC_FP32_MIXED, 1e-5), (sgl.PREC_FP64, 1e-11)])
+# the reference is the same computation on other plans (measured difference 0 in both precisions)
+@pytest.mark.parametrize("prec,tol", [(sgl.PREC_FP32_MIXED, 1e-7), (sgl.PREC_FP64, 1e-11)])
 def test_points_may_be_overwritten_right_after_set_points(prec, tol):
     B, M = 32, 1_000_000
     c = gpu(inputs.coefficients(B, 7100))
@@ -49,7 +51,7 @@ def test_points_may_be_overwritten_right_after_set_points(prec, tol):
     x.mul_(0.25).add_(0.5)           # the caller reuses its buffer in stream order
     f = p.forward(c)
     torch.cuda.synchronize()
-    assert rel(f, batch_reference(B, M, prec, x0, "forward", c)) <= tol      # stale points: O(1)
+    check("overwritten points forward prec=%d" % prec, rel(f, batch_reference(B, M, prec, x0, "forward", c)), tol)  # stale: O(1)
 
 
 def test_consecutive_set_points_keep_the_last_points():
@@ -64,8 +66,9 @@ def test_consecutive_set_points_keep_the_last_points():
     a = p.adjoint(y)                 # the adjoint straight after the binning: spreading joins it
     f = p.forward(c)
     torch.cuda.synchronize()
-    assert rel(a, batch_reference(B, M, sgl.PREC_FP32_MIXED, x2, "adjoint", y)) <= 1e-4
-    assert rel(f, batch_reference(B, M, sgl.PREC_FP32_MIXED, x2, "forward", c)) <= 1e-5
+    # spreading adds atomically in no fixed order (measured 2.3e-8); the forward is deterministic
+    check("consecutive set_points adjoint", rel(a, batch_reference(B, M, sgl.PREC_FP32_MIXED, x2, "adjoint", y)), 1.5e-7)
+    check("consecutive set_points forward", rel(f, batch_reference(B, M, sgl.PREC_FP32_MIXED, x2, "forward", c)), 1e-7)
 
 
 def test_side_stream_plan_on_a_torch_stream_and_rho():
@@ -83,7 +86,7 @@ def test_side_stream_plan_on_a_torch_stream_and_rho():
     s.synchronize()
     r = float(torch.sqrt((x * x).sum(1).max()))
     assert r <= rho <= r * (1 + 2e-6)
-    assert rel(f, batch_reference(B, M, sgl.PREC_FP32_MIXED, x, "forward", c)) <= 1e-5
+    check("side stream forward", rel(f, batch_reference(B, M, sgl.PREC_FP32_MIXED, x, "forward", c)), 1e-7)
     assert torch.isfinite(gx).all()
 
 
