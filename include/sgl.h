@@ -251,9 +251,21 @@ sgl_status sgl_midpoint_guess(sgl_plan *plan, const double *vals_dev, const doub
  * sgl_eta_l1: ||eta||_1 of coef_dev (complex128 [Nc], device) for the plan's current points (rho
  *   enters eta); synchronizes the stream.  bound * ||eta||_1 bounds this transform's error.
  */
+/*
+ * sgl_choose_params: error-driven choice of both NFFT parameters.  Over the oversampling factors
+ *   sigma in {1.5, 2, 2.5, 3, 4}, takes for each the smallest q whose bound (as sgl_nfft_error_bound)
+ *   is <= tol, and returns the pair that a cost model of one forward plus one adjoint transform of M
+ *   points rates cheapest: M (2q)^3 c_tap + (stored grid cells) c_cell milliseconds, with per-tap
+ *   and per-cell costs of the windowed loops and the FFT passes measured on GB300 for the given
+ *   precision (the conversions, which depend on neither parameter, are left out).  sigma, q: the
+ *   choice; model_ms (may be NULL): the model's estimate in milliseconds.  SGL_ERR_UNSUPPORTED if
+ *   no pair reaches tol; SGL_ERR_ARG for invalid B, M < 0, precision, window or tol <= 0.
+ */
 sgl_status sgl_nfft_error_bound(int B, int window, int q, double sigma, double *bound);
 sgl_status sgl_plan_error_bound(const sgl_plan *plan, double *bound);
 sgl_status sgl_choose_cutoff(int B, int window, double sigma, double tol, int *q);
+sgl_status sgl_choose_params(int B, int64_t M, int precision, int window, double tol, double *sigma, int *q,
+                             double *model_ms);
 sgl_status sgl_eta_l1(sgl_plan *plan, const double *coef_dev, double *l1);
 
 /*
@@ -314,6 +326,22 @@ const char *sgl_stage_name(int stage);
 int sgl_noalloc_max_b(void);
 sgl_status sgl_trig_coeffs_noalloc(int B, const double *xyz_dev, int64_t M, const double *coef_dev,
                                    double *eta_dev, void *cuda_stream);
+
+/*
+ * Fault injection for tests of the failure paths (the paper has no counterpart).
+ * sgl_test_hooks: hooks bit SGL_TEST_WITHHOLD_ARRIVAL makes the prep warps of the tensor-core
+ *   interpolation and gradient kernels withhold their operand arrival, so that the kernel's bounded
+ *   waits run out: it issues no tensor-core product, drains its loads, frees its tensor memory and
+ *   returns, and the next sgl_sync reports SGL_ERR_TIMEOUT (that call's results are invalid).
+ *   wait_cycles: the limit of those waits in clock cycles (0: the default, about a second); hooks 0
+ *   and wait_cycles 0 restore normal operation.  SGL_ERR_ARG for unknown bits or wait_cycles < 0.
+ * sgl_test_fail_alloc: after >= 0 lets that many further device allocations of the library
+ *   succeed and fails the next one (once), as if cudaMalloc had run out of memory; after < 0 turns
+ *   the injection off.  Process-wide.
+ */
+#define SGL_TEST_WITHHOLD_ARRIVAL 1u
+sgl_status sgl_test_hooks(sgl_plan *plan, unsigned hooks, int64_t wait_cycles);
+sgl_status sgl_test_fail_alloc(int after);
 
 /* Synchronize the plan's stream and report deferred device errors (non-finite points). */
 sgl_status sgl_sync(sgl_plan *plan);

@@ -8,7 +8,7 @@ transform call loads the library and fails loudly when it is missing.
 """
 _BINDING_NAMES = (
     "Plan", "BatchPlan", "SGLError", "num_coeffs", "library_path", "load_library",
-    "PREC_FP64", "PREC_FP32_MIXED", "WIN_KB", "WIN_GAUSS", "nfft_error_bound", "choose_cutoff",
+    "PREC_FP64", "PREC_FP32_MIXED", "WIN_KB", "WIN_GAUSS", "nfft_error_bound", "choose_cutoff", "choose_params",
 )
 
 

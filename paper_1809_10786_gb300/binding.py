@@ -79,6 +79,9 @@ def load_library(build_if_missing=True):
                            ("sgl_choose_cutoff", [ctypes.c_int, ctypes.c_int, ctypes.c_double, ctypes.c_double,
                                                   ctypes.POINTER(ctypes.c_int)]),
                            ("sgl_eta_l1", [vp, vp, dp]),
+                           ("sgl_test_hooks", [vp, ctypes.c_uint, i64]), ("sgl_test_fail_alloc", [ctypes.c_int]),
+                           ("sgl_choose_params", [ctypes.c_int, i64, ctypes.c_int, ctypes.c_int, ctypes.c_double, dp,
+                                                  ctypes.POINTER(ctypes.c_int), dp]),
                            ("sgl_forward_grad_host", [vp, vp, i64, vp, vp, vp, vp]),
                            ("sgl_profile", [vp, dp, ctypes.POINTER(i64)]), ("sgl_sync", [vp]),
                            ("sgl_trig_coeffs_noalloc", [ctypes.c_int, vp, i64, vp, vp, vp])]:
@@ -128,6 +131,15 @@ def choose_cutoff(B, tol, window=WIN_KB, sigma=2.0):
     q = ctypes.c_int()
     _check(load_library().sgl_choose_cutoff(int(B), int(window), float(sigma), float(tol), ctypes.byref(q)))
     return q.value
+
+
+def choose_params(B, M, tol, precision=PREC_FP64, window=WIN_KB):
+    """sgl_choose_params: (sigma, q, model_ms) -- the cheapest pair (by the GB300 cost model) whose
+    bound per unit ||eta||_1 is <= tol."""
+    sg, q, ms = ctypes.c_double(), ctypes.c_int(), ctypes.c_double()
+    _check(load_library().sgl_choose_params(int(B), int(M), int(precision), int(window), float(tol), ctypes.byref(sg),
+                                            ctypes.byref(q), ctypes.byref(ms)))
+    return sg.value, q.value, ms.value
 
 
 def _stream_handle(device):

@@ -131,8 +131,8 @@ sgl_status sgl_batch_create(sgl_batch **out, int n, const int *B, const int64_t 
         b->bytesA = std::max(b->bytesA, a);
         b->bytesB = std::max(b->bytesB, c);
     }
-    cudaError_t e = cudaMalloc(&b->bufA, b->bytesA);
-    if (e == cudaSuccess) e = cudaMalloc(&b->bufB, b->bytesB);
+    cudaError_t e = sgl::device_malloc(&b->bufA, b->bytesA);
+    if (e == cudaSuccess) e = sgl::device_malloc(&b->bufB, b->bytesB);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming);

@@ -4,6 +4,7 @@
 #include "sgl_internal.cuh"
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
@@ -86,6 +87,22 @@ void release_side(sgl_plan *p) {
 sgl_status set_error(sgl_status code, const std::string &msg) {
     g_last_error = msg;
     return code;
+}
+
+// Allocation-failure injection (sgl_test_fail_alloc): the number of further device allocations
+// that succeed before one fails; negative: off.
+static std::atomic<long long> g_fail_alloc_after{-1};
+
+cudaError_t device_malloc(void **p, size_t bytes) {
+    *p = nullptr;
+    long long left = g_fail_alloc_after.load();
+    while (left >= 0) {
+        if (g_fail_alloc_after.compare_exchange_weak(left, left - 1)) {
+            if (left == 0) return cudaErrorMemoryAllocation;      // the injected failure (one-shot)
+            break;
+        }
+    }
+    return cudaMalloc(p, bytes);
 }
 
 namespace {
@@ -373,7 +390,7 @@ struct DevAlloc {
         *p = nullptr;
         if (count == 0) count = 1;
         void *q = nullptr;
-        cudaError_t e = cudaMalloc(&q, count * sizeof(T));
+        cudaError_t e = device_malloc(&q, count * sizeof(T));
         if (e != cudaSuccess) return e;
         ptrs.push_back(q);
         bytes += (int64_t)(count * sizeof(T));
@@ -1008,6 +1025,51 @@ sgl_status sgl_choose_cutoff(int B, int window, double sigma, double tol, int *q
     return set_error(SGL_ERR_UNSUPPORTED, "no cutoff q <= 16 reaches the requested bound");
 }
 
+// Cost model of sgl_choose_params: one forward and one adjoint transform at M points cost
+//   M (2q)^3 c_tap + (stored grid cells) c_cell   milliseconds,
+// windowed loops (interpolation + spreading) per tap and FFT passes (forward + adjoint) per grid
+// cell, measured on GB300 at B = 64, 10^6 points, q = 8, sigma = 2 (FP32-mixed: 0.89 + 1.49 ms of
+// loops, 0.69 ms of FFT passes over 273 x 145 x 256 cells; FP64 with double-float loops: 9.3 +
+// 15.9 ms and 3.81 ms).  The conversions do not depend on (sigma, q) and are left out.
+namespace {
+constexpr double kTapMs[2] = {(9.3 + 15.9) / 4.096e9, (0.89 + 1.49) / 4.096e9};   // [SGL_FP64, SGL_FP32_MIXED]
+constexpr double kCellMs[2] = {3.81 / (273.0 * 145.0 * 256.0), 0.69 / (273.0 * 145.0 * 256.0)};
+}  // namespace
+
+sgl_status sgl_choose_params(int B, int64_t M, int precision, int window, double tol, double *sigma, int *q,
+                             double *model_ms) {
+    if (!sigma || !q) return set_error(SGL_ERR_ARG, "sigma and q must be non-NULL");
+    if (!(tol > 0.0)) return set_error(SGL_ERR_ARG, "tol must be positive");
+    if (M < 0) return set_error(SGL_ERR_ARG, "M must be >= 0");
+    if (precision != SGL_FP64 && precision != SGL_FP32_MIXED) return set_error(SGL_ERR_ARG, "unknown precision");
+    if (B < 1 || B > 128 || (window != SGL_WIN_KB && window != SGL_WIN_GAUSS))
+        return set_error(SGL_ERR_ARG, "invalid B or window");
+    const int nsz[3] = {4 * B, 2 * B, 2 * B}, K[3] = {2 * B - 2, B - 1, B - 1};
+    double best = -1.0, best_sigma = 0.0;
+    int best_q = 0;
+    for (double sg : {1.5, 2.0, 2.5, 3.0, 4.0}) {
+        int N[3];
+        for (int d = 0; d < 3; ++d) N[d] = next_fft_size(sg * nsz[d]);
+        // the bound falls with q: bisection for the smallest q <= 16 (and < every N) that meets tol
+        int lo = 1, hi = std::min(kMaxQ, std::min(N[0], std::min(N[1], N[2])) - 1);
+        if (hi < 1 || error_bound_of(window, N, nsz, K, hi) > tol) continue;
+        while (lo < hi) {
+            const int mid = (lo + hi) / 2;
+            if (error_bound_of(window, N, nsz, K, mid) <= tol) hi = mid; else lo = mid + 1;
+        }
+        double cells = 1.0;
+        for (int d = 0; d < 3; ++d) cells *= (d < 2 && N[d] / 2 + 2 * lo + 1 <= N[d]) ? N[d] / 2 + 2 * lo + 1 : N[d];
+        const double taps = 8.0 * lo * lo * lo;
+        const double cost = (double)M * taps * kTapMs[precision] + cells * kCellMs[precision];
+        if (best < 0.0 || cost < best) { best = cost; best_sigma = sg; best_q = lo; }
+    }
+    if (best < 0.0) return set_error(SGL_ERR_UNSUPPORTED, "no oversampling factor with q <= 16 reaches the requested bound");
+    *sigma = best_sigma;
+    *q = best_q;
+    if (model_ms) *model_ms = best;
+    return ok();
+}
+
 sgl_status sgl_eta_l1(sgl_plan *plan, const double *coef_dev, double *l1) {
     if (sgl_status s = check_plan(plan)) return s;
     if (!plan->points_set) return set_error(SGL_ERR_STATE, "sgl_set_points has not been called");
@@ -1026,6 +1088,20 @@ sgl_status sgl_eta_l1(sgl_plan *plan, const double *coef_dev, double *l1) {
     SGL_CUDA_TRY(cudaGetLastError());
     SGL_CUDA_TRY(cudaMemcpyAsync(l1, plan->b.scalar, sizeof(double), cudaMemcpyDeviceToHost, plan->stream));
     return sgl_sync(plan);
+}
+
+sgl_status sgl_test_hooks(sgl_plan *plan, unsigned hooks, int64_t wait_cycles) {
+    if (sgl_status s = check_plan(plan)) return s;
+    if (hooks & ~SGL_TEST_WITHHOLD_ARRIVAL) return set_error(SGL_ERR_ARG, "unknown test hook bits");
+    if (wait_cycles < 0) return set_error(SGL_ERR_ARG, "wait_cycles must be >= 0");
+    plan->test_hooks = hooks;
+    plan->wait_cycles = wait_cycles;
+    return ok();
+}
+
+sgl_status sgl_test_fail_alloc(int after) {
+    g_fail_alloc_after.store(after < 0 ? -1 : after);
+    return ok();
 }
 
 sgl_status sgl_sync(sgl_plan *plan) {

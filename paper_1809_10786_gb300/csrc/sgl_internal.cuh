@@ -169,6 +169,8 @@ struct sgl_plan {
     bool points_set;
     bool tc;                            // tensor-core kernels usable (planes and TMA map exist)
     bool tc_interp, tc_grad, tc_spread; // ... and chosen for the interpolation / gradient / spreading
+    unsigned test_hooks;                // sgl_test_hooks: fault injection for tests (0 in normal use)
+    long long wait_cycles;              // limit of the tensor-core kernels' waits (0: the default)
     alignas(64) unsigned char tc_map[2][128];   // TMA descriptors of b.planes (CUtensorMap): interpolation, gradient
     sgl::Buffers b;
 };
@@ -211,6 +213,9 @@ int64_t tc_plane_floats(const sgl_plan *p);
 cudaError_t tc_make_tensor_map(sgl_plan *p);
 cudaError_t launch_interp_tc(sgl_plan *p, double2 *vals);
 cudaError_t launch_grad_tc(sgl_plan *p, const double2 *gout, double *gxyz, double2 *vals);
+
+// cudaMalloc, or a failure injected by sgl_test_fail_alloc (every device allocation of the library)
+cudaError_t device_malloc(void **p, size_t bytes);
 
 // Host tables of the conversions for bandwidth B (sgl_capi.cu): the polar matrices P [B][B][B]
 // ([m >= 0][kappa1][l]) and cos(m pi / 4B), m < 8B; leg is caller scratch of 2 B^3 doubles.  No

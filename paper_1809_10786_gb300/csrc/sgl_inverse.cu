@@ -112,11 +112,11 @@ sgl_status ensure_work(sgl_plan *p) {
     InverseWork *w = new (std::nothrow) InverseWork();
     if (!w) return set_error(SGL_ERR_ALLOC, "host allocation failed");
     const size_t Mc = (size_t)std::max<int64_t>(p->M_max, 1), Nc = (size_t)p->Nc;
-    cudaError_t e = cudaMalloc(&w->r, sizeof(double2) * Mc);
-    if (e == cudaSuccess) e = cudaMalloc(&w->w, sizeof(double2) * Mc);
-    if (e == cudaSuccess) e = cudaMalloc(&w->z, sizeof(double2) * Nc);
-    if (e == cudaSuccess) e = cudaMalloc(&w->p, sizeof(double2) * Nc);
-    if (e == cudaSuccess) e = cudaMalloc(&w->part, sizeof(double) * 1024);
+    cudaError_t e = device_malloc((void **)&w->r, sizeof(double2) * Mc);
+    if (e == cudaSuccess) e = device_malloc((void **)&w->w, sizeof(double2) * Mc);
+    if (e == cudaSuccess) e = device_malloc((void **)&w->z, sizeof(double2) * Nc);
+    if (e == cudaSuccess) e = device_malloc((void **)&w->p, sizeof(double2) * Nc);
+    if (e == cudaSuccess) e = device_malloc((void **)&w->part, sizeof(double) * 1024);
     if (e == cudaSuccess) e = cudaMallocHost(&w->part_host, sizeof(double) * 1024);
     if (e != cudaSuccess) {
         cudaFree(w->r); cudaFree(w->w); cudaFree(w->z); cudaFree(w->p); cudaFree(w->part);

@@ -107,6 +107,8 @@ struct TcArgs {
     double2 *gvals;                         // gradient form: the values too (NULL: not wanted)
     int *dev_flags;
     int TB1;                                // tile rows per slab (multiple of 8, >= C1 + 2q - 1)
+    long long wait_cycles;                  // limit of every mbarrier wait (clock cycles)
+    int withhold;                           // test hook: the prep warps withhold their operand arrival
 };
 
 __device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -183,11 +185,12 @@ __device__ __forceinline__ bool mbar_try(uint32_t mbar, uint32_t parity) {
 }
 
 // wait for the phase of the given parity to complete; false after about a second
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
+// (limit: kWaitCycles unless a test shortens it, see sgl_test_hooks)
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity, long long limit) {
     if (mbar_try(mbar, parity)) return true;
     const long long t0 = clock64();
     while (!mbar_try(mbar, parity))
-        if (clock64() - t0 > kWaitCycles) return false;
+        if (clock64() - t0 > limit) return false;
     return true;
 }
 
@@ -328,6 +331,7 @@ k_nufft_tc(const __grid_constant__ CUtensorMap tmap, NGeom g, TcArgs args) {
     tc_fence_after();
     const uint32_t tmem = sm.tmem_base;
     volatile int *abort_flag = &sm.abort;
+    const long long lim = args.wait_cycles;
 
     if (warp == 0) {
         // ---------------- TMA producer: raw Re / Im tiles of every slab group of every pass
@@ -344,7 +348,7 @@ k_nufft_tc(const __grid_constant__ CUtensorMap tmap, NGeom g, TcArgs args) {
                 bool ok = true;
                 for (int gi = 0; gi < NG; ++gi, ++s) {
                     const int st = s % NS;
-                    if (s >= NS && !mbar_wait(smem_addr(&sm.empty[st]), ((s / NS) + 1) & 1)) ok = false;
+                    if (s >= NS && !mbar_wait(smem_addr(&sm.empty[st]), ((s / NS) + 1) & 1, lim)) ok = false;
                     if (!ok || *abort_flag) { ok = false; break; }
                     const uint32_t fb = smem_addr(&sm.tma_full[st]);
                     mbar_expect_tx(fb, tx);
@@ -355,7 +359,7 @@ k_nufft_tc(const __grid_constant__ CUtensorMap tmap, NGeom g, TcArgs args) {
                 if (!ok) { *abort_flag = 1; break; }
             }
             // the last loads issued into each stage have landed before the CTA may exit
-            for (int k = (s > NS ? s - NS : 0); k < s; ++k) mbar_wait(smem_addr(&sm.tma_full[k % NS]), (k / NS) & 1);
+            for (int k = (s > NS ? s - NS : 0); k < s; ++k) mbar_wait(smem_addr(&sm.tma_full[k % NS]), (k / NS) & 1, lim);
         }
     } else if (warp >= 2 && warp < Cfg::WPREP) {
         // ---------------- split warps: raw tiles -> TF32 head (in place) + remainder
@@ -367,7 +371,7 @@ k_nufft_tc(const __grid_constant__ CUtensorMap tmap, NGeom g, TcArgs args) {
         while (ok && next_pass(it, args)) {
             for (int gi = 0; gi < NG; ++gi, ++s) {
                 const int st = s % NS;
-                ok = __all_sync(0xffffffffu, mbar_wait(smem_addr(&sm.tma_full[st]), (s / NS) & 1) && !*abort_flag);
+                ok = __all_sync(0xffffffffu, mbar_wait(smem_addr(&sm.tma_full[st]), (s / NS) & 1, lim) && !*abort_flag);
                 if (!ok) break;
                 float4 *hi = reinterpret_cast<float4 *>(sm.b[st][0]);
                 float4 *lo = reinterpret_cast<float4 *>(sm.b[st][1]);
@@ -397,13 +401,13 @@ k_nufft_tc(const __grid_constant__ CUtensorMap tmap, NGeom g, TcArgs args) {
             PassIter it;
             while (ok && next_pass(it, args)) {
                 const int abuf = k % Cfg::ABUF;
-                ok = mbar_wait(smem_addr(&sm.afull[abuf]), (k / Cfg::ABUF) & 1) && !*abort_flag;
+                ok = mbar_wait(smem_addr(&sm.afull[abuf]), (k / Cfg::ABUF) & 1, lim) && !*abort_flag;
                 tc_fence_after();
                 const uint32_t a = tmem + Cfg::ABASE + (uint32_t)abuf * Cfg::ACOLS;
                 for (int gi = 0; gi < NG && ok; ++gi, ++s) {
                     const int st = s % NS, buf = s % Cfg::DBUF, use = s / Cfg::DBUF;
-                    ok = mbar_wait(smem_addr(&sm.conv_full[st]), (s / NS) & 1);
-                    if (ok && use >= 1) ok = mbar_wait(smem_addr(&sm.tempty[buf]), (use + 1) & 1);
+                    ok = mbar_wait(smem_addr(&sm.conv_full[st]), (s / NS) & 1, lim);
+                    if (ok && use >= 1) ok = mbar_wait(smem_addr(&sm.tempty[buf]), (use + 1) & 1, lim);
                     if (!ok || *abort_flag) { ok = false; break; }
                     tc_fence_after();
                     const uint32_t bhi = smem_addr(sm.b[st][0]), blo = smem_addr(sm.b[st][1]);
@@ -435,7 +439,7 @@ k_nufft_tc(const __grid_constant__ CUtensorMap tmap, NGeom g, TcArgs args) {
             if (!ok) *abort_flag = 1;
             // every MMA issued above has completed before tensor memory is released
             mma_commit(smem_addr(&sm.done));
-            mbar_wait(smem_addr(&sm.done), 0);
+            mbar_wait(smem_addr(&sm.done), 0, lim);
         }
     } else {
         // ---------------- point warps (one thread per point; TMEM lane = point)
@@ -458,9 +462,9 @@ k_nufft_tc(const __grid_constant__ CUtensorMap tmap, NGeom g, TcArgs args) {
             while (ok && next_pass(it, args)) {
                 const int abuf = n % Cfg::ABUF, use = n / Cfg::ABUF;
                 const int tbuf = n & 1, tuse = n >> 1;        // window tables: two buffers in shared memory
-                if (use >= 1) ok = __all_sync(0xffffffffu, mbar_wait(smem_addr(&sm.aempty[abuf]), (use + 1) & 1) && !*abort_flag);
+                if (use >= 1) ok = __all_sync(0xffffffffu, mbar_wait(smem_addr(&sm.aempty[abuf]), (use + 1) & 1, lim) && !*abort_flag);
                 if (ok && tuse >= 1)
-                    ok = __all_sync(0xffffffffu, mbar_wait(smem_addr(&sm.tabfree[tbuf]), (tuse + 1) & 1) && !*abort_flag);
+                    ok = __all_sync(0xffffffffu, mbar_wait(smem_addr(&sm.tabfree[tbuf]), (tuse + 1) & 1, lim) && !*abort_flag);
                 if (!ok) break;
                 tc_fence_after();
                 const int idx = it.pass * kPM + p;
@@ -545,7 +549,7 @@ k_nufft_tc(const __grid_constant__ CUtensorMap tmap, NGeom g, TcArgs args) {
                 tc_fence_before();
                 __syncwarp();
                 if (lane == 0) {
-                    mbar_arrive(smem_addr(&sm.afull[abuf]));
+                    if (!args.withhold) mbar_arrive(smem_addr(&sm.afull[abuf]));
                     mbar_arrive(smem_addr(&sm.tabfull[tbuf]));
                 }
                 ++n;
@@ -558,7 +562,7 @@ k_nufft_tc(const __grid_constant__ CUtensorMap tmap, NGeom g, TcArgs args) {
             int s = 0, n = 0;
             while (ok && next_pass(it, args)) {
                 const int tbuf = n & 1, tuse = n >> 1;
-                ok = __all_sync(0xffffffffu, mbar_wait(smem_addr(&sm.tabfull[tbuf]), tuse & 1) && !*abort_flag);
+                ok = __all_sync(0xffffffffu, mbar_wait(smem_addr(&sm.tabfull[tbuf]), tuse & 1, lim) && !*abort_flag);
                 if (!ok) break;
                 const int idx = it.pass * kPM + p;
                 const bool live = idx < it.np;
@@ -577,7 +581,7 @@ k_nufft_tc(const __grid_constant__ CUtensorMap tmap, NGeom g, TcArgs args) {
                 float2 acc = make_float2(0.f, 0.f), acc1 = acc, acc2 = acc, accv = acc;
                 for (int gi = 0; gi < NG; ++gi, ++s) {
                     const int buf = s % Cfg::DBUF, use = s / Cfg::DBUF;
-                    ok = __all_sync(0xffffffffu, mbar_wait(smem_addr(&sm.tfull[buf]), use & 1) && !*abort_flag);
+                    ok = __all_sync(0xffffffffu, mbar_wait(smem_addr(&sm.tfull[buf]), use & 1, lim) && !*abort_flag);
                     if (!ok) break;
                     tc_fence_after();
                     const uint32_t taddr = tmem + lane_base + (uint32_t)buf * Cfg::DCOLS;
@@ -649,7 +653,7 @@ k_nufft_tc(const __grid_constant__ CUtensorMap tmap, NGeom g, TcArgs args) {
                 // partner warps (same lane quadrant) combine their partial sums; the half-0 warp writes
                 const int xs = n & 1;
                 if (half == 1) {
-                    if (n >= 2) ok = __all_sync(0xffffffffu, mbar_wait(smem_addr(&sm.xfree[xs]), ((n >> 1) + 1) & 1) && !*abort_flag);
+                    if (n >= 2) ok = __all_sync(0xffffffffu, mbar_wait(smem_addr(&sm.xfree[xs]), ((n >> 1) + 1) & 1, lim) && !*abort_flag);
                     if (!ok) break;
                     sm.xch[xs][0][p] = acc.x;
                     sm.xch[xs][1][p] = acc.y;
@@ -664,7 +668,7 @@ k_nufft_tc(const __grid_constant__ CUtensorMap tmap, NGeom g, TcArgs args) {
                     __syncwarp();
                     if (lane == 0) mbar_arrive(smem_addr(&sm.xfull[xs]));
                 } else {
-                    ok = __all_sync(0xffffffffu, mbar_wait(smem_addr(&sm.xfull[xs]), (n >> 1) & 1) && !*abort_flag);
+                    ok = __all_sync(0xffffffffu, mbar_wait(smem_addr(&sm.xfull[xs]), (n >> 1) & 1, lim) && !*abort_flag);
                     if (!ok) break;
                     acc.x += sm.xch[xs][0][p];
                     acc.y += sm.xch[xs][1][p];
@@ -819,6 +823,8 @@ TcArgs base_args(const sgl_plan *p) {
     a.r2max = p->b.r2max;
     a.dev_flags = p->b.dev_flags;
     a.TB1 = tile_rows(p->q);
+    a.wait_cycles = p->wait_cycles > 0 ? p->wait_cycles : kWaitCycles;
+    a.withhold = (p->test_hooks & SGL_TEST_WITHHOLD_ARRIVAL) ? 1 : 0;
     return a;
 }
 

@@ -95,3 +95,13 @@ def test_batch_create_rejects_bad_arguments_without_cuda(lib):
     assert "SGL_FLAG_OVERLAP_POINTS" in lib.sgl_last_error().decode()
     assert lib.sgl_batch_forward(None, None, None) == 1
     lib.sgl_batch_destroy(None)
+
+
+def test_fault_injection_entry_points_without_cuda(lib):
+    # the test hooks need a plan; the allocation injection is process-wide and one-shot
+    assert lib.sgl_test_hooks(None, 0, 0) == 1
+    assert lib.sgl_test_fail_alloc(0) == 0
+    out = ctypes.c_void_p()
+    assert lib.sgl_plan_create(ctypes.byref(out), 8, 10, 0, 0, 8, 2.0, 0, None) == 2      # SGL_ERR_ALLOC
+    assert out.value is None
+    assert lib.sgl_test_fail_alloc(-1) == 0

@@ -143,3 +143,55 @@ def test_bound_is_attained_by_the_worst_single_frequency():
     for d in range(3):
         b *= 1.0 + nfft.single_frequency_error(int(round(sigma * n[d])), n[d], n[d] // 2, q, window)
     assert 0.5 * e0 <= worst <= b - 1.0
+
+
+# ---- error-driven choice of (sigma, q) with the GB300 cost model (host code)
+SIGMAS = (1.5, 2.0, 2.5, 3.0, 4.0)
+TAP_MS = {0: (9.3 + 15.9) / 4.096e9, 1: (0.89 + 1.49) / 4.096e9}
+CELL_MS = {0: 3.81 / (273 * 145 * 256), 1: 0.69 / (273 * 145 * 256)}
+
+
+def model_ms(B, M, prec, sigma, q):
+    cells = 1.0
+    for d, n in enumerate((4 * B, 2 * B, 2 * B)):
+        N = nfft.fft_size(sigma * n)
+        cells *= N // 2 + 2 * q + 1 if d < 2 and N // 2 + 2 * q + 1 <= N else N
+    return M * (2 * q) ** 3 * TAP_MS[prec] + cells * CELL_MS[prec]
+
+
+def choose(lib, B, M, prec, tol, window=KB):
+    sg, q, ms = ctypes.c_double(), ctypes.c_int(), ctypes.c_double()
+    st = lib.sgl_choose_params(B, M, prec, window, ctypes.c_double(tol), ctypes.byref(sg), ctypes.byref(q), ctypes.byref(ms))
+    return st, sg.value, q.value, ms.value
+
+
+@pytest.mark.parametrize("B,M,prec,tol", [(16, 10**4, 1, 1e-6), (32, 10**6, 1, 1e-6), (32, 10**6, 0, 1e-12),
+                                          (64, 10**3, 0, 1e-9), (64, 10**7, 1, 1e-4), (8, 0, 0, 1e-10)])
+def test_choose_params_meets_tol_at_the_cheapest_modelled_pair(lib, B, M, prec, tol):
+    st, sg, q, ms = choose(lib, B, M, prec, tol)
+    assert st == 0
+    assert c_bound(lib, B, KB, q, sg) <= tol
+    if q > 1:
+        assert c_bound(lib, B, KB, q - 1, sg) > tol          # smallest q for that sigma
+    assert ms == pytest.approx(model_ms(B, M, prec, sg, q), rel=1e-9)
+    # no other candidate sigma reaches tol more cheaply (each at its own smallest q)
+    for s2 in SIGMAS:
+        for q2 in range(1, 17):
+            if c_bound(lib, B, KB, q2, s2) <= tol:
+                assert model_ms(B, M, prec, s2, q2) >= ms * (1 - 1e-12)
+                break
+
+
+def test_choose_params_trades_grid_for_taps(lib):
+    # many points make taps dear (a larger sigma with a smaller q wins); few points make the grid dear
+    _, sg_many, q_many, _ = choose(lib, 32, 10**8, 1, 1e-7)
+    _, sg_few, q_few, _ = choose(lib, 32, 10**2, 1, 1e-7)
+    assert sg_many > sg_few and q_many < q_few
+
+
+def test_choose_params_argument_errors(lib):
+    sg, q = ctypes.c_double(), ctypes.c_int()
+    assert lib.sgl_choose_params(0, 10, 0, KB, ctypes.c_double(1e-6), ctypes.byref(sg), ctypes.byref(q), None) == 1
+    assert lib.sgl_choose_params(8, -1, 0, KB, ctypes.c_double(1e-6), ctypes.byref(sg), ctypes.byref(q), None) == 1
+    assert lib.sgl_choose_params(8, 10, 0, KB, ctypes.c_double(0.0), ctypes.byref(sg), ctypes.byref(q), None) == 1
+    assert lib.sgl_choose_params(8, 10, 0, KB, ctypes.c_double(1e-40), ctypes.byref(sg), ctypes.byref(q), None) == 6

@@ -82,3 +82,20 @@ def test_chosen_cutoff_meets_a_target_accuracy():
     p.close()
     ref, _ = direct.forward(B, x, c)
     assert np.abs(f - ref).max() <= tol * l1 + 1e-12 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("M,tol", [(1500, 1e-9), (1500, 1e-5)])
+def test_chosen_sigma_and_cutoff_meet_a_target_accuracy(M, tol):
+    # (sigma, q) from the cost model and the bound; the plan built with them meets tol per unit ||eta||_1
+    B = 16
+    sigma, q, _ = sgl.choose_params(B, M, tol, precision=sgl.PREC_FP64)
+    x = inputs.points_gaussian(M, 7500)
+    c = inputs.coefficients(B, 7501)
+    p = sgl.Plan(B, M, precision=sgl.PREC_FP64, q=q, sigma=sigma, device=DEV)
+    assert p.error_bound() <= tol
+    p.set_points(gpu(x))
+    l1 = p.eta_l1(gpu(c))
+    f = p.forward(gpu(c)).cpu().numpy()
+    p.close()
+    ref, _ = direct.forward(B, x, c)
+    assert np.abs(f - ref).max() <= tol * l1 + 1e-12 * np.abs(ref).max()
