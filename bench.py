@@ -331,7 +331,9 @@ def run_ours(args):
         inverse_line = {"setup": "Sect. 8 last test: Cartesian grid G_N, N=50 (M=125000), kappa=5, KB q=8, sigma=2, FP64; "
                                  "CGNR (sgl_inverse) from the mid-point rule (sgl_midpoint_guess); samples from the FP64 "
                                  "forward transform of seeded random coefficients U[-1/2,1/2]^2"}
-        for Bi, iters in ((8, 200), (16, 20)):
+        # B = 8: a fixed budget of 200 iterations; B = 16: until the relative residual is 1e-4
+        # (at most 600 iterations), reporting the iterations that took
+        for Bi, iters, tol in ((8, 200, 0.0), (16, 600, 1e-4)):
             ip = sgl.Plan(Bi, Mi, precision=sgl.PREC_FP64, window=sgl.WIN_KB, q=8, sigma=2.0, device=dev)
             ip.set_points(torch.from_numpy(xg).to(dev))
             c_true = torch.from_numpy(inputs.coefficients(Bi, inputs.seed_for(5))).to(dev)
@@ -340,7 +342,7 @@ def run_ours(args):
             ip.inverse(f_in, coef0=c0, iters=2)          # warm-up (work vectors)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            ci, resi, ki = ip.inverse(f_in, coef0=c0, iters=iters, method="cgnr")
+            ci, resi, ki = ip.inverse(f_in, coef0=c0, iters=iters, tol=tol, method="cgnr")
             torch.cuda.synchronize()
             el = time.perf_counter() - t0
 
@@ -348,10 +350,58 @@ def run_ours(args):
                 d = (c - c_true).abs()
                 return [float(d.max()), float((d / c_true.abs()).max())]
             inverse_line["B=%d" % Bi] = {
-                "Nc": int(ip.Nc), "iterations": ki, "ms_per_iteration": round(el / max(ki, 1) * 1e3, 3),
+                "Nc": int(ip.Nc), "iterations": ki, "iteration_budget": iters, "residual_target": tol,
+                "ms_per_iteration": round(el / max(ki, 1) * 1e3, 3),
                 "relative_residual": resi, "max_abs_rel_error_initial": errs(c0), "max_abs_rel_error_final": errs(ci)}
             ip.close()
             del ip
+            torch.cuda.empty_cache()
+
+    # ---- the batch workload (256 instances, B uniform in 8..48, M = 10^U[3,5], q = 8): forward +
+    # adjoint of every instance on fixed points, graph-captured with the autotuned lane count
+    # against one launch after another on a single lane; Mpoints/s = all instances' points / time
+    batch_line = None
+    if not args.no_batch and rank == 0:
+        specs = inputs.batch_instances(256, inputs.seed_for(3))
+        tot = sum(M for _, M in specs)
+        bcs = [torch.from_numpy(inputs.coefficients(Bi, inputs.seed_for(3, 10 + i))).to(dev) for i, (Bi, _) in enumerate(specs)]
+        bxs = [torch.from_numpy(inputs.points_gaussian(Mi, inputs.seed_for(3, 1000 + i))).to(dev) for i, (_, Mi) in enumerate(specs)]
+        bys = [torch.from_numpy(inputs.values(Mi, inputs.seed_for(3, 2000 + i))).to(dev) for i, (_, Mi) in enumerate(specs)]
+        bfo = [torch.empty(Mi, dtype=torch.complex128, device=dev) for _, Mi in specs]
+        bao = [torch.empty(sgl.num_coeffs(Bi), dtype=torch.complex128, device=dev) for Bi, _ in specs]
+        batch_line = {"workload": "256 instances, B uniform in 8..48, M = round(10^U[3,5]) (%d points in all), KB q=8, "
+                                  "sigma=2; step = batch forward + batch adjoint on fixed points" % tot,
+                      "unit": UNIT}
+        for prec_name, prec in (("fp32_mixed", sgl.PREC_FP32_MIXED), ("fp64", sgl.PREC_FP64)):
+            if prec_name == "fp64" and args.no_fp64:
+                continue
+            bp = sgl.BatchPlan([Bi for Bi, _ in specs], [Mi for _, Mi in specs], precision=prec, q=8, device=dev)
+            bp.set_points(bxs)
+            res = {}
+            for mode in ("one_launch_per_instance", "graph_autotuned_lanes"):
+                if mode == "graph_autotuned_lanes":
+                    bp.use_graph(True)
+                    lanes, _ = bp.autotune(None)
+                else:
+                    bp.use_graph(False)
+                    bp.set_lanes(1)
+                    lanes = 1
+                for _ in range(args.warmup):
+                    bp.forward(bcs, bfo)
+                    bp.adjoint(bys, bao)
+                barrier()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                for _ in range(args.steps):
+                    bp.forward(bcs, bfo)
+                    bp.adjoint(bys, bao)
+                e1.record()
+                barrier()
+                ms = e0.elapsed_time(e1) / args.steps
+                res[mode] = {"value": round(tot / (ms * 1e-3) / 1e6, 4), "ms_per_step": round(ms, 3), "lanes": lanes}
+            batch_line[prec_name] = res
+            bp.close()
+            del bp
             torch.cuda.empty_cache()
 
     # ---- end to end through the C-ABI with host buffers (copies inside the timed region)
@@ -401,6 +451,13 @@ def run_ours(args):
     line = {"metric": METRIC, "value": round(head["value"], 4), "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(head["ms_per_step"], 4), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+            "fp32_mixed_vs_fp64": None if "fp64" not in results else {
+                "fp64_double_float_loops": {"value": round(results["fp64"]["value"], 4),
+                                            "ratio": round(head["value"] / results["fp64"]["value"], 3)},
+                "fp64_binary64_loops": {"value": round(results["fp64_native"]["value"], 4),
+                                        "ratio": round(head["value"] / results["fp64_native"]["value"], 3)},
+                "note": "same step; FP64 plan = binary64 everywhere except the three windowed loops, which run in "
+                        "double-float (default) or binary64 (SGL_FLAG_NATIVE_FP64) arithmetic"},
             "data": "synthetic (seeded): coefficients U[-1/2,1/2]^2, points N(0, I/2) in |x| <= 5, values U[-1/2,1/2]^2",
             "config": {"workload": "B=64 (Nc=89440), M=1e6 points per GPU, sigma=2, Kaiser-Bessel q=8; step = set_points"
                                    " + forward values with point gradient (sgl_forward_grad, one pass) + adjoint",
@@ -425,6 +482,7 @@ def run_ours(args):
             "fp32_mixed_other_cutoffs": by_q,
             "by_call": by_call,
             "inverse": inverse_line,
+            "batch": batch_line,
             "e2e": e2e}
 
     # ---- CPU baseline (oracle on the host cores, rank 0, N = 1) and the measured error on its sample
@@ -541,6 +599,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extra-q", action="store_true")
     ap.add_argument("--no-inverse", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 256-instance batch leg")
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 comparison run (profiling captures)")
     args = ap.parse_args()
     if args.warmup < 3:

@@ -349,13 +349,23 @@ sgl_status sgl_sync(sgl_plan *plan);
 /*
  * Batches: n independent transforms, instance i with bandwidth B[i] and at most
  * M_max[i] points, all with the same precision, window, q and sigma, issued together
- * on one stream (Def. of the NDSGLFT applied per instance).  The instances run in
- * stream order and share the FFT work buffers (sized for the largest instance).
- * With sgl_batch_use_graph(b, 1) a batch forward or adjoint is captured into a CUDA
- * graph the first time and replayed while the pointer arrays and point counts are the
- * same as at capture (a change recaptures).  Pointer arrays are host arrays of n
- * device pointers, with the per-instance layouts of sgl_forward / sgl_adjoint.
- * SGL_FLAG_PROFILE and SGL_FLAG_OVERLAP_POINTS are not accepted for batches.
+ * (Def. of the NDSGLFT applied per instance).  The instances are spread over L lanes -- each a
+ * stream of its own with FFT work buffers shared by the instances of that lane -- by a cost
+ * estimate (longest first onto the least loaded lane), so that small instances run side by side;
+ * every batch call forks from the batch's stream into the lanes and joins back, so its results
+ * are ordered on the batch's stream like a single call.  L starts at min(n, 8); sgl_batch_set_lanes
+ * changes it (1 <= L <= min(n, 32)) and sgl_batch_autotune chooses it by timing.
+ * With sgl_batch_use_graph(b, 1) a batch forward or adjoint (fork, every lane's kernels, join) is
+ * captured into one CUDA graph the first time and replayed while the pointer arrays and point
+ * counts are the same as at capture (a change, new points or new lanes recapture).  Pointer
+ * arrays are host arrays of n device pointers, with the per-instance layouts of sgl_forward /
+ * sgl_adjoint.  SGL_FLAG_PROFILE and SGL_FLAG_OVERLAP_POINTS are not accepted for batches.
+ * sgl_batch_autotune: with cache_path (may be NULL) naming a JSON file that already holds this
+ *   batch's entry (keyed on precision, window, q, sigma, n and a hash of the (B, M_max) list), takes
+ *   its lane count; otherwise times a forward plus an adjoint (two untimed, three timed, graph mode
+ *   as set) for L = 1, 2, 4, 8, 16, 32 (<= n), keeps the fastest and records all timings in the
+ *   file.  Needs sgl_batch_set_points; allocates and releases one block of timing inputs.
+ *   lanes_out, ms_out (may be NULL): the choice and its time per forward + adjoint (-1 if cached).
  */
 typedef struct sgl_batch sgl_batch;
 sgl_status sgl_batch_create(sgl_batch **out, int n, const int *B, const int64_t *M_max, int precision, int window,
@@ -367,6 +377,9 @@ sgl_status sgl_batch_forward(sgl_batch *batch, const double *const *coef_dev, do
 sgl_status sgl_batch_adjoint(sgl_batch *batch, const double *const *vals_dev, double *const *coef_dev);
 /* n, graph replays so far, device bytes owned (any output may be NULL) */
 sgl_status sgl_batch_info(const sgl_batch *batch, int *n, int64_t *graph_launches, int64_t *workspace_bytes);
+sgl_status sgl_batch_set_lanes(sgl_batch *batch, int lanes);
+sgl_status sgl_batch_lanes(const sgl_batch *batch, int *lanes);
+sgl_status sgl_batch_autotune(sgl_batch *batch, const char *cache_path, int *lanes_out, double *ms_out);
 /* synchronize the stream and report deferred device errors of any instance */
 sgl_status sgl_batch_sync(sgl_batch *batch);
 

@@ -98,7 +98,9 @@ def load_library(build_if_missing=True):
         for name, args in [("sgl_batch_use_graph", [vp, ctypes.c_int]), ("sgl_batch_set_points", [vp, pp, ctypes.POINTER(i64)]),
                            ("sgl_batch_forward", [vp, pp, pp]), ("sgl_batch_adjoint", [vp, pp, pp]),
                            ("sgl_batch_info", [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(i64), ctypes.POINTER(i64)]),
-                           ("sgl_batch_sync", [vp])]:
+                           ("sgl_batch_sync", [vp]), ("sgl_batch_set_lanes", [vp, ctypes.c_int]),
+                           ("sgl_batch_lanes", [vp, ctypes.POINTER(ctypes.c_int)]),
+                           ("sgl_batch_autotune", [vp, ctypes.c_char_p, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)])]:
             f = getattr(lib, name)
             f.restype = ctypes.c_int
             f.argtypes = args
@@ -422,6 +424,21 @@ class BatchPlan:
 
     def sync(self):
         _check(self.lib.sgl_batch_sync(self._h))
+
+    def set_lanes(self, lanes):
+        _check(self.lib.sgl_batch_set_lanes(self._h, int(lanes)))
+
+    def lanes(self):
+        v = ctypes.c_int()
+        _check(self.lib.sgl_batch_lanes(self._h, ctypes.byref(v)))
+        return v.value
+
+    def autotune(self, cache_path=None):
+        """sgl_batch_autotune: (lanes, ms per forward + adjoint, or -1 when taken from the cache)."""
+        L, ms = ctypes.c_int(), ctypes.c_double()
+        _check(self.lib.sgl_batch_autotune(self._h, cache_path.encode() if cache_path else None, ctypes.byref(L),
+                                           ctypes.byref(ms)))
+        return L.value, ms.value
 
 
 def noalloc_max_b():
