@@ -578,6 +578,7 @@ sgl_status plan_create_impl(sgl_plan **out, int B, int64_t M_max, int precision,
     ALLOC(b.scalar, 1);
     ALLOC(b.sched, 4);
     ALLOC(b.wtab, (size_t)kWinTab);
+    ALLOC(b.rot, (size_t)(2 * kRotK + 1));
     if (flags & SGL_FLAG_HOST_IO) {
         ALLOC(b.io_xyz, 3 * Mc);
         ALLOC(b.io_coef, (size_t)(2 * p->Nc));
@@ -641,6 +642,18 @@ sgl_status plan_create_impl(sgl_plan **out, int B, int64_t M_max, int precision,
         std::vector<double> wt;
         window_tables(p, wt);
         if ((e = upload(b.wtab, wt, p->stream)) != cudaSuccess) return fail(SGL_ERR_CUDA, "upload window tables");
+    }
+    {
+        static const std::vector<double2> rot = [] {
+            std::vector<double2> v(2 * kRotK + 1);
+            const long double pi = 3.14159265358979323846264338327950288L;
+            for (int k = -kRotK; k <= kRotK; ++k) {
+                const long double th = pi * k / kRotK;
+                v[k + kRotK] = make_double2((double)cosl(th), (double)sinl(th));
+            }
+            return v;
+        }();
+        if ((e = upload(b.rot, rot, p->stream)) != cudaSuccess) return fail(SGL_ERR_CUDA, "upload angle table");
     }
     if ((e = cudaMemsetAsync(b.dev_flags, 0, sizeof(int), p->stream)) != cudaSuccess) return fail(SGL_ERR_CUDA, "memset");
     if ((flags & SGL_FLAG_OVERLAP_POINTS) && !shared) {   // the plans of a batch bin on the batch stream

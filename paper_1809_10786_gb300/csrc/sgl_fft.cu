@@ -282,6 +282,23 @@ __global__ void __launch_bounds__(256) k_fft_pass(FftPass ps, int TB, int lgTB, 
         __syncthreads();
     }
 
+    // ---- split-plane output with a wrapped halo (one line after the other, consecutive columns)
+    if constexpr (std::is_same<OutC, float2>::value) {
+        if (ps.planes) {
+            for (int bl = 0; bl < nlines; ++bl) {
+                float *row = ps.planes + (inner0 + bl) * ps.pitch;
+                for (int k = tid; k < ps.pitch; k += NT) {
+                    int e = (k - ps.halo) % N;       // the halo can span more than one period of short lines
+                    if (e < 0) e += N;
+                    const C2<T> v = buf[bl * LS + __ldg(ps.rev + e)];
+                    row[k] = narrow<float>(v.x);
+                    row[ps.plane_n + k] = narrow<float>(v.y);
+                }
+            }
+            return;
+        }
+    }
+
     // ---- store the output window (digit-reversed slots), optional scale on output
     const bool out_elem_fast = (ps.out_se == 1);
     const int bl_fast = tid & (TB - 1), pos_step = NT >> lgTB;
@@ -379,6 +396,12 @@ cudaError_t forward_passes(sgl_plan *p) {
     c.nb_outer = 1; c.nb_inner = (int64_t)A0.rows * A1.rows;
     c.in_so = 0; c.in_si = W; c.in_se = 1;
     c.out_so = 0; c.out_si = A2.N; c.out_se = 1;
+    if (f32 && p->tc_interp) {                    // the tensor-core interpolation reads the planes only
+        c.planes = p->b.planes;
+        c.pitch = tc_pitch(A2.N);
+        c.halo = tc_halo(p->q);
+        c.plane_n = c.nb_inner * c.pitch;
+    }
     return run_pass<T, C2<T>, C2<T>, LOAD_STRIDED>(p, c, p->b.bufB, p->b.bufA, zs, 0);
 }
 

@@ -33,6 +33,10 @@ struct BinGeom {
 // CTA of the CUDA-core spreading kernel).
 constexpr int kTcPass = 128;
 
+// angles of the points (sgl_points.cu): a binary32 first guess picks the nearest k pi / kRotK, whose
+// cosine and sine come from a table; an arctangent series in binary64 adds the small rest
+constexpr int kRotK = 2048;
+
 // Tabulated windows of the double-float FP64 kernels: psi (even) and psi' (odd) of each axis on
 // [0, q] as kWinNI pieces of degree kWinDeg in the offset from the piece's midpoint (psi is an
 // entire function of x: sinh(b s) / s is a power series in s^2 = q^2 - x^2), fitted on the host in
@@ -87,6 +91,12 @@ struct FftPass {
     const double *line_scale;       // optional factor per flattened line index outer*nb_inner+inner
     const void *tw;                 // twiddle table (double2 or float2)
     const int *rev;
+    // optional FP32 split-plane output (the tensor-core interpolation's layout): instead of out,
+    // line i writes Re, Im of position (e - halo) mod N at planes[i pitch + e], planes[plane_n + i pitch + e],
+    // e in [0, pitch)
+    float *planes;
+    int64_t plane_n;
+    int pitch, halo;
 };
 
 struct Buffers {
@@ -119,6 +129,7 @@ struct Buffers {
     double *scalar;            // [1] device accumulator of small reductions (sgl_eta_l1)
     int *sched;                // [4] work counters of the persistent kernels (zeroed before each launch)
     double *wtab;              // [kWinTab] tabulated windows (FP64 plans)
+    double2 *rot;              // [2 kRotK + 1] (cos, sin) of k pi / kRotK, k = -kRotK .. kRotK (point angles)
     // host-IO staging
     double *io_xyz, *io_coef, *io_vals, *io_grad, *io_out;
     // tensor-core interpolation (FP32-mixed): grid as planes Re, Im [rows0][rows1][pitch] with an azimuthal halo
@@ -197,7 +208,7 @@ cudaError_t launch_polar_forward(sgl_plan *p);
 cudaError_t launch_trig_export(sgl_plan *p, double2 *eta);
 cudaError_t launch_polar_adjoint(sgl_plan *p, const double2 *eta_full);
 cudaError_t launch_radial_adjoint(sgl_plan *p, double2 *coef);
-cudaError_t launch_fft_forward(sgl_plan *p);    // zeta -> grid (bufA)
+cudaError_t launch_fft_forward(sgl_plan *p);    // zeta -> grid (bufA; b.planes when the interpolation is on tensor cores)
 cudaError_t launch_fft_adjoint(sgl_plan *p);    // grid (bufA) -> eta' full support (bufB, FP64)
 cudaError_t launch_interp(sgl_plan *p, double2 *vals);
 cudaError_t launch_spread(sgl_plan *p, const double2 *vals);

@@ -16,10 +16,9 @@
 // product at FP32 accuracy.  The gradient adds a second product with the derivative weights
 // w2' and contracts D_ta with w0', w1' as well.
 //
-// Data: the forward FFT's grid is copied once per call into two FP32 planes (Re, Im) with a
-// wrapped halo on the azimuthal axis, so that the tiles of G slabs are one TMA box (32 lanes
-// x TB1 rows x G slabs, 128-byte swizzle) per plane; the split into head and remainder happens
-// on chip.
+// Data: the forward FFT's last pass writes the grid as two FP32 planes (Re, Im) with a wrapped
+// halo on the azimuthal axis, so that the tiles of G slabs are one TMA box (32 lanes x TB1 rows
+// x G slabs, 128-byte swizzle) per plane; the split into head and remainder happens on chip.
 //
 // One persistent CTA per SM walks its super-bins in 128-point passes.  Warp 0 issues the TMA
 // loads into a ring of tile stages, warps 2-3 split each landed tile in place, warp 1 owns
@@ -706,21 +705,6 @@ k_nufft_tc(const __grid_constant__ CUtensorMap tmap, NGeom g, TcArgs args) {
     }
 }
 
-// grid[r0][r1][c] (FP32 complex) -> planes[2][r0][r1][pitch]: Re, Im at halo column e = c + L
-// (every e in [0, pitch) holds grid column (e - L) mod N2)
-__global__ void k_halo_planes(const float2 *__restrict__ grid, float *__restrict__ planes, int64_t lines, int N2, int pitch,
-                              int L) {
-    const int64_t n = lines * pitch;
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t line = t / pitch;
-        const int e = (int)(t - line * pitch);
-        const float2 v = grid[line * N2 + wrap_index(e - L, N2)];
-        planes[t] = v.x;
-        planes[n + t] = v.y;
-    }
-}
-
-
 int tile_rows(int q) { return (kC1 + 2 * q - 1 + 7) / 8 * 8; }
 
 }  // namespace
@@ -738,7 +722,7 @@ bool tc_eligible(const sgl_plan *p) {
 void tc_choose(sgl_plan *p) {
     const bool use = p->tc && ((p->flags & SGL_FLAG_TC) || p->q >= 6);
     p->tc_interp = use;
-    p->tc_grad = use;
+    p->tc_grad = use;         // equal: the forward FFT then writes only the planes both kernels read
     p->tc_spread = false;     // spreading: the CUDA-core kernel (sgl_nufft.cu) wins in time and accuracy
 }
 
@@ -785,22 +769,9 @@ cudaError_t tc_make_tensor_map(sgl_plan *p) {
 
 namespace {
 
-cudaError_t halo_planes(sgl_plan *p) {
-    const int64_t lines = (int64_t)p->ax[0].rows * p->ax[1].rows;
-    const int pitch = tc_pitch(p->ax[2].N);
-    const int64_t n = lines * pitch;
-    int64_t blocks = (n + 255) / 256;
-    if (blocks > (int64_t)p->num_sms * 8) blocks = (int64_t)p->num_sms * 8;
-    k_halo_planes<<<(unsigned)blocks, 256, 0, p->stream>>>((const float2 *)p->b.bufA, p->b.planes, lines, p->ax[2].N, pitch,
-                                                          tc_halo(p->q));
-    p->launches += 1;
-    return cudaGetLastError();
-}
-
 template <int WIN, bool GRAD>
 cudaError_t run_tc(sgl_plan *p, TcArgs a) {
-    cudaError_t e = halo_planes(p);
-    if (e != cudaSuccess) return e;
+    cudaError_t e;
     // the 512 TMEM columns a CTA allocates are the whole SM's: ask for enough shared memory that
     // no second CTA of this kernel fits beside it (its allocation would wait for the first)
     const size_t smem = std::max<size_t>(sizeof(TcSmem<GRAD>) + 1024, (size_t)120 * 1024);

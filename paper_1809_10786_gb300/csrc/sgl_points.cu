@@ -47,16 +47,37 @@ __device__ __forceinline__ double rho_of(const unsigned long long *r2max) {
     return rho > 0.0 ? rho : 1.0;
 }
 
-// grid coordinates u_d = N_d t_d / (2 pi) of one point
+// atan2(a, b) in binary64 (a published method: argument reduction by a table of angles plus a
+// Taylor series).  A binary32 first guess g (on the operands scaled by a power of two, so neither
+// overflows nor underflows in binary32) picks th_k = k pi / kRotK nearest to it; with c = cos th_k,
+// s = sin th_k from the table, tan(theta - th_k) = (a c - b s) / (b c + a s), and
+// theta = th_k + atan(t), |t| <= tan(pi / 2 kRotK + 1e-6) < 8e-4, by the series t - t^3/3 + t^5/5 -
+// t^7/7 (the next term is below 1e-27).  atan2(0, 0) = 0.
+__device__ __forceinline__ double atan2_tab(double a, double b, const double2 *__restrict__ rot) {
+    const double m = fmax(fabs(a), fabs(b));
+    if (!(m > 0.0)) return 0.0;
+    const int e = max(min((int)((__double_as_longlong(m) >> 52) & 0x7ff) - 1023, 1000), -1000);   // m = 1.f 2^e
+    const double sc = __longlong_as_double((long long)(1023 - e) << 52);                         // 2^-e (exact)
+    const float g = atan2f((float)(a * sc), (float)(b * sc));
+    const int k = __float2int_rn(g * ((float)kRotK / 3.14159265f));
+    const double2 cs = __ldg(rot + (k + kRotK));
+    const double num = fma(a, cs.x, -b * cs.y);                // r sin(theta - th_k)
+    const double den = fma(b, cs.x, a * cs.y);                 // r cos(theta - th_k) > 0
+    const double t = num / den, t2 = t * t;
+    const double at = fma(t * t2, fma(t2, fma(t2, -1.0 / 7.0, 1.0 / 5.0), -1.0 / 3.0), t);
+    return fma((double)k, kPi / kRotK, at);
+}
+
+// grid coordinates u_d = N_d t_d / (2 pi) of one point.  t0 = arccos(gamma), gamma = (2r - rho)/rho,
+// is atan2(sqrt(1 - gamma^2), gamma) with the common factor 2/rho left out:
+// atan2(2 sqrt(r (rho - r)), 2r - rho) (r <= rho: rho carries the 2^-20 margin).
 __device__ __forceinline__ void grid_coords(double x, double y, double z, double rho, const PointGeom &g,
-                                            double &u0, double &u1, double &u2) {
-    const double rxy = hypot(x, y);
-    const double r = hypot(rxy, z);
-    double gam = (2.0 * r - rho) / rho;
-    gam = fmin(1.0, fmax(-1.0, gam));
-    const double t0 = acos(gam);
-    const double t1 = atan2(rxy, z);           // [0, pi]
-    double t2 = atan2(y, x);                   // (-pi, pi]
+                                            const double2 *__restrict__ rot, double &u0, double &u1, double &u2) {
+    const double rxy2 = fma(x, x, y * y);
+    const double rxy = sqrt(rxy2), r = sqrt(fma(z, z, rxy2));
+    const double t0 = atan2_tab(2.0 * sqrt(fmax(r * (rho - r), 0.0)), 2.0 * r - rho, rot);
+    const double t1 = atan2_tab(rxy, z, rot);                  // [0, pi]
+    double t2 = atan2_tab(y, x, rot);                          // [-pi, pi]
     if (t2 < 0.0) t2 += 2.0 * kPi;
     const double inv2pi = 1.0 / (2.0 * kPi);
     u0 = g.N[0] * t0 * inv2pi;
@@ -77,14 +98,14 @@ __device__ __forceinline__ int bin_of_coords(double u0, double u1, double u2, co
 }
 
 __global__ void k_transform_points(const double *__restrict__ xyz, int64_t M, const unsigned long long *__restrict__ r2max,
-                                   PointGeom g, double *__restrict__ u_tmp, int *__restrict__ bin_of,
+                                   PointGeom g, const double2 *__restrict__ rot, double *__restrict__ u_tmp, int *__restrict__ bin_of,
                                    int *__restrict__ rank_of, int *__restrict__ bin_count) {
     const double rho = rho_of(r2max);
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < M; i += (int64_t)gridDim.x * blockDim.x) {
         double x = xyz[3 * i], y = xyz[3 * i + 1], z = xyz[3 * i + 2];
         if (!(isfinite(x) && isfinite(y) && isfinite(z))) { x = 0.0; y = 0.0; z = 0.0; }
         double u0, u1, u2;
-        grid_coords(x, y, z, rho, g, u0, u1, u2);
+        grid_coords(x, y, z, rho, g, rot, u0, u1, u2);
         u_tmp[3 * i] = u0; u_tmp[3 * i + 1] = u1; u_tmp[3 * i + 2] = u2;
         const int b = bin_of_coords(u0, u1, u2, g);
         bin_of[i] = b;
@@ -255,7 +276,7 @@ cudaError_t launch_points_bins(sgl_plan *p, const double *xyz, int64_t M, cudaSt
     g.cmax0 = p->ax[0].N / 2;
     g.cmax1 = p->ax[1].N / 2;
     if (M > 0) {
-        k_transform_points<<<grid_blocks(M, kThreads), kThreads, 0, s>>>(xyz, M, b.r2max, g, b.u_tmp, b.bin_of, b.rank_of, b.bin_count);
+        k_transform_points<<<grid_blocks(M, kThreads), kThreads, 0, s>>>(xyz, M, b.r2max, g, b.rot, b.u_tmp, b.bin_of, b.rank_of, b.bin_count);
         scan(b.bin_count, p->nbins, b.scan_tmp, b.bin_off, s);
         k_scatter_points<<<grid_blocks(M, kThreads), kThreads, 0, s>>>(M, b.u_tmp, b.bin_of, b.rank_of, b.bin_off, g, b.u_sorted,
                                                                        b.pts32, b.perm);
