@@ -108,11 +108,18 @@ def test_paper_last_test_setup_small(native, later):
     w = (2.0 * kappa / N) ** 3 * np.exp(-np.sum(x * x, axis=1))
     p = plan(B, x, native=native)
     c0 = p.midpoint_guess(gpu(f), gpu(w))
-    c, res, k = p.inverse(gpu(f), coef0=c0, iters=40, method="cgnr")
     L = inverse.matrix(B, x)
     c_or, res_or = inverse.cgnr(L, f, c0.cpu().numpy(), 40)
-    assert res == pytest.approx(res_or[-1] / np.linalg.norm(f), rel=later)     # sensitivity: module docstring
-    assert res <= res_or[0] / np.linalg.norm(f)
+    nf = np.linalg.norm(f)
+    # Nc = 30 unknowns: in exact arithmetic CGNR ends by iteration 30, and past it the residual is
+    # set by rounding (the oracle alone gave 8.9e-9 and 5.5e-9 at iteration 40 from initial
+    # guesses 1e-16 apart).  Iteration 20 moves by 0.3 % under 1e-15 perturbations of the pair
+    # (1.7 % under 1e-14), so it carries the pin; iteration 40 only its size.
+    c, res, k = p.inverse(gpu(f), coef0=c0, iters=20, method="cgnr")
+    assert res == pytest.approx(res_or[20] / nf, rel=later)     # sensitivity: module docstring
+    c, res, k = p.inverse(gpu(f), coef0=c0, iters=40, method="cgnr")
+    assert res <= res_or[0] / nf
+    assert res <= 10.0 * res_or[40] / nf
     # run to convergence: the consistent system gives back the coefficients
     c, res, k = p.inverse(gpu(f), coef0=c0, iters=2000, tol=1e-10, method="cgnr")
     assert res <= 1e-10
