@@ -562,6 +562,7 @@ sgl_status plan_create_impl(sgl_plan **out, int B, int64_t M_max, int precision,
     ALLOC(b.u_tmp, 3 * Mc);
     ALLOC(b.u_sorted, 3 * Mc);
     ALLOC(b.pts32, Mc);
+    ALLOC(b.rec_tmp, Mc);
     if (precision == SGL_FP32_MIXED) ALLOC(b.ys32, Mc);
     ALLOC(b.perm, Mc);
     ALLOC(b.bin_of, Mc);
@@ -579,6 +580,7 @@ sgl_status plan_create_impl(sgl_plan **out, int B, int64_t M_max, int precision,
     ALLOC(b.sched, 4);
     ALLOC(b.wtab, (size_t)kWinTab);
     ALLOC(b.rot, (size_t)(2 * kRotK + 1));
+    ALLOC(b.rotf, (size_t)(2 * kRotK + 1));
     if (flags & SGL_FLAG_HOST_IO) {
         ALLOC(b.io_xyz, 3 * Mc);
         ALLOC(b.io_coef, (size_t)(2 * p->Nc));
@@ -644,16 +646,28 @@ sgl_status plan_create_impl(sgl_plan **out, int B, int64_t M_max, int precision,
         if ((e = upload(b.wtab, wt, p->stream)) != cudaSuccess) return fail(SGL_ERR_CUDA, "upload window tables");
     }
     {
-        static const std::vector<double2> rot = [] {
-            std::vector<double2> v(2 * kRotK + 1);
+        // (cos, sin) of k pi / kRotK in extended precision, rounded to binary64 and to double-float pairs
+        struct RotTables { std::vector<double2> d; std::vector<float4> f; };
+        static const RotTables rot = [] {
+            RotTables t;
+            t.d.resize(2 * kRotK + 1);
+            t.f.resize(2 * kRotK + 1);
             const long double pi = 3.14159265358979323846264338327950288L;
+            auto pair = [](long double v, float &h, float &l) {
+                h = (float)v;
+                l = (float)(v - (long double)h);
+            };
             for (int k = -kRotK; k <= kRotK; ++k) {
-                const long double th = pi * k / kRotK;
-                v[k + kRotK] = make_double2((double)cosl(th), (double)sinl(th));
+                const long double th = pi * k / kRotK, c = cosl(th), s = sinl(th);
+                t.d[k + kRotK] = make_double2((double)c, (double)s);
+                float4 &f = t.f[k + kRotK];
+                pair(c, f.x, f.y);
+                pair(s, f.z, f.w);
             }
-            return v;
+            return t;
         }();
-        if ((e = upload(b.rot, rot, p->stream)) != cudaSuccess) return fail(SGL_ERR_CUDA, "upload angle table");
+        if ((e = upload(b.rot, rot.d, p->stream)) != cudaSuccess || (e = upload(b.rotf, rot.f, p->stream)) != cudaSuccess)
+            return fail(SGL_ERR_CUDA, "upload angle tables");
     }
     if ((e = cudaMemsetAsync(b.dev_flags, 0, sizeof(int), p->stream)) != cudaSuccess) return fail(SGL_ERR_CUDA, "memset");
     if ((flags & SGL_FLAG_OVERLAP_POINTS) && !shared) {   // the plans of a batch bin on the batch stream

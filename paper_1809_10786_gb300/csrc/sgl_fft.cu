@@ -19,6 +19,7 @@
 // points: a binary32 radial pass alone made the adjoint coefficients 2.4e-5 wrong relative to
 // their maximum; binary32 angular passes, whose errors stay on the rows of their own radius, and
 // binary32 spreading 2e-8 and 6e-8).
+#include "sgl_dfl.cuh"
 #include "sgl_internal.cuh"
 
 #include <type_traits>
@@ -26,38 +27,7 @@
 namespace sgl {
 namespace {
 
-// Double-float scalar: the unevaluated sum h + l of two binary32 numbers.  Sums by TwoSum
-// (Knuth), products by TwoProduct (Dekker; exact with a fused multiply-add), each renormalized
-// by Fast2Sum: a relative rounding of about 2^-44 per operation, normwise through a DFT.  The
-// rounded intrinsics keep the compiler from fusing or reordering the error terms.
-struct dfl {
-    float h, l;
-    dfl() = default;
-    __host__ __device__ constexpr dfl(float hh, float ll) : h(hh), l(ll) {}
-    __host__ __device__ constexpr dfl(int v) : h((float)v), l(0.f) {}
-    __host__ __device__ constexpr dfl(float v) : h(v), l(0.f) {}
-    __host__ __device__ constexpr dfl(double v) : h((float)v), l((float)(v - (double)(float)v)) {}
-};
-struct dfl2 { dfl x, y; };
-__device__ __forceinline__ dfl fast_two_sum(float a, float b) {       // |a| >= |b| (else a rounding of b's size)
-    const float s = __fadd_rn(a, b);
-    return dfl(s, __fsub_rn(b, __fsub_rn(s, a)));
-}
-__device__ __forceinline__ dfl operator+(dfl a, dfl b) {
-    const float s = __fadd_rn(a.h, b.h);
-    const float bb = __fsub_rn(s, a.h);
-    const float e = __fadd_rn(__fsub_rn(a.h, __fsub_rn(s, bb)), __fsub_rn(b.h, bb));   // a.h + b.h = s + e exactly
-    return fast_two_sum(s, __fadd_rn(e, __fadd_rn(a.l, b.l)));
-}
-__device__ __forceinline__ dfl operator-(dfl a) { return dfl(-a.h, -a.l); }
-__device__ __forceinline__ dfl operator-(dfl a, dfl b) { return a + (-b); }
-__device__ __forceinline__ dfl operator*(dfl a, dfl b) {
-    const float p = __fmul_rn(a.h, b.h);
-    float e = fmaf(a.h, b.h, -p);                                      // a.h b.h = p + e exactly
-    e = fmaf(a.h, b.l, e);
-    e = fmaf(a.l, b.h, e);
-    return fast_two_sum(p, e);
-}
+// Double-float scalars (sgl_dfl.cuh) carry the radial passes of FP32-mixed plans.
 // multiplication by a sign s = +1 or -1 (the transform direction)
 __device__ __forceinline__ dfl operator*(int s, dfl a) { return s > 0 ? a : -a; }
 __device__ __forceinline__ dfl operator*(dfl a, int s) { return s > 0 ? a : -a; }

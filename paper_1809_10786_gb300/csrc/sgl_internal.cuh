@@ -130,6 +130,8 @@ struct Buffers {
     int *sched;                // [4] work counters of the persistent kernels (zeroed before each launch)
     double *wtab;              // [kWinTab] tabulated windows (FP64 plans)
     double2 *rot;              // [2 kRotK + 1] (cos, sin) of k pi / kRotK, k = -kRotK .. kRotK (point angles)
+    float4 *rotf;              // [2 kRotK + 1] the same as double-float pairs (cos h, cos l, sin h, sin l)
+    float4 *rec_tmp;           // [M] binary32 point records (as pts32) in input order
     // host-IO staging
     double *io_xyz, *io_coef, *io_vals, *io_grad, *io_out;
     // tensor-core interpolation (FP32-mixed): grid as planes Re, Im [rows0][rows1][pitch] with an azimuthal halo

@@ -3,6 +3,7 @@
 //   xtilde_i = [arccos gamma(r_i), theta_i, phi_i] with gamma(r) = (2r - rho)/rho
 //   (Sect. 6, eq. of the transformed points), their oversampled-grid coordinates
 //   u_d = N_d xtilde_d / (2 pi), and a counting sort of the points by spatial bin.
+#include "sgl_dfl.cuh"
 #include "sgl_internal.cuh"
 
 namespace sgl {
@@ -40,6 +41,7 @@ struct PointGeom {
     int S2, C0, C1;     // azimuthal chunk, columns per super-bin
     int nsb1, nsb2;     // super-bins along axes 1 and 2
     int cmax0, cmax1;   // largest cell index on axes 0 and 1 (N/2)
+    float2 scale[3];    // N_d / (2 pi) as a double-float (h, l)
 };
 
 __device__ __forceinline__ double rho_of(const unsigned long long *r2max) {
@@ -87,27 +89,143 @@ __device__ __forceinline__ void grid_coords(double x, double y, double z, double
     if (u2 < 0.0) u2 = 0.0;
 }
 
+// ---- the same angles in double-float arithmetic (FP32-mixed plans): every operation on the
+// FP32 pipe, relative rounding about 1e-13, far below the binary32 offsets the kernels read.
+
+// x 2^-E as a double-float, from the bit pattern alone: the leading 24 significand bits give h,
+// the other 29 (rounded to 24) give l.  Zero when x 2^-E lies below 2^-126 (subnormal doubles too).
+__device__ __forceinline__ dfl split_scaled(double x, int E) {
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
+    const int ex = (int)((bits >> 52) & 0x7ff);
+    const int e = ex - 1023 - E;
+    if (ex == 0 || e < -126 || e > 127) return dfl(0.f, 0.f);
+    const unsigned sign = (unsigned)(bits >> 32) & 0x80000000u;
+    const unsigned long long m = bits & 0xfffffffffffffull;
+    const float h = __int_as_float((int)(sign | ((unsigned)(e + 127) << 23) | (unsigned)(m >> 29)));
+    float l = 0.f;
+    if (e >= -74) {
+        const float v = __fmul_rn((float)(unsigned)(m & 0x1fffffffu), __int_as_float((e - 52 + 127) << 23));
+        l = sign ? -v : v;
+    }
+    return dfl(h, l);
+}
+
+// finiteness from the exponent field (integer operations only)
+__device__ __forceinline__ bool finite_bits(double x) {
+    return ((((unsigned long long)__double_as_longlong(x)) >> 52) & 0x7ff) != 0x7ff;
+}
+
+// unbiased exponent field of a double (-1023 for zero and subnormals)
+__device__ __forceinline__ int exponent_of(double x) {
+    return (int)(((unsigned long long)__double_as_longlong(x) >> 52) & 0x7ff) - 1023;
+}
+
+// atan2(a, b) in double-float: the table step of atan2_tab with (cos, sin) of k pi / kRotK as
+// double-float pairs; atan(t) = t - t^3/3 (the next term is below 7e-17).  atan2(0, 0) = 0.
+__device__ __forceinline__ dfl atan2_df(dfl a, dfl b, const float4 *__restrict__ rotf) {
+    if (a.h == 0.f && b.h == 0.f) return dfl(0.f, 0.f);
+    const float g = atan2f(a.h, b.h);
+    const int k = __float2int_rn(g * ((float)kRotK / 3.14159265f));
+    const float4 cs = __ldg(rotf + (k + kRotK));             // (cos h, cos l, sin h, sin l)
+    const dfl c(cs.x, cs.y), sn(cs.z, cs.w);
+    const dfl num = a * c - b * sn;
+    const dfl den = b * c + a * sn;
+    const dfl t = df_div(num, den);
+    const float t3 = __fmul_rn(__fmul_rn(t.h, t.h), t.h) * (-1.f / 3.f);
+    constexpr dfl step(kPi / kRotK);                          // pi / kRotK
+    const float kf = (float)k;                                // |k| <= kRotK: exact
+    const float p = __fmul_rn(kf, step.h);
+    const dfl th = fast_two_sum(p, fmaf(kf, step.l, fmaf(kf, step.h, -p)));
+    return th + (t + dfl(t3));
+}
+
+// cell c = floor(u) (clamped to [0, cmax]) and the binary32 offset u - c of a double-float u
+__device__ __forceinline__ int cell_df(dfl u, int cmax, float &frac) {
+    float c = floorf(u.h);
+    if (u.h == c && u.l < 0.f) c -= 1.f;
+    const int ci = min(max((int)c, 0), cmax);
+    frac = __fadd_rn(__fsub_rn(u.h, (float)ci), u.l);
+    return ci;
+}
+
 // bin key: super-bin (axis 0, azimuthal chunk, axis 1) first, then the column inside it, so the
 // points of one column are contiguous and the columns of one super-bin are contiguous
-__device__ __forceinline__ int bin_of_coords(double u0, double u1, double u2, const PointGeom &g) {
-    const int c0 = min(max((int)floor(u0), 0), g.cmax0);
-    const int c1 = min(max((int)floor(u1), 0), g.cmax1);
-    const int c2 = min(max((int)floor(u2), 0), g.N[2] - 1);
+__device__ __forceinline__ int bin_of_cells(int c0, int c1, int c2, const PointGeom &g) {
     const int sb = ((c0 / g.C0) * g.nsb2 + c2 / g.S2) * g.nsb1 + c1 / g.C1;
     return (sb * g.C0 + c0 % g.C0) * g.C1 + c1 % g.C1;
 }
 
-__global__ void k_transform_points(const double *__restrict__ xyz, int64_t M, const unsigned long long *__restrict__ r2max,
-                                   PointGeom g, const double2 *__restrict__ rot, double *__restrict__ u_tmp, int *__restrict__ bin_of,
-                                   int *__restrict__ rank_of, int *__restrict__ bin_count) {
-    const double rho = rho_of(r2max);
+__device__ __forceinline__ float4 record(float f0, float f1, float f2, int c0, int c1, int c2) {
+    return make_float4(f0, f1, f2, __int_as_float(c0 | (c1 << 10) | (c2 << 20)));
+}
+
+// Transform, cells, binary32 record and bin key of each point in input order, and its rank in
+// its bin (atomic counter).  DF: double-float angles; u_tmp (binary64 coordinates) written when
+// non-NULL.
+template <bool DF>
+__global__ void __launch_bounds__(256) k_transform_points(const double *__restrict__ xyz, int64_t M,
+                                                          const unsigned long long *__restrict__ r2max, PointGeom g,
+                                                          const double2 *__restrict__ rot, const float4 *__restrict__ rotf,
+                                                          double *__restrict__ u_tmp, float4 *__restrict__ rec_tmp,
+                                                          int *__restrict__ bin_of, int *__restrict__ rank_of,
+                                                          int *__restrict__ bin_count) {
+    // rho (binary64 plans) or rho 2^-Erho as a double-float (rho = sqrt(max r^2)(1 + 2^-20))
+    double rho = 1.0;
+    dfl rho_s(1.f, 0.f);
+    int Erho = 0;
+    if constexpr (DF) {
+        const double r2 = __longlong_as_double((long long)*r2max);
+        if (r2 > 0.0) {
+            const int E2 = exponent_of(r2) & ~1;                  // even: sqrt(r2 2^-E2) = sqrt(r2) 2^-E2/2
+            const dfl s = df_sqrt(split_scaled(r2, E2));           // in [1, 2)
+            rho_s = s + df_mul(s, 0x1p-20f);
+            Erho = E2 / 2;
+        }
+    } else {
+        rho = rho_of(r2max);
+    }
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < M; i += (int64_t)gridDim.x * blockDim.x) {
         double x = xyz[3 * i], y = xyz[3 * i + 1], z = xyz[3 * i + 2];
-        if (!(isfinite(x) && isfinite(y) && isfinite(z))) { x = 0.0; y = 0.0; z = 0.0; }
-        double u0, u1, u2;
-        grid_coords(x, y, z, rho, g, rot, u0, u1, u2);
-        u_tmp[3 * i] = u0; u_tmp[3 * i + 1] = u1; u_tmp[3 * i + 2] = u2;
-        const int b = bin_of_coords(u0, u1, u2, g);
+        if (!(finite_bits(x) && finite_bits(y) && finite_bits(z))) { x = 0.0; y = 0.0; z = 0.0; }
+        int c0, c1, c2;
+        float f0, f1, f2;
+        if constexpr (DF) {
+            const int E = max(max(exponent_of(x), exponent_of(y)), exponent_of(z));
+            const dfl xs = split_scaled(x, E), ys = split_scaled(y, E), zs = split_scaled(z, E);
+            const dfl rxy2 = xs * xs + ys * ys;
+            const dfl rxy = df_sqrt(rxy2), r = df_sqrt(rxy2 + zs * zs);      // times 2^-E
+            // t0 on the common scale 2^-Erho (E <= Erho: rho >= r >= every coordinate)
+            const int d = E - Erho;
+            const dfl rr = d >= -100 ? df_scale2(r, d) : dfl(0.f, 0.f);
+            const dfl t0 = atan2_df(df_mul(df_sqrt(rr * (rho_s - rr)), 2.f), df_mul(rr, 2.f) - rho_s, rotf);
+            const dfl t1 = atan2_df(rxy, zs, rotf);
+            dfl t2 = atan2_df(ys, xs, rotf);
+            constexpr dfl two_pi(2.0 * kPi);
+            if (t2.h < 0.f) t2 = t2 + two_pi;
+            const dfl u0 = t0 * dfl(g.scale[0].x, g.scale[0].y);
+            const dfl u1 = t1 * dfl(g.scale[1].x, g.scale[1].y);
+            dfl u2 = t2 * dfl(g.scale[2].x, g.scale[2].y);
+            const float n2 = (float)g.N[2];
+            if (u2.h > n2 || (u2.h == n2 && u2.l >= 0.f)) u2 = u2 - dfl(n2);
+            if (u2.h < 0.f) u2 = dfl(0.f, 0.f);
+            c0 = cell_df(u0, g.cmax0, f0);
+            c1 = cell_df(u1, g.cmax1, f1);
+            c2 = cell_df(u2, g.N[2] - 1, f2);
+            if (u_tmp) {
+                u_tmp[3 * i] = df_to_double(u0); u_tmp[3 * i + 1] = df_to_double(u1); u_tmp[3 * i + 2] = df_to_double(u2);
+            }
+        } else {
+            double u0, u1, u2;
+            grid_coords(x, y, z, rho, g, rot, u0, u1, u2);
+            u_tmp[3 * i] = u0; u_tmp[3 * i + 1] = u1; u_tmp[3 * i + 2] = u2;
+            // cells as in the bin key; offsets relative to them (exact in binary64, rounded once)
+            c0 = min(max((int)floor(u0), 0), g.cmax0);
+            c1 = min(max((int)floor(u1), 0), g.cmax1);
+            c2 = min(max((int)floor(u2), 0), g.N[2] - 1);
+            f0 = (float)(u0 - c0); f1 = (float)(u1 - c1); f2 = (float)(u2 - c2);
+        }
+        rec_tmp[i] = record(f0, f1, f2, c0, c1, c2);
+        const int b = bin_of_cells(c0, c1, c2, g);
         bin_of[i] = b;
         rank_of[i] = atomicAdd(&bin_count[b], 1);
     }
@@ -157,40 +275,71 @@ __global__ void k_scan_totals(int *__restrict__ totals, int nblk) {
     }
 }
 
-__global__ void k_scan_final(const int *__restrict__ cnt, int64_t n, const int *__restrict__ totals, int *__restrict__ off) {
-    __shared__ int buf[kScanBlock];
+// offsets of one block of kScanBlock counts: each thread scans its kScanItems consecutive counts,
+// the threads' totals are scanned by warp shuffles and the warps' totals by warp 0
+__global__ void __launch_bounds__(kThreads) k_scan_final(const int *__restrict__ cnt, int64_t n, const int *__restrict__ totals,
+                                                         int *__restrict__ off) {
+    __shared__ __align__(16) int buf[kScanBlock];
+    __shared__ int wsum[kThreads / 32];
     const int64_t base = (int64_t)blockIdx.x * kScanBlock;
     for (int k = 0; k < kScanItems; ++k) {
-        int j = k * kThreads + threadIdx.x;
+        const int j = k * kThreads + threadIdx.x;
         buf[j] = (base + j < n) ? cnt[base + j] : 0;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {      // serial scan inside the block keeps this simple; n/kScanBlock blocks run in parallel
-        int acc = totals[blockIdx.x];
-        for (int j = 0; j < kScanBlock; ++j) { int v = buf[j]; buf[j] = acc; acc += v; }
+    int v[kScanItems];
+    const int4 *b4 = reinterpret_cast<const int4 *>(buf + kScanItems * threadIdx.x);
+    static_assert(kScanItems == 8, "two int4 per thread");
+    const int4 lo = b4[0], hi = b4[1];
+    v[0] = lo.x; v[1] = lo.y; v[2] = lo.z; v[3] = lo.w; v[4] = hi.x; v[5] = hi.y; v[6] = hi.z; v[7] = hi.w;
+    int t = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) { const int c = v[k]; v[k] = t; t += c; }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int inc = t;                                        // inclusive scan of the threads' totals in the warp
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int u = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += u;
+    }
+    if (lane == 31) wsum[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        int w = lane < kThreads / 32 ? wsum[lane] : 0;
+        int wi = w;
+#pragma unroll
+        for (int o = 1; o < kThreads / 32; o <<= 1) {
+            const int u = __shfl_up_sync(0xffffffffu, wi, o);
+            if (lane >= o) wi += u;
+        }
+        if (lane < kThreads / 32) wsum[lane] = wi - w;  // exclusive
     }
     __syncthreads();
+    const int add = totals[blockIdx.x] + wsum[warp] + inc - t;
+    int4 *o4 = reinterpret_cast<int4 *>(buf + kScanItems * threadIdx.x);
+    o4[0] = make_int4(v[0] + add, v[1] + add, v[2] + add, v[3] + add);
+    o4[1] = make_int4(v[4] + add, v[5] + add, v[6] + add, v[7] + add);
+    __syncthreads();
     for (int k = 0; k < kScanItems; ++k) {
-        int j = k * kThreads + threadIdx.x;
+        const int j = k * kThreads + threadIdx.x;
         if (base + j < n) off[base + j] = buf[j];
     }
 }
 
-__global__ void k_scatter_points(int64_t M, const double *__restrict__ u_tmp, const int *__restrict__ bin_of,
-                                 const int *__restrict__ rank_of, const int *__restrict__ off, PointGeom g,
-                                 double *__restrict__ u_sorted, float4 *__restrict__ pts32, int *__restrict__ perm) {
+// points in bin order: record, permutation and (when u_tmp is non-NULL) binary64 coordinates
+__global__ void __launch_bounds__(256) k_scatter_points(int64_t M, const float4 *__restrict__ rec_tmp, const double *__restrict__ u_tmp,
+                                                        const int *__restrict__ bin_of, const int *__restrict__ rank_of,
+                                                        const int *__restrict__ off, double *__restrict__ u_sorted,
+                                                        float4 *__restrict__ pts32, int *__restrict__ perm) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < M; i += (int64_t)gridDim.x * blockDim.x) {
         const int pos = off[bin_of[i]] + rank_of[i];
-        const double u0 = u_tmp[3 * i], u1 = u_tmp[3 * i + 1], u2 = u_tmp[3 * i + 2];
-        u_sorted[3 * pos] = u0;
-        u_sorted[3 * pos + 1] = u1;
-        u_sorted[3 * pos + 2] = u2;
-        // cells as in the bin key; fractional parts relative to them (exact in binary64, rounded once)
-        const int c0 = min(max((int)floor(u0), 0), g.cmax0);
-        const int c1 = min(max((int)floor(u1), 0), g.cmax1);
-        const int c2 = min(max((int)floor(u2), 0), g.N[2] - 1);
-        pts32[pos] = make_float4((float)(u0 - c0), (float)(u1 - c1), (float)(u2 - c2), __int_as_float(c0 | (c1 << 10) | (c2 << 20)));
+        pts32[pos] = rec_tmp[i];
         perm[pos] = (int)i;
+        if (u_tmp) {
+            u_sorted[3 * pos] = u_tmp[3 * i];
+            u_sorted[3 * pos + 1] = u_tmp[3 * i + 1];
+            u_sorted[3 * pos + 2] = u_tmp[3 * i + 2];
+        }
     }
 }
 
@@ -243,10 +392,10 @@ void scan(const int *cnt, int64_t n, int *tmp, int *off, cudaStream_t s) {
     k_scan_final<<<nblk, kThreads, 0, s>>>(cnt, n, tmp, off);
 }
 
-int grid_blocks(int64_t work, int threads) {
+int grid_blocks(int64_t work, int threads, int64_t cap = 152 * 32) {
     int64_t b = (work + threads - 1) / threads;
     if (b < 1) b = 1;
-    if (b > 152 * 32) b = 152 * 32;
+    if (b > cap) b = cap;
     return (int)b;
 }
 
@@ -256,7 +405,9 @@ cudaError_t launch_points_rho(sgl_plan *p, const double *xyz, int64_t M, double 
     cudaError_t e;
     if ((e = cudaMemsetAsync(p->b.r2max, 0, sizeof(unsigned long long), p->stream)) != cudaSuccess) return e;
     if (M > 0) {
-        k_max_radius<<<grid_blocks(M, kThreads), kThreads, 0, p->stream>>>(xyz, M, p->b.r2max, p->b.dev_flags, copy);
+        // a few CTAs per SM: one atomicMax per CTA on the same word
+        k_max_radius<<<grid_blocks(M, kThreads, 8 * (int64_t)p->num_sms), kThreads, 0, p->stream>>>(xyz, M, p->b.r2max,
+                                                                                                    p->b.dev_flags, copy);
         p->launches += 1;
     }
     return cudaGetLastError();
@@ -275,11 +426,25 @@ cudaError_t launch_points_bins(sgl_plan *p, const double *xyz, int64_t M, cudaSt
     g.nsb2 = p->bins.nsb[2];
     g.cmax0 = p->ax[0].N / 2;
     g.cmax1 = p->ax[1].N / 2;
+    for (int d = 0; d < 3; ++d) {
+        const dfl sc(p->ax[d].N / (2.0 * kPi));
+        g.scale[d] = make_float2(sc.h, sc.l);
+    }
     if (M > 0) {
-        k_transform_points<<<grid_blocks(M, kThreads), kThreads, 0, s>>>(xyz, M, b.r2max, g, b.rot, b.u_tmp, b.bin_of, b.rank_of, b.bin_count);
+        // FP32-mixed plans: double-float angles; binary64 coordinates only for the generic
+        // spreading kernel (cutoffs above 8); binary64 plans: binary64 throughout
+        const bool df = p->prec == SGL_FP32_MIXED;
+        double *u_tmp = (!df || p->q > 8) ? b.u_tmp : nullptr;
+        const int blocks = grid_blocks(M, kThreads);
+        if (df)
+            k_transform_points<true><<<blocks, kThreads, 0, s>>>(xyz, M, b.r2max, g, b.rot, b.rotf, u_tmp, b.rec_tmp, b.bin_of,
+                                                                 b.rank_of, b.bin_count);
+        else
+            k_transform_points<false><<<blocks, kThreads, 0, s>>>(xyz, M, b.r2max, g, b.rot, b.rotf, u_tmp, b.rec_tmp, b.bin_of,
+                                                                  b.rank_of, b.bin_count);
         scan(b.bin_count, p->nbins, b.scan_tmp, b.bin_off, s);
-        k_scatter_points<<<grid_blocks(M, kThreads), kThreads, 0, s>>>(M, b.u_tmp, b.bin_of, b.rank_of, b.bin_off, g, b.u_sorted,
-                                                                       b.pts32, b.perm);
+        k_scatter_points<<<blocks, kThreads, 0, s>>>(M, b.rec_tmp, u_tmp, b.bin_of, b.rank_of, b.bin_off, b.u_sorted, b.pts32,
+                                                     b.perm);
         const int64_t ns = p->bins.nsuper;
         const int bps = p->bins.C0 * p->bins.C1, P1 = spread_chunk(p->prec);
         k_piece_count<<<grid_blocks(ns, kThreads), kThreads, 0, s>>>(b.bin_off, ns, bps, M, kTcPass, P1, b.piece_cnt);
@@ -294,7 +459,7 @@ cudaError_t launch_points_bins(sgl_plan *p, const double *xyz, int64_t M, cudaSt
 }
 
 cudaError_t launch_max_radius_raw(cudaStream_t s, const double *xyz, int64_t M, unsigned long long *r2max, int *flags) {
-    if (M > 0) k_max_radius<<<grid_blocks(M, kThreads), kThreads, 0, s>>>(xyz, M, r2max, flags, nullptr);
+    if (M > 0) k_max_radius<<<grid_blocks(M, kThreads, 8 * 152), kThreads, 0, s>>>(xyz, M, r2max, flags, nullptr);
     return cudaGetLastError();
 }
 
