@@ -91,6 +91,10 @@ typedef enum {
                                  10^6 points it made set_points + forward 8 % faster and
                                  set_points + forward with the gradient + adjoint 4 % slower.
                                  Not accepted for batches */
+#define SGL_FLAG_GENERIC_FFT 64u  /* run every FFT pass with the generic mixed-radix kernel (tiles of
+                                 lines staged in shared memory, one radix stage per pass over
+                                 the tile) instead of the register kernels that power-of-two
+                                 lengths 64 ... 1024 take by default.  Same results to rounding */
 
 /* stages reported by sgl_profile (index order) */
 #define SGL_NUM_STAGES 12

@@ -431,6 +431,16 @@ cudaError_t upload(T *dst, const std::vector<T> &src, cudaStream_t s) {
     return cudaMemcpyAsync(dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice, s);
 }
 
+// binary64 values as double-float pairs (h = v rounded to binary32, l = the rest rounded)
+std::vector<float2> df_pairs(const std::vector<double> &v) {
+    std::vector<float2> o(v.size());
+    for (size_t i = 0; i < v.size(); ++i) {
+        const float h = (float)v[i];
+        o[i] = make_float2(h, (float)(v[i] - (double)h));
+    }
+    return o;
+}
+
 }  // namespace
 }  // namespace sgl
 
@@ -461,7 +471,8 @@ sgl_status plan_create_impl(sgl_plan **out, int B, int64_t M_max, int precision,
     if (window != SGL_WIN_KB && window != SGL_WIN_GAUSS) return set_error(SGL_ERR_ARG, "unknown window");
     if (q < 1 || q > kMaxQ) return set_error(SGL_ERR_ARG, "q must be in [1, 16]");
     if (!(sigma >= 1.5 && sigma <= 4.0)) return set_error(SGL_ERR_ARG, "sigma must be in [1.5, 4]");
-    if (flags & ~(SGL_FLAG_HOST_IO | SGL_FLAG_PROFILE | SGL_FLAG_SIMT | SGL_FLAG_TC | SGL_FLAG_NATIVE_FP64 | SGL_FLAG_OVERLAP_POINTS))
+    if (flags & ~(SGL_FLAG_HOST_IO | SGL_FLAG_PROFILE | SGL_FLAG_SIMT | SGL_FLAG_TC | SGL_FLAG_NATIVE_FP64 | SGL_FLAG_OVERLAP_POINTS |
+                  SGL_FLAG_GENERIC_FFT))
         return set_error(SGL_ERR_ARG, "unknown flag bits");
     if ((flags & SGL_FLAG_SIMT) && (flags & SGL_FLAG_TC)) return set_error(SGL_ERR_ARG, "SGL_FLAG_SIMT and SGL_FLAG_TC exclude each other");
 
@@ -538,6 +549,7 @@ sgl_status plan_create_impl(sgl_plan **out, int B, int64_t M_max, int precision,
     ALLOC(b.beta, (size_t)(2 * B - 1) * (K0 + 1) * B);
     ALLOC(b.zeta, (size_t)(K0 + 1) * (K1 + 1) * W);
     ALLOC(b.linescale, (size_t)(W * W));
+    ALLOC(b.linescale_df, (size_t)(W * W));
     if (shared && shared->bufA && shared->bufB && shared->bytesA >= nA * csz && shared->bytesB >= bytesB) {
         b.bufA = shared->bufA; b.bufB = shared->bufB;
         b.bufA_bytes = shared->bytesA; b.bufB_bytes = shared->bytesB;
@@ -555,6 +567,7 @@ sgl_status plan_create_impl(sgl_plan **out, int B, int64_t M_max, int precision,
         ALLOC(a.tw_df, (size_t)a.N);
         ALLOC(a.rev, (size_t)a.N);
         ALLOC(a.deconv, (size_t)(2 * a.K + 1));
+        ALLOC(a.deconv_df, (size_t)(2 * a.K + 1));
     }
     ALLOC(b.r2max, 1);
     ALLOC(b.dev_flags, 1);
@@ -633,10 +646,12 @@ sgl_status plan_create_impl(sgl_plan **out, int B, int64_t M_max, int precision,
         if ((e = upload(a.tw_df, twdf, p->stream)) != cudaSuccess) return fail(SGL_ERR_CUDA, "upload twiddles");
         if ((e = upload(a.rev, rev, p->stream)) != cudaSuccess) return fail(SGL_ERR_CUDA, "upload digit reversal");
         if ((e = upload(a.deconv, dec[d], p->stream)) != cudaSuccess) return fail(SGL_ERR_CUDA, "upload deconvolution");
+        if ((e = upload(a.deconv_df, df_pairs(dec[d]), p->stream)) != cudaSuccess) return fail(SGL_ERR_CUDA, "upload deconvolution");
     }
     std::vector<double> ls((size_t)(W * W));
     for (int k1 = -K1; k1 <= K1; ++k1)
         for (int m = -K1; m <= K1; ++m) ls[(size_t)(k1 + K1) * W + (m + K1)] = dec[1][k1 + K1] * dec[2][m + K1];
+    if ((e = upload(b.linescale_df, df_pairs(ls), p->stream)) != cudaSuccess) return fail(SGL_ERR_CUDA, "upload line scales");
     if ((e = upload(b.P, P, p->stream)) != cudaSuccess) return fail(SGL_ERR_CUDA, "upload polar matrices");
     if ((e = upload(b.costab, costab, p->stream)) != cudaSuccess) return fail(SGL_ERR_CUDA, "upload cosine table");
     if ((e = upload(b.linescale, ls, p->stream)) != cudaSuccess) return fail(SGL_ERR_CUDA, "upload line scales");

@@ -75,4 +75,36 @@ __device__ __forceinline__ dfl df_scale2(dfl a, int k) {
 }
 __device__ __forceinline__ double df_to_double(dfl a) { return (double)a.h + (double)a.l; }
 
+// x 2^-E as a double-float, from the bit pattern alone (integer operations, no FP64 pipe): the
+// leading 24 significand bits give h, the other 29 (rounded to 24) give l.  Zero when x 2^-E lies
+// below 2^-126 (subnormal doubles too); +-infinity (NaN for NaN) above the binary32 range.
+__device__ __forceinline__ dfl df_split_bits(double x, int E = 0) {
+    const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
+    const int ex = (int)((bits >> 52) & 0x7ff);
+    const int e = ex - 1023 - E;
+    const unsigned sign = (unsigned)(bits >> 32) & 0x80000000u;
+    const unsigned long long m = bits & 0xfffffffffffffull;
+    if (ex == 0 || e < -126) return dfl(0.f, 0.f);
+    if (e > 127) return dfl(__int_as_float((int)(sign | 0x7f800000u | (m ? 0x400000u : 0u))), 0.f);
+    const float h = __int_as_float((int)(sign | ((unsigned)(e + 127) << 23) | (unsigned)(m >> 29)));
+    float l = 0.f;
+    if (e >= -74) {
+        const float v = __fmul_rn((float)(unsigned)(m & 0x1fffffffu), __int_as_float((e - 52 + 127) << 23));
+        l = sign ? -v : v;
+    }
+    return dfl(h, l);
+}
+
+// a binary32 number as a binary64 one from its bit pattern (integer operations; subnormals -> 0)
+__device__ __forceinline__ double f2d_bits(float f) {
+    const unsigned u = (unsigned)__float_as_int(f);
+    const unsigned ex = (u >> 23) & 0xff;
+    const unsigned long long sign = (unsigned long long)(u & 0x80000000u) << 32;
+    if (ex == 0) return __longlong_as_double((long long)sign);
+    const unsigned long long dex = ex == 0xff ? 0x7ffull : (unsigned long long)(ex - 127 + 1023);
+    return __longlong_as_double((long long)(sign | (dex << 52) | ((unsigned long long)(u & 0x7fffffu) << 29)));
+}
+// h + l rounded to binary64 (one binary64 addition)
+__device__ __forceinline__ double df_to_double_bits(dfl a) { return f2d_bits(a.h) + f2d_bits(a.l); }
+
 }  // namespace sgl

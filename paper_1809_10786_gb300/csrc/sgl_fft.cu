@@ -109,6 +109,38 @@ __device__ __forceinline__ void dft5(C2<T> *x, int s) {
     x[0] = y0; x[1] = add<T>(m1, n1); x[4] = sub<T>(m1, n1); x[2] = add<T>(m2, n2); x[3] = sub<T>(m2, n2);
 }
 
+// 16 = 4 x 4: DFT-4 over n2 for each n1, twiddles W16^(n1 k2), DFT-4 over n1 for each k2; output
+// index k2 + 4 k1
+template <typename T>
+__device__ __forceinline__ void dft16(C2<T> *x, int s) {
+    constexpr T c1 = T(0.92387953251128675613), s1 = T(0.38268343236508977173), h = T(0.70710678118654752440);
+    C2<T> y[4][4];
+#pragma unroll
+    for (int n1 = 0; n1 < 4; ++n1) {
+        C2<T> a[4] = {x[n1], x[n1 + 4], x[n1 + 8], x[n1 + 12]};
+        dft4<T>(a, s);
+#pragma unroll
+        for (int k2 = 0; k2 < 4; ++k2) y[n1][k2] = a[k2];
+    }
+    // W16^j = e^{s 2 pi i j / 16}, j = n1 k2 in {1, 2, 3, 4, 6, 9}
+    y[1][1] = mul<T>(y[1][1], mk<T>(c1, s * s1));
+    y[1][2] = mul<T>(y[1][2], mk<T>(h, s * h));
+    y[1][3] = mul<T>(y[1][3], mk<T>(s1, s * c1));
+    y[2][1] = mul<T>(y[2][1], mk<T>(h, s * h));
+    y[2][2] = mul_si<T>(y[2][2], s);
+    y[2][3] = mul<T>(y[2][3], mk<T>(-h, s * h));
+    y[3][1] = mul<T>(y[3][1], mk<T>(s1, s * c1));
+    y[3][2] = mul<T>(y[3][2], mk<T>(-h, s * h));
+    y[3][3] = mul<T>(y[3][3], mk<T>(-c1, -s * s1));
+#pragma unroll
+    for (int k2 = 0; k2 < 4; ++k2) {
+        C2<T> b[4] = {y[0][k2], y[1][k2], y[2][k2], y[3][k2]};
+        dft4<T>(b, s);
+#pragma unroll
+        for (int k1 = 0; k1 < 4; ++k1) x[k2 + 4 * k1] = b[k1];
+    }
+}
+
 enum { LOAD_STRIDED = 0, LOAD_ZETA = 1 };
 
 struct ZetaSrc {
@@ -124,7 +156,8 @@ __device__ __forceinline__ void dft_r(C2<T> *x, int s) {
     else if constexpr (R == 3) dft3<T>(x, s);
     else if constexpr (R == 4) dft4<T>(x, s);
     else if constexpr (R == 5) dft5<T>(x, s);
-    else dft8<T>(x, s);
+    else if constexpr (R == 8) dft8<T>(x, s);
+    else dft16<T>(x, s);
 }
 
 // q / d and q % d for d > 0; a shift and a mask when d is a power of two
@@ -298,6 +331,212 @@ __global__ void __launch_bounds__(256) k_fft_pass(FftPass ps, int TB, int lgTB, 
     }
 }
 
+// ---------------------------------------------------------------- register Stockham passes
+// Power-of-two lengths N = R1 R2 (R3): each thread holds E = max radix elements of one line and
+// TPL = N / E threads share a line (TB = 256 / TPL lines per CTA).  Stage j (radix R, L = product
+// of the earlier radices, M = N / L, Q = M / R) takes butterflies b = (c, n1) = (b mod L, b / L):
+// z_k = W_M^(n1 k) sum_{n2 < R} y_c[n1 + Q n2] W_R^(n2 k), which is y_{c + L k}[n1] of the next
+// stage (Stockham autosort: input and output in natural order).  The first stage reads its
+// elements straight from global memory, the last one writes them there; between stages the line
+// goes through shared memory once (index i stored at i + i / E: no bank conflicts on the stride-E
+// writes).  Thread t takes butterflies t + TPL i of every stage.
+template <int N, int R1, int R2, int R3>
+struct RegFft {
+    static constexpr int E = R1 > R2 ? (R1 > R3 ? R1 : R3) : (R2 > R3 ? R2 : R3);
+    static constexpr int TPL = N / E;
+    static constexpr int TB = 256 / TPL;
+    static constexpr int LS = (N + N / E) | 1;          // odd line stride (64-bit words) in shared memory
+    static_assert(R1 * R2 * R3 == N && E % R1 == 0 && E % R2 == 0 && E % R3 == 0 && TPL <= 256, "radices");
+};
+
+__device__ __forceinline__ int pad_e(int i, int E) { return i + i / E; }
+
+// load: FFT position pos of a line holds input element e = (pos - in_first) mod N (zero if e >= L_in)
+template <typename T, typename InC, int MODE>
+__device__ __forceinline__ C2<T> reg_load(const FftPass &ps, const InC *__restrict__ in, const ZetaSrc &zs, int64_t outer,
+                                          int64_t inner, bool valid, int e, int scale_on_output) {
+    if (!valid || e >= ps.L_in) return mk<T>(T(0), T(0));
+    C2<T> v;
+    if constexpr (MODE == LOAD_ZETA) {
+        const int W = 2 * zs.K1 + 1;
+        const int mi = (int)(inner % W);
+        const int k1 = (int)(inner / W) - zs.K1;
+        const int k0 = e - zs.K0;
+        double2 d = zs.zeta[((int64_t)abs(k0) * (zs.K1 + 1) + abs(k1)) * W + mi];
+        if (k1 < 0 && ((mi - zs.K1) & 1)) { d.x = -d.x; d.y = -d.y; }
+        if constexpr (std::is_same<T, dfl>::value) { v.x = df_split_bits(d.x); v.y = df_split_bits(d.y); }
+        else { v.x = T(d.x); v.y = T(d.y); }
+    } else {
+        const InC x = in[outer * ps.in_so + inner * ps.in_si + (int64_t)e * ps.in_se];
+        if constexpr (std::is_same<T, dfl>::value && sizeof(x.x) == 8) { v.x = df_split_bits(x.x); v.y = df_split_bits(x.y); }
+        else { v.x = T(x.x); v.y = T(x.y); }
+    }
+    if (!scale_on_output && (ps.elem_scale || ps.line_scale)) {
+        if constexpr (std::is_same<T, dfl>::value) {
+            dfl f(1.f, 0.f);
+            if (ps.elem_scale_df) f = dfl(ps.elem_scale_df[e].x, ps.elem_scale_df[e].y);
+            if (ps.line_scale_df) {
+                const float2 l = ps.line_scale_df[outer * ps.nb_inner + inner];
+                f = f * dfl(l.x, l.y);
+            }
+            v.x = v.x * f; v.y = v.y * f;
+        } else {
+            double f = 1.0;
+            if (ps.elem_scale) f *= ps.elem_scale[e];
+            if (ps.line_scale) f *= ps.line_scale[outer * ps.nb_inner + inner];
+            v.x = T(widen(v.x) * f); v.y = T(widen(v.y) * f);
+        }
+    }
+    return v;
+}
+
+// store output element e (position (e + out_first) mod N), optional scale on output
+template <typename T, typename OutC>
+__device__ __forceinline__ void reg_store(const FftPass &ps, OutC *__restrict__ out, int64_t outer, int64_t inner, int e, C2<T> v,
+                                          int scale_on_output) {
+    using S = decltype(OutC::x);
+    OutC o;
+    if (scale_on_output && (ps.elem_scale || ps.line_scale)) {
+        if constexpr (std::is_same<T, dfl>::value) {
+            dfl f(1.f, 0.f);
+            if (ps.elem_scale_df) f = dfl(ps.elem_scale_df[e].x, ps.elem_scale_df[e].y);
+            if (ps.line_scale_df) {
+                const float2 l = ps.line_scale_df[outer * ps.nb_inner + inner];
+                f = f * dfl(l.x, l.y);
+            }
+            v.x = v.x * f; v.y = v.y * f;
+        } else {
+            double f = 1.0;
+            if (ps.elem_scale) f *= ps.elem_scale[e];
+            if (ps.line_scale) f *= ps.line_scale[outer * ps.nb_inner + inner];
+            o.x = (S)(widen(v.x) * f);
+            o.y = (S)(widen(v.y) * f);
+            out[outer * ps.out_so + inner * ps.out_si + (int64_t)e * ps.out_se] = o;
+            return;
+        }
+    }
+    if constexpr (std::is_same<T, dfl>::value && sizeof(S) == 8) {
+        o.x = df_to_double_bits(v.x);
+        o.y = df_to_double_bits(v.y);
+    } else {
+        o.x = narrow<S>(v.x);
+        o.y = narrow<S>(v.y);
+    }
+    out[outer * ps.out_so + inner * ps.out_si + (int64_t)e * ps.out_se] = o;
+}
+
+// one stage on the registers: E / R butterflies of radix R, then the twiddles W_M^(n1 k)
+template <typename T, int N, int E, int TPL, int R, int L>
+__device__ __forceinline__ void reg_stage(C2<T> *v, int t, int sign, const C2<T> *__restrict__ tw) {
+#pragma unroll
+    for (int i = 0; i < E / R; ++i) {
+        dft_r<T, R>(v + i * R, sign);
+        if constexpr (L * R < N) {                                 // not the last stage (there n1 = 0)
+            const int n1 = (t + TPL * i) / L;
+#pragma unroll
+            for (int k = 1; k < R; ++k) {
+                C2<T> w = tw[L * n1 * k];                          // W_M^(n1 k) = W_N^(L n1 k), L n1 k < N
+                if (sign < 0) w.y = -w.y;
+                v[i * R + k] = mul<T>(v[i * R + k], w);
+            }
+        }
+    }
+}
+
+// stage outputs -> shared memory (new layout c + L' n, L' = L R) -> the next stage's inputs
+template <typename T, int N, int E, int TPL, int R, int L, int RN>
+__device__ __forceinline__ void reg_exchange(C2<T> *v, C2<T> *line, int t) {
+#pragma unroll
+    for (int i = 0; i < E / R; ++i) {
+        const int b = t + TPL * i, c = b % L, n1 = b / L;
+#pragma unroll
+        for (int k = 0; k < R; ++k) line[pad_e(c + L * k + L * R * n1, E)] = v[i * R + k];
+    }
+    __syncthreads();
+    constexpr int L2 = L * R, Q2 = N / L2 / RN;
+#pragma unroll
+    for (int i = 0; i < E / RN; ++i) {
+        const int b = t + TPL * i, c = b % L2, n1 = b / L2;
+#pragma unroll
+        for (int n2 = 0; n2 < RN; ++n2) v[i * RN + n2] = line[pad_e(c + L2 * (n1 + Q2 * n2), E)];
+    }
+    __syncthreads();
+}
+
+template <typename T, typename InC, typename OutC, int MODE, int N, int R1, int R2, int R3>
+__global__ void __launch_bounds__(256) k_fft_reg(FftPass ps, const InC *__restrict__ in, OutC *__restrict__ out, ZetaSrc zs,
+                                                 int scale_on_output, int line_fast) {
+    using G = RegFft<N, R1, R2, R3>;
+    constexpr int E = G::E, TPL = G::TPL, TB = G::TB;
+    extern __shared__ unsigned char smem_raw[];
+    C2<T> *sbuf = reinterpret_cast<C2<T> *>(smem_raw);       // [TB][LS]
+    const int64_t tiles_inner = (ps.nb_inner + TB - 1) / TB;
+    const int64_t outer = blockIdx.x / tiles_inner;
+    const int64_t inner0 = (blockIdx.x % tiles_inner) * TB;
+    const int tid = threadIdx.x;
+    const int bl = line_fast ? tid % TB : tid / TPL;
+    const int t = line_fast ? tid / TB : tid % TPL;
+    const int64_t inner = inner0 + bl;
+    const bool valid = inner < ps.nb_inner;
+    C2<T> *line = sbuf + bl * G::LS;
+    const C2<T> *tw = reinterpret_cast<const C2<T> *>(ps.tw);
+
+    // stage 1 inputs: butterfly b = n1 (L = 1) reads positions n1 + (N / R1) n2
+    C2<T> v[E];
+#pragma unroll
+    for (int i = 0; i < E / R1; ++i) {
+        const int n1 = t + TPL * i;
+#pragma unroll
+        for (int n2 = 0; n2 < R1; ++n2) {
+            int e = n1 + (N / R1) * n2 - ps.in_first;
+            e = e >= N ? e - N : (e < 0 ? e + N : e);
+            v[i * R1 + n2] = reg_load<T, InC, MODE>(ps, in, zs, outer, inner, valid, e, scale_on_output);
+        }
+    }
+    reg_stage<T, N, E, TPL, R1, 1>(v, t, ps.sign, tw);
+    reg_exchange<T, N, E, TPL, R1, 1, R2>(v, line, t);
+    reg_stage<T, N, E, TPL, R2, R1>(v, t, ps.sign, tw);
+    constexpr int RL = R3 > 1 ? R3 : R2, LL = N / RL;              // last stage: radix, L
+    if constexpr (R3 > 1) {
+        reg_exchange<T, N, E, TPL, R2, R1, R3>(v, line, t);
+        reg_stage<T, N, E, TPL, R3, R1 * R2>(v, t, ps.sign, tw);
+    }
+
+    // last stage outputs: butterfly b = c (n1 = 0) holds positions c + LL k
+    if constexpr (std::is_same<OutC, float2>::value) {
+        if (ps.planes) {                                           // split planes with a wrapped halo
+            if (!valid) return;
+            float *row = ps.planes + inner * ps.pitch;
+#pragma unroll
+            for (int i = 0; i < E / RL; ++i) {
+#pragma unroll
+                for (int k = 0; k < RL; ++k) {
+                    const int pos = t + TPL * i + LL * k;
+                    const float re = narrow<float>(v[i * RL + k].x), im = narrow<float>(v[i * RL + k].y);
+                    int col = pos + ps.halo;                       // < pitch: pitch >= N + 32, halo <= 8
+                    row[col] = re; row[ps.plane_n + col] = im;
+                    col = pos + ps.halo + N;
+                    if (col < ps.pitch) { row[col] = re; row[ps.plane_n + col] = im; }
+                    col = pos + ps.halo - N;
+                    if (col >= 0) { row[col] = re; row[ps.plane_n + col] = im; }
+                }
+            }
+            return;
+        }
+    }
+    if (!valid) return;
+#pragma unroll
+    for (int i = 0; i < E / RL; ++i) {
+#pragma unroll
+        for (int k = 0; k < RL; ++k) {
+            const int pos = t + TPL * i + LL * k;
+            int e = pos - ps.out_first;
+            e = e >= N ? e - N : (e < 0 ? e + N : e);
+            if (e < ps.L_out) reg_store<T, OutC>(ps, out, outer, inner, e, v[i * RL + k], scale_on_output);
+        }
+    }
+}
+
 // lines per tile: a power of two in [8, 64] with about 4096 elements per tile
 int lines_per_tile(int N, int &lg) {
     lg = 3;
@@ -305,8 +544,34 @@ int lines_per_tile(int N, int &lg) {
     return 1 << lg;
 }
 
+template <typename T, typename InC, typename OutC, int MODE, int N, int R1, int R2, int R3>
+cudaError_t run_reg(sgl_plan *p, const FftPass &ps, const void *in, void *out, ZetaSrc zs, int scale_on_output) {
+    using G = RegFft<N, R1, R2, R3>;
+    const size_t smem = (size_t)G::TB * G::LS * sizeof(C2<T>);
+    auto kern = k_fft_reg<T, InC, OutC, MODE, N, R1, R2, R3>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int64_t tiles = ps.nb_outer * ((ps.nb_inner + G::TB - 1) / G::TB);
+    if (tiles <= 0) return cudaSuccess;
+    // threads of a line adjacent when its elements are adjacent in memory, else lines adjacent
+    const int line_fast = (MODE == LOAD_ZETA || ps.in_se != 1) ? 1 : 0;
+    kern<<<(unsigned)tiles, 256, smem, p->stream>>>(ps, (const InC *)in, (OutC *)out, zs, scale_on_output, line_fast);
+    p->launches += 1;
+    return cudaGetLastError();
+}
+
 template <typename T, typename InC, typename OutC, int MODE>
 cudaError_t run_pass(sgl_plan *p, FftPass ps, const void *in, void *out, ZetaSrc zs, int scale_on_output) {
+    if (!(p->flags & SGL_FLAG_GENERIC_FFT)) {
+        switch (ps.N) {
+            case 64: return run_reg<T, InC, OutC, MODE, 64, 8, 8, 1>(p, ps, in, out, zs, scale_on_output);
+            case 128: return run_reg<T, InC, OutC, MODE, 128, 16, 8, 1>(p, ps, in, out, zs, scale_on_output);
+            case 256: return run_reg<T, InC, OutC, MODE, 256, 16, 16, 1>(p, ps, in, out, zs, scale_on_output);
+            case 512: return run_reg<T, InC, OutC, MODE, 512, 8, 8, 8>(p, ps, in, out, zs, scale_on_output);
+            case 1024: return run_reg<T, InC, OutC, MODE, 1024, 16, 8, 8>(p, ps, in, out, zs, scale_on_output);
+            default: break;
+        }
+    }
     int lgTB = 0;
     const int TB = lines_per_tile(ps.N, lgTB);
     const size_t smem = (size_t)TB * (ps.N + 1) * sizeof(C2<T>);
@@ -347,6 +612,7 @@ cudaError_t forward_passes(sgl_plan *p) {
     a.elem_scale = A0.deconv; a.line_scale = p->b.linescale;
     if constexpr (f32) {
         a.tw = A0.tw_df;                          // radial pass in double-float (file comment)
+        a.elem_scale_df = A0.deconv_df; a.line_scale_df = p->b.linescale_df;
         if ((e = run_pass<dfl, double2, C2<T>, LOAD_ZETA>(p, a, nullptr, p->b.bufA, zs, 0)) != cudaSuccess) return e;
     } else if ((e = run_pass<T, double2, C2<T>, LOAD_ZETA>(p, a, nullptr, p->b.bufA, zs, 0)) != cudaSuccess) {
         return e;
@@ -408,6 +674,7 @@ cudaError_t adjoint_passes(sgl_plan *p) {
     a.elem_scale = A0.deconv; a.line_scale = p->b.linescale;
     if constexpr (f32) {
         a.tw = A0.tw_df;                          // radial pass in double-float (file comment)
+        a.elem_scale_df = A0.deconv_df; a.line_scale_df = p->b.linescale_df;
         return run_pass<dfl, C2<T>, double2, LOAD_STRIDED>(p, a, p->b.bufA, p->b.bufB, zs, 1);
     }
     return run_pass<T, C2<T>, double2, LOAD_STRIDED>(p, a, p->b.bufA, p->b.bufB, zs, 1);

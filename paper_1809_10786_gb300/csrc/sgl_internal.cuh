@@ -76,6 +76,7 @@ struct Axis {
     float4 *tw_df;  // the same as double-float pairs (re hi, re lo, im hi, im lo)
     int *rev;       // digit-reversed slot of output index p after the DIF passes
     double *deconv; // 1 / Psihat(2 pi k / N), k = -K..K (index k + K)
+    float2 *deconv_df; // the same as double-float pairs (h, l)
 };
 
 // Description of one batched, pruned 1-D DFT pass (see sgl_fft.cu).
@@ -89,6 +90,8 @@ struct FftPass {
     int64_t out_so, out_si, out_se; // output strides in complex elements
     const double *elem_scale;       // optional factor per element index (input or output side, per launch)
     const double *line_scale;       // optional factor per flattened line index outer*nb_inner+inner
+    const float2 *elem_scale_df;    // the same factors as double-float pairs (double-float passes)
+    const float2 *line_scale_df;
     const void *tw;                 // twiddle table (double2 or float2)
     const int *rev;
     // optional FP32 split-plane output (the tensor-core interpolation's layout): instead of out,
@@ -108,6 +111,7 @@ struct Buffers {
     double2 *beta;    // [2B-1][K0+1][B]     beta_{kappa0, l, m}, kappa0 >= 0
     double2 *zeta;    // [K0+1][K1+1][2B-1]  zeta_{kappa0, kappa1, m}, kappa0, kappa1 >= 0
     double *linescale;// [(2K1+1)^2] d1[k1] d2[m]
+    float2 *linescale_df; // the same as double-float pairs (h, l)
     // FFT work buffers (complex, precision of the plan)
     void *bufA, *bufB;
     size_t bufA_bytes, bufB_bytes;

@@ -92,24 +92,6 @@ __device__ __forceinline__ void grid_coords(double x, double y, double z, double
 // ---- the same angles in double-float arithmetic (FP32-mixed plans): every operation on the
 // FP32 pipe, relative rounding about 1e-13, far below the binary32 offsets the kernels read.
 
-// x 2^-E as a double-float, from the bit pattern alone: the leading 24 significand bits give h,
-// the other 29 (rounded to 24) give l.  Zero when x 2^-E lies below 2^-126 (subnormal doubles too).
-__device__ __forceinline__ dfl split_scaled(double x, int E) {
-    const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
-    const int ex = (int)((bits >> 52) & 0x7ff);
-    const int e = ex - 1023 - E;
-    if (ex == 0 || e < -126 || e > 127) return dfl(0.f, 0.f);
-    const unsigned sign = (unsigned)(bits >> 32) & 0x80000000u;
-    const unsigned long long m = bits & 0xfffffffffffffull;
-    const float h = __int_as_float((int)(sign | ((unsigned)(e + 127) << 23) | (unsigned)(m >> 29)));
-    float l = 0.f;
-    if (e >= -74) {
-        const float v = __fmul_rn((float)(unsigned)(m & 0x1fffffffu), __int_as_float((e - 52 + 127) << 23));
-        l = sign ? -v : v;
-    }
-    return dfl(h, l);
-}
-
 // finiteness from the exponent field (integer operations only)
 __device__ __forceinline__ bool finite_bits(double x) {
     return ((((unsigned long long)__double_as_longlong(x)) >> 52) & 0x7ff) != 0x7ff;
@@ -177,7 +159,7 @@ __global__ void __launch_bounds__(256) k_transform_points(const double *__restri
         const double r2 = __longlong_as_double((long long)*r2max);
         if (r2 > 0.0) {
             const int E2 = exponent_of(r2) & ~1;                  // even: sqrt(r2 2^-E2) = sqrt(r2) 2^-E2/2
-            const dfl s = df_sqrt(split_scaled(r2, E2));           // in [1, 2)
+            const dfl s = df_sqrt(df_split_bits(r2, E2));           // in [1, 2)
             rho_s = s + df_mul(s, 0x1p-20f);
             Erho = E2 / 2;
         }
@@ -191,7 +173,7 @@ __global__ void __launch_bounds__(256) k_transform_points(const double *__restri
         float f0, f1, f2;
         if constexpr (DF) {
             const int E = max(max(exponent_of(x), exponent_of(y)), exponent_of(z));
-            const dfl xs = split_scaled(x, E), ys = split_scaled(y, E), zs = split_scaled(z, E);
+            const dfl xs = df_split_bits(x, E), ys = df_split_bits(y, E), zs = df_split_bits(z, E);
             const dfl rxy2 = xs * xs + ys * ys;
             const dfl rxy = df_sqrt(rxy2), r = df_sqrt(rxy2 + zs * zs);      // times 2^-E
             // t0 on the common scale 2^-Erho (E <= Erho: rho >= r >= every coordinate)
