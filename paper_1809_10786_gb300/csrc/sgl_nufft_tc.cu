@@ -461,11 +461,6 @@ k_nufft_tc(const __grid_constant__ CUtensorMap tmap, NGeom g, TcArgs args) {
             while (ok && next_pass(it, args)) {
                 const int abuf = n % Cfg::ABUF, use = n / Cfg::ABUF;
                 const int tbuf = n & 1, tuse = n >> 1;        // window tables: two buffers in shared memory
-                if (use >= 1) ok = __all_sync(0xffffffffu, mbar_wait(smem_addr(&sm.aempty[abuf]), (use + 1) & 1, lim) && !*abort_flag);
-                if (ok && tuse >= 1)
-                    ok = __all_sync(0xffffffffu, mbar_wait(smem_addr(&sm.tabfree[tbuf]), (tuse + 1) & 1, lim) && !*abort_flag);
-                if (!ok) break;
-                tc_fence_after();
                 const int idx = it.pass * kPM + p;
                 const bool live = idx < it.np;
                 const float4 pt = args.pts[it.first + (live ? idx : 0)];
@@ -474,83 +469,85 @@ k_nufft_tc(const __grid_constant__ CUtensorMap tmap, NGeom g, TcArgs args) {
                 const int sb1 = (int)(it.sb % g.nsb1), sb2 = (int)((it.sb / g.nsb1) % g.nsb2);
                 const int k0 = c2 - q + 1 - (sb2 * g.S2 - tc_halo(q));     // lane of the point's first tap
                 const int d1 = c1 - sb1 * kC1;
-                const uint32_t ta_ = tmem + lane_base + Cfg::ABASE + (uint32_t)abuf * Cfg::ACOLS;
-                // the 2q nonzero weights per axis (compile-time tap index: independent chains), placed
-                // at the point's runtime offsets through shared memory
-                float *row = sm.lanes[p];
-                float w[kLanes];
-                if constexpr (GRAD) {
-                    // psi' goes to the table rows first, psi to the lanes; then the lanes take psi'
-                    float dv[16];
+                // Order: the axis-2 weights into registers first, then the window tables (their
+                // own two buffers), and only then the wait for the operand buffer, so that the
+                // tensor pipe waits for nothing but the operand stores between passes.  The 2q
+                // nonzero weights per axis come from compile-time tap indices (independent chains).
+                float v2[16], e2[GRAD ? 16 : 1];
 #pragma unroll
-                    for (int k = 0; k < kLanes; ++k) row[k] = 0.f;
-#pragma unroll
-                    for (int rel = 0; rel < 16; ++rel) {
+                for (int rel = 0; rel < 16; ++rel) {
+                    if constexpr (GRAD) {
                         const float2 v = win_both_fast<WIN>(pt.z + (float)(q - 1 - rel), qf, par2, nrm2, edge2);
-                        dv[rel] = v.y;
-                        if (live && rel < q2) row[k0 + rel] = v.x;
+                        v2[rel] = v.x;
+                        e2[rel] = v.y;
+                    } else {
+                        v2[rel] = win_fast<WIN>(pt.z + (float)(q - 1 - rel), qf, par2, nrm2, edge2);
                     }
+                }
+                if (tuse >= 1)
+                    ok = __all_sync(0xffffffffu, mbar_wait(smem_addr(&sm.tabfree[tbuf]), (tuse + 1) & 1, lim) && !*abort_flag);
+                if (!ok) break;
 #pragma unroll
-                    for (int k = 0; k < kLanes; ++k) w[k] = row[k];
-                    store_split_tmem(ta_, w);
+                for (int tb = 0; tb < kTB1Max; ++tb) {
+                    sm.w1tab[tbuf][0][tb][p] = 0.f;
+                    if constexpr (GRAD) sm.w1tab[tbuf][GRAD ? 1 : 0][tb][p] = 0.f;
+                }
 #pragma unroll
-                    for (int rel = 0; rel < 16; ++rel)
-                        if (live && rel < q2) row[k0 + rel] = dv[rel];
-#pragma unroll
-                    for (int k = 0; k < kLanes; ++k) w[k] = row[k];
-                    store_split_tmem(ta_ + 64, w);
-#pragma unroll
-                    for (int tb = 0; tb < kTB1Max; ++tb) {
-                        sm.w1tab[tbuf][0][tb][p] = 0.f;
-                        sm.w1tab[tbuf][GRAD ? 1 : 0][tb][p] = 0.f;
-                    }
-#pragma unroll
-                    for (int rel = 0; rel < 16; ++rel) {
+                for (int rel = 0; rel < 16; ++rel) {
+                    if constexpr (GRAD) {
                         const float2 v = win_both_fast<WIN>(pt.y + (float)(q - 1 - rel), qf, par1, nrm1, edge1);
                         if (live && rel < q2) {
                             sm.w1tab[tbuf][0][d1 + rel][p] = v.x;
                             sm.w1tab[tbuf][GRAD ? 1 : 0][d1 + rel][p] = v.y;
                         }
+                    } else {
+                        const float v = win_fast<WIN>(pt.y + (float)(q - 1 - rel), qf, par1, nrm1, edge1);
+                        if (live && rel < q2) sm.w1tab[tbuf][0][d1 + rel][p] = v;
                     }
+                }
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) {
+                for (int j = 0; j < 16; ++j) {
+                    if constexpr (GRAD) {
                         const float2 v = win_both_fast<WIN>(pt.x + (float)(q - 1 - j), qf, par0, nrm0, edge0);
                         if (j < q2) {
                             sm.w0tab[tbuf][0][j][p] = v.x;
                             sm.w0tab[tbuf][GRAD ? 1 : 0][j][p] = v.y;
                         }
-                    }
-                } else {
-#pragma unroll
-                    for (int k = 0; k < kLanes; ++k) row[k] = 0.f;
-#pragma unroll
-                    for (int rel = 0; rel < 16; ++rel) {
-                        const float v = win_fast<WIN>(pt.z + (float)(q - 1 - rel), qf, par2, nrm2, edge2);
-                        if (live && rel < q2) row[k0 + rel] = v;
-                    }
-#pragma unroll
-                    for (int k = 0; k < kLanes; ++k) w[k] = row[k];
-                    store_split_tmem(ta_, w);
-#pragma unroll
-                    for (int tb = 0; tb < kTB1Max; ++tb) sm.w1tab[tbuf][0][tb][p] = 0.f;
-#pragma unroll
-                    for (int rel = 0; rel < 16; ++rel) {
-                        const float v = win_fast<WIN>(pt.y + (float)(q - 1 - rel), qf, par1, nrm1, edge1);
-                        if (live && rel < q2) sm.w1tab[tbuf][0][d1 + rel][p] = v;
-                    }
-#pragma unroll
-                    for (int j = 0; j < 16; ++j) {
+                    } else {
                         const float v = win_fast<WIN>(pt.x + (float)(q - 1 - j), qf, par0, nrm0, edge0);
                         if (j < q2) sm.w0tab[tbuf][0][j][p] = v;
                     }
                 }
+                __syncwarp();
+                if (lane == 0) mbar_arrive(smem_addr(&sm.tabfull[tbuf]));
+                // operands: the axis-2 weights placed on the 32 lanes at the point's offset k0
+                // (through this thread's row of shared memory), split, into TMEM
+                if (use >= 1) ok = __all_sync(0xffffffffu, mbar_wait(smem_addr(&sm.aempty[abuf]), (use + 1) & 1, lim) && !*abort_flag);
+                if (!ok) break;
+                tc_fence_after();
+                const uint32_t ta_ = tmem + lane_base + Cfg::ABASE + (uint32_t)abuf * Cfg::ACOLS;
+                float *row = sm.lanes[p];
+                float w[kLanes];
+#pragma unroll
+                for (int k = 0; k < kLanes; ++k) row[k] = 0.f;
+#pragma unroll
+                for (int rel = 0; rel < 16; ++rel)
+                    if (live && rel < q2) row[k0 + rel] = v2[rel];
+#pragma unroll
+                for (int k = 0; k < kLanes; ++k) w[k] = row[k];
+                store_split_tmem(ta_, w);
+                if constexpr (GRAD) {
+#pragma unroll
+                    for (int rel = 0; rel < 16; ++rel)
+                        if (live && rel < q2) row[k0 + rel] = e2[rel];
+#pragma unroll
+                    for (int k = 0; k < kLanes; ++k) w[k] = row[k];
+                    store_split_tmem(ta_ + 64, w);
+                }
                 tmem_wait_st();
                 tc_fence_before();
                 __syncwarp();
-                if (lane == 0) {
-                    if (!args.withhold) mbar_arrive(smem_addr(&sm.afull[abuf]));
-                    mbar_arrive(smem_addr(&sm.tabfull[tbuf]));
-                }
+                if (lane == 0 && !args.withhold) mbar_arrive(smem_addr(&sm.afull[abuf]));
                 ++n;
             }
         } else {
