@@ -265,12 +265,15 @@ __device__ __forceinline__ void store_split_tmem(uint32_t taddr, const float *w)
 // list (at most 128 points of one super-bin each, full passes first), so every CTA gets the same
 // number of full passes to within one.  Every role walks the same sequence.
 static_assert(kPM == kTcPass, "pass size and work-list piece size disagree");
+// A pass's points are sorted by cell column, axis-0 offset d0 first, so they touch only the slabs
+// d0(first point) ... d0(last point) + 2q - 1: the slab groups g0 ... g1 (the others would add
+// nothing).  Every role derives the same range from the pass's first and last point records.
 struct PassIter {
     int64_t sb = -1;
-    int k = -1, pass = 0, first = 0, np = 0;
+    int k = -1, pass = 0, first = 0, np = 0, g0 = 0, g1 = -1;
 };
 
-__device__ __forceinline__ bool next_pass(PassIter &it, const TcArgs &a) {
+__device__ __forceinline__ bool next_pass(PassIter &it, const TcArgs &a, const NGeom &g, int G, int NG) {
     it.k = (it.k < 0) ? (int)blockIdx.x : it.k + (int)gridDim.x;
     if (it.k >= __ldg(a.npasses)) return false;
     const int4 e = __ldg(a.passes + it.k);
@@ -278,6 +281,12 @@ __device__ __forceinline__ bool next_pass(PassIter &it, const TcArgs &a) {
     it.first = e.y;
     it.np = e.z;
     it.pass = 0;
+    const int sb0 = (int)(it.sb / ((int64_t)g.nsb1 * g.nsb2));
+    int c0a, c0b, c1, c2;
+    unpack_cells(__ldg(a.pts + e.y).w, c0a, c1, c2);
+    unpack_cells(__ldg(a.pts + e.y + max(e.z, 1) - 1).w, c0b, c1, c2);
+    it.g0 = max(c0a - sb0 * kC0, 0) / G;
+    it.g1 = min((c0b - sb0 * kC0 + 2 * g.q - 1) / G, NG - 1);
     return true;
 }
 
@@ -338,14 +347,14 @@ k_nufft_tc(const __grid_constant__ CUtensorMap tmap, NGeom g, TcArgs args) {
             const uint32_t tx = 2u * (uint32_t)(G * TB1) * 128u;
             int s = 0;
             PassIter it;
-            while (!*abort_flag && next_pass(it, args)) {
+            while (!*abort_flag && next_pass(it, args, g, G, NG)) {
                 const int sb1 = (int)(it.sb % g.nsb1), sb2 = (int)((it.sb / g.nsb1) % g.nsb2);
                 const int sb0 = (int)(it.sb / ((int64_t)g.nsb1 * g.nsb2));
                 const int x = sb2 * g.S2;             // halo-shifted azimuthal coordinate of lane 0
                 const int y = sb1 * kC1 + 1;          // stored row of tile row 0 on axis 1 (first = -q)
                 const int z0 = sb0 * kC0 + 1;         // stored row of slab 0 on axis 0
                 bool ok = true;
-                for (int gi = 0; gi < NG; ++gi, ++s) {
+                for (int gi = it.g0; gi <= it.g1; ++gi, ++s) {
                     const int st = s % NS;
                     if (s >= NS && !mbar_wait(smem_addr(&sm.empty[st]), ((s / NS) + 1) & 1, lim)) ok = false;
                     if (!ok || *abort_flag) { ok = false; break; }
@@ -367,8 +376,8 @@ k_nufft_tc(const __grid_constant__ CUtensorMap tmap, NGeom g, TcArgs args) {
         int s = 0;
         PassIter it;
         bool ok = true;
-        while (ok && next_pass(it, args)) {
-            for (int gi = 0; gi < NG; ++gi, ++s) {
+        while (ok && next_pass(it, args, g, G, NG)) {
+            for (int gi = it.g0; gi <= it.g1; ++gi, ++s) {
                 const int st = s % NS;
                 ok = __all_sync(0xffffffffu, mbar_wait(smem_addr(&sm.tma_full[st]), (s / NS) & 1, lim) && !*abort_flag);
                 if (!ok) break;
@@ -398,12 +407,12 @@ k_nufft_tc(const __grid_constant__ CUtensorMap tmap, NGeom g, TcArgs args) {
             int s = 0, k = 0;
             bool ok = true;
             PassIter it;
-            while (ok && next_pass(it, args)) {
+            while (ok && next_pass(it, args, g, G, NG)) {
                 const int abuf = k % Cfg::ABUF;
                 ok = mbar_wait(smem_addr(&sm.afull[abuf]), (k / Cfg::ABUF) & 1, lim) && !*abort_flag;
                 tc_fence_after();
                 const uint32_t a = tmem + Cfg::ABASE + (uint32_t)abuf * Cfg::ACOLS;
-                for (int gi = 0; gi < NG && ok; ++gi, ++s) {
+                for (int gi = it.g0; gi <= it.g1 && ok; ++gi, ++s) {
                     const int st = s % NS, buf = s % Cfg::DBUF, use = s / Cfg::DBUF;
                     ok = mbar_wait(smem_addr(&sm.conv_full[st]), (s / NS) & 1, lim);
                     if (ok && use >= 1) ok = mbar_wait(smem_addr(&sm.tempty[buf]), (use + 1) & 1, lim);
@@ -458,7 +467,7 @@ k_nufft_tc(const __grid_constant__ CUtensorMap tmap, NGeom g, TcArgs args) {
             const float edge1 = kb ? 2.f * par1 * expf(-par1 * qf) : 0.5f / par1;
             const float edge2 = kb ? 2.f * par2 * expf(-par2 * qf) : 0.5f / par2;
             int n = 0;
-            while (ok && next_pass(it, args)) {
+            while (ok && next_pass(it, args, g, G, NG)) {
                 const int abuf = n % Cfg::ABUF, use = n / Cfg::ABUF;
                 const int tbuf = n & 1, tuse = n >> 1;        // window tables: two buffers in shared memory
                 const int idx = it.pass * kPM + p;
@@ -556,7 +565,7 @@ k_nufft_tc(const __grid_constant__ CUtensorMap tmap, NGeom g, TcArgs args) {
             if constexpr (GRAD) rho = rho_from_r2max(args.r2max);
             const int half = (warp - Cfg::WRED) >> 2;     // this warp takes slabs z = half, half + 2, ... of a group
             int s = 0, n = 0;
-            while (ok && next_pass(it, args)) {
+            while (ok && next_pass(it, args, g, G, NG)) {
                 const int tbuf = n & 1, tuse = n >> 1;
                 ok = __all_sync(0xffffffffu, mbar_wait(smem_addr(&sm.tabfull[tbuf]), tuse & 1, lim) && !*abort_flag);
                 if (!ok) break;
@@ -575,7 +584,7 @@ k_nufft_tc(const __grid_constant__ CUtensorMap tmap, NGeom g, TcArgs args) {
                     if constexpr (GRAD) e1[tb] = sm.w1tab[tbuf][GRAD ? 1 : 0][tb][p];
                 }
                 float2 acc = make_float2(0.f, 0.f), acc1 = acc, acc2 = acc, accv = acc;
-                for (int gi = 0; gi < NG; ++gi, ++s) {
+                for (int gi = it.g0; gi <= it.g1; ++gi, ++s) {
                     const int buf = s % Cfg::DBUF, use = s / Cfg::DBUF;
                     ok = __all_sync(0xffffffffu, mbar_wait(smem_addr(&sm.tfull[buf]), use & 1, lim) && !*abort_flag);
                     if (!ok) break;
