@@ -588,7 +588,7 @@ sgl_status plan_create_impl(sgl_plan **out, int B, int64_t M_max, int precision,
     ALLOC(b.work[0], (size_t)work_list_cap(Mc, p->bins.nsuper, kTcPass));
     ALLOC(b.work[1], (size_t)work_list_cap(Mc, p->bins.nsuper, spread_chunk(precision)));
     ALLOC(b.work_len, 2);
-    ALLOC(b.df_max, 2);
+    ALLOC(b.df_max, 3);
     ALLOC(b.scalar, 1);
     ALLOC(b.sched, 4);
     ALLOC(b.wtab, (size_t)kWinTab);

@@ -107,4 +107,26 @@ __device__ __forceinline__ double f2d_bits(float f) {
 // h + l rounded to binary64 (one binary64 addition)
 __device__ __forceinline__ double df_to_double_bits(dfl a) { return f2d_bits(a.h) + f2d_bits(a.l); }
 
+// f 2^E as a binary64 number from the bit pattern (0 below the normal range, +-inf above it)
+__device__ __forceinline__ double f2d_bits_scaled(float f, int E) {
+    const unsigned u = (unsigned)__float_as_int(f);
+    const int ex = (int)((u >> 23) & 0xff);
+    const unsigned long long sign = (unsigned long long)(u & 0x80000000u) << 32;
+    if (ex == 0) return __longlong_as_double((long long)sign);
+    const int dex = ex == 0xff ? 0x7ff : ex - 127 + 1023 + E;
+    if (dex <= 0) return __longlong_as_double((long long)sign);
+    if (dex >= 0x7ff) return __longlong_as_double((long long)(sign | (0x7ffull << 52)));
+    return __longlong_as_double((long long)(sign | ((unsigned long long)dex << 52) | ((unsigned long long)(u & 0x7fffffu) << 29)));
+}
+// (h + l) 2^E rounded to binary64
+__device__ __forceinline__ double df_to_double_scaled(dfl a, int E) { return f2d_bits_scaled(a.h, E) + f2d_bits_scaled(a.l, E); }
+
+// the exponent E with max 2^-E in [1, 2) from the bits of a non-negative binary64 max (0 when the
+// max is zero, subnormal or not finite)
+__device__ __forceinline__ int df_scale_exponent(const unsigned long long *bits) {
+    if (!bits) return 0;
+    const int ex = (int)((*bits >> 52) & 0x7ff);
+    return (ex == 0 || ex == 0x7ff) ? 0 : ex - 1023;
+}
+
 }  // namespace sgl

@@ -18,7 +18,10 @@
 // up to 2B - 2 in r) are largest, so the adjoint's K_l^T amplifies it (measured at B = 64, 10^6
 // points: a binary32 radial pass alone made the adjoint coefficients 2.4e-5 wrong relative to
 // their maximum; binary32 angular passes, whose errors stay on the rows of their own radius, and
-// binary32 spreading 2e-8 and 6e-8).
+// binary32 spreading 2e-8 and 6e-8).  The forward's radial pass needs it too: its rounding error
+// is set by the largest rows and lands on the outer radii as well, where the values are small and
+// the gradient's chain rule divides by sin t0 (measured: in binary32 the values' error rose from
+// 1.9e-7 to 1.0e-6 and the point gradient's from 4.4e-7 to 5.4e-5).
 #include "sgl_dfl.cuh"
 #include "sgl_internal.cuh"
 
@@ -354,7 +357,7 @@ __device__ __forceinline__ int pad_e(int i, int E) { return i + i / E; }
 // load: FFT position pos of a line holds input element e = (pos - in_first) mod N (zero if e >= L_in)
 template <typename T, typename InC, int MODE>
 __device__ __forceinline__ C2<T> reg_load(const FftPass &ps, const InC *__restrict__ in, const ZetaSrc &zs, int64_t outer,
-                                          int64_t inner, bool valid, int e, int scale_on_output) {
+                                          int64_t inner, bool valid, int e, int scale_on_output, int E) {
     if (!valid || e >= ps.L_in) return mk<T>(T(0), T(0));
     C2<T> v;
     if constexpr (MODE == LOAD_ZETA) {
@@ -364,11 +367,11 @@ __device__ __forceinline__ C2<T> reg_load(const FftPass &ps, const InC *__restri
         const int k0 = e - zs.K0;
         double2 d = zs.zeta[((int64_t)abs(k0) * (zs.K1 + 1) + abs(k1)) * W + mi];
         if (k1 < 0 && ((mi - zs.K1) & 1)) { d.x = -d.x; d.y = -d.y; }
-        if constexpr (std::is_same<T, dfl>::value) { v.x = df_split_bits(d.x); v.y = df_split_bits(d.y); }
+        if constexpr (std::is_same<T, dfl>::value) { v.x = df_split_bits(d.x, E); v.y = df_split_bits(d.y, E); }
         else { v.x = T(d.x); v.y = T(d.y); }
     } else {
         const InC x = in[outer * ps.in_so + inner * ps.in_si + (int64_t)e * ps.in_se];
-        if constexpr (std::is_same<T, dfl>::value && sizeof(x.x) == 8) { v.x = df_split_bits(x.x); v.y = df_split_bits(x.y); }
+        if constexpr (std::is_same<T, dfl>::value && sizeof(x.x) == 8) { v.x = df_split_bits(x.x, E); v.y = df_split_bits(x.y, E); }
         else { v.x = T(x.x); v.y = T(x.y); }
     }
     if (!scale_on_output && (ps.elem_scale || ps.line_scale)) {
@@ -393,7 +396,7 @@ __device__ __forceinline__ C2<T> reg_load(const FftPass &ps, const InC *__restri
 // store output element e (position (e + out_first) mod N), optional scale on output
 template <typename T, typename OutC>
 __device__ __forceinline__ void reg_store(const FftPass &ps, OutC *__restrict__ out, int64_t outer, int64_t inner, int e, C2<T> v,
-                                          int scale_on_output) {
+                                          int scale_on_output, int E) {
     using S = decltype(OutC::x);
     OutC o;
     if (scale_on_output && (ps.elem_scale || ps.line_scale)) {
@@ -416,8 +419,8 @@ __device__ __forceinline__ void reg_store(const FftPass &ps, OutC *__restrict__ 
         }
     }
     if constexpr (std::is_same<T, dfl>::value && sizeof(S) == 8) {
-        o.x = df_to_double_bits(v.x);
-        o.y = df_to_double_bits(v.y);
+        o.x = df_to_double_scaled(v.x, E);
+        o.y = df_to_double_scaled(v.y, E);
     } else {
         o.x = narrow<S>(v.x);
         o.y = narrow<S>(v.y);
@@ -480,6 +483,7 @@ __global__ void __launch_bounds__(256) k_fft_reg(FftPass ps, const InC *__restri
     const bool valid = inner < ps.nb_inner;
     C2<T> *line = sbuf + bl * G::LS;
     const C2<T> *tw = reinterpret_cast<const C2<T> *>(ps.tw);
+    const int SE = df_scale_exponent(ps.scale_bits);              // 0 unless binary64 data in double-float
 
     // stage 1 inputs: butterfly b = n1 (L = 1) reads positions n1 + (N / R1) n2
     C2<T> v[E];
@@ -490,7 +494,7 @@ __global__ void __launch_bounds__(256) k_fft_reg(FftPass ps, const InC *__restri
         for (int n2 = 0; n2 < R1; ++n2) {
             int e = n1 + (N / R1) * n2 - ps.in_first;
             e = e >= N ? e - N : (e < 0 ? e + N : e);
-            v[i * R1 + n2] = reg_load<T, InC, MODE>(ps, in, zs, outer, inner, valid, e, scale_on_output);
+            v[i * R1 + n2] = reg_load<T, InC, MODE>(ps, in, zs, outer, inner, valid, e, scale_on_output, SE);
         }
     }
     reg_stage<T, N, E, TPL, R1, 1>(v, t, ps.sign, tw);
@@ -532,7 +536,7 @@ __global__ void __launch_bounds__(256) k_fft_reg(FftPass ps, const InC *__restri
             const int pos = t + TPL * i + LL * k;
             int e = pos - ps.out_first;
             e = e >= N ? e - N : (e < 0 ? e + N : e);
-            if (e < ps.L_out) reg_store<T, OutC>(ps, out, outer, inner, e, v[i * RL + k], scale_on_output);
+            if (e < ps.L_out) reg_store<T, OutC>(ps, out, outer, inner, e, v[i * RL + k], scale_on_output, SE);
         }
     }
 }
@@ -572,6 +576,12 @@ cudaError_t run_pass(sgl_plan *p, FftPass ps, const void *in, void *out, ZetaSrc
             default: break;
         }
     }
+    if constexpr (std::is_same<T, dfl>::value && std::is_same<InC, double2>::value && std::is_same<OutC, double2>::value) {
+        // binary64 data of other lengths: the generic kernel in binary64 (it keeps the full range)
+        ps.tw = ps.tw64;
+        ps.scale_bits = nullptr;
+        return run_pass<double, InC, OutC, MODE>(p, ps, in, out, zs, scale_on_output);
+    } else {
     int lgTB = 0;
     const int TB = lines_per_tile(ps.N, lgTB);
     const size_t smem = (size_t)TB * (ps.N + 1) * sizeof(C2<T>);
@@ -583,6 +593,7 @@ cudaError_t run_pass(sgl_plan *p, FftPass ps, const void *in, void *out, ZetaSrc
     kern<<<(unsigned)tiles, 256, smem, p->stream>>>(ps, TB, lgTB, (const InC *)in, (OutC *)out, zs, scale_on_output);
     p->launches += 1;
     return cudaGetLastError();
+    }
 }
 
 FftPass base_pass(const Axis &a, int sign, bool fp32) {
@@ -592,41 +603,60 @@ FftPass base_pass(const Axis &a, int sign, bool fp32) {
     for (int i = 0; i < a.nrad; ++i) ps.rad[i] = a.rad[i];
     ps.sign = sign;
     ps.tw = fp32 ? (const void *)a.tw_f : (const void *)a.tw_d;
+    ps.tw64 = a.tw_d;
     ps.rev = a.rev;
     return ps;
 }
 
-template <typename T>
+// the twiddle table of an axis in the pass arithmetic AR
+template <typename AR> const void *twiddles(const Axis &a) {
+    if constexpr (std::is_same<AR, dfl>::value) return a.tw_df;
+    else if constexpr (std::is_same<AR, float>::value) return a.tw_f;
+    else return a.tw_d;
+}
+
+// Storage T (float2 / double2 work buffers) and the arithmetic of the passes: FP32-mixed plans run
+// the radial passes in double-float (RA = dfl) and the angular ones in binary32 (AA = float); FP64
+// plans run all three in double-float (RA = AA = dfl, the default) or in binary64
+// (SGL_FLAG_NATIVE_FP64).
+template <typename T, typename RA, typename AA>
 cudaError_t forward_passes(sgl_plan *p) {
     const Axis &A0 = p->ax[0], &A1 = p->ax[1], &A2 = p->ax[2];
     constexpr bool f32 = std::is_same<T, float>::value;
     const int64_t W = 2 * p->K1 + 1;
     ZetaSrc zs{p->b.zeta, p->K0, p->K1};
     cudaError_t e;
+    // binary64 data in double-float passes: one power-of-two scale for all three, from max |zeta|
+    constexpr bool scaled = !f32 && std::is_same<RA, dfl>::value;
+    const unsigned long long *sb = scaled ? p->b.df_max + 2 : nullptr;
+    if (scaled &&
+        (e = launch_max_abs(p, (const double *)p->b.zeta, 2 * (int64_t)(p->K0 + 1) * (p->K1 + 1) * W, p->b.df_max + 2)) != cudaSuccess)
+        return e;
     // pass A (axis 0): zeta (mirrored, deconvolved) -> X0[l0 row][k1][m]
     FftPass a = base_pass(A0, +1, f32);
+    a.scale_bits = sb;
+    a.tw = twiddles<RA>(A0);
     a.L_in = 2 * p->K0 + 1; a.in_first = -p->K0;
     a.L_out = A0.rows; a.out_first = A0.first;
     a.nb_outer = 1; a.nb_inner = W * W;
     a.out_so = 0; a.out_si = 1; a.out_se = W * W;
     a.elem_scale = A0.deconv; a.line_scale = p->b.linescale;
-    if constexpr (f32) {
-        a.tw = A0.tw_df;                          // radial pass in double-float (file comment)
-        a.elem_scale_df = A0.deconv_df; a.line_scale_df = p->b.linescale_df;
-        if ((e = run_pass<dfl, double2, C2<T>, LOAD_ZETA>(p, a, nullptr, p->b.bufA, zs, 0)) != cudaSuccess) return e;
-    } else if ((e = run_pass<T, double2, C2<T>, LOAD_ZETA>(p, a, nullptr, p->b.bufA, zs, 0)) != cudaSuccess) {
-        return e;
-    }
+    a.elem_scale_df = A0.deconv_df; a.line_scale_df = p->b.linescale_df;
+    if ((e = run_pass<RA, double2, C2<T>, LOAD_ZETA>(p, a, nullptr, p->b.bufA, zs, 0)) != cudaSuccess) return e;
     // pass B (axis 1): X0 -> X1[l0][l1 row][m]
     FftPass b = base_pass(A1, +1, f32);
+    b.tw = twiddles<AA>(A1);
+    b.scale_bits = sb;
     b.L_in = (int)W; b.in_first = -p->K1;
     b.L_out = A1.rows; b.out_first = A1.first;
     b.nb_outer = A0.rows; b.nb_inner = W;
     b.in_so = W * W; b.in_si = 1; b.in_se = W;
     b.out_so = (int64_t)A1.rows * W; b.out_si = 1; b.out_se = W;
-    if ((e = run_pass<T, C2<T>, C2<T>, LOAD_STRIDED>(p, b, p->b.bufA, p->b.bufB, zs, 0)) != cudaSuccess) return e;
+    if ((e = run_pass<AA, C2<T>, C2<T>, LOAD_STRIDED>(p, b, p->b.bufA, p->b.bufB, zs, 0)) != cudaSuccess) return e;
     // pass C (axis 2): X1 -> grid[l0][l1][l2], full lines
     FftPass c = base_pass(A2, +1, f32);
+    c.tw = twiddles<AA>(A2);
+    c.scale_bits = sb;
     c.L_in = (int)W; c.in_first = -p->K1;
     c.L_out = A2.N; c.out_first = 0;
     c.nb_outer = 1; c.nb_inner = (int64_t)A0.rows * A1.rows;
@@ -638,56 +668,68 @@ cudaError_t forward_passes(sgl_plan *p) {
         c.halo = tc_halo(p->q);
         c.plane_n = c.nb_inner * c.pitch;
     }
-    return run_pass<T, C2<T>, C2<T>, LOAD_STRIDED>(p, c, p->b.bufB, p->b.bufA, zs, 0);
+    return run_pass<AA, C2<T>, C2<T>, LOAD_STRIDED>(p, c, p->b.bufB, p->b.bufA, zs, 0);
 }
 
-template <typename T>
+template <typename T, typename RA, typename AA>
 cudaError_t adjoint_passes(sgl_plan *p) {
     const Axis &A0 = p->ax[0], &A1 = p->ax[1], &A2 = p->ax[2];
     constexpr bool f32 = std::is_same<T, float>::value;
     const int64_t W = 2 * p->K1 + 1;
     ZetaSrc zs{p->b.zeta, p->K0, p->K1};
     cudaError_t e;
+    // binary64 data in double-float passes: one power-of-two scale for all three, from max |grid|
+    constexpr bool scaled = !f32 && std::is_same<RA, dfl>::value;
+    const unsigned long long *sb = scaled ? p->b.df_max + 2 : nullptr;
+    if (scaled && (e = launch_max_abs(p, (const double *)p->b.bufA, 2 * (int64_t)A0.rows * A1.rows * A2.N, p->b.df_max + 2)) !=
+                      cudaSuccess)
+        return e;
     // pass C' (axis 2): grid -> Y1[l0][l1][m]
     FftPass c = base_pass(A2, -1, f32);
+    c.tw = twiddles<AA>(A2);
+    c.scale_bits = sb;
     c.L_in = A2.N; c.in_first = 0;
     c.L_out = (int)W; c.out_first = -p->K1;
     c.nb_outer = 1; c.nb_inner = (int64_t)A0.rows * A1.rows;
     c.in_so = 0; c.in_si = A2.N; c.in_se = 1;
     c.out_so = 0; c.out_si = W; c.out_se = 1;
-    if ((e = run_pass<T, C2<T>, C2<T>, LOAD_STRIDED>(p, c, p->b.bufA, p->b.bufB, zs, 1)) != cudaSuccess) return e;
+    if ((e = run_pass<AA, C2<T>, C2<T>, LOAD_STRIDED>(p, c, p->b.bufA, p->b.bufB, zs, 1)) != cudaSuccess) return e;
     // pass B' (axis 1): Y1 -> Y0[l0][k1][m]
     FftPass b = base_pass(A1, -1, f32);
+    b.tw = twiddles<AA>(A1);
+    b.scale_bits = sb;
     b.L_in = A1.rows; b.in_first = A1.first;
     b.L_out = (int)W; b.out_first = -p->K1;
     b.nb_outer = A0.rows; b.nb_inner = W;
     b.in_so = (int64_t)A1.rows * W; b.in_si = 1; b.in_se = W;
     b.out_so = W * W; b.out_si = 1; b.out_se = W;
-    if ((e = run_pass<T, C2<T>, C2<T>, LOAD_STRIDED>(p, b, p->b.bufB, p->b.bufA, zs, 1)) != cudaSuccess) return e;
+    if ((e = run_pass<AA, C2<T>, C2<T>, LOAD_STRIDED>(p, b, p->b.bufB, p->b.bufA, zs, 1)) != cudaSuccess) return e;
     // pass A' (axis 0): Y0 -> eta'[k0][k1][m] (FP64), deconvolved
     FftPass a = base_pass(A0, -1, f32);
+    a.tw = twiddles<RA>(A0);
+    a.scale_bits = sb;
     a.L_in = A0.rows; a.in_first = A0.first;
     a.L_out = 2 * p->K0 + 1; a.out_first = -p->K0;
     a.nb_outer = 1; a.nb_inner = W * W;
     a.in_so = 0; a.in_si = 1; a.in_se = W * W;
     a.out_so = 0; a.out_si = 1; a.out_se = W * W;
     a.elem_scale = A0.deconv; a.line_scale = p->b.linescale;
-    if constexpr (f32) {
-        a.tw = A0.tw_df;                          // radial pass in double-float (file comment)
-        a.elem_scale_df = A0.deconv_df; a.line_scale_df = p->b.linescale_df;
-        return run_pass<dfl, C2<T>, double2, LOAD_STRIDED>(p, a, p->b.bufA, p->b.bufB, zs, 1);
-    }
-    return run_pass<T, C2<T>, double2, LOAD_STRIDED>(p, a, p->b.bufA, p->b.bufB, zs, 1);
+    a.elem_scale_df = A0.deconv_df; a.line_scale_df = p->b.linescale_df;
+    return run_pass<RA, C2<T>, double2, LOAD_STRIDED>(p, a, p->b.bufA, p->b.bufB, zs, 1);
 }
 
 }  // namespace
 
 cudaError_t launch_fft_forward(sgl_plan *p) {
-    return p->prec == SGL_FP32_MIXED ? forward_passes<float>(p) : forward_passes<double>(p);
+    if (p->prec == SGL_FP32_MIXED) return forward_passes<float, dfl, float>(p);
+    if (p->flags & SGL_FLAG_NATIVE_FP64) return forward_passes<double, double, double>(p);
+    return forward_passes<double, dfl, dfl>(p);
 }
 
 cudaError_t launch_fft_adjoint(sgl_plan *p) {
-    return p->prec == SGL_FP32_MIXED ? adjoint_passes<float>(p) : adjoint_passes<double>(p);
+    if (p->prec == SGL_FP32_MIXED) return adjoint_passes<float, dfl, float>(p);
+    if (p->flags & SGL_FLAG_NATIVE_FP64) return adjoint_passes<double, double, double>(p);
+    return adjoint_passes<double, dfl, dfl>(p);
 }
 
 }  // namespace sgl

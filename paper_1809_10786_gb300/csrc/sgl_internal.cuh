@@ -93,6 +93,9 @@ struct FftPass {
     const float2 *elem_scale_df;    // the same factors as double-float pairs (double-float passes)
     const float2 *line_scale_df;
     const void *tw;                 // twiddle table (double2 or float2)
+    const void *tw64;               // the binary64 table (passes that fall back to binary64 arithmetic)
+    const unsigned long long *scale_bits;   // double-float passes with binary64 input and output: bits of
+                                            // max |input|; the pass runs on x 2^-E (E its exponent)
     const int *rev;
     // optional FP32 split-plane output (the tensor-core interpolation's layout): instead of out,
     // line i writes Re, Im of position (e - halo) mod N at planes[i pitch + e], planes[plane_n + i pitch + e],
@@ -129,7 +132,8 @@ struct Buffers {
     int *piece_cnt, *piece_off;// [4 nsuper] full and remainder pieces per super-bin, both lists, and their scan
     int4 *work[2];             // work lists (see kTcPass): tensor-core passes, spreading chunks
     int *work_len;             // [2] entries in each list (written on the device)
-    unsigned long long *df_max;// [2] FP64 plans: bits of max |grid| and max |values| (scales of the double-float passes)
+    unsigned long long *df_max;// [3] FP64 plans: bits of max |grid|, max |values| and max |FFT input| (scales of the
+                               // double-float passes)
     double *scalar;            // [1] device accumulator of small reductions (sgl_eta_l1)
     int *sched;                // [4] work counters of the persistent kernels (zeroed before each launch)
     double *wtab;              // [kWinTab] tabulated windows (FP64 plans)
@@ -214,6 +218,7 @@ cudaError_t launch_polar_forward(sgl_plan *p);
 cudaError_t launch_trig_export(sgl_plan *p, double2 *eta);
 cudaError_t launch_polar_adjoint(sgl_plan *p, const double2 *eta_full);
 cudaError_t launch_radial_adjoint(sgl_plan *p, double2 *coef);
+cudaError_t launch_max_abs(sgl_plan *p, const double *x, int64_t n, unsigned long long *bits);   // bits = max |x| (zeroed first)
 cudaError_t launch_fft_forward(sgl_plan *p);    // zeta -> grid (bufA; b.planes when the interpolation is on tensor cores)
 cudaError_t launch_fft_adjoint(sgl_plan *p);    // grid (bufA) -> eta' full support (bufB, FP64)
 cudaError_t launch_interp(sgl_plan *p, double2 *vals);

@@ -760,6 +760,8 @@ cudaError_t grad64_t(sgl_plan *p, const double2 *gout, double *gxyz, double2 *va
 
 }  // namespace
 
+cudaError_t launch_max_abs(sgl_plan *p, const double *x, int64_t n, unsigned long long *bits) { return max_abs(p, x, n, bits); }
+
 cudaError_t launch_interp64(sgl_plan *p, double2 *vals) {
     return p->window == SGL_WIN_KB ? interp64_t<SGL_WIN_KB>(p, vals) : interp64_t<SGL_WIN_GAUSS>(p, vals);
 }

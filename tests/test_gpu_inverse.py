@@ -97,8 +97,8 @@ def test_midpoint_guess_matches_the_oracle():
     assert rel(g, inverse.midpoint_guess(B, x, f, kappa, N)) <= 1e-10
 
 
-@pytest.mark.parametrize("native,later", [(True, 0.02), (False, 0.25)])
-def test_paper_last_test_setup_small(native, later):
+@pytest.mark.parametrize("native", [True, False])
+def test_paper_last_test_setup_small(native):
     # Sect. 8, last test, at a size the dense oracle handles: Cartesian grid G_N, kappa = 5,
     # exact samples of random coefficients, CGNR from the mid-point rule
     B, N, kappa = 4, 14, 5.0
@@ -113,10 +113,12 @@ def test_paper_last_test_setup_small(native, later):
     nf = np.linalg.norm(f)
     # Nc = 30 unknowns: in exact arithmetic CGNR ends by iteration 30, and past it the residual is
     # set by rounding (the oracle alone gave 8.9e-9 and 5.5e-9 at iteration 40 from initial
-    # guesses 1e-16 apart).  Iteration 20 moves by 0.3 % under 1e-15 perturbations of the pair
-    # (1.7 % under 1e-14), so it carries the pin; iteration 40 only its size.
-    c, res, k = p.inverse(gpu(f), coef0=c0, iters=20, method="cgnr")
-    assert res == pytest.approx(res_or[20] / nf, rel=later)     # sensitivity: module docstring
+    # guesses 1e-16 apart).  Iterations 10, 16 and 20 move by up to 26 %, 38 % and 64 % under
+    # independent 1e-13 perturbations of the forward and adjoint matrices (the size of the
+    # double-float transforms' rounding), iteration 15 by 2.6e-8 (1.5e-5 under 1e-12; 16 seeds
+    # each), so iteration 15 carries the pin; iteration 40 only its size.
+    c, res, k = p.inverse(gpu(f), coef0=c0, iters=15, method="cgnr")
+    assert res == pytest.approx(res_or[15] / nf, rel=1e-3)
     c, res, k = p.inverse(gpu(f), coef0=c0, iters=40, method="cgnr")
     assert res <= res_or[0] / nf
     assert res <= 10.0 * res_or[40] / nf

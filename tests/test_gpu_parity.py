@@ -251,9 +251,11 @@ def test_forward_grad_host_buffers():
 
 @pytest.mark.parametrize("q", [4, 8])
 def test_double_float_and_binary64_loops_agree(q):
-    # the FP64 plan's double-float hot loops (relative rounding ~2^-48 per operation) against the
-    # binary64 loops of SGL_FLAG_NATIVE_FP64 (same window, so the same approximation), on a size
-    # with many points per bin and tile; q = 4 and 8 take the two spreading-kernel sizes
+    # the FP64 plan's double-float hot loops and FFT passes (relative rounding ~2^-48 per
+    # operation) against the binary64 ones of SGL_FLAG_NATIVE_FP64 (same window, so the same
+    # approximation), on a size with many points per bin and tile; q = 4 and 8 take the two
+    # spreading-kernel sizes.  Measured: adjoint 2.1e-13 (the FFT passes; 1.1e-13 with
+    # binary64 FFT passes), the rest below 1e-13.
     B, M = 16, 20000
     c, x, y = case(B, M, 5100)
     g = y[::-1].copy()
@@ -265,15 +267,18 @@ def test_double_float_and_binary64_loops_agree(q):
         fv, gx = p.forward_grad(gpu(c), gpu(g))
         out[native] = (f, a, fv.cpu().numpy(), gx.cpu().numpy())
         p.close()
-    for k, tol in zip(range(4), (1e-13, 1e-13, 1e-13, 1e-11)):
+    for k, tol in zip(range(4), (2e-13, 6e-13, 2e-13, 1e-11)):
         assert rel(out[False][k], out[True][k]) <= tol
 
 
+@pytest.mark.parametrize("B", [10, 16])
 @pytest.mark.parametrize("scale", [1e-200, 1e-30, 1e40, 1e200])
-def test_fp64_plan_is_linear_over_the_whole_binary64_range(scale):
-    # the double-float loops work on power-of-two scaled data, so magnitudes far outside the
-    # binary32 range (the SGL polynomials reach 1e15 at r ~ 9 for B = 16) keep full accuracy
-    B, M = 10, 3000
+def test_fp64_plan_is_linear_over_the_whole_binary64_range(scale, B):
+    # the double-float loops and FFT passes work on power-of-two scaled data, so magnitudes far
+    # outside the binary32 range (the SGL polynomials reach 1e15 at r ~ 9 for B = 16) keep full
+    # accuracy; B = 16 takes the double-float register FFT (lengths 128, 64), B = 10 the generic
+    # kernel in binary64 (lengths 80, 40)
+    M = 3000
     c, x, y = case(B, M, 5200)
     p = plan_for(B, M, x=x)
     f1 = p.forward(gpu(c)).cpu().numpy()
@@ -283,8 +288,8 @@ def test_fp64_plan_is_linear_over_the_whole_binary64_range(scale):
     _, gs = p.forward_grad(gpu(c * scale), gpu(y))
     _, g1 = p.forward_grad(gpu(c), gpu(y))
     assert np.isfinite(fs).all() and np.isfinite(as_).all()
-    assert rel(fs / scale, f1) <= 1e-13
-    assert rel(as_ / scale, a1) <= 1e-13
+    assert rel(fs / scale, f1) <= 3e-13
+    assert rel(as_ / scale, a1) <= 3e-13
     assert rel(gs.cpu().numpy() / scale, g1.cpu().numpy()) <= 1e-11
 
 
