@@ -592,6 +592,7 @@ sgl_status plan_create_impl(sgl_plan **out, int B, int64_t M_max, int precision,
     ALLOC(b.scalar, 1);
     ALLOC(b.sched, 4);
     ALLOC(b.wtab, (size_t)kWinTab);
+    ALLOC(b.wtab_df, (size_t)kWinTab);
     ALLOC(b.rot, (size_t)(2 * kRotK + 1));
     ALLOC(b.rotf, (size_t)(2 * kRotK + 1));
     if (flags & SGL_FLAG_HOST_IO) {
@@ -659,6 +660,7 @@ sgl_status plan_create_impl(sgl_plan **out, int B, int64_t M_max, int precision,
         std::vector<double> wt;
         window_tables(p, wt);
         if ((e = upload(b.wtab, wt, p->stream)) != cudaSuccess) return fail(SGL_ERR_CUDA, "upload window tables");
+        if ((e = upload(b.wtab_df, df_pairs(wt), p->stream)) != cudaSuccess) return fail(SGL_ERR_CUDA, "upload window tables");
     }
     {
         // (cos, sin) of k pi / kRotK in extended precision, rounded to binary64 and to double-float pairs

@@ -137,6 +137,7 @@ struct Buffers {
     double *scalar;            // [1] device accumulator of small reductions (sgl_eta_l1)
     int *sched;                // [4] work counters of the persistent kernels (zeroed before each launch)
     double *wtab;              // [kWinTab] tabulated windows (FP64 plans)
+    float2 *wtab_df;           // [kWinTab] the same as double-float pairs (FP64 plans)
     double2 *rot;              // [2 kRotK + 1] (cos, sin) of k pi / kRotK, k = -kRotK .. kRotK (point angles)
     float4 *rotf;              // [2 kRotK + 1] the same as double-float pairs (cos h, cos l, sin h, sin l)
     float4 *rec_tmp;           // [M] binary32 point records (as pts32) in input order

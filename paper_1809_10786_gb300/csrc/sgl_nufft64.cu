@@ -558,55 +558,47 @@ __global__ void __launch_bounds__(32 * (C0 + Q2MAX - 1)) k_spread_slab64x(NGeom 
                                                                           double2 *__restrict__ grid) {
     using S = Spread64xSmem<Q2MAX, C1>;
     constexpr int T1M = S::T1, RH = (T1M + 1) / 2;
-    constexpr int E = Q2MAX + T1M + 32 + 1;
+    constexpr int E = 3 * Q2MAX + 1;             // staged items per point: the taps of three axes, the value
     extern __shared__ __align__(16) unsigned char smem_raw[];
     S &sm = *reinterpret_cast<S *>(smem_raw);
     const int lane = threadIdx.x & 31, ta = threadIdx.x >> 5;
     const int q = g.q, q2 = 2 * q;
-    const double qd = (double)q;
     if ((int)blockIdx.x >= __ldg(work_len)) return;
     const int vexp = df_exponent(maxbits);
-    const double vscale = ldexp(1.0, -vexp), unscale = ldexp(1.0, vexp);
     const int4 piece = __ldg(work + blockIdx.x);
     const int64_t sb = piece.x;
     const int cs = piece.y, np = min(piece.z, S::PCH);
     const int sb1 = (int)(sb % g.nsb1), sb2 = (int)((sb / g.nsb1) % g.nsb2), sb0 = (int)(sb / ((int64_t)g.nsb1 * g.nsb2));
     const int ta_org = sb0 * C0 - q + 1, tb_org = sb1 * C1 - q + 1, cbase = sb2 * g.S2 - q + 1;
     const int T1 = C1 + q2 - 1;
+    // staging: the tile rows and lanes no tap reaches are zero; then only the 2q taps per axis are
+    // evaluated (double-float windows on the FP32 pipe), and the values split into pairs with the
+    // power-of-two scale 2^-vexp taken out of their exponents
+    for (int t = threadIdx.x; t < np * (T1M + 32); t += blockDim.x) {
+        const int p = t / (T1M + 32), e = t - p * (T1M + 32);
+        if (e < T1M) sm.w1[p][e] = make_float2(0.f, 0.f);
+        else sm.w2[p][e - T1M] = make_float2(0.f, 0.f);
+    }
+    __syncthreads();
     for (int t = threadIdx.x; t < np * E; t += blockDim.x) {
-        const int p = t / E, e = t % E;
+        const int p = t / E, e = t - p * E;
         const int64_t pi = cs + p;
-        const double u0 = u_sorted[3 * pi], u1 = u_sorted[3 * pi + 1], u2 = u_sorted[3 * pi + 2];
-        const int c0 = cell_clamped(u0, g.cmax0), c1 = cell_clamped(u1, g.cmax1);
-        const int c2 = min(max((int)floor(u2), 0), g.N[2] - 1);
-        if (e < Q2MAX + T1M + 32) {
-            double x;
-            float2 *dst;
-            bool ok;
-            int d;
-            if (e < Q2MAX) {
-                ok = e < q2; x = u0 - c0 + (double)(q - 1 - e); d = 0; dst = &sm.w0[p][e];
-            } else if (e < Q2MAX + T1M) {
-                const int tb = e - Q2MAX;
-                const int rel = tb - (c1 - sb1 * C1);
-                ok = rel >= 0 && rel < q2 && tb < T1; x = u1 - c1 + (double)(q - 1 - rel); d = 1;
-                dst = &sm.w1[p][tb];
-            } else {
-                const int L = e - Q2MAX - T1M;
-                const int rel = cbase + L - (c2 - q + 1);
-                ok = rel >= 0 && rel < q2; x = u2 - c2 + (double)(q - 1 - rel); d = 2;
-                dst = &sm.w2[p][L];
-            }
-            float h, l;
-            df_split(ok ? window_tab<0>(g, d, x) : 0.0, h, l);
-            *dst = make_float2(h, l);
+        if (e < 3 * Q2MAX) {
+            const int d = e / Q2MAX, j = e - d * Q2MAX;              // axis, tap
+            if (j >= q2) continue;
+            const double u = u_sorted[3 * pi + d];
+            const int c = d == 0 ? cell_clamped(u, g.cmax0) : (d == 1 ? cell_clamped(u, g.cmax1) : min(max((int)floor(u), 0), g.N[d] - 1));
+            const dfl x = df_split_bits(u - c) + dfl((float)(q - 1 - j));   // u - c exact; the tap's offset
+            const dfl w = window_tab_df<0>(g, d, x);
+            const float2 v = make_float2(w.h, w.l);
+            if (d == 0) sm.w0[p][j] = v;
+            else if (d == 1) sm.w1[p][c - sb1 * C1 + j] = v;
+            else sm.w2[p][c - q + 1 + j - cbase] = v;
         } else {
             const double2 y = vals[perm[pi]];
-            float4 v;
-            df_split(y.x * vscale, v.x, v.z);
-            df_split(y.y * vscale, v.y, v.w);
-            sm.y[p] = v;
-            sm.ta0[p] = c0 - sb0 * C0;
+            const dfl yx = df_split_bits(y.x, vexp), yy = df_split_bits(y.y, vexp);
+            sm.y[p] = make_float4(yx.h, yy.h, yx.l, yy.l);
+            sm.ta0[p] = cell_clamped(u_sorted[3 * pi], g.cmax0) - sb0 * C0;
         }
     }
     __syncthreads();
@@ -647,7 +639,8 @@ __global__ void __launch_bounds__(32 * (C0 + Q2MAX - 1)) k_spread_slab64x(NGeom 
             const int r1 = row_checked(tb_org + tb, g.first[1], g.rows[1], g.N[1]);
             // cells no point reached: skipped before any FP64 conversion
             if (r1 < 0 || (acc[r].x == 0.f && acc[r].y == 0.f && acc[r].z == 0.f && acc[r].w == 0.f)) continue;
-            const double vx = df_value(acc[r].x, acc[r].y) * unscale, vy = df_value(acc[r].z, acc[r].w) * unscale;
+            const double vx = df_to_double_scaled(dfl(acc[r].x, acc[r].y), vexp);
+            const double vy = df_to_double_scaled(dfl(acc[r].z, acc[r].w), vexp);
             if (vx != 0.0 || vy != 0.0) {
                 atomicAdd(&colp[r1 * s1].x, vx);
                 atomicAdd(&colp[r1 * s1].y, vy);

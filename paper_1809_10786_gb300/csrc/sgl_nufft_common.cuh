@@ -2,6 +2,7 @@
 // interpolation / spreading kernels (SIMT in sgl_nufft.cu, tensor-core in sgl_nufft_tc.cu).
 #pragma once
 
+#include "sgl_dfl.cuh"
 #include "sgl_internal.cuh"
 
 namespace sgl {
@@ -56,7 +57,9 @@ struct NGeom {
     double par[3], norm[3];
     float parf[3], normf[3];   // the same in binary32 (read from the parameter bank by the FP32 kernels)
     const double *wtab;        // tabulated windows (FP64 plans; see kWinNI)
+    const float2 *wtab_df;     // the same coefficients as double-float pairs (h, l)
     double wh, winv;           // piece width q / kWinNI of the table, and its reciprocal
+    float whf, winvf;          // the same in binary32 (exact: q / kWinNI is a short binary fraction)
     double tpn[3], ntp[3];     // 2 pi / N_d and N_d / (2 pi)
     // bins (see BinGeom): azimuthal chunk, columns per super-bin, super-bins per axis
     int S2, C0, C1, nsb0, nsb1, nsb2, cmax0, cmax1;
@@ -75,6 +78,30 @@ __device__ __forceinline__ double window_tab(const NGeom &g, int d, double x) {
 #pragma unroll
     for (int k = kWinDeg - 1; k >= 0; --k) r = fma(r, t, __ldg(c + k));
     return (D == 1 && x < 0.0) ? -r : r;
+}
+
+// window_tab for a double-float argument, from the double-float copy of the table, in
+// double-float arithmetic on the FP32 pipe: |t| <= q / (2 kWinNI), so the terms of degree >= 8
+// are below 1e-9 of psi's peak and take binary32 Horner steps; the others take double-float ones
+template <int D>
+__device__ __forceinline__ dfl window_tab_df(const NGeom &g, int d, dfl x) {
+    const bool neg = x.h < 0.f;
+    const dfl ax = neg ? -x : x;
+    const float qf = (float)g.q;
+    if (ax.h > qf || (ax.h == qf && ax.l > 0.f)) return dfl(0.f, 0.f);
+    const int i = min((int)(ax.h * g.winvf), kWinNI - 1);
+    const dfl t = ax - dfl(((float)i + 0.5f) * g.whf);         // the midpoint is exact in binary32
+    const float2 *c = g.wtab_df + ((d * 2 + D) * kWinNI + i) * (kWinDeg + 1);
+    float rf = __ldg(c + kWinDeg).x;
+#pragma unroll
+    for (int k = kWinDeg - 1; k >= 8; --k) rf = fmaf(rf, t.h, __ldg(c + k).x);
+    dfl r(rf, 0.f);
+#pragma unroll
+    for (int k = 7; k >= 0; --k) {
+        const float2 ck = __ldg(c + k);
+        r = r * t + dfl(ck.x, ck.y);
+    }
+    return (D == 1 && neg) ? -r : r;
 }
 
 __device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
@@ -135,8 +162,11 @@ inline NGeom make_geom(const sgl_plan *p) {
     }
     g.q = p->q;
     g.wtab = p->b.wtab;
+    g.wtab_df = p->b.wtab_df;
     g.wh = (double)p->q / kWinNI;
     g.winv = kWinNI / (double)p->q;
+    g.whf = (float)g.wh;
+    g.winvf = (float)g.winv;
     g.S2 = p->bins.S2;
     g.C0 = p->bins.C0;
     g.C1 = p->bins.C1;
