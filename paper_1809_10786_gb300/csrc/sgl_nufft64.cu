@@ -51,6 +51,15 @@ __device__ __forceinline__ void df_mul(float &ph, float &pl, float wh, float wl,
 
 __device__ __forceinline__ double df_value(float h, float l) { return (double)h + (double)l; }
 
+// a running pair (ah, al) of df_fma as a normalized double-float number (|ah| >= |al| holds for the
+// sums here; a zero ah gives al itself)
+__device__ __forceinline__ dfl df_norm(float ah, float al) { return fast_two_sum(ah, al); }
+__device__ __forceinline__ dfl shfl_xor_df(dfl v, int o) {
+    return dfl(__shfl_xor_sync(0xffffffffu, v.h, o), __shfl_xor_sync(0xffffffffu, v.l, o));
+}
+// the double-float window argument u - (c - q + 1 + j) = (u - c) + (q - 1 - j) (u - c exact in binary64)
+__device__ __forceinline__ dfl tap_arg(double u, int c, int q, int j) { return df_split_bits(u - c) + dfl((float)(q - 1 - j)); }
+
 // Double-float has the exponent range of binary32, and the SGL basis functions are polynomials
 // that grow like r^(2B) (they are orthonormal under the weight e^{-|x|^2}), so grids and values
 // of 1e40 and more are ordinary at moderate B.  Every double-float pass therefore works on
@@ -393,10 +402,9 @@ template <int WIN, int G>
 __global__ void __launch_bounds__(256, 4) k_interp64x(NGeom g, int64_t M, const double *__restrict__ u_sorted,
                                                    const int *__restrict__ perm, const float4 *__restrict__ grid,
                                                    const unsigned long long *__restrict__ maxbits, double2 *__restrict__ vals) {
-    const double unscale = ldexp(1.0, df_exponent(maxbits));
+    const int vexp = df_exponent(maxbits);
     const int lane = threadIdx.x & 31, gl = lane & (G - 1);
     const int q = g.q, q2 = 2 * q;
-    const double qd = (double)q;
     const int64_t s1 = g.N[2], s0 = (int64_t)g.rows[1] * g.N[2];
     constexpr int PPW = 32 / G;
     const int64_t warp0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) / 32;
@@ -406,13 +414,14 @@ __global__ void __launch_bounds__(256, 4) k_interp64x(NGeom g, int64_t M, const 
         const bool live = i < M;
         const int64_t ii = live ? i : M - 1;
         const double u0 = u_sorted[3 * ii], u1 = u_sorted[3 * ii + 1], u2 = u_sorted[3 * ii + 2];
-        const int a0 = cell_clamped(u0, g.cmax0) - q + 1, a1 = cell_clamped(u1, g.cmax1) - q + 1;
-        const int a2 = min(max((int)floor(u2), 0), g.N[2] - 1) - q + 1;
+        const int c0 = cell_clamped(u0, g.cmax0), c1 = cell_clamped(u1, g.cmax1), c2 = min(max((int)floor(u2), 0), g.N[2] - 1);
+        const int a0 = c0 - q + 1, a1 = c1 - q + 1, a2 = c2 - q + 1;
         const bool tap = gl < q2;
-        float w0h_own, w0l_own, w1h_own, w1l_own;
-        df_split(tap ? window_tab<0>(g, 0, u0 - (a0 + gl)) : 0.0, w0h_own, w0l_own);
-        df_split(tap ? window_tab<0>(g, 1, u1 - (a1 + gl)) : 0.0, w1h_own, w1l_own);
-        const double w2 = tap ? window_tab<0>(g, 2, u2 - (a2 + gl)) : 0.0;
+        // this lane's tap on each axis: double-float windows (FP32 pipe)
+        const dfl w0 = tap ? window_tab_df<0>(g, 0, tap_arg(u0, c0, q, gl)) : dfl(0.f, 0.f);
+        const dfl w1 = tap ? window_tab_df<0>(g, 1, tap_arg(u1, c1, q, gl)) : dfl(0.f, 0.f);
+        const dfl w2 = tap ? window_tab_df<0>(g, 2, tap_arg(u2, c2, q, gl)) : dfl(0.f, 0.f);
+        const float w0h_own = w0.h, w0l_own = w0.l, w1h_own = w1.h, w1l_own = w1.l;
         const int col = tap ? wrap_index(a2 + gl, g.N[2]) : 0;
 
         float axh = 0.f, axl = 0.f, ayh = 0.f, ayl = 0.f;
@@ -432,27 +441,26 @@ __global__ void __launch_bounds__(256, 4) k_interp64x(NGeom g, int64_t M, const 
             df_fma(axh, axl, w0h, w0l, rxh, rxl);
             df_fma(ayh, ayl, w0h, w0l, ryh, ryl);
         }
-        double ax = df_value(axh, axl) * w2, ay = df_value(ayh, ayl) * w2;
+        dfl ax = df_norm(axh, axl) * w2, ay = df_norm(ayh, ayl) * w2;
 #pragma unroll
         for (int o = G / 2; o > 0; o >>= 1) {
-            ax += __shfl_xor_sync(0xffffffffu, ax, o);
-            ay += __shfl_xor_sync(0xffffffffu, ay, o);
+            ax = ax + shfl_xor_df(ax, o);
+            ay = ay + shfl_xor_df(ay, o);
         }
-        if (live && gl == 0) vals[perm[i]] = make_double2(ax * unscale, ay * unscale);
+        if (live && gl == 0) vals[perm[i]] = make_double2(df_to_double_scaled(ax, vexp), df_to_double_scaled(ay, vexp));
     }
 }
 
 // ---- double-float window-derivative interpolation (values, ds/du0, ds/du1, ds/du2), layout of k_grad64
 template <int WIN, int G>
-__global__ void __launch_bounds__(256, 4) k_grad64x(NGeom g, int64_t M, const double *__restrict__ u_sorted,
+__global__ void __launch_bounds__(256, G == 8 ? 3 : 4) k_grad64x(NGeom g, int64_t M, const double *__restrict__ u_sorted,
                                                  const int *__restrict__ perm, const unsigned long long *__restrict__ r2max,
                                                  const float4 *__restrict__ grid, const unsigned long long *__restrict__ maxbits,
                                                  const double2 *__restrict__ gout, double *__restrict__ gxyz,
                                                  double2 *__restrict__ vals) {
-    const double unscale = ldexp(1.0, df_exponent(maxbits));
+    const int vexp = df_exponent(maxbits);
     const int lane = threadIdx.x & 31, gl = lane & (G - 1);
     const int q = g.q, q2 = 2 * q;
-    const double qd = (double)q;
     const int64_t s1 = g.N[2], s0 = (int64_t)g.rows[1] * g.N[2];
     double rho = sqrt(__longlong_as_double((long long)*r2max)) * (1.0 + 0x1p-20);
     if (!(rho > 0.0)) rho = 1.0;
@@ -464,17 +472,22 @@ __global__ void __launch_bounds__(256, 4) k_grad64x(NGeom g, int64_t M, const do
         const bool live = i < M;
         const int64_t ii = live ? i : M - 1;
         const double u0 = u_sorted[3 * ii], u1 = u_sorted[3 * ii + 1], u2 = u_sorted[3 * ii + 2];
-        const int a0 = cell_clamped(u0, g.cmax0) - q + 1, a1 = cell_clamped(u1, g.cmax1) - q + 1;
-        const int a2 = min(max((int)floor(u2), 0), g.N[2] - 1) - q + 1;
+        const int c0 = cell_clamped(u0, g.cmax0), c1 = cell_clamped(u1, g.cmax1), c2 = min(max((int)floor(u2), 0), g.N[2] - 1);
+        const int a0 = c0 - q + 1, a1 = c1 - q + 1, a2 = c2 - q + 1;
         const bool tap = gl < q2;
-        const double x0 = u0 - (a0 + gl), x1 = u1 - (a1 + gl), x2 = u2 - (a2 + gl);
-        float w0h_own, w0l_own, d0h_own, d0l_own, w1h_own, w1l_own, d1h_own, d1l_own;
-        df_split(tap ? window_tab<0>(g, 0, x0) : 0.0, w0h_own, w0l_own);
-        df_split(tap ? window_tab<1>(g, 0, x0) : 0.0, d0h_own, d0l_own);
-        df_split(tap ? window_tab<0>(g, 1, x1) : 0.0, w1h_own, w1l_own);
-        df_split(tap ? window_tab<1>(g, 1, x1) : 0.0, d1h_own, d1l_own);
-        const double w2 = tap ? window_tab<0>(g, 2, x2) : 0.0;
-        const double d2 = tap ? window_tab<1>(g, 2, x2) : 0.0;
+        // this lane's tap on each axis: double-float psi and psi' (FP32 pipe)
+        // (one axis at a time: the evaluations would otherwise interleave and spill)
+        dfl w0(0.f, 0.f), d0 = w0, w1 = w0, d1 = w0, w2 = w0, d2 = w0;
+        if (tap) {
+#pragma unroll 1
+            for (int k = 0; k < 3; ++k) {
+                const dfl x = tap_arg(k == 0 ? u0 : (k == 1 ? u1 : u2), k == 0 ? c0 : (k == 1 ? c1 : c2), q, gl);
+                const dfl w = window_tab_df<0>(g, k, x), d = window_tab_df<1>(g, k, x);
+                if (k == 0) { w0 = w; d0 = d; } else if (k == 1) { w1 = w; d1 = d; } else { w2 = w; d2 = d; }
+            }
+        }
+        const float w0h_own = w0.h, w0l_own = w0.l, d0h_own = d0.h, d0l_own = d0.l;
+        const float w1h_own = w1.h, w1l_own = w1.l, d1h_own = d1.h, d1l_own = d1.l;
         const int col = tap ? wrap_index(a2 + gl, g.N[2]) : 0;
         float fxh = 0.f, fxl = 0.f, fyh = 0.f, fyl = 0.f;     // sum psi0 psi1 grid
         float axh = 0.f, axl = 0.f, ayh = 0.f, ayl = 0.f;     // sum psi0' psi1 grid
@@ -503,30 +516,33 @@ __global__ void __launch_bounds__(256, 4) k_grad64x(NGeom g, int64_t M, const do
             df_fma(bxh, bxl, w0h, w0l, sxh, sxl);
             df_fma(byh, byl, w0h, w0l, syh, syl);
         }
-        const double fx = df_value(fxh, fxl) * unscale, fy = df_value(fyh, fyl) * unscale;
-        double f2x = d2 * fx, f2y = d2 * fy;
-        double sx = w2 * fx, sy = w2 * fy;             // the value s itself (forward with gradient)
-        double ax = df_value(axh, axl) * unscale * w2, ay = df_value(ayh, ayl) * unscale * w2;
-        double bx = df_value(bxh, bxl) * unscale * w2, by = df_value(byh, byl) * unscale * w2;
+        // the azimuthal weights and the reduction over the group in double-float, on 2^-vexp data
+        const dfl fx = df_norm(fxh, fxl), fy = df_norm(fyh, fyl);
+        dfl f2x = d2 * fx, f2y = d2 * fy;
+        dfl sx = w2 * fx, sy = w2 * fy;                // the value s itself (forward with gradient)
+        dfl ax = df_norm(axh, axl) * w2, ay = df_norm(ayh, ayl) * w2;
+        dfl bx = df_norm(bxh, bxl) * w2, by = df_norm(byh, byl) * w2;
 #pragma unroll
         for (int o = G / 2; o > 0; o >>= 1) {
-            ax += __shfl_xor_sync(0xffffffffu, ax, o);
-            ay += __shfl_xor_sync(0xffffffffu, ay, o);
-            bx += __shfl_xor_sync(0xffffffffu, bx, o);
-            by += __shfl_xor_sync(0xffffffffu, by, o);
-            f2x += __shfl_xor_sync(0xffffffffu, f2x, o);
-            f2y += __shfl_xor_sync(0xffffffffu, f2y, o);
+            ax = ax + shfl_xor_df(ax, o);
+            ay = ay + shfl_xor_df(ay, o);
+            bx = bx + shfl_xor_df(bx, o);
+            by = by + shfl_xor_df(by, o);
+            f2x = f2x + shfl_xor_df(f2x, o);
+            f2y = f2y + shfl_xor_df(f2y, o);
             if (vals) {
-                sx += __shfl_xor_sync(0xffffffffu, sx, o);
-                sy += __shfl_xor_sync(0xffffffffu, sy, o);
+                sx = sx + shfl_xor_df(sx, o);
+                sy = sy + shfl_xor_df(sy, o);
             }
         }
         {
             const bool w = live && gl == 0;
             const int dst = w ? perm[i] : 0;
-            point_gradient_lanes<G>(g, gl, rho, u0, u1, u2, ax, ay, bx, by, f2x, f2y, w, w ? gout[dst] : make_double2(0.0, 0.0),
+            point_gradient_lanes<G>(g, gl, rho, u0, u1, u2, df_to_double_scaled(ax, vexp), df_to_double_scaled(ay, vexp),
+                                    df_to_double_scaled(bx, vexp), df_to_double_scaled(by, vexp), df_to_double_scaled(f2x, vexp),
+                                    df_to_double_scaled(f2y, vexp), w, w ? gout[dst] : make_double2(0.0, 0.0),
                                     gxyz + 3 * (int64_t)dst);
-            if (w && vals) vals[dst] = make_double2(sx, sy);
+            if (w && vals) vals[dst] = make_double2(df_to_double_scaled(sx, vexp), df_to_double_scaled(sy, vexp));
         }
     }
 }
