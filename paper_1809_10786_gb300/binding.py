@@ -17,6 +17,7 @@ PREC_FP64, PREC_FP32_MIXED = 0, 1
 WIN_KB, WIN_GAUSS = 0, 1
 FLAG_HOST_IO, FLAG_PROFILE, FLAG_SIMT, FLAG_TC, FLAG_NATIVE_FP64, FLAG_OVERLAP_POINTS = 1, 2, 4, 8, 16, 32
 FLAG_GENERIC_FFT = 64
+FLAG_FULL_GRID = 128
 NUM_STAGES = 12
 
 _STATUS = {0: "SGL_OK", 1: "SGL_ERR_ARG", 2: "SGL_ERR_ALLOC", 3: "SGL_ERR_CUDA", 4: "SGL_ERR_NONFINITE",
@@ -166,7 +167,7 @@ class Plan:
 
     def __init__(self, B, M_max, precision=PREC_FP64, window=WIN_KB, q=8, sigma=2.0, host_io=False, profile=False,
                  device=None, simt=False, tensor_cores=False, native_fp64=False, overlap_points=False,
-                 generic_fft=False):
+                 generic_fft=False, full_grid=False):
         if not torch.cuda.is_available():
             raise SGLError(3, "no CUDA device: the NFSGLFT runs only on the GPU")
         self.lib = load_library()
@@ -180,7 +181,8 @@ class Plan:
                                           (FLAG_HOST_IO if host_io else 0) | (FLAG_PROFILE if profile else 0) | (FLAG_SIMT if simt else 0)
                                           | (FLAG_TC if tensor_cores else 0) | (FLAG_NATIVE_FP64 if native_fp64 else 0)
                                           | (FLAG_OVERLAP_POINTS if overlap_points else 0)
-                                          | (FLAG_GENERIC_FFT if generic_fft else 0),
+                                          | (FLAG_GENERIC_FFT if generic_fft else 0)
+                                          | (FLAG_FULL_GRID if full_grid else 0),
                                           _stream_handle(self.device))
         _check(st)
         self.Nc = num_coeffs(self.B)

@@ -472,7 +472,7 @@ sgl_status plan_create_impl(sgl_plan **out, int B, int64_t M_max, int precision,
     if (q < 1 || q > kMaxQ) return set_error(SGL_ERR_ARG, "q must be in [1, 16]");
     if (!(sigma >= 1.5 && sigma <= 4.0)) return set_error(SGL_ERR_ARG, "sigma must be in [1.5, 4]");
     if (flags & ~(SGL_FLAG_HOST_IO | SGL_FLAG_PROFILE | SGL_FLAG_SIMT | SGL_FLAG_TC | SGL_FLAG_NATIVE_FP64 | SGL_FLAG_OVERLAP_POINTS |
-                  SGL_FLAG_GENERIC_FFT))
+                  SGL_FLAG_GENERIC_FFT | SGL_FLAG_FULL_GRID))
         return set_error(SGL_ERR_ARG, "unknown flag bits");
     if ((flags & SGL_FLAG_SIMT) && (flags & SGL_FLAG_TC)) return set_error(SGL_ERR_ARG, "SGL_FLAG_SIMT and SGL_FLAG_TC exclude each other");
 
@@ -511,6 +511,16 @@ sgl_status plan_create_impl(sgl_plan **out, int B, int64_t M_max, int precision,
         factor(a.N, a.rad, a.nrad);
     }
     {
+        // symmetry-reduced FFT passes: axes 0 and 1 windowed, every length one of the register
+        // kernels' powers of two
+        bool ok = !(flags & (SGL_FLAG_FULL_GRID | SGL_FLAG_GENERIC_FFT)) && p->ax[0].windowed && p->ax[1].windowed;
+        for (int d = 0; d < 3; ++d) {
+            const int n = p->ax[d].N;
+            ok = ok && n >= 64 && n <= 1024 && (n & (n - 1)) == 0;
+        }
+        p->half_grid = ok;
+    }
+    {
         BinGeom &g = p->bins;
         // FP32 plans with q <= 8: a multiple of 4, so that the tensor-core kernels' TMA boxes start
         // 16-byte aligned (lanes from sb2 * S2 - tc_halo(q)); otherwise as wide as one warp allows
@@ -538,7 +548,9 @@ sgl_status plan_create_impl(sgl_plan **out, int B, int64_t M_max, int precision,
     const int64_t W = 2 * K1 + 1;
     const size_t csz = precision == SGL_FP32_MIXED ? sizeof(float2) : sizeof(double2);
     const Axis &A0 = p->ax[0], &A1 = p->ax[1], &A2 = p->ax[2];
-    const size_t nA = std::max<size_t>((size_t)A0.rows * W * W, (size_t)A0.rows * A1.rows * A2.N);
+    // bufA also holds the symmetry-reduced adjoint's eta'[2K0+1][K1+1][W] (binary64)
+    const size_t nA = std::max<size_t>(std::max<size_t>((size_t)A0.rows * W * W, (size_t)A0.rows * A1.rows * A2.N),
+                                       ((size_t)(2 * K0 + 1) * (K1 + 1) * W * sizeof(double2) + csz - 1) / csz);
     const size_t bytesB = std::max<size_t>((size_t)A0.rows * A1.rows * W * csz, (size_t)(2 * K0 + 1) * W * W * sizeof(double2));
     cudaError_t e = cudaSuccess;
 #define ALLOC(ptr, n) do { if ((e = A.get(&(ptr), (n))) != cudaSuccess) return fail(SGL_ERR_ALLOC, std::string("cudaMalloc: ") + cudaGetErrorString(e)); } while (0)
@@ -710,7 +722,8 @@ sgl_status plan_work_sizes(int B, int precision, int q, double sigma, size_t *by
     }
     const int64_t W = 2 * (B - 1) + 1;
     const size_t csz = precision == SGL_FP32_MIXED ? sizeof(float2) : sizeof(double2);
-    *bytesA = std::max<size_t>((size_t)rows[0] * W * W, (size_t)rows[0] * rows[1] * N[2]) * csz;
+    *bytesA = std::max<size_t>(std::max<size_t>((size_t)rows[0] * W * W, (size_t)rows[0] * rows[1] * N[2]) * csz,
+                               (size_t)(2 * (2 * B - 2) + 1) * B * W * sizeof(double2));
     *bytesB = std::max<size_t>((size_t)rows[0] * rows[1] * W * csz, (size_t)(2 * (2 * B - 2) + 1) * W * W * sizeof(double2));
     return SGL_OK;
 }
@@ -881,7 +894,8 @@ sgl_status sgl_adjoint(sgl_plan *plan, const double *vals_dev, double *coef_dev)
     if (e != cudaSuccess) return launch_status(e, "adjoint FFT");
     {
         StageScope sc(plan, ST_POLAR_ADJ);
-        e = launch_polar_adjoint(plan, (const double2 *)plan->b.bufB);
+        // the adjoint FFT's output: eta' in bufB, or (symmetry-reduced) its kappa1 >= 0 half in bufA
+        e = launch_polar_adjoint(plan, (const double2 *)(plan->half_grid ? plan->b.bufA : plan->b.bufB));
     }
     if (e != cudaSuccess) return launch_status(e, "adjoint polar conversion");
     StageScope sc(plan, ST_RADIAL_ADJ);

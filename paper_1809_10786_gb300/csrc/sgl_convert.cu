@@ -141,8 +141,10 @@ __global__ void k_trig_export(int K0, int K1, const double2 *__restrict__ zeta, 
     eta[idx] = v;
 }
 
-// adjoint of the mirroring: zeta'[kappa0][kappa1][m] = sum over the preimages of eta'
-__global__ void k_fold(int K0, int K1, const double2 *__restrict__ etap, double2 *__restrict__ zetap) {
+// adjoint of the mirroring: zeta'[kappa0][kappa1][m] = sum over the preimages of eta'.  With
+// `half`, eta' holds kappa1 >= 0 only ([2K0+1][K1+1][2K1+1]: the symmetry-reduced adjoint FFT has
+// folded kappa1 already) and only kappa0 is folded here.
+__global__ void k_fold(int K0, int K1, int half, const double2 *__restrict__ etap, double2 *__restrict__ zetap) {
     const int W = 2 * K1 + 1;
     const int64_t total = (int64_t)(K0 + 1) * (K1 + 1) * W;
     const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -155,10 +157,11 @@ __global__ void k_fold(int K0, int K1, const double2 *__restrict__ etap, double2
     double re = 0.0, im = 0.0;
     for (int s0 = 0; s0 < (k0 ? 2 : 1); ++s0) {
         const int kk0 = s0 ? -k0 : k0;
-        for (int s1 = 0; s1 < (k1 ? 2 : 1); ++s1) {
+        for (int s1 = 0; s1 < (k1 && !half ? 2 : 1); ++s1) {
             const int kk1 = s1 ? -k1 : k1;
             const double f = s1 ? par : 1.0;
-            const double2 v = etap[((int64_t)(kk0 + K0) * W + (kk1 + K1)) * W + mi];
+            const int64_t at = half ? ((int64_t)(kk0 + K0) * (K1 + 1) + k1) * W + mi : ((int64_t)(kk0 + K0) * W + (kk1 + K1)) * W + mi;
+            const double2 v = etap[at];
             re = fma(f, v.x, re);
             im = fma(f, v.y, im);
         }
@@ -256,7 +259,8 @@ cudaError_t launch_trig_export(sgl_plan *p, double2 *eta) {
 cudaError_t launch_polar_adjoint(sgl_plan *p, const double2 *eta_full) {
     const int B = p->B, K0 = p->K0, K1 = p->K1;
     const int64_t W = 2 * K1 + 1;
-    k_fold<<<blocks_for((int64_t)(K0 + 1) * (K1 + 1) * W, kT), kT, 0, p->stream>>>(K0, K1, eta_full, p->b.zeta);
+    k_fold<<<blocks_for((int64_t)(K0 + 1) * (K1 + 1) * W, kT), kT, 0, p->stream>>>(K0, K1, p->half_grid ? 1 : 0, eta_full,
+                                                                                    p->b.zeta);
     k_polar_adjoint<<<blocks_for(W * (K0 + 1) * B, kT), kT, 0, p->stream>>>(B, K0, K1, p->b.P, p->b.zeta, p->b.beta);
     p->launches += 2;
     return cudaGetLastError();

@@ -149,6 +149,7 @@ enum { LOAD_STRIDED = 0, LOAD_ZETA = 1 };
 struct ZetaSrc {
     const double2 *zeta;   // [K0+1][K1+1][2K1+1]
     int K0, K1;
+    int half;              // lines (kappa1 >= 0, m) only: inner = kappa1 (2K1+1) + m + K1
 };
 
 template <typename C> __device__ __forceinline__ double2 to_d2(C v) { return make_double2((double)v.x, (double)v.y); }
@@ -363,14 +364,17 @@ __device__ __forceinline__ C2<T> reg_load(const FftPass &ps, const InC *__restri
     if constexpr (MODE == LOAD_ZETA) {
         const int W = 2 * zs.K1 + 1;
         const int mi = (int)(inner % W);
-        const int k1 = (int)(inner / W) - zs.K1;
+        const int k1 = (int)(inner / W) - (zs.half ? 0 : zs.K1);
         const int k0 = e - zs.K0;
         double2 d = zs.zeta[((int64_t)abs(k0) * (zs.K1 + 1) + abs(k1)) * W + mi];
         if (k1 < 0 && ((mi - zs.K1) & 1)) { d.x = -d.x; d.y = -d.y; }
         if constexpr (std::is_same<T, dfl>::value) { v.x = df_split_bits(d.x, E); v.y = df_split_bits(d.y, E); }
         else { v.x = T(d.x); v.y = T(d.y); }
     } else {
-        const InC x = in[outer * ps.in_so + inner * ps.in_si + (int64_t)e * ps.in_se];
+        // element e at |e - mir_c| (plain lines: mir_c = 0), with the polar parity below mir_c
+        const int k = e - ps.mir_c;
+        InC x = in[outer * ps.in_so + inner * ps.in_si + (int64_t)abs(k) * ps.in_se];
+        if (k < 0 && ((inner - ps.mir_c) & 1)) { x.x = -x.x; x.y = -x.y; }
         if constexpr (std::is_same<T, dfl>::value && sizeof(x.x) == 8) { v.x = df_split_bits(x.x, E); v.y = df_split_bits(x.y, E); }
         else { v.x = T(x.x); v.y = T(x.y); }
     }
@@ -379,14 +383,14 @@ __device__ __forceinline__ C2<T> reg_load(const FftPass &ps, const InC *__restri
             dfl f(1.f, 0.f);
             if (ps.elem_scale_df) f = dfl(ps.elem_scale_df[e].x, ps.elem_scale_df[e].y);
             if (ps.line_scale_df) {
-                const float2 l = ps.line_scale_df[outer * ps.nb_inner + inner];
+                const float2 l = ps.line_scale_df[outer * ps.nb_inner + inner + ps.ls_off];
                 f = f * dfl(l.x, l.y);
             }
             v.x = v.x * f; v.y = v.y * f;
         } else {
             double f = 1.0;
             if (ps.elem_scale) f *= ps.elem_scale[e];
-            if (ps.line_scale) f *= ps.line_scale[outer * ps.nb_inner + inner];
+            if (ps.line_scale) f *= ps.line_scale[outer * ps.nb_inner + inner + ps.ls_off];
             v.x = T(widen(v.x) * f); v.y = T(widen(v.y) * f);
         }
     }
@@ -404,14 +408,14 @@ __device__ __forceinline__ void reg_store(const FftPass &ps, OutC *__restrict__ 
             dfl f(1.f, 0.f);
             if (ps.elem_scale_df) f = dfl(ps.elem_scale_df[e].x, ps.elem_scale_df[e].y);
             if (ps.line_scale_df) {
-                const float2 l = ps.line_scale_df[outer * ps.nb_inner + inner];
+                const float2 l = ps.line_scale_df[outer * ps.nb_inner + inner + ps.ls_off];
                 f = f * dfl(l.x, l.y);
             }
             v.x = v.x * f; v.y = v.y * f;
         } else {
             double f = 1.0;
             if (ps.elem_scale) f *= ps.elem_scale[e];
-            if (ps.line_scale) f *= ps.line_scale[outer * ps.nb_inner + inner];
+            if (ps.line_scale) f *= ps.line_scale[outer * ps.nb_inner + inner + ps.ls_off];
             o.x = (S)(widen(v.x) * f);
             o.y = (S)(widen(v.y) * f);
             out[outer * ps.out_so + inner * ps.out_si + (int64_t)e * ps.out_se] = o;
@@ -510,7 +514,7 @@ __global__ void __launch_bounds__(256) k_fft_reg(FftPass ps, const InC *__restri
     if constexpr (std::is_same<OutC, float2>::value) {
         if (ps.planes) {                                           // split planes with a wrapped halo
             if (!valid) return;
-            float *row = ps.planes + inner * ps.pitch;
+            float *row = ps.planes + (outer * ps.plane_so + inner + ps.plane_off) * ps.pitch;
 #pragma unroll
             for (int i = 0; i < E / RL; ++i) {
 #pragma unroll
@@ -539,6 +543,133 @@ __global__ void __launch_bounds__(256) k_fft_reg(FftPass ps, const InC *__restri
             if (e < ps.L_out) reg_store<T, OutC>(ps, out, outer, inner, e, v[i * RL + k], scale_on_output, SE);
         }
     }
+}
+
+// ---------------------------------------------------------------- symmetry-reduced grid
+// eta is even in kappa0 and has the parity of m in kappa1 (Sect. 6), so the oversampled grid of the
+// NFFT is even in l0 and alpha(l0, -l1, l2) = alpha(l0, l1, l2 + N2/2).  Plans whose axes 0 and 1
+// are windowed and whose lengths all take the register kernels transform half of the lines: pass A
+// the radial lines kappa1 >= 0 (pass B reads kappa1 < 0 back through the parity), passes B and C the
+// grid lines (l0, l1) in [0, N0/2] x [0, N1/2].  The q halo rows on each side of the two windowed axes
+// are then copies of the rows they mirror: row -l (1 <= l <= q) and row N - l (N/2 - q <= l < N/2)
+// hold line l, shifted by N2/2 on axis 1.  The adjoint first adds every halo row onto the row it
+// mirrors, transforms the same half, folds kappa1 < 0 onto kappa1 >= 0 (parity) before pass A', and
+// folds kappa0 < 0 onto kappa0 >= 0 after it (sgl_convert.cu).
+struct HaloGeom {
+    int q, N0h, N1h, R1, N2;    // q, N0/2, N1/2, rows kept on axis 1, azimuthal length (a power of two)
+};
+
+// storage row (first row -q) -> the grid line l in [0, N/2] it holds, and whether it is a mirror
+__device__ __forceinline__ int halo_source(int r, int q, int Nh) {
+    const int l = r - q;
+    return l < 0 ? -l : (l > Nh ? 2 * Nh - l : l);
+}
+
+// the halo rows, enumerated: axis-0 halo rows (2q) x all rows of axis 1, then the rows of axis 0
+// inside [0, N0/2] x the axis-1 halo rows (2q)
+__device__ __forceinline__ void halo_row(int64_t idx, const HaloGeom &h, int &a, int &b) {
+    const int q2 = 2 * h.q;
+    if (idx < (int64_t)q2 * h.R1) {
+        const int ai = (int)(idx / h.R1);
+        b = (int)(idx - (int64_t)ai * h.R1);
+        a = ai < h.q ? ai : h.N0h + h.q + 1 + (ai - h.q);
+    } else {
+        const int64_t j = idx - (int64_t)q2 * h.R1;
+        a = h.q + (int)(j / q2);
+        const int bi = (int)(j % q2);
+        b = bi < h.q ? bi : h.N1h + h.q + 1 + (bi - h.q);
+    }
+}
+inline int64_t halo_rows(const HaloGeom &h) { return (int64_t)2 * h.q * h.R1 + (int64_t)(h.N0h + 1) * 2 * h.q; }
+
+// forward: every halo row (blockIdx.x) copied from the row it mirrors
+template <typename C>
+__global__ void __launch_bounds__(256) k_halo_mirror(HaloGeom h, C *__restrict__ grid) {
+    int a, b;
+    halo_row(blockIdx.x, h, a, b);
+    const int l0 = halo_source(a, h.q, h.N0h), l1 = halo_source(b, h.q, h.N1h);
+    const int sh = (b - h.q < 0 || b - h.q > h.N1h) ? h.N2 / 2 : 0;
+    const C *src = grid + ((int64_t)(l0 + h.q) * h.R1 + l1 + h.q) * h.N2;
+    C *dst = grid + ((int64_t)a * h.R1 + b) * h.N2;
+    for (int c = threadIdx.x; c < h.N2; c += blockDim.x) dst[c] = src[(c + sh) & (h.N2 - 1)];
+}
+
+// the same on the tensor-core planes (Re, Im; column k holds position (k - halo) mod N2)
+__global__ void __launch_bounds__(256) k_halo_mirror_planes(HaloGeom h, float *__restrict__ planes, int64_t plane_n, int pitch,
+                                                            int halo) {
+    int a, b;
+    halo_row(blockIdx.x, h, a, b);
+    const int l0 = halo_source(a, h.q, h.N0h), l1 = halo_source(b, h.q, h.N1h);
+    const int sh = (b - h.q < 0 || b - h.q > h.N1h) ? h.N2 / 2 : 0;
+    const float *src = planes + ((int64_t)(l0 + h.q) * h.R1 + l1 + h.q) * pitch;
+    float *dst = planes + ((int64_t)a * h.R1 + b) * pitch;
+    for (int k = threadIdx.x; k < pitch; k += blockDim.x) {
+        const int pos = (k - halo + sh + h.N2) & (h.N2 - 1);   // k - halo >= -halo > -N2
+        dst[k] = src[pos + halo];
+        dst[plane_n + k] = src[plane_n + pos + halo];
+    }
+}
+
+// adjoint of the mirrors: every halo row (blockIdx.x) added onto the row it mirrors.  Each row
+// with mirrors gathers them itself (one block per line (l0, l1) that has any), so no two blocks
+// write one row.
+__device__ __forceinline__ int halo_mirror_row(int l, int q, int Nh) {
+    if (l >= 1 && l <= q) return q - l;
+    if (l >= Nh - q && l < Nh) return 2 * Nh - l + q;
+    return -1;
+}
+template <typename C>
+__global__ void __launch_bounds__(256) k_halo_fold(HaloGeom h, C *__restrict__ grid) {
+    // lines with an axis-0 mirror (2q values of l0) x all l1, then the other l0 x the 2q l1 with a mirror
+    const int q2 = 2 * h.q, H1 = h.N1h + 1;
+    const int64_t idx = blockIdx.x;
+    int l0, l1;
+    if (idx < (int64_t)q2 * H1) {
+        const int li = (int)(idx / H1);
+        l1 = (int)(idx - (int64_t)li * H1);
+        l0 = li < h.q ? 1 + li : h.N0h - h.q + (li - h.q);
+    } else {
+        const int64_t j = idx - (int64_t)q2 * H1;
+        const int li = (int)(j / q2), bi = (int)(j % q2);
+        l0 = li == 0 ? 0 : (li <= h.N0h - q2 - 1 ? h.q + li : h.N0h);
+        l1 = bi < h.q ? 1 + bi : h.N1h - h.q + (bi - h.q);
+    }
+    const int m0 = halo_mirror_row(l0, h.q, h.N0h), m1 = halo_mirror_row(l1, h.q, h.N1h);
+    const int64_t r0 = l0 + h.q, r1 = l1 + h.q;
+    C *dst = grid + (r0 * h.R1 + r1) * h.N2;
+    const C *s0 = m0 >= 0 ? grid + ((int64_t)m0 * h.R1 + r1) * h.N2 : nullptr;
+    const C *s1 = m1 >= 0 ? grid + (r0 * h.R1 + m1) * h.N2 : nullptr;
+    const C *s01 = (m0 >= 0 && m1 >= 0) ? grid + ((int64_t)m0 * h.R1 + m1) * h.N2 : nullptr;
+    for (int c = threadIdx.x; c < h.N2; c += blockDim.x) {
+        const int cs = (c + h.N2 / 2) & (h.N2 - 1);
+        C v = dst[c];
+        if (s0) { const C w = s0[c]; v.x += w.x; v.y += w.y; }
+        if (s1) { const C w = s1[cs]; v.x += w.x; v.y += w.y; }
+        if (s01) { const C w = s01[cs]; v.x += w.x; v.y += w.y; }
+        dst[c] = v;
+    }
+}
+inline int64_t halo_fold_rows(const HaloGeom &h) { return (int64_t)2 * h.q * (h.N1h + 1) + (int64_t)(h.N0h + 1 - 2 * h.q) * 2 * h.q; }
+
+// adjoint of the polar parity: Yh[l0][k][m] = Y[l0][K1 + k][m] + (-1)^m Y[l0][K1 - k][m] (k > 0)
+template <typename C>
+__global__ void __launch_bounds__(256) k_fold_kappa1(int64_t H0, int K1, const C *__restrict__ Y, C *__restrict__ Yh) {
+    const int W = 2 * K1 + 1;
+    const int64_t total = H0 * (K1 + 1) * W;
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= total) return;
+    const int mi = (int)(i % W);
+    const int k = (int)((i / W) % (K1 + 1));
+    const int64_t l0 = i / ((int64_t)W * (K1 + 1));
+    const C *row = Y + l0 * W * W;
+    C v = row[(K1 + k) * W + mi];
+    if (k > 0) {
+        const C w = row[(K1 - k) * W + mi];
+        const bool neg = (mi - K1) & 1;
+        v.x += neg ? -w.x : w.x;
+        v.y += neg ? -w.y : w.y;
+    }
+    Yh[i] = v;
 }
 
 // lines per tile: a power of two in [8, 64] with about 4096 elements per tile
@@ -632,43 +763,67 @@ cudaError_t forward_passes(sgl_plan *p) {
     if (scaled &&
         (e = launch_max_abs(p, (const double *)p->b.zeta, 2 * (int64_t)(p->K0 + 1) * (p->K1 + 1) * W, p->b.df_max + 2)) != cudaSuccess)
         return e;
+    // symmetry-reduced grid: half of the lines on axes 0 and 1, then the halo rows by mirroring
+    const bool half = p->half_grid;
+    const int H0 = A0.N / 2 + 1, H1 = A1.N / 2 + 1;
+    const int64_t K1p = p->K1 + 1, k1_lines = half ? K1p : W;   // kappa1 lines of pass A
+    const int64_t interior = ((int64_t)p->q * A1.rows + p->q) * A2.N;   // grid offset of line (0, 0)
+    zs.half = half ? 1 : 0;
     // pass A (axis 0): zeta (mirrored, deconvolved) -> X0[l0 row][k1][m]
     FftPass a = base_pass(A0, +1, f32);
     a.scale_bits = sb;
     a.tw = twiddles<RA>(A0);
     a.L_in = 2 * p->K0 + 1; a.in_first = -p->K0;
-    a.L_out = A0.rows; a.out_first = A0.first;
-    a.nb_outer = 1; a.nb_inner = W * W;
-    a.out_so = 0; a.out_si = 1; a.out_se = W * W;
+    a.L_out = half ? H0 : A0.rows; a.out_first = half ? 0 : A0.first;
+    a.nb_outer = 1; a.nb_inner = k1_lines * W;
+    a.out_so = 0; a.out_si = 1; a.out_se = k1_lines * W;
     a.elem_scale = A0.deconv; a.line_scale = p->b.linescale;
     a.elem_scale_df = A0.deconv_df; a.line_scale_df = p->b.linescale_df;
+    a.ls_off = half ? p->K1 * W : 0;
     if ((e = run_pass<RA, double2, C2<T>, LOAD_ZETA>(p, a, nullptr, p->b.bufA, zs, 0)) != cudaSuccess) return e;
-    // pass B (axis 1): X0 -> X1[l0][l1 row][m]
+    // pass B (axis 1): X0 -> X1[l0][l1 row][m] (reduced: kappa1 < 0 read through the polar parity)
     FftPass b = base_pass(A1, +1, f32);
     b.tw = twiddles<AA>(A1);
     b.scale_bits = sb;
     b.L_in = (int)W; b.in_first = -p->K1;
-    b.L_out = A1.rows; b.out_first = A1.first;
-    b.nb_outer = A0.rows; b.nb_inner = W;
-    b.in_so = W * W; b.in_si = 1; b.in_se = W;
-    b.out_so = (int64_t)A1.rows * W; b.out_si = 1; b.out_se = W;
+    b.L_out = half ? H1 : A1.rows; b.out_first = half ? 0 : A1.first;
+    b.nb_outer = half ? H0 : A0.rows; b.nb_inner = W;
+    b.in_so = k1_lines * W; b.in_si = 1; b.in_se = W;
+    b.out_so = (int64_t)b.L_out * W; b.out_si = 1; b.out_se = W;
+    b.mir_c = half ? p->K1 : 0;
     if ((e = run_pass<AA, C2<T>, C2<T>, LOAD_STRIDED>(p, b, p->b.bufA, p->b.bufB, zs, 0)) != cudaSuccess) return e;
-    // pass C (axis 2): X1 -> grid[l0][l1][l2], full lines
+    // pass C (axis 2): X1 -> grid[l0][l1][l2], full lines (reduced: the lines of [0, N0/2] x [0, N1/2])
     FftPass c = base_pass(A2, +1, f32);
     c.tw = twiddles<AA>(A2);
     c.scale_bits = sb;
     c.L_in = (int)W; c.in_first = -p->K1;
     c.L_out = A2.N; c.out_first = 0;
-    c.nb_outer = 1; c.nb_inner = (int64_t)A0.rows * A1.rows;
-    c.in_so = 0; c.in_si = W; c.in_se = 1;
-    c.out_so = 0; c.out_si = A2.N; c.out_se = 1;
-    if (f32 && p->tc_interp) {                    // the tensor-core interpolation reads the planes only
+    if (half) {
+        c.nb_outer = H0; c.nb_inner = H1;
+        c.in_so = (int64_t)H1 * W; c.in_si = W; c.in_se = 1;
+        c.out_so = (int64_t)A1.rows * A2.N; c.out_si = A2.N; c.out_se = 1;
+    } else {
+        c.nb_outer = 1; c.nb_inner = (int64_t)A0.rows * A1.rows;
+        c.in_so = 0; c.in_si = W; c.in_se = 1;
+        c.out_so = 0; c.out_si = A2.N; c.out_se = 1;
+    }
+    const bool planes = f32 && p->tc_interp;      // the tensor-core interpolation reads the planes only
+    if (planes) {
         c.planes = p->b.planes;
         c.pitch = tc_pitch(A2.N);
         c.halo = tc_halo(p->q);
-        c.plane_n = c.nb_inner * c.pitch;
+        c.plane_n = (int64_t)A0.rows * A1.rows * c.pitch;
+        if (half) { c.plane_so = A1.rows; c.plane_off = (int64_t)p->q * A1.rows + p->q; }
     }
-    return run_pass<AA, C2<T>, C2<T>, LOAD_STRIDED>(p, c, p->b.bufB, p->b.bufA, zs, 0);
+    if ((e = run_pass<AA, C2<T>, C2<T>, LOAD_STRIDED>(p, c, p->b.bufB, (C2<T> *)p->b.bufA + (half ? interior : 0), zs, 0)) !=
+        cudaSuccess)
+        return e;
+    if (!half) return cudaSuccess;
+    const HaloGeom h{p->q, A0.N / 2, A1.N / 2, A1.rows, A2.N};
+    if (planes) k_halo_mirror_planes<<<(unsigned)halo_rows(h), 128, 0, p->stream>>>(h, c.planes, c.plane_n, c.pitch, c.halo);
+    else k_halo_mirror<C2<T>><<<(unsigned)halo_rows(h), 128, 0, p->stream>>>(h, (C2<T> *)p->b.bufA);
+    p->launches += 1;
+    return cudaGetLastError();
 }
 
 template <typename T, typename RA, typename AA>
@@ -681,6 +836,18 @@ cudaError_t adjoint_passes(sgl_plan *p) {
     // binary64 data in double-float passes: one power-of-two scale for all three, from max |grid|
     constexpr bool scaled = !f32 && std::is_same<RA, dfl>::value;
     const unsigned long long *sb = scaled ? p->b.df_max + 2 : nullptr;
+    // symmetry-reduced grid: the halo rows folded onto the rows they mirror, half of the lines on
+    // axes 1 and 0, kappa1 < 0 folded onto kappa1 >= 0 between them; eta'[k0][k1 >= 0][m] in bufA
+    const bool half = p->half_grid;
+    const int H0 = A0.N / 2 + 1, H1 = A1.N / 2 + 1;
+    const int64_t K1p = p->K1 + 1, k1_lines = half ? K1p : W;
+    const int64_t interior = ((int64_t)p->q * A1.rows + p->q) * A2.N;
+    if (half) {
+        const HaloGeom h{p->q, A0.N / 2, A1.N / 2, A1.rows, A2.N};
+        k_halo_fold<C2<T>><<<(unsigned)halo_fold_rows(h), 128, 0, p->stream>>>(h, (C2<T> *)p->b.bufA);
+        p->launches += 1;
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
     if (scaled && (e = launch_max_abs(p, (const double *)p->b.bufA, 2 * (int64_t)A0.rows * A1.rows * A2.N, p->b.df_max + 2)) !=
                       cudaSuccess)
         return e;
@@ -690,32 +857,50 @@ cudaError_t adjoint_passes(sgl_plan *p) {
     c.scale_bits = sb;
     c.L_in = A2.N; c.in_first = 0;
     c.L_out = (int)W; c.out_first = -p->K1;
-    c.nb_outer = 1; c.nb_inner = (int64_t)A0.rows * A1.rows;
-    c.in_so = 0; c.in_si = A2.N; c.in_se = 1;
-    c.out_so = 0; c.out_si = W; c.out_se = 1;
-    if ((e = run_pass<AA, C2<T>, C2<T>, LOAD_STRIDED>(p, c, p->b.bufA, p->b.bufB, zs, 1)) != cudaSuccess) return e;
+    if (half) {
+        c.nb_outer = H0; c.nb_inner = H1;
+        c.in_so = (int64_t)A1.rows * A2.N; c.in_si = A2.N; c.in_se = 1;
+        c.out_so = (int64_t)H1 * W; c.out_si = W; c.out_se = 1;
+    } else {
+        c.nb_outer = 1; c.nb_inner = (int64_t)A0.rows * A1.rows;
+        c.in_so = 0; c.in_si = A2.N; c.in_se = 1;
+        c.out_so = 0; c.out_si = W; c.out_se = 1;
+    }
+    if ((e = run_pass<AA, C2<T>, C2<T>, LOAD_STRIDED>(p, c, (const C2<T> *)p->b.bufA + (half ? interior : 0), p->b.bufB, zs, 1)) !=
+        cudaSuccess)
+        return e;
     // pass B' (axis 1): Y1 -> Y0[l0][k1][m]
     FftPass b = base_pass(A1, -1, f32);
     b.tw = twiddles<AA>(A1);
     b.scale_bits = sb;
-    b.L_in = A1.rows; b.in_first = A1.first;
+    b.L_in = half ? H1 : A1.rows; b.in_first = half ? 0 : A1.first;
     b.L_out = (int)W; b.out_first = -p->K1;
-    b.nb_outer = A0.rows; b.nb_inner = W;
-    b.in_so = (int64_t)A1.rows * W; b.in_si = 1; b.in_se = W;
+    b.nb_outer = half ? H0 : A0.rows; b.nb_inner = W;
+    b.in_so = (int64_t)b.L_in * W; b.in_si = 1; b.in_se = W;
     b.out_so = W * W; b.out_si = 1; b.out_se = W;
     if ((e = run_pass<AA, C2<T>, C2<T>, LOAD_STRIDED>(p, b, p->b.bufB, p->b.bufA, zs, 1)) != cudaSuccess) return e;
-    // pass A' (axis 0): Y0 -> eta'[k0][k1][m] (FP64), deconvolved
+    const void *y0 = p->b.bufA;
+    if (half) {                                   // Y0 -> Y0h[l0][k1 >= 0][m] (bufB)
+        const int64_t n = (int64_t)H0 * K1p * W;
+        k_fold_kappa1<C2<T>><<<(unsigned)((n + 255) / 256), 256, 0, p->stream>>>(H0, p->K1, (const C2<T> *)p->b.bufA,
+                                                                                   (C2<T> *)p->b.bufB);
+        p->launches += 1;
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        y0 = p->b.bufB;
+    }
+    // pass A' (axis 0): Y0 -> eta'[k0][k1][m] (FP64), deconvolved (bufB; reduced: k1 >= 0, bufA)
     FftPass a = base_pass(A0, -1, f32);
     a.tw = twiddles<RA>(A0);
     a.scale_bits = sb;
-    a.L_in = A0.rows; a.in_first = A0.first;
+    a.L_in = half ? H0 : A0.rows; a.in_first = half ? 0 : A0.first;
     a.L_out = 2 * p->K0 + 1; a.out_first = -p->K0;
-    a.nb_outer = 1; a.nb_inner = W * W;
-    a.in_so = 0; a.in_si = 1; a.in_se = W * W;
-    a.out_so = 0; a.out_si = 1; a.out_se = W * W;
+    a.nb_outer = 1; a.nb_inner = k1_lines * W;
+    a.in_so = 0; a.in_si = 1; a.in_se = k1_lines * W;
+    a.out_so = 0; a.out_si = 1; a.out_se = k1_lines * W;
     a.elem_scale = A0.deconv; a.line_scale = p->b.linescale;
     a.elem_scale_df = A0.deconv_df; a.line_scale_df = p->b.linescale_df;
-    return run_pass<RA, C2<T>, double2, LOAD_STRIDED>(p, a, p->b.bufA, p->b.bufB, zs, 1);
+    a.ls_off = half ? p->K1 * W : 0;
+    return run_pass<RA, C2<T>, double2, LOAD_STRIDED>(p, a, y0, half ? p->b.bufA : p->b.bufB, zs, 1);
 }
 
 }  // namespace

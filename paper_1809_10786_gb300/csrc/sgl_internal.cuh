@@ -103,6 +103,12 @@ struct FftPass {
     float *planes;
     int64_t plane_n;
     int pitch, halo;
+    // symmetry-reduced passes (register kernels only; see sgl_fft.cu): element e of a line is read
+    // at |e - mir_c| (mir_c = 0: plain), negated where e < mir_c and inner - mir_c is odd (the polar
+    // parity (-1)^m); the line-scale index is offset by ls_off; with planes, line (outer, inner) is
+    // plane row outer * plane_so + inner + plane_off
+    int mir_c;
+    int64_t ls_off, plane_so, plane_off;
 };
 
 struct Buffers {
@@ -191,6 +197,7 @@ struct sgl_plan {
     bool points_set;
     bool tc;                            // tensor-core kernels usable (planes and TMA map exist)
     bool tc_interp, tc_grad, tc_spread; // ... and chosen for the interpolation / gradient / spreading
+    bool half_grid;                     // symmetry-reduced FFT passes (sgl_fft.cu)
     unsigned test_hooks;                // sgl_test_hooks: fault injection for tests (0 in normal use)
     long long wait_cycles;              // limit of the tensor-core kernels' waits (0: the default)
     alignas(64) unsigned char tc_map[2][128];   // TMA descriptors of b.planes (CUtensorMap): interpolation, gradient

@@ -115,9 +115,10 @@ __device__ __forceinline__ void point_gradient_lanes(const NGeom &g, int gl, dou
     const int lane = threadIdx.x & 31, base = lane - gl;
     const int sel = min(gl, 2);
     const double ud = sel == 0 ? u0 : (sel == 1 ? u1 : u2);
-    const double t = g.tpn[sel] * ud;
     double sn, cs;
-    sincos(sel == 0 ? 0.5 * t : t, &sn, &cs);        // lane 0: t0 / 2, lane 1: t1, lane 2: t2
+    // lane 0: t0 / 2, lane 1: t1, lane 2: t2, as multiples of pi (t_d / pi = 2 u_d / N_d), so that the
+    // singular places r = 0 (t0 = pi) and sin theta = 0 give exact zeros below
+    sincospi(sel == 0 ? ud / g.N[0] : 2.0 * ud / g.N[sel], &sn, &cs);
     const double sh = __shfl_sync(0xffffffffu, sn, base, 32), ch = __shfl_sync(0xffffffffu, cs, base, 32);
     const double st1 = __shfl_sync(0xffffffffu, sn, base + 1, 32), ct1 = __shfl_sync(0xffffffffu, cs, base + 1, 32);
     const double sp = __shfl_sync(0xffffffffu, sn, base + 2, 32), cp = __shfl_sync(0xffffffffu, cs, base + 2, 32);

@@ -60,7 +60,7 @@ def test_plan_create_rejects_bad_arguments_without_cuda(lib, args, word):
     assert word in lib.sgl_last_error().decode()
 
 
-@pytest.mark.parametrize("flags,word", [(128, "flag"), (1 << 31, "flag"), (4 | 8, "SGL_FLAG_SIMT")])
+@pytest.mark.parametrize("flags,word", [(256, "flag"), (1 << 31, "flag"), (4 | 8, "SGL_FLAG_SIMT")])
 def test_plan_create_rejects_bad_flags_without_cuda(lib, flags, word):
     h = ctypes.c_void_p(123)
     st = lib.sgl_plan_create(ctypes.byref(h), 8, 10, 1, 0, 8, 2.0, flags, None)
