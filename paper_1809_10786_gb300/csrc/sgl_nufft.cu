@@ -375,6 +375,202 @@ __global__ void __launch_bounds__(32 * (8 + Q2M - 1), rs_ctas_per_sm<Q2M>()) k_s
     rs_copy_wait();
 }
 
+// FP32 spreading with a sliding azimuthal window (2q <= 16, C0 = C1 = 8).  One CTA per work-list
+// entry (at most spread_chunk points of one super-bin).  The entry's points are sorted by their
+// first azimuthal tap s (tile column) in shared memory.  Warp w keeps tile slabs w SPW ... w SPW +
+// SPW - 1 (LG lanes each: 16, or 8 for 2q <= 8), and lane k of a slab keeps, for every tile row of
+// axis 1, the one tile column c = k (mod LG) inside the window [cur, cur + LG).  A point's taps
+// [s, s + 2q) lie inside the window once cur = s + 2q - LG; since the points come in s order the
+// window only moves forward, and a column that leaves it has received all its taps: it is added
+// to the grid then (atomically; neighbouring entries overlap it) and the lane takes column c + LG.
+// So every lane of a slab the point reaches does one useful multiply-add per tile row (none on a
+// zero weight when 2q = LG), and each tile cell goes to the grid once per entry.  A point's rows of
+// axis 1 start at tb0 in [0, 8): a switch on tb0 picks the statically indexed registers.
+template <int Q2M>
+struct CwGeom {
+    static constexpr int LG = Q2M <= 8 ? 8 : 16;       // lanes per slab (a power of two)
+    static constexpr int SPW = 32 / LG;                // slabs per warp
+    static constexpr int SLABS = 8 + Q2M - 1;          // tile slabs (axis 0)
+    static constexpr int NW = (SLABS + SPW - 1) / SPW;  // warps
+    static constexpr int SLABP = NW * SPW;             // slabs with a lane group (the last may be padding)
+    static constexpr int T1E = 8 + Q2M - 1;            // tile rows (axis 1)
+    static constexpr int PCH = 64;                     // points per staged chunk
+    static constexpr int PMAX = SGL_SPREAD_CHUNK32;    // points per work-list entry
+};
+
+// A staged chunk: the point's 2q window values on each axis (zero past 2q), its value and where
+// its taps start.
+template <int Q2M>
+struct CwStage {
+    float w0[64][Q2M];
+    float w1[64][Q2M];
+    float w2[64][Q2M];
+    float2 y[64];
+    int meta[64];             // first slab ta0 | first tile row tb0 << 8 | first tile column s << 16
+};
+
+template <int Q2M>
+struct CwSmem {
+    float4 pt[CwGeom<Q2M>::PMAX];
+    float2 y[CwGeom<Q2M>::PMAX];
+    short order[CwGeom<Q2M>::PMAX];   // sorted position -> index in the entry
+    int hist[32], cursor[32];
+    CwStage<Q2M> st[2];
+};
+
+// acc[T0 + i] += w1[i] z, i < Q2M (T0 + i < 8 + Q2M - 1: always a tile row)
+template <int T0, int Q2M, int T1E>
+__device__ __forceinline__ void cw_rows(float2 (&acc)[T1E], const float *w1, float2 z) {
+#pragma unroll
+    for (int h = 0; h < Q2M / 4; ++h) {
+        const float4 w = reinterpret_cast<const float4 *>(w1)[h];
+        acc[T0 + 4 * h] = ffma2(make_float2(w.x, w.x), z, acc[T0 + 4 * h]);
+        acc[T0 + 4 * h + 1] = ffma2(make_float2(w.y, w.y), z, acc[T0 + 4 * h + 1]);
+        acc[T0 + 4 * h + 2] = ffma2(make_float2(w.z, w.z), z, acc[T0 + 4 * h + 2]);
+        acc[T0 + 4 * h + 3] = ffma2(make_float2(w.w, w.w), z, acc[T0 + 4 * h + 3]);
+    }
+}
+
+template <int WIN, int Q2M, int N2T>
+__global__ void __launch_bounds__(32 * CwGeom<Q2M>::NW, 2) k_spread_cw(NGeom g, const int4 *__restrict__ work,
+                                                                       const int *__restrict__ work_len,
+                                                                       const float4 *__restrict__ pts32,
+                                                                       const float2 *__restrict__ ys, float2 *__restrict__ grid) {
+    using G = CwGeom<Q2M>;
+    constexpr int LG = G::LG, SPW = G::SPW, T1E = G::T1E, PCH = G::PCH;
+    static_assert(Q2M % 4 == 0 && Q2M <= 16 && Q2M <= LG && G::NW <= 20, "taps per axis: a multiple of 4, at most one slab's lanes");
+    extern __shared__ __align__(16) unsigned char cw_smem[];
+    CwSmem<Q2M> &sm = *reinterpret_cast<CwSmem<Q2M> *>(cw_smem);
+    if (blockIdx.x >= __ldg(work_len + 1)) return;
+    const int4 piece = __ldg(work + blockIdx.x);
+    const int sb = piece.x, first = piece.y, np = piece.z;
+    const int q = g.q, q2 = 2 * q, S2 = g.S2;
+    const int sb1 = sb % g.nsb1, sb2 = (sb / g.nsb1) % g.nsb2, sb0 = sb / (g.nsb1 * g.nsb2);
+    const int tid = threadIdx.x, NT = blockDim.x;
+
+    // the entry's records and values, and a counting sort by the first azimuthal tap s = c2 - sb2 S2
+    if (tid < 32) sm.hist[tid] = 0;
+    __syncthreads();
+    for (int i = tid; i < np; i += NT) {
+        const float4 pt = pts32[first + i];
+        sm.pt[i] = pt;
+        sm.y[i] = ys[first + i];
+        int c0, c1, c2;
+        unpack_cells(pt.w, c0, c1, c2);
+        atomicAdd(&sm.hist[c2 - sb2 * S2], 1);
+    }
+    __syncthreads();
+    if (tid < 32) {                               // exclusive scan of the S2 <= 32 counts
+        const int v = sm.hist[tid];
+        int x = v;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, x, o);
+            if (tid >= o) x += t;
+        }
+        sm.cursor[tid] = x - v;
+    }
+    __syncthreads();
+    for (int i = tid; i < np; i += NT) {
+        int c0, c1, c2;
+        unpack_cells(sm.pt[i].w, c0, c1, c2);
+        sm.order[atomicAdd(&sm.cursor[c2 - sb2 * S2], 1)] = (short)i;
+    }
+    __syncthreads();
+
+    // window values of a chunk of sorted points (all threads)
+    const float par0 = g.parf[0], par1 = g.parf[1], par2 = g.parf[2];
+    const float nrm0 = g.normf[0], nrm1 = g.normf[1], nrm2 = g.normf[2];
+    auto stage = [&](int ch, CwStage<Q2M> &b) {
+        constexpr int E = 3 * Q2M + 1;            // staged items per point
+        const int n = min(PCH, np - ch * PCH);
+#pragma unroll 4
+        for (int t = tid; t < n * E; t += NT) {
+            const int p = t / E, e = t - p * E;
+            const int i = sm.order[ch * PCH + p];
+            const float4 pt = sm.pt[i];
+            if (e < 3 * Q2M) {
+                const int ax = e / Q2M, j = e - ax * Q2M;
+                const float f = ax == 0 ? pt.x : (ax == 1 ? pt.y : pt.z);
+                const float par = ax == 0 ? par0 : (ax == 1 ? par1 : par2), nrm = ax == 0 ? nrm0 : (ax == 1 ? nrm1 : nrm2);
+                // tap j sits at grid index c - q + 1 + j: x = (u - c) + q - 1 - j
+                const float v = window_pair32<WIN>(f + (float)(q - 1 - j), (float)q, par, nrm).x;
+                float *dst = ax == 0 ? &b.w0[p][j] : (ax == 1 ? &b.w1[p][j] : &b.w2[p][j]);
+                *dst = j < q2 ? v : 0.f;
+            } else {
+                int c0, c1, c2;
+                unpack_cells(pt.w, c0, c1, c2);
+                b.y[p] = sm.y[i];
+                b.meta[p] = (c0 - sb0 * 8) | ((c1 - sb1 * 8) << 8) | ((c2 - sb2 * S2) << 16);
+            }
+        }
+    };
+
+    const int warp = tid >> 5, lane = tid & 31, slot = lane & (LG - 1);
+    const int ta = warp * SPW + lane / LG;        // this lane's tile slab
+    float2 acc[T1E];
+#pragma unroll
+    for (int tb = 0; tb < T1E; ++tb) acc[tb] = make_float2(0.f, 0.f);
+    // grid coordinates of this lane's slab and of tile row 0 (axis 1 windowed: rows stored in order)
+    const int r0 = ta < G::SLABS ? row_checked(sb0 * 8 - q + 1 + ta, g.first[0], g.rows[0], g.N[0]) : -1;
+    const int n2 = N2T ? N2T : g.N[2], tile_w = S2 + q2 - 1, rows1 = g.rows[1];
+    const int r1 = sb1 * 8 - q + 1 - g.first[1];
+    // add column col of the lane's registers to the grid and clear them (constant row stride when
+    // N2T is set, so that the 2q + 7 atomic adds share one address register)
+    // tile rows stored on axis 1, as a bit mask (T1E <= 23)
+    const unsigned rows_ok = (r0 < 0) ? 0u : (((1u << min(T1E, max(rows1 - r1, 0))) - 1u) & ~((1u << min(T1E, max(-r1, 0))) - 1u));
+    auto flush = [&](int col) {
+        const unsigned ok = col < tile_w ? rows_ok : 0u;
+        float2 *gp = grid + ((int64_t)max(r0, 0) * rows1 + r1) * n2 + wrap_index(sb2 * S2 - q + 1 + col, n2);
+#pragma unroll
+        for (int tb = 0; tb < T1E; ++tb) {
+            const float2 v = acc[tb];
+            acc[tb] = make_float2(0.f, 0.f);
+            if (((ok >> tb) & 1u) && (v.x != 0.f || v.y != 0.f)) atomicAdd(gp + tb * n2, v);
+        }
+    };
+
+    const int nch = (np + PCH - 1) / PCH;
+    stage(0, sm.st[0]);
+    __syncthreads();
+    int cur = 0;                                  // window start (tile column), the same in every warp
+    for (int ch = 0; ch < nch; ++ch) {
+        if (ch + 1 < nch) stage(ch + 1, sm.st[(ch + 1) & 1]);
+        const CwStage<Q2M> &b = sm.st[ch & 1];
+        const int n = min(PCH, np - ch * PCH);
+        for (int p = 0; p < n; ++p) {
+            const int meta = b.meta[p];
+            const int ta0 = meta & 255, tb0 = (meta >> 8) & 255, s = meta >> 16;
+            if (s + q2 - LG > cur) {              // move the window: columns below s + 2q - LG are complete
+                const int nc = s + q2 - LG;
+                const int col = cur + ((slot - cur) & (LG - 1));
+                if (col < nc) flush(col);
+                cur = nc;
+            }
+            if (warp * SPW + SPW - 1 < ta0 || warp * SPW > ta0 + q2 - 1) continue;   // no slab of this warp
+            const int j0 = ta - ta0, j2 = cur + ((slot - cur) & (LG - 1)) - s;
+            const float a0 = (unsigned)j0 < (unsigned)q2 ? b.w0[p][j0] : 0.f;
+            const float a2 = (unsigned)j2 < (unsigned)q2 ? b.w2[p][j2] : 0.f;
+            const float wz = a0 * a2;
+            const float2 y = b.y[p];
+            const float2 z = make_float2(y.x * wz, y.y * wz);
+            const float *w1 = b.w1[p];
+            switch (tb0) {
+                case 0: cw_rows<0, Q2M, T1E>(acc, w1, z); break;
+                case 1: cw_rows<1, Q2M, T1E>(acc, w1, z); break;
+                case 2: cw_rows<2, Q2M, T1E>(acc, w1, z); break;
+                case 3: cw_rows<3, Q2M, T1E>(acc, w1, z); break;
+                case 4: cw_rows<4, Q2M, T1E>(acc, w1, z); break;
+                case 5: cw_rows<5, Q2M, T1E>(acc, w1, z); break;
+                case 6: cw_rows<6, Q2M, T1E>(acc, w1, z); break;
+                default: cw_rows<7, Q2M, T1E>(acc, w1, z); break;
+            }
+        }
+        __syncthreads();
+    }
+    flush(cur + ((slot - cur) & (LG - 1)));
+}
+
 template <typename T, int WIN>
 cudaError_t interp_t(sgl_plan *p, double2 *vals) {
     NGeom g = make_geom(p);
@@ -413,10 +609,35 @@ cudaError_t spread_rs_t(sgl_plan *p, const NGeom &g, const double2 *vals) {
     return cudaGetLastError();
 }
 
+template <int WIN, int Q2M>
+cudaError_t spread_cw_t(sgl_plan *p, const NGeom &g, const double2 *vals) {
+    if (g.C0 != 8 || g.C1 != 8 || 2 * p->q > Q2M || g.S2 > 32 || p->ax[1].rows == p->ax[1].N) return cudaErrorInvalidConfiguration;
+    k_gather_sorted<<<nufft_blocks(p->M, 1), 256, 0, p->stream>>>(p->M, p->b.perm, vals, p->b.ys32);
+    const int n2 = p->ax[2].N;
+    auto kern = n2 == 128 ? k_spread_cw<WIN, Q2M, 128>
+                          : (n2 == 256 ? k_spread_cw<WIN, Q2M, 256> : (n2 == 512 ? k_spread_cw<WIN, Q2M, 512> : k_spread_cw<WIN, Q2M, 0>));
+    const int smem = (int)sizeof(CwSmem<Q2M>);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    const int64_t blocks = work_list_cap(p->M, p->bins.nsuper, spread_chunk(p->prec));   // entries past work_len[1] return
+    kern<<<(unsigned)blocks, 32 * CwGeom<Q2M>::NW, smem, p->stream>>>(g, p->b.work[1], p->b.work_len, p->b.pts32, p->b.ys32,
+                                                                      (float2 *)p->b.bufA);
+    p->launches += 2;
+    return cudaGetLastError();
+}
+
 template <typename T, int WIN>
 cudaError_t spread_t(sgl_plan *p, const double2 *vals) {
     NGeom g = make_geom(p);
     if constexpr (sizeof(T) == 4) {
+        // the sliding-window kernel wherever axis 1 is windowed (measured at B = 64, 10^6 points:
+        // 1.49 -> 1.30 ms at q = 8, 1.26 -> 1.01 at q = 6, 0.80 -> 0.58 at q = 4); the
+        // register-tile kernel for the small grids whose axis 1 is periodic
+        if (g.C0 == 8 && g.C1 == 8 && g.S2 <= 32 && p->ax[1].rows < p->ax[1].N) {
+            if (p->q <= 4) return spread_cw_t<WIN, 8>(p, g, vals);
+            if (p->q <= 6) return spread_cw_t<WIN, 12>(p, g, vals);
+            if (p->q <= 8) return spread_cw_t<WIN, 16>(p, g, vals);
+        }
         if (p->q <= 4) return spread_rs_t<WIN, 8>(p, g, vals);
         if (p->q <= 6) return spread_rs_t<WIN, 12>(p, g, vals);
         if (p->q <= 8) return spread_rs_t<WIN, 16>(p, g, vals);
