@@ -105,12 +105,27 @@ def stage_work(info, M, q, prec):
     rows0, rows1, N2 = info["rows"][0], info["rows"][1], info["N"][2]
     cs = 8 if prec == "fp32_mixed" else 16
     taps = (2 * q) ** 3
-    fft_fwd = ((K0 + 1) * (K1 + 1) * W * 16 + rows0 * W * W * cs          # pass A: zeta in, X0 out
-               + rows0 * W * W * cs + rows0 * rows1 * W * cs                # pass B
-               + rows0 * rows1 * W * cs + rows0 * rows1 * N2 * cs)          # pass C
-    fft_adj = (rows0 * rows1 * N2 * cs + rows0 * rows1 * W * cs
-               + rows0 * rows1 * W * cs + rows0 * W * W * cs
-               + rows0 * W * W * cs + (2 * K0 + 1) * W * W * 16)
+    if info.get("sym_grid"):
+        # symmetry-reduced passes: radial lines kappa1 >= 0 (K1 + 1), grid lines of
+        # [0, N0/2] x [0, N1/2] (H0 x H1), the halo rows copied (forward) or folded (adjoint)
+        H0, H1, K1p = info["N"][0] // 2 + 1, info["N"][1] // 2 + 1, K1 + 1
+        halo = (rows0 * rows1 - H0 * H1) * N2 * cs
+        fft_fwd = ((K0 + 1) * K1p * W * 16 + H0 * K1p * W * cs               # pass A: zeta in, X0 out
+                   + H0 * K1p * W * cs + H0 * H1 * W * cs                    # pass B
+                   + H0 * H1 * W * cs + H0 * H1 * N2 * cs                    # pass C
+                   + 2 * halo)                                               # halo rows: read sources, write
+        fft_adj = (3 * halo                                                  # halo fold: read, read + write partners
+                   + H0 * H1 * N2 * cs + H0 * H1 * W * cs                    # pass C'
+                   + H0 * H1 * W * cs + H0 * W * W * cs                      # pass B'
+                   + H0 * W * W * cs + H0 * K1p * W * cs                     # kappa1 fold
+                   + H0 * K1p * W * cs + (2 * K0 + 1) * K1p * W * 16)        # pass A'
+    else:
+        fft_fwd = ((K0 + 1) * (K1 + 1) * W * 16 + rows0 * W * W * cs          # pass A: zeta in, X0 out
+                   + rows0 * W * W * cs + rows0 * rows1 * W * cs                # pass B
+                   + rows0 * rows1 * W * cs + rows0 * rows1 * N2 * cs)          # pass C
+        fft_adj = (rows0 * rows1 * N2 * cs + rows0 * rows1 * W * cs
+                   + rows0 * rows1 * W * cs + rows0 * W * W * cs
+                   + rows0 * W * W * cs + (2 * K0 + 1) * W * W * 16)
     radial = 4 * sum((K0 + 1) * (2 * l + 1) * (B - l) for l in range(B))
     polar = 4 * (K0 + 1) * (K1 + 1) * sum(B - abs(m) for m in range(-(B - 1), B))
     # FP64 plans run the three windowed loops in double-float arithmetic unless native: a

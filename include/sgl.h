@@ -126,6 +126,8 @@ typedef struct {
     int64_t kernel_launches;  /* CUDA kernels this plan has launched so far */
     int tensor_cores;         /* bit 0: interpolation, bit 1: gradient run on the tcgen05 kernels;
                                  bit 2 (spreading) is 0: spreading runs on the CUDA cores */
+    int sym_grid;             /* 1: the FFT passes use the symmetry-reduced grid (see
+                                 SGL_FLAG_FULL_GRID), 0: they transform every kept line */
 } sgl_plan_info_t;
 
 /* Nc = B(B+1)(2B+1)/6 (Sect. 1); -1 if B < 1. */

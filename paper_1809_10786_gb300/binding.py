@@ -38,7 +38,7 @@ class PlanInfo(ctypes.Structure):
                 ("num_coeffs", ctypes.c_int64), ("M_max", ctypes.c_int64), ("M", ctypes.c_int64),
                 ("n", ctypes.c_int * 3), ("N", ctypes.c_int * 3), ("rows", ctypes.c_int * 3),
                 ("sigma_eff", ctypes.c_double * 3), ("workspace_bytes", ctypes.c_int64),
-                ("kernel_launches", ctypes.c_int64), ("tensor_cores", ctypes.c_int)]
+                ("kernel_launches", ctypes.c_int64), ("tensor_cores", ctypes.c_int), ("sym_grid", ctypes.c_int)]
 
 
 def library_path():
@@ -211,7 +211,8 @@ class Plan:
                 "rows": list(inf.rows), "sigma_eff": list(inf.sigma_eff), "workspace_bytes": inf.workspace_bytes,
                 "kernel_launches": inf.kernel_launches,
                 "tensor_cores": {"interp": bool(inf.tensor_cores & 1), "grad": bool(inf.tensor_cores & 2),
-                                 "spread": bool(inf.tensor_cores & 4)}}
+                                 "spread": bool(inf.tensor_cores & 4)},
+                "sym_grid": bool(inf.sym_grid)}
 
     def profile(self):
         """{stage: (milliseconds, timed calls)} since the last call (plan made with profile=True)."""

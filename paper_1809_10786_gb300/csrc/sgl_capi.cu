@@ -767,6 +767,7 @@ sgl_status sgl_plan_info(const sgl_plan *plan, sgl_plan_info_t *info) {
     info->workspace_bytes = plan->work_bytes;
     info->kernel_launches = plan->launches;
     info->tensor_cores = (plan->tc_interp ? 1 : 0) | (plan->tc_grad ? 2 : 0) | (plan->tc_spread ? 4 : 0);
+    info->sym_grid = plan->half_grid ? 1 : 0;
     return ok();
 }
 

@@ -107,3 +107,11 @@ def test_reduced_grid_adjoint_identity():
     lhs = np.vdot(y, f)
     rhs = np.vdot(a, c)
     assert abs(lhs - rhs) <= 1e-12 * np.abs(y).sum() * np.abs(f).max()
+
+
+@pytest.mark.parametrize("B,kw,expect", [(32, {}, True), (32, {"full_grid": True}, False), (32, {"generic_fft": True}, False),
+                                         (8, {}, False), (24, {}, False)])
+def test_plan_reports_where_the_reduced_grid_applies(B, kw, expect):
+    # B = 8: axis 1 is periodic at q = 8; B = 24: lengths 192 and 96 are not powers of two
+    p = sgl.Plan(B, 10, precision=sgl.PREC_FP32_MIXED, q=8, device=DEV, **kw)
+    assert p.info()["sym_grid"] is expect
