@@ -35,50 +35,91 @@ __device__ __forceinline__ double rho_from(const unsigned long long *r2max) {
 
 // V_l[j, k] = N_nl R_nl(r_j), n = l + 1 + k, via the normalized Laguerre recurrence
 //   psi_{k+1} = ((2k+1+a-x) psi_k - sqrt(k(k+a)) psi_{k-1}) / sqrt((k+1)(k+1+a)),  a = l + 1/2, x = r^2,
-// started from psi_0 = r^l / sqrt(Gamma(l + 3/2)) (so N_nl R_nl = sqrt(2) psi_k).
-__global__ void k_radial_values(int B, const unsigned long long *__restrict__ r2max, const double *__restrict__ costab,
-                                double *__restrict__ radv) {
+// started from psi_0 = r^l / sqrt(Gamma(l + 3/2)) (so N_nl R_nl = sqrt(2) psi_k).  The square
+// roots depend on l and k only: the block (one l) computes them once into shared memory, so that
+// each thread's recurrence step is a few multiply-adds (FP64 square roots and divisions are long
+// instruction sequences on GB300's FP64 pipe).
+constexpr int kRvMax = 128;                    // B <= 128
+__global__ void __launch_bounds__(128) k_radial_values(int B, const unsigned long long *__restrict__ r2max,
+                                                       const double *__restrict__ costab, double *__restrict__ radv) {
+    __shared__ double sq[kRvMax], isq[kRvMax], fac[kRvMax];
     const int l = blockIdx.y;
+    const int K = B - l;
+    const double a = l + 0.5;
+    for (int k = threadIdx.x; k < K; k += blockDim.x) {
+        sq[k] = sqrt(k * (k + a));                          // sqrt(k (k + a))
+        isq[k] = 1.0 / sqrt((k + 1.0) * (k + 1.0 + a));     // 1 / sqrt((k + 1)(k + 1 + a))
+    }
+    for (int i = threadIdx.x; i < l; i += blockDim.x) fac[i] = 1.0 / sqrt(i + 1.5);   // 1 / sqrt(i' + 1/2), i' = i + 1
+    __syncthreads();
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (l >= B || j >= 2 * B) return;
     const double rho = rho_from(r2max);
     const double r = 0.5 * rho * (1.0 + costab[2 * j + 1]);   // cos w_j = cos((2j+1) pi / 4B)
     const double x = r * r;
-    const double a = l + 0.5;
     // r^l / sqrt(Gamma(l + 3/2)) = prod_{i=1}^{l} r / sqrt(i + 1/2) / sqrt(Gamma(3/2))
     double t = 1.0 / sqrt(0.5 * sqrt(kPi));
-    for (int i = 1; i <= l; ++i) t *= r / sqrt(i + 0.5);
-    const int K = B - l;
+    for (int i = 0; i < l; ++i) t *= r * fac[i];
     double *out = radv + radv_off(B, l) + (int64_t)j * K;
     double pm1 = 0.0, p = t;
     out[0] = 1.4142135623730951 * p;
     for (int k = 0; k + 1 < K; ++k) {
-        const double nx = ((2.0 * k + 1.0 + a - x) * p - sqrt(k * (k + a)) * pm1) / sqrt((k + 1.0) * (k + 1.0 + a));
+        const double nx = fma(2.0 * k + 1.0 + a - x, p, -sq[k] * pm1) * isq[k];
         pm1 = p;
         p = nx;
         out[k + 1] = 1.4142135623730951 * p;
     }
 }
 
-// K_l[kappa0, k] = (1/2B) sum_j cos(kappa0 w_j) V_l[j, k],  kappa0 = 0..K0
-__global__ void k_radial_matrix(int B, int K0, const double *__restrict__ costab, const double *__restrict__ radv,
-                                double *__restrict__ Kmat) {
+// K_l[kappa0, k] = (1/2B) sum_j cos(kappa0 w_j) V_l[j, k],  kappa0 = 0..K0.  A thread takes
+// kRmK0 kappa0 and kRmK k (each V loaded serves kRmK0 multiply-adds; small tiles keep enough
+// threads in flight); cos(kappa0 w_j) comes from the table cos(m pi / 4B),
+// m = (2j + 1) kappa0 mod 8B, stepped by 2 kappa0 per j.
+constexpr int kRmK0 = 2, kRmK = 1;
+__global__ void __launch_bounds__(128) k_radial_matrix(int B, int K0, const double *__restrict__ costab,
+                                                       const double *__restrict__ radv, double *__restrict__ Kmat) {
     const int l = blockIdx.y;
     const int K = B - l;
+    const int nk = (K + kRmK - 1) / kRmK;
     const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= (K0 + 1) * K) return;
-    const int kap = idx / K, k = idx % K;
-    const double *v = radv + radv_off(B, l) + k;
+    if (idx >= ((K0 + 1 + kRmK0 - 1) / kRmK0) * nk) return;
+    const int ka = (idx / nk) * kRmK0, k = (idx % nk) * kRmK;
+    const double *v = radv + radv_off(B, l);
     const int per = 8 * B;                     // costab holds cos(m pi / 4B), m < 8B
-    double s = 0.0;
-    int m = kap % per;                         // (2j+1) kap mod 8B, stepping by 2 kap
-    const int step = (2 * kap) % per;
-    for (int j = 0; j < 2 * B; ++j) {
-        s = fma(costab[m], v[(int64_t)j * K], s);
-        m += step;
-        if (m >= per) m -= per;
+    int m[kRmK0], step[kRmK0];
+#pragma unroll
+    for (int a = 0; a < kRmK0; ++a) {
+        const int kap = min(ka + a, K0);
+        m[a] = kap % per;
+        step[a] = (2 * kap) % per;
     }
-    Kmat[kmat_off(B, K0, l) + idx] = s / (2.0 * B);
+    double s[kRmK0][kRmK] = {};
+    for (int j = 0; j < 2 * B; ++j) {
+        double vv[kRmK];
+#pragma unroll
+        for (int b = 0; b < kRmK; ++b) vv[b] = k + b < K ? v[(int64_t)j * K + k + b] : 0.0;
+#pragma unroll
+        for (int a = 0; a < kRmK0; ++a) {
+            const double c = costab[m[a]];
+#pragma unroll
+            for (int b = 0; b < kRmK; ++b) s[a][b] = fma(c, vv[b], s[a][b]);
+            m[a] += step[a];
+            if (m[a] >= per) m[a] -= per;
+        }
+    }
+    double *out = Kmat + kmat_off(B, K0, l);
+    const double n2 = 2.0 * B;
+#pragma unroll
+    for (int a = 0; a < kRmK0; ++a) {
+        if (ka + a > K0) break;
+#pragma unroll
+        for (int b = 0; b < kRmK; ++b)
+            if (k + b < K) out[(int64_t)(ka + a) * K + k + b] = s[a][b] / n2;
+    }
+}
+inline dim3 radial_matrix_grid(int B, int K0, int threads) {
+    const int tiles = ((K0 + 1 + kRmK0 - 1) / kRmK0) * ((B + kRmK - 1) / kRmK);   // the largest (l = 0)
+    return dim3((unsigned)((tiles + threads - 1) / threads), (unsigned)B);
 }
 
 // beta[m + B - 1][kappa0][l] = sum_k K_l[kappa0, k] fhat_{l+1+k, l, m}
@@ -103,30 +144,55 @@ __global__ void k_radial_forward(int B, int K0, const double *__restrict__ Kmat,
 
 // zeta[kappa0][kappa1][m + K1] = c_m sum_{l=|m|}^{B-1} P[|m|][kappa1][l] beta[m][kappa0][l],
 // c_m = (-1)^m for m < 0 (P_{-m} = (-1)^m P_m), times -i for odd m (W_m carries 1/(4i)).
-__global__ void k_polar_forward(int B, int K0, int K1, const double *__restrict__ P, const double2 *__restrict__ beta,
-                                double2 *__restrict__ zeta) {
-    const int64_t total = (int64_t)(K0 + 1) * (K1 + 1) * (2 * K1 + 1);
-    const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (idx >= total) return;
-    const int mi = (int)(idx % (2 * K1 + 1));
-    const int k1 = (int)((idx / (2 * K1 + 1)) % (K1 + 1));
-    const int k0 = (int)(idx / ((int64_t)(2 * K1 + 1) * (K1 + 1)));
-    const int m = mi - K1, am = m < 0 ? -m : m;
-    const double *pr = P + ((int64_t)am * (K1 + 1) + k1) * B;
-    const double2 *br = beta + ((int64_t)(m + B - 1) * (K0 + 1) + k0) * B;
-    double re = 0.0, im = 0.0;
+// One m per blockIdx.y; a thread takes two kappa0 and four kappa1, so that each loaded P entry
+// and beta value serves several multiply-adds (P_m and beta_m of one m stay in L1).
+constexpr int kPfK0 = 2, kPfK1 = 4;
+__global__ void __launch_bounds__(128) k_polar_forward(int B, int K0, int K1, const double *__restrict__ P,
+                                                       const double2 *__restrict__ beta, double2 *__restrict__ zeta) {
+    const int W = 2 * K1 + 1;
+    const int mi = blockIdx.y, m = mi - K1, am = m < 0 ? -m : m;
+    const int n1 = (K1 + 1 + kPfK1 - 1) / kPfK1;
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= ((K0 + 1 + kPfK0 - 1) / kPfK0) * n1) return;
+    const int k1a = (idx % n1) * kPfK1, k0a = (idx / n1) * kPfK0;
+    const double *pr[kPfK1];
+    const double2 *br[kPfK0];
+#pragma unroll
+    for (int i = 0; i < kPfK1; ++i) pr[i] = P + ((int64_t)am * (K1 + 1) + min(k1a + i, K1)) * B;
+#pragma unroll
+    for (int j = 0; j < kPfK0; ++j) br[j] = beta + ((int64_t)(m + B - 1) * (K0 + 1) + min(k0a + j, K0)) * B;
+    double re[kPfK0][kPfK1] = {}, im[kPfK0][kPfK1] = {};
     for (int l = am; l < B; ++l) {
-        const double w = pr[l];
-        const double2 v = br[l];
-        re = fma(w, v.x, re);
-        im = fma(w, v.y, im);
+        double w[kPfK1];
+        double2 v[kPfK0];
+#pragma unroll
+        for (int i = 0; i < kPfK1; ++i) w[i] = pr[i][l];
+#pragma unroll
+        for (int j = 0; j < kPfK0; ++j) v[j] = br[j][l];
+#pragma unroll
+        for (int j = 0; j < kPfK0; ++j)
+#pragma unroll
+            for (int i = 0; i < kPfK1; ++i) {
+                re[j][i] = fma(w[i], v[j].x, re[j][i]);
+                im[j][i] = fma(w[i], v[j].y, im[j][i]);
+            }
     }
-    if (m < 0 && (am & 1)) { re = -re; im = -im; }
-    if (am & 1) { const double t = re; re = im; im = -t; }      // multiply by -i
-    zeta[idx] = make_double2(re, im);
+#pragma unroll
+    for (int j = 0; j < kPfK0; ++j)
+#pragma unroll
+        for (int i = 0; i < kPfK1; ++i) {
+            if (k0a + j > K0 || k1a + i > K1) continue;
+            double a = re[j][i], b = im[j][i];
+            if (m < 0 && (am & 1)) { a = -a; b = -b; }
+            if (am & 1) { const double t = a; a = b; b = -t; }      // multiply by -i
+            zeta[((int64_t)(k0a + j) * (K1 + 1) + (k1a + i)) * W + mi] = make_double2(a, b);
+        }
+}
+inline dim3 polar_forward_grid(int K0, int K1, int threads) {
+    const int tiles = ((K0 + 1 + kPfK0 - 1) / kPfK0) * ((K1 + 1 + kPfK1 - 1) / kPfK1);
+    return dim3((unsigned)((tiles + threads - 1) / threads), (unsigned)(2 * K1 + 1));
 }
 
-// eta over the full support from zeta (mirror in kappa0 (even) and kappa1 (parity of m)).
 __global__ void k_trig_export(int K0, int K1, const double2 *__restrict__ zeta, double2 *__restrict__ eta) {
     const int W = 2 * K1 + 1;
     const int64_t total = (int64_t)(2 * K0 + 1) * W * W;
@@ -169,28 +235,49 @@ __global__ void k_fold(int K0, int K1, int half, const double2 *__restrict__ eta
     zetap[idx] = make_double2(re, im);
 }
 
-// beta'[m][kappa0][l] = conj(c_m) sum_{kappa1} P[|m|][kappa1][l] zeta'[kappa0][kappa1][m],  l >= |m|
-__global__ void k_polar_adjoint(int B, int K0, int K1, const double *__restrict__ P, const double2 *__restrict__ zetap,
-                                double2 *__restrict__ beta) {
+// beta'[m][kappa0][l] = conj(c_m) sum_{kappa1} P[|m|][kappa1][l] zeta'[kappa0][kappa1][m],  l >= |m|.
+// One m per blockIdx.y; a thread takes four consecutive l of one kappa0 (one loaded zeta' value
+// serves four multiply-adds; a larger tile leaves too few threads to hide the loads).
+constexpr int kPaL = 4, kPaK0 = 1;
+__global__ void __launch_bounds__(128) k_polar_adjoint(int B, int K0, int K1, const double *__restrict__ P,
+                                                       const double2 *__restrict__ zetap, double2 *__restrict__ beta) {
     const int W = 2 * K1 + 1;
-    const int64_t total = (int64_t)W * (K0 + 1) * B;
-    const int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (idx >= total) return;
-    const int l = (int)(idx % B);
-    const int k0 = (int)((idx / B) % (K0 + 1));
-    const int mi = (int)(idx / ((int64_t)B * (K0 + 1)));
-    const int m = mi - K1, am = m < 0 ? -m : m;
-    if (l < am) return;
-    double re = 0.0, im = 0.0;
+    const int mi = blockIdx.y, m = mi - K1, am = m < 0 ? -m : m;
+    const int nl = (B - am + kPaL - 1) / kPaL;
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= ((K0 + 1 + kPaK0 - 1) / kPaK0) * nl) return;
+    const int la = am + (idx % nl) * kPaL, k0a = (idx / nl) * kPaK0;
+    double re[kPaK0][kPaL] = {}, im[kPaK0][kPaL] = {};
+    const double *pbase = P + (int64_t)am * (K1 + 1) * B;
     for (int k1 = 0; k1 <= K1; ++k1) {
-        const double w = P[((int64_t)am * (K1 + 1) + k1) * B + l];
-        const double2 v = zetap[((int64_t)k0 * (K1 + 1) + k1) * W + mi];
-        re = fma(w, v.x, re);
-        im = fma(w, v.y, im);
+        double w[kPaL];
+        double2 v[kPaK0];
+#pragma unroll
+        for (int i = 0; i < kPaL; ++i) w[i] = pbase[(int64_t)k1 * B + min(la + i, B - 1)];
+#pragma unroll
+        for (int j = 0; j < kPaK0; ++j) v[j] = zetap[((int64_t)min(k0a + j, K0) * (K1 + 1) + k1) * W + mi];
+#pragma unroll
+        for (int j = 0; j < kPaK0; ++j)
+#pragma unroll
+            for (int i = 0; i < kPaL; ++i) {
+                re[j][i] = fma(w[i], v[j].x, re[j][i]);
+                im[j][i] = fma(w[i], v[j].y, im[j][i]);
+            }
     }
-    if (m < 0 && (am & 1)) { re = -re; im = -im; }
-    if (am & 1) { const double t = re; re = -im; im = t; }      // conj(-i) = +i
-    beta[idx] = make_double2(re, im);
+#pragma unroll
+    for (int j = 0; j < kPaK0; ++j)
+#pragma unroll
+        for (int i = 0; i < kPaL; ++i) {
+            if (k0a + j > K0 || la + i >= B) continue;
+            double a = re[j][i], b = im[j][i];
+            if (m < 0 && (am & 1)) { a = -a; b = -b; }
+            if (am & 1) { const double t = a; a = -b; b = t; }      // conj(-i) = +i
+            beta[((int64_t)mi * (K0 + 1) + (k0a + j)) * B + (la + i)] = make_double2(a, b);
+        }
+}
+inline dim3 polar_adjoint_grid(int B, int K0, int K1, int threads) {
+    const int tiles = ((K0 + 1 + kPaK0 - 1) / kPaK0) * ((B + kPaL - 1) / kPaL);   // the largest (m = 0)
+    return dim3((unsigned)((tiles + threads - 1) / threads), (unsigned)(2 * K1 + 1));
 }
 
 // fhat'_{n l m} = sum_{kappa0} K_l[kappa0, n-l-1] beta'[m][kappa0][l]
@@ -227,8 +314,7 @@ cudaError_t launch_radial_matrices(sgl_plan *p) {
     Buffers &b = p->b;
     dim3 g1(blocks_for(2 * B, 128), B);
     k_radial_values<<<g1, 128, 0, p->stream>>>(B, b.r2max, b.costab, b.radv);
-    dim3 g2(blocks_for((int64_t)(K0 + 1) * B, kT), B);
-    k_radial_matrix<<<g2, kT, 0, p->stream>>>(B, K0, b.costab, b.radv, b.Kmat);
+    k_radial_matrix<<<radial_matrix_grid(B, K0, 128), 128, 0, p->stream>>>(B, K0, b.costab, b.radv, b.Kmat);
     p->launches += 2;
     return cudaGetLastError();
 }
@@ -243,7 +329,8 @@ cudaError_t launch_radial_forward(sgl_plan *p, const double2 *coef) {
 
 cudaError_t launch_polar_forward(sgl_plan *p) {
     const int64_t total = (int64_t)(p->K0 + 1) * (p->K1 + 1) * (2 * p->K1 + 1);
-    k_polar_forward<<<blocks_for(total, kT), kT, 0, p->stream>>>(p->B, p->K0, p->K1, p->b.P, p->b.beta, p->b.zeta);
+    (void)total;
+    k_polar_forward<<<polar_forward_grid(p->K0, p->K1, 128), 128, 0, p->stream>>>(p->B, p->K0, p->K1, p->b.P, p->b.beta, p->b.zeta);
     p->launches += 1;
     return cudaGetLastError();
 }
@@ -261,7 +348,7 @@ cudaError_t launch_polar_adjoint(sgl_plan *p, const double2 *eta_full) {
     const int64_t W = 2 * K1 + 1;
     k_fold<<<blocks_for((int64_t)(K0 + 1) * (K1 + 1) * W, kT), kT, 0, p->stream>>>(K0, K1, p->half_grid ? 1 : 0, eta_full,
                                                                                     p->b.zeta);
-    k_polar_adjoint<<<blocks_for(W * (K0 + 1) * B, kT), kT, 0, p->stream>>>(B, K0, K1, p->b.P, p->b.zeta, p->b.beta);
+    k_polar_adjoint<<<polar_adjoint_grid(B, K0, K1, 128), 128, 0, p->stream>>>(B, K0, K1, p->b.P, p->b.zeta, p->b.beta);
     p->launches += 2;
     return cudaGetLastError();
 }
@@ -271,9 +358,9 @@ cudaError_t launch_trig_raw(cudaStream_t s, int B, const unsigned long long *r2m
     const int K0 = 2 * B - 2, K1 = B - 1;
     const int64_t W = 2 * K1 + 1;
     k_radial_values<<<dim3(blocks_for(2 * B, 128), B), 128, 0, s>>>(B, r2max, costab, radv);
-    k_radial_matrix<<<dim3(blocks_for((int64_t)(K0 + 1) * B, kT), B), kT, 0, s>>>(B, K0, costab, radv, Kmat);
+    k_radial_matrix<<<radial_matrix_grid(B, K0, 128), 128, 0, s>>>(B, K0, costab, radv, Kmat);
     k_radial_forward<<<dim3(blocks_for((int64_t)(2 * B - 1) * (K0 + 1), kT), B), kT, 0, s>>>(B, K0, Kmat, coef, beta);
-    k_polar_forward<<<blocks_for((int64_t)(K0 + 1) * (K1 + 1) * W, kT), kT, 0, s>>>(B, K0, K1, P, beta, zeta);
+    k_polar_forward<<<polar_forward_grid(K0, K1, 128), 128, 0, s>>>(B, K0, K1, P, beta, zeta);
     k_trig_export<<<blocks_for((int64_t)(2 * K0 + 1) * W * W, kT), kT, 0, s>>>(K0, K1, zeta, eta);
     return cudaGetLastError();
 }
