@@ -538,6 +538,7 @@ __global__ void __launch_bounds__(32 * CwGeom<Q2M>::NW, 2) k_spread_cw(NGeom g, 
         if (ch + 1 < nch) stage(ch + 1, sm.st[(ch + 1) & 1]);
         const CwStage<Q2M> &b = sm.st[ch & 1];
         const int n = min(PCH, np - ch * PCH);
+#pragma unroll 2
         for (int p = 0; p < n; ++p) {
             const int meta = b.meta[p];
             const int ta0 = meta & 255, tb0 = (meta >> 8) & 255, s = meta >> 16;
