@@ -86,11 +86,13 @@ typedef enum {
                                  (rho stays on the plan's stream), so that the binning overlaps
                                  the conversions and the FFT of the next forward; the first
                                  call that reads the bins waits for it.  Results and the stream
-                                 semantics of every call are unchanged.  The binning and the
-                                 conversions both load the FP64 pipe: on one GB300 at B = 64,
-                                 10^6 points it made set_points + forward 8 % faster and
-                                 set_points + forward with the gradient + adjoint 4 % slower.
-                                 Not accepted for batches */
+                                 semantics of every call are unchanged.  Measured on one GB300
+                                 at B = 64, 10^6 points, FP32-mixed, step = set_points + forward
+                                 with the gradient + adjoint: 3.344 -> 3.253 ms when the host
+                                 waits for every step, but 3.375 -> 3.52 ms when steps are
+                                 queued back to back.  FP64 plans compute the points' angles on
+                                 the FP64 pipe, where they compete with the conversions.  Not
+                                 accepted for batches */
 #define SGL_FLAG_GENERIC_FFT 64u  /* run every FFT pass with the generic mixed-radix kernel (tiles of
                                  lines staged in shared memory, one radix stage per pass over
                                  the tile) instead of the register kernels that power-of-two

@@ -102,3 +102,27 @@ def test_points_stage_is_timed_once_per_set_points():
     ms, n = st["points"]
     assert n == 3 and ms > 0.0
     assert st["interp"][1] == 3
+
+
+def test_host_buffer_calls_with_overlapped_binning():
+    # the host-buffer path the end-to-end benchmark takes: points, coefficients and seeds from
+    # pinned host memory, the adjoint reusing the plan's points (xyz None)
+    B, M = 32, 200_000
+    c = inputs.coefficients(B, 7500)
+    x = inputs.points_gaussian(M, 7501)
+    g = inputs.complex_normal(M, 7502)
+    y = inputs.values(M, 7503)
+    outs = []
+    for ov in (True, False):
+        p = sgl.Plan(B, M, precision=sgl.PREC_FP32_MIXED, window=sgl.WIN_KB, q=8, sigma=2.0, host_io=True,
+                     overlap_points=ov)
+        xp, cp, gp, yp = (torch.from_numpy(a).pin_memory() for a in (x, c, g, y))
+        fo = torch.empty(M, dtype=torch.complex128).pin_memory()
+        go = torch.empty((M, 3), dtype=torch.float64).pin_memory()
+        ao = torch.empty(p.Nc, dtype=torch.complex128).pin_memory()
+        for _ in range(2):                          # a second round reuses the plan's side stream
+            p.forward_grad_host(xp, cp, gp, fo, go)
+            p.adjoint_host(None, yp, ao)
+        outs.append((fo.clone(), go.clone(), ao.clone()))
+    for k, name in enumerate(("values", "gradient", "adjoint")):
+        check("overlapped host calls %s" % name, rel(outs[0][k], outs[1][k]), 1e-7)
