@@ -133,6 +133,7 @@ __global__ void k_radial_forward(int B, int K0, const double *__restrict__ Kmat,
     const int m = idx / (K0 + 1) - l;
     const double *kr = Kmat + kmat_off(B, K0, l) + (int64_t)kap * K;
     double re = 0.0, im = 0.0;
+#pragma unroll 4
     for (int k = 0; k < K; ++k) {
         const double2 c = coef[mu_index(l + 1 + k, l, m)];
         const double w = kr[k];
@@ -249,6 +250,7 @@ __global__ void __launch_bounds__(128) k_polar_adjoint(int B, int K0, int K1, co
     const int la = am + (idx % nl) * kPaL, k0a = (idx / nl) * kPaK0;
     double re[kPaK0][kPaL] = {}, im[kPaK0][kPaL] = {};
     const double *pbase = P + (int64_t)am * (K1 + 1) * B;
+#pragma unroll 4
     for (int k1 = 0; k1 <= K1; ++k1) {
         double w[kPaL];
         double2 v[kPaK0];
@@ -296,6 +298,7 @@ __global__ void k_radial_adjoint(int B, int K0, int64_t Nc, const double *__rest
     const double *kr = Kmat + kmat_off(B, K0, l) + k;
     const double2 *br = beta + (int64_t)(m + B - 1) * (K0 + 1) * B + l;
     double re = 0.0, im = 0.0;
+#pragma unroll 4
     for (int kap = 0; kap <= K0; ++kap) {
         const double w = kr[(int64_t)kap * K];
         const double2 v = br[(int64_t)kap * B];
