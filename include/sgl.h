@@ -98,8 +98,7 @@ typedef enum {
                                  the tile) instead of the register kernels that power-of-two
                                  lengths 64 ... 1024 take by default.  Same results to rounding */
 #define SGL_FLAG_FULL_GRID 128u  /* transform the whole kept grid.  By default, where axes 0 and 1 are
-                                 windowed and every FFT length is a power of two in 64 ... 1024,
-                                 the FFT passes use the symmetries of eta (Sect. 6: even in
+                                 windowed, the FFT passes use the symmetries of eta (Sect. 6: even in
                                  kappa0, parity of m in kappa1): the radial pass transforms the
                                  lines kappa1 >= 0 only, and the two angular passes the grid
                                  lines of [0, N0/2] x [0, N1/2], whose mirrors fill the q halo

@@ -532,14 +532,9 @@ sgl_status plan_create_impl(sgl_plan **out, int B, int64_t M_max, int precision,
         factor(a.N, a.rad, a.nrad);
     }
     {
-        // symmetry-reduced FFT passes: axes 0 and 1 windowed, every length one of the register
-        // kernels' powers of two
-        bool ok = !(flags & (SGL_FLAG_FULL_GRID | SGL_FLAG_GENERIC_FFT)) && p->ax[0].windowed && p->ax[1].windowed;
-        for (int d = 0; d < 3; ++d) {
-            const int n = p->ax[d].N;
-            ok = ok && n >= 64 && n <= 1024 && (n & (n - 1)) == 0;
-        }
-        p->half_grid = ok;
+        // symmetry-reduced FFT passes: axes 0 and 1 windowed (the halo rows then lie inside one
+        // period), the azimuthal length even (the half-period shift); every FFT length is even
+        p->half_grid = !(flags & SGL_FLAG_FULL_GRID) && p->ax[0].windowed && p->ax[1].windowed && p->ax[2].N % 2 == 0;
     }
     {
         BinGeom &g = p->bins;

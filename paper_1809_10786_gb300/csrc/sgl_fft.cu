@@ -248,22 +248,28 @@ __global__ void __launch_bounds__(256) k_fft_pass(FftPass ps, int TB, int lgTB, 
                     // line = (k1, m) over (2K1+1)^2, element = k0 + K0; eta mirrored from zeta
                     const int W = 2 * zs.K1 + 1;
                     const int mi = (int)(inner % W);
-                    const int k1 = (int)(inner / W) - zs.K1;
+                    const int k1 = (int)(inner / W) - (zs.half ? 0 : zs.K1);
                     const int k0 = e - zs.K0;
                     d = zs.zeta[((int64_t)abs(k0) * (zs.K1 + 1) + abs(k1)) * W + mi];
                     if (k1 < 0 && ((mi - zs.K1) & 1)) { d.x = -d.x; d.y = -d.y; }
-                } else if (scale_on_output || (!ps.elem_scale && !ps.line_scale)) {
-                    // no factor on the input: straight conversion to the pass arithmetic
-                    const InC x = in[outer * ps.in_so + inner * ps.in_si + (int64_t)e * ps.in_se];
-                    v[u] = mk<T>(T(x.x), T(x.y));
-                    continue;
                 } else {
-                    d = to_d2(in[outer * ps.in_so + inner * ps.in_si + (int64_t)e * ps.in_se]);
+                    // element e at |e - mir_c| (plain lines: mir_c = 0), with the polar parity below mir_c
+                    const int k = e - ps.mir_c;
+                    const int64_t at = outer * ps.in_so + inner * ps.in_si + (int64_t)abs(k) * ps.in_se;
+                    const bool neg = k < 0 && ((inner - ps.mir_c) & 1);
+                    if (scale_on_output || (!ps.elem_scale && !ps.line_scale)) {
+                        // no factor on the input: straight conversion to the pass arithmetic
+                        const InC x = in[at];
+                        v[u] = neg ? mk<T>(-T(x.x), -T(x.y)) : mk<T>(T(x.x), T(x.y));
+                        continue;
+                    }
+                    d = to_d2(in[at]);
+                    if (neg) { d.x = -d.x; d.y = -d.y; }
                 }
                 if (!scale_on_output) {
                     double f = 1.0;
                     if (ps.elem_scale) f *= ps.elem_scale[e];
-                    if (ps.line_scale) f *= ps.line_scale[outer * ps.nb_inner + inner];
+                    if (ps.line_scale) f *= ps.line_scale[outer * ps.nb_inner + inner + ps.ls_off];
                     d.x *= f; d.y *= f;
                 }
                 v[u] = mk<T>(T(d.x), T(d.y));
@@ -293,7 +299,7 @@ __global__ void __launch_bounds__(256) k_fft_pass(FftPass ps, int TB, int lgTB, 
     if constexpr (std::is_same<OutC, float2>::value) {
         if (ps.planes) {
             for (int bl = 0; bl < nlines; ++bl) {
-                float *row = ps.planes + (inner0 + bl) * ps.pitch;
+                float *row = ps.planes + (outer * ps.plane_so + inner0 + bl + ps.plane_off) * ps.pitch;
                 for (int k = tid; k < ps.pitch; k += NT) {
                     int e = (k - ps.halo) % N;       // the halo can span more than one period of short lines
                     if (e < 0) e += N;
@@ -327,7 +333,7 @@ __global__ void __launch_bounds__(256) k_fft_pass(FftPass ps, int TB, int lgTB, 
             }
             double f = 1.0;
             if (ps.elem_scale) f *= ps.elem_scale[e];
-            if (ps.line_scale) f *= ps.line_scale[outer * ps.nb_inner + inner];
+            if (ps.line_scale) f *= ps.line_scale[outer * ps.nb_inner + inner + ps.ls_off];
             o.x = (S)(widen(v.x) * f);
             o.y = (S)(widen(v.y) * f);
             out[outer * ps.out_so + inner * ps.out_si + (int64_t)e * ps.out_se] = o;
@@ -548,15 +554,16 @@ __global__ void __launch_bounds__(256) k_fft_reg(FftPass ps, const InC *__restri
 // ---------------------------------------------------------------- symmetry-reduced grid
 // eta is even in kappa0 and has the parity of m in kappa1 (Sect. 6), so the oversampled grid of the
 // NFFT is even in l0 and alpha(l0, -l1, l2) = alpha(l0, l1, l2 + N2/2).  Plans whose axes 0 and 1
-// are windowed and whose lengths all take the register kernels transform half of the lines: pass A
+// are windowed transform half of the lines: pass A
 // the radial lines kappa1 >= 0 (pass B reads kappa1 < 0 back through the parity), passes B and C the
 // grid lines (l0, l1) in [0, N0/2] x [0, N1/2].  The q halo rows on each side of the two windowed axes
 // are then copies of the rows they mirror: row -l (1 <= l <= q) and row N - l (N/2 - q <= l < N/2)
 // hold line l, shifted by N2/2 on axis 1.  The adjoint first adds every halo row onto the row it
 // mirrors, transforms the same half, folds kappa1 < 0 onto kappa1 >= 0 (parity) before pass A', and
-// folds kappa0 < 0 onto kappa0 >= 0 after it (sgl_convert.cu).
+// folds kappa0 < 0 onto kappa0 >= 0 after it (sgl_convert.cu).  Both FFT kernels (register and
+// generic) read the mirrored lines and write the plane rows of the reduced layout.
 struct HaloGeom {
-    int q, N0h, N1h, R1, N2;    // q, N0/2, N1/2, rows kept on axis 1, azimuthal length (a power of two)
+    int q, N0h, N1h, R1, N2;    // q, N0/2, N1/2, rows kept on axis 1, azimuthal length (even)
 };
 
 // storage row (first row -q) -> the grid line l in [0, N/2] it holds, and whether it is a mirror
@@ -591,7 +598,7 @@ __global__ void __launch_bounds__(256) k_halo_mirror(HaloGeom h, C *__restrict__
     const int sh = (b - h.q < 0 || b - h.q > h.N1h) ? h.N2 / 2 : 0;
     const C *src = grid + ((int64_t)(l0 + h.q) * h.R1 + l1 + h.q) * h.N2;
     C *dst = grid + ((int64_t)a * h.R1 + b) * h.N2;
-    for (int c = threadIdx.x; c < h.N2; c += blockDim.x) dst[c] = src[(c + sh) & (h.N2 - 1)];
+    for (int c = threadIdx.x; c < h.N2; c += blockDim.x) dst[c] = src[c + sh < h.N2 ? c + sh : c + sh - h.N2];
 }
 
 // the same on the tensor-core planes (Re, Im; column k holds position (k - halo) mod N2)
@@ -604,7 +611,7 @@ __global__ void __launch_bounds__(256) k_halo_mirror_planes(HaloGeom h, float *_
     const float *src = planes + ((int64_t)(l0 + h.q) * h.R1 + l1 + h.q) * pitch;
     float *dst = planes + ((int64_t)a * h.R1 + b) * pitch;
     for (int k = threadIdx.x; k < pitch; k += blockDim.x) {
-        const int pos = (k - halo + sh + h.N2) & (h.N2 - 1);   // k - halo >= -halo > -N2
+        const int pos = (k - halo + sh + h.N2) % h.N2;         // k - halo >= -halo > -N2
         dst[k] = src[pos + halo];
         dst[plane_n + k] = src[plane_n + pos + halo];
     }
@@ -641,7 +648,7 @@ __global__ void __launch_bounds__(256) k_halo_fold(HaloGeom h, C *__restrict__ g
     const C *s1 = m1 >= 0 ? grid + (r0 * h.R1 + m1) * h.N2 : nullptr;
     const C *s01 = (m0 >= 0 && m1 >= 0) ? grid + ((int64_t)m0 * h.R1 + m1) * h.N2 : nullptr;
     for (int c = threadIdx.x; c < h.N2; c += blockDim.x) {
-        const int cs = (c + h.N2 / 2) & (h.N2 - 1);
+        const int cs = c + h.N2 / 2 < h.N2 ? c + h.N2 / 2 : c - h.N2 / 2;
         C v = dst[c];
         if (s0) { const C w = s0[c]; v.x += w.x; v.y += w.y; }
         if (s1) { const C w = s1[cs]; v.x += w.x; v.y += w.y; }

@@ -103,7 +103,7 @@ struct FftPass {
     float *planes;
     int64_t plane_n;
     int pitch, halo;
-    // symmetry-reduced passes (register kernels only; see sgl_fft.cu): element e of a line is read
+    // symmetry-reduced passes (see sgl_fft.cu): element e of a line is read
     // at |e - mir_c| (mir_c = 0: plain), negated where e < mir_c and inner - mir_c is odd (the polar
     // parity (-1)^m); the line-scale index is offset by ls_off; with planes, line (outer, inner) is
     // plane row outer * plane_so + inner + plane_off

@@ -2,9 +2,10 @@
 
 eta is even in kappa0 and has the parity of m in kappa1 (Sect. 6), so the oversampled grid of the
 NFFT (Sect. 2) is even in l0 and alpha(l0, -l1, l2) = alpha(l0, l1, l2 + N2/2).  By default the
-register FFT passes transform the radial lines kappa1 >= 0 and the angular lines of
+FFT passes transform the radial lines kappa1 >= 0 and the angular lines of
 [0, N0/2] x [0, N1/2] only, and fill the q halo rows on each side of both windowed axes by
-mirroring; the adjoint folds in the same places.  SGL_FLAG_FULL_GRID transforms every kept line.
+mirroring; the adjoint folds in the same places (in both the register and the generic FFT
+kernels).  SGL_FLAG_FULL_GRID transforms every kept line.
 Both compute the same operator, so they agree to rounding.
 
 Points at the origin (t0 = pi), at the largest radius (t0 = 0) and on both poles (theta = 0, pi)
@@ -70,7 +71,8 @@ CONFIGS = [("fp64", sgl.PREC_FP64, {}, 2e-12), ("fp64-native", sgl.PREC_FP64, {"
            ("fp32-tc", sgl.PREC_FP32_MIXED, {}, 2e-6), ("fp32-simt", sgl.PREC_FP32_MIXED, {"simt": True}, 2e-6)]
 
 
-@pytest.mark.parametrize("B", [16, 32, 64])
+# B = 20, 24: lengths 160 / 80 and 192 / 96, which take the generic FFT kernel
+@pytest.mark.parametrize("B", [16, 20, 24, 32, 64])
 @pytest.mark.parametrize("name,prec,kw,tol", CONFIGS)
 def test_reduced_grid_matches_full_grid(B, name, prec, kw, tol):
     x = edge_points(2000, 9700 + B)
@@ -86,7 +88,7 @@ def test_reduced_grid_matches_full_grid(B, name, prec, kw, tol):
                                                       (32, sgl.PREC_FP64, 1e-10, 1e-10, 1e-9),
                                                       (32, sgl.PREC_FP32_MIXED, 3e-6, 3e-6, 3e-5)])
 def test_reduced_grid_against_the_oracle(B, prec, tol_f, tol_a, tol_g):
-    # B = 24: grid lengths 192 and 96 are not powers of two, so that plan keeps the whole grid
+    # B = 24: grid lengths 192 and 96 take the generic FFT kernel
     x = edge_points(300, 9800 + B)
     (f, gx, a), (c, y, g) = run(B, x, prec, False, 9810 + B)
     f_ref, _ = direct.forward(B, x, c)
@@ -109,9 +111,9 @@ def test_reduced_grid_adjoint_identity():
     assert abs(lhs - rhs) <= 1e-12 * np.abs(y).sum() * np.abs(f).max()
 
 
-@pytest.mark.parametrize("B,kw,expect", [(32, {}, True), (32, {"full_grid": True}, False), (32, {"generic_fft": True}, False),
-                                         (8, {}, False), (24, {}, False)])
+@pytest.mark.parametrize("B,kw,expect", [(32, {}, True), (32, {"full_grid": True}, False), (32, {"generic_fft": True}, True),
+                                         (8, {}, False), (24, {}, True)])
 def test_plan_reports_where_the_reduced_grid_applies(B, kw, expect):
-    # B = 8: axis 1 is periodic at q = 8; B = 24: lengths 192 and 96 are not powers of two
+    # B = 8: axis 1 is periodic at q = 8
     p = sgl.Plan(B, 10, precision=sgl.PREC_FP32_MIXED, q=8, device=DEV, **kw)
     assert p.info()["sym_grid"] is expect
