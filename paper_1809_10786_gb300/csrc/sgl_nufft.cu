@@ -398,14 +398,13 @@ struct CwGeom {
     static constexpr int PMAX = SGL_SPREAD_CHUNK32;    // points per work-list entry
 };
 
-// A staged chunk: the point's 2q window values on each axis (zero past 2q), its value and where
-// its taps start.
+// A staged chunk: the point's value times its 2q axis-0 window values, its 2q window values on
+// axes 1 and 2 (zero past 2q), and where its taps start.
 template <int Q2M>
 struct CwStage {
-    float w0[64][Q2M];
+    float2 yw0[64][Q2M];      // y psi_0(tap j)
     float w1[64][Q2M];
     float w2[64][Q2M];
-    float2 y[64];
     int meta[64];             // first slab ta0 | first tile row tb0 << 8 | first tile column s << 16
 };
 
@@ -495,12 +494,16 @@ __global__ void __launch_bounds__(32 * CwGeom<Q2M>::NW, 2) k_spread_cw(NGeom g, 
                 const float par = ax == 0 ? par0 : (ax == 1 ? par1 : par2), nrm = ax == 0 ? nrm0 : (ax == 1 ? nrm1 : nrm2);
                 // tap j sits at grid index c - q + 1 + j: x = (u - c) + q - 1 - j
                 const float v = window_pair32<WIN>(f + (float)(q - 1 - j), (float)q, par, nrm).x;
-                float *dst = ax == 0 ? &b.w0[p][j] : (ax == 1 ? &b.w1[p][j] : &b.w2[p][j]);
-                *dst = j < q2 ? v : 0.f;
+                const float w = j < q2 ? v : 0.f;
+                if (ax == 0) {
+                    const float2 y = sm.y[i];
+                    b.yw0[p][j] = make_float2(y.x * w, y.y * w);
+                } else {
+                    (ax == 1 ? b.w1[p] : b.w2[p])[j] = w;
+                }
             } else {
                 int c0, c1, c2;
                 unpack_cells(pt.w, c0, c1, c2);
-                b.y[p] = sm.y[i];
                 b.meta[p] = (c0 - sb0 * 8) | ((c1 - sb1 * 8) << 8) | ((c2 - sb2 * S2) << 16);
             }
         }
@@ -534,6 +537,7 @@ __global__ void __launch_bounds__(32 * CwGeom<Q2M>::NW, 2) k_spread_cw(NGeom g, 
     stage(0, sm.st[0]);
     __syncthreads();
     int cur = 0;                                  // window start (tile column), the same in every warp
+    int col = slot;                               // this lane's tile column: cur + ((slot - cur) mod LG)
     for (int ch = 0; ch < nch; ++ch) {
         if (ch + 1 < nch) stage(ch + 1, sm.st[(ch + 1) & 1]);
         const CwStage<Q2M> &b = sm.st[ch & 1];
@@ -544,17 +548,15 @@ __global__ void __launch_bounds__(32 * CwGeom<Q2M>::NW, 2) k_spread_cw(NGeom g, 
             const int ta0 = meta & 255, tb0 = (meta >> 8) & 255, s = meta >> 16;
             if (s + q2 - LG > cur) {              // move the window: columns below s + 2q - LG are complete
                 const int nc = s + q2 - LG;
-                const int col = cur + ((slot - cur) & (LG - 1));
                 if (col < nc) flush(col);
                 cur = nc;
+                col = cur + ((slot - cur) & (LG - 1));
             }
             if (warp * SPW + SPW - 1 < ta0 || warp * SPW > ta0 + q2 - 1) continue;   // no slab of this warp
-            const int j0 = ta - ta0, j2 = cur + ((slot - cur) & (LG - 1)) - s;
-            const float a0 = (unsigned)j0 < (unsigned)q2 ? b.w0[p][j0] : 0.f;
+            const int j0 = ta - ta0, j2 = col - s;
+            const float2 yw = (unsigned)j0 < (unsigned)q2 ? b.yw0[p][j0] : make_float2(0.f, 0.f);
             const float a2 = (unsigned)j2 < (unsigned)q2 ? b.w2[p][j2] : 0.f;
-            const float wz = a0 * a2;
-            const float2 y = b.y[p];
-            const float2 z = make_float2(y.x * wz, y.y * wz);
+            const float2 z = make_float2(yw.x * a2, yw.y * a2);
             const float *w1 = b.w1[p];
             switch (tb0) {
                 case 0: cw_rows<0, Q2M, T1E>(acc, w1, z); break;
@@ -569,7 +571,7 @@ __global__ void __launch_bounds__(32 * CwGeom<Q2M>::NW, 2) k_spread_cw(NGeom g, 
         }
         __syncthreads();
     }
-    flush(cur + ((slot - cur) & (LG - 1)));
+    flush(col);
 }
 
 template <typename T, int WIN>
