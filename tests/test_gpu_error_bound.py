@@ -43,27 +43,33 @@ def test_plan_bound_equals_the_parameter_bound():
     p.close()
 
 
-def test_error_grows_with_the_spreading_radius():
+@pytest.mark.parametrize("q", [4, 6])
+def test_error_grows_with_the_spreading_radius(q):
     # Sect. 8 (error vs kappa), B = 32, M = 1000 uniform in the ball of radius kappa: the bound
-    # holds at every kappa and the error grows with kappa (Sect. 7: rho enters as e^{rho^2 / 2})
-    B, q = 32, 4
+    # holds at every kappa and the error grows with kappa (Sect. 7: rho enters as e^{rho^2 / 2}).
+    # Prints one row per kappa (run with -s for the table).
+    B = 32
     c = inputs.coefficients(B, 7200)
     errs = []
     for kappa in (1.0, 2.0, 3.0, 4.0, 5.0):
         x = inputs.points_ball(1000, 7201, radius=kappa)
         err, bound, fmax = measured_and_bound(B, x, c, q)
+        print("\nerror vs kappa: q=%d B=%d kappa=%.0f  max abs error %.2e  bound*||eta||_1 %.2e  max|f| %.2e"
+              % (q, B, kappa, err, bound, fmax), end="")
         assert err <= bound + 1e-12 * fmax
         errs.append(err)
     assert errs[-1] > 10 * errs[0]
 
 
-def test_error_grows_slowly_with_the_bandwidth():
-    # Sect. 8 (error vs B), kappa = 5: the bound holds and the error grows with B
-    q = 4
+@pytest.mark.parametrize("q", [4, 6])
+def test_error_grows_slowly_with_the_bandwidth(q):
+    # Sect. 8 (error vs B), kappa = 5: the bound holds and the error grows with B (-s prints the rows)
     x = inputs.points_ball(1000, 7301, radius=5.0)
     errs = []
-    for B in (8, 16, 24, 32):
+    for B in (8, 16, 24, 32, 48):
         err, bound, fmax = measured_and_bound(B, x, inputs.coefficients(B, 7300 + B), q)
+        print("\nerror vs B: q=%d kappa=5 B=%d  max abs error %.2e  bound*||eta||_1 %.2e  max|f| %.2e"
+              % (q, B, err, bound, fmax), end="")
         assert err <= bound + 1e-12 * fmax
         errs.append(err)
     assert errs[-1] > errs[0]
