@@ -477,34 +477,36 @@ __global__ void __launch_bounds__(32 * CwGeom<Q2M>::NW, 2) k_spread_cw(NGeom g, 
     }
     __syncthreads();
 
-    // window values of a chunk of sorted points (all threads)
+    // window values of a chunk of sorted points: one (point, axis) unit per thread, the warps
+    // taken edge first (0, NW - 1, 1, NW - 2, ...) since the warps of the outer slabs reach the
+    // fewest points in the sweep below (a chunk's 3 x 64 units leave the middle warps out)
     const float par0 = g.parf[0], par1 = g.parf[1], par2 = g.parf[2];
     const float nrm0 = g.normf[0], nrm1 = g.normf[1], nrm2 = g.normf[2];
+    const int nwarps = NT >> 5, wq = tid >> 5;
+    const int srank = (wq < (nwarps + 1) / 2 ? 2 * wq : 2 * (nwarps - 1 - wq) + 1) * 32 + (tid & 31);
     auto stage = [&](int ch, CwStage<Q2M> &b) {
-        constexpr int E = 3 * Q2M + 1;            // staged items per point
         const int n = min(PCH, np - ch * PCH);
-#pragma unroll 4
-        for (int t = tid; t < n * E; t += NT) {
-            const int p = t / E, e = t - p * E;
+        for (int unit = srank; unit < 3 * n; unit += NT) {
+            const int p = unit / 3, ax = unit - 3 * p;
             const int i = sm.order[ch * PCH + p];
             const float4 pt = sm.pt[i];
-            if (e < 3 * Q2M) {
-                const int ax = e / Q2M, j = e - ax * Q2M;
-                const float f = ax == 0 ? pt.x : (ax == 1 ? pt.y : pt.z);
-                const float par = ax == 0 ? par0 : (ax == 1 ? par1 : par2), nrm = ax == 0 ? nrm0 : (ax == 1 ? nrm1 : nrm2);
-                // tap j sits at grid index c - q + 1 + j: x = (u - c) + q - 1 - j
-                const float v = window_pair32<WIN>(f + (float)(q - 1 - j), (float)q, par, nrm).x;
-                const float w = j < q2 ? v : 0.f;
-                if (ax == 0) {
-                    const float2 y = sm.y[i];
-                    b.yw0[p][j] = make_float2(y.x * w, y.y * w);
-                } else {
-                    (ax == 1 ? b.w1[p] : b.w2[p])[j] = w;
-                }
-            } else {
+            const float f = ax == 0 ? pt.x : (ax == 1 ? pt.y : pt.z);
+            const float par = ax == 0 ? par0 : (ax == 1 ? par1 : par2), nrm = ax == 0 ? nrm0 : (ax == 1 ? nrm1 : nrm2);
+            float2 y = make_float2(0.f, 0.f);
+            if (ax == 0) {
+                y = sm.y[i];
                 int c0, c1, c2;
                 unpack_cells(pt.w, c0, c1, c2);
                 b.meta[p] = (c0 - sb0 * 8) | ((c1 - sb1 * 8) << 8) | ((c2 - sb2 * S2) << 16);
+            }
+            float *dst = ax == 1 ? b.w1[p] : b.w2[p];
+#pragma unroll 4
+            for (int j = 0; j < Q2M; ++j) {
+                // tap j sits at grid index c - q + 1 + j: x = (u - c) + q - 1 - j
+                const float v = window_pair32<WIN>(f + (float)(q - 1 - j), (float)q, par, nrm).x;
+                const float w = j < q2 ? v : 0.f;
+                if (ax == 0) b.yw0[p][j] = make_float2(y.x * w, y.y * w);
+                else dst[j] = w;
             }
         }
     };
